@@ -1,0 +1,349 @@
+"""Pins for the CPU oracle: each test ties it to something other than itself
+(values printed in the paper, published known answers, definitions evaluated
+another way, exact enumeration, brute force, invariants, statistics)."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def inst_of(gen):
+    n, off, lits, w = gen
+    return oracle.Instance(n, off, lits, w)
+
+
+# --------------------------------------------------------------------------
+# Randomness: Philox4x32-10 known-answer values (Salmon et al., SC'11; the
+# Random123 distribution's published known-answer vectors).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ctr,key,expect", [
+    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+])
+def test_philox_known_answers(ctr, key, expect):
+    assert list(oracle.philox4x32_10(ctr, key)) == expect
+
+
+def test_draw16_lanes_and_uniformity():
+    seed = 0x123456789ABCDEF0
+    out = oracle.philox4x32_10([7, (16 >> 3) | (2 << 24), 5, 2], [seed & 0xFFFFFFFF, seed >> 32])
+    lanes = [(int(out[l >> 1]) >> (16 * (l & 1))) & 0xFFFF for l in range(8)]
+    assert [oracle.draw16(seed, 2, 5, 7, 2, 16 + l) for l in range(8)] == lanes
+    u = np.array([oracle.draw16(1, 3, t, i, 0, b) for t in range(4) for i in range(64)
+                  for b in range(32)])
+    assert abs(u.mean() / 65536 - 0.5) < 0.02
+    assert u.min() >= 0 and u.max() < 65536
+
+
+# --------------------------------------------------------------------------
+# Cost: worked examples of the paper's text (Sec. 4.3, Sec. 4.4), hand-scored
+# --------------------------------------------------------------------------
+def _paper_examples():
+    cases, cur = [], None
+    with open(os.path.join(GOLDEN, "paper_examples.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("formula"):
+                head, body = line.split("|")
+                n = int(head.split()[1])
+                clauses = [[int(t) for t in c.split()] for c in body.split(";")]
+                cur = (n, clauses, [])
+                cases.append(cur)
+            else:
+                _, bits, _, cost = line.split()
+                cur[2].append(([int(ch) for ch in bits], int(cost)))
+    return cases
+
+
+def test_eval_paper_examples():
+    cases = _paper_examples()
+    assert len(cases) == 2
+    for n, clauses, rows in cases:
+        inst = oracle.Instance.from_clauses(n, clauses)
+        X = np.array([r[0] for r in rows], np.uint8)
+        assert list(oracle.evaluate(inst, X)) == [r[1] for r in rows]
+
+
+def test_eval_matches_matrix_form():
+    """count_c = (C s + len_c) / 2 with s = 2x - 1 and C the signed
+    clause-literal matrix; satisfied iff count > 0; weighted cost."""
+    rng = np.random.default_rng(3)
+    n, off, lits, w = workloads.mixed_length(n=40, m=300, cap=12, seed=5)
+    inst = oracle.Instance(n, off, lits, w)
+    # duplicates, tautologies and an empty clause on top of the random ones
+    extra = [[1, 1, 2], [3, -3], [], [-4, -4], [5]]
+    cl = inst.clauses() + extra
+    ws = list(w) + [7, 9, 11, 13, 17]
+    inst = oracle.Instance.from_clauses(n, cl, ws)
+    C = np.zeros((inst.m, n))
+    for c, lc in enumerate(cl):
+        for l in lc:
+            C[c, abs(l) - 1] += np.sign(l)
+    ln = np.diff(inst.off)
+    X = rng.integers(0, 2, size=(200, n)).astype(np.uint8)
+    S = 2.0 * X - 1.0
+    count = (S @ C.T + ln[None, :]) / 2
+    assert np.all(count == np.round(count)) and count.min() >= 0
+    # brute count of true literal occurrences agrees
+    for b in range(5):
+        for c, lc in enumerate(cl):
+            assert count[b, c] == sum((l > 0) == bool(X[b, abs(l) - 1]) for l in lc)
+    cost = ((count == 0) * inst.w[None, :]).sum(axis=1)
+    assert np.array_equal(oracle.evaluate(inst, X), cost)
+
+
+def test_printed_count_form_misses_negated_literals():
+    """The count printed in the appendix listing tests only positive
+    polarities, so a clause made only of negated literals is never counted as
+    satisfied. The text (Sec. 4.3) compares signs with the Boolean values; the
+    oracle follows the text."""
+    inst = oracle.Instance.from_clauses(2, [[-1, -2]])
+    x = np.array([[0, 0]], np.uint8)
+    assert oracle.evaluate(inst, x)[0] == 0  # NOT x1 is true
+    gathered = x[0][[0, 1]]  # values of the clause's variables
+    polarity = np.array([-1, -1])
+    printed_any = bool(((polarity > 0) * gathered).any())
+    assert printed_any is False  # the printed form would call it unsatisfied
+
+
+def test_brute_force_small_independent():
+    """Brute-force optimum via the oracle equals a pure-Python enumeration."""
+    inst = inst_of(workloads.random_ksat(10, 43, 3, seed=2, wmax=9))
+    cl = inst.clauses()
+    best = min(sum(int(inst.w[c]) for c, lc in enumerate(cl)
+                   if not any((l > 0) == bool(v[abs(l) - 1]) for l in lc))
+               for v in itertools.product([0, 1], repeat=inst.n))
+    assert oracle.brute_force_optimum(inst) == best
+
+
+# --------------------------------------------------------------------------
+# RBM pins
+# --------------------------------------------------------------------------
+def _tiny_table(lengths, fstars, iters=4000):
+    return oracle.make_table(lengths, fstars, n_buckets=1, iters=iters)
+
+
+def test_fit_reaches_or_targets():
+    """Sec. 4.1: F(0) ~ 0 and F(v) ~ F_s = -F* for v != 0."""
+    for K, fs in [(2, 0.528), (3, 0.528), (3, 0.068)]:
+        W, b = oracle.fit_or_rbm(K, fs)
+        V = np.array(list(itertools.product([0.0, 1.0], repeat=K)))
+        F = oracle.or_free_energy(W, b, V)
+        assert abs(F[0]) < 0.05
+        assert np.max(np.abs(F[1:] + fs)) < 0.05
+        Wq, bq = oracle.quantise(K, fs, W, b)
+        assert np.all(Wq * 16 == np.round(Wq * 16))
+        assert np.all(bq * 2 ** 24 == np.round(bq * 2 ** 24))
+        assert oracle.fit_loss(K, fs, Wq, bq) < 4 * oracle.fit_loss(K, fs, W, b) + 1e-3
+
+
+def test_tied_weights_cannot_fit_or():
+    """Reading check: with one weight shared by all inputs of a hidden unit,
+    -F(s) = sum_h softplus(b_h + w_h s) is convex in the count s, while the OR
+    target (0, F*, F*, ...) is not, so the general per-position W of the paper
+    is required. A tied fit stays far from the target; the general fit does
+    not."""
+    K, fs = 3, 0.528
+    s = np.arange(K + 1, dtype=float)
+    # best tied fit by brute-force search over a grid of 2 hidden units
+    best = np.inf
+    grid = np.linspace(-6, 6, 49)
+    for w1, b1, w2, b2 in itertools.product(grid[::4], grid[::4], grid[::4], grid[::4]):
+        F = -(np.logaddexp(0, b1 + w1 * s) + np.logaddexp(0, b2 + w2 * s))
+        F = F - F[0]  # free energies matter up to a constant
+        err = np.array([3, 3, 1]) @ (F[1:] + fs) ** 2
+        best = min(best, err)
+    assert best > 0.05
+    W, b = oracle.fit_or_rbm(K, fs)
+    assert oracle.fit_loss(K, fs, W, b) < 0.01
+
+
+def test_free_energy_matches_hidden_enumeration():
+    """Eq. 1 (softplus form) equals -log sum_h exp(-E(v, h)) with
+    E = -v^T W_f h - b_f^T h, enumerated over every hidden configuration of
+    the formula RBM (product of clause RBMs, Sec. 4.1)."""
+    table = _tiny_table([2, 3], [0.528])
+    inst = oracle.Instance.from_clauses(4, [[1, -2, 3], [-1, 4], [-3, -4, 2]])
+    Wf, bf = oracle.formula_rbm(inst, table, temp=0)
+    H = np.array(list(itertools.product([0.0, 1.0], repeat=Wf.shape[1])))
+    X = oracle.all_assignments(4)
+    Fo = oracle.free_energy(inst, table, X, temp=0)
+    for r, v in enumerate(X.astype(float)):
+        negE = H @ (Wf.T @ v) + H @ bf
+        F_enum = -np.log(np.exp(negE).sum())
+        assert abs(F_enum - Fo[r]) < 1e-9
+
+
+def test_negation_transform_eq4():
+    """Eq. 4: the transformed clause RBM on v equals the canonical one on the
+    input with negated literals flipped."""
+    table = _tiny_table([3], [0.528])
+    s = table.get(3, 0, 0)
+    W, b = s["W"], s["b"]
+    clause = [2, -1, -3]
+    inst = oracle.Instance.from_clauses(3, [clause])
+    X = oracle.all_assignments(3)
+    F_t = oracle.free_energy(inst, table, X, temp=0)
+    for r, x in enumerate(X):
+        u = np.array([x[abs(l) - 1] if l > 0 else 1 - x[abs(l) - 1] for l in clause], float)
+        F_c = -np.logaddexp(0, u @ W + b).sum()
+        assert abs(F_c - F_t[r]) < 1e-12
+
+
+def test_formula_free_energy_orders_by_satisfied_clauses():
+    """Sec. 4.1: each satisfied clause contributes ~F_s < 0, an unsatisfied
+    one ~0, so F tracks the number of satisfied clauses."""
+    table = _tiny_table([3], [0.528], iters=20000)
+    inst = inst_of(workloads.random_ksat(8, 30, 3, seed=1))
+    X = oracle.all_assignments(8)
+    F = oracle.free_energy(inst, table, X, temp=0)
+    sat = inst.m - oracle.evaluate(inst, X)
+    slope = np.polyfit(sat, F, 1)[0]
+    assert abs(slope + 0.528) < 0.05
+
+
+def _exact_one_step(inst, table, x0):
+    """Exact distribution of x' after one Gibbs round from x0 with the 16-bit
+    probabilities P/65536 of the sampling contract: sum over hidden states of
+    p(h|x0) p(x'|h), from the dense formula RBM (Eqs. 2, 3)."""
+    Wf, bf = oracle.formula_rbm(inst, table, temp=0)
+    q = lambda a: np.rint(65536.0 / (1.0 + np.exp(-a))) / 65536.0
+    ph = q(bf + Wf.T @ x0.astype(float))
+    H = np.array(list(itertools.product([0.0, 1.0], repeat=len(bf))))
+    X = oracle.all_assignments(inst.n).astype(float)
+    dist = np.zeros(len(X))
+    for h in H:
+        p_h = np.prod(np.where(h > 0, ph, 1 - ph))
+        pv = q(Wf @ h)
+        dist += p_h * np.prod(np.where(X > 0, pv, 1 - pv), axis=1)
+    return dist
+
+
+def test_one_step_transition_matches_enumeration():
+    """One round of the oracle from a fixed state, over many chains, matches
+    the exact transition kernel (catches a dropped term, a wrong sign or a
+    wrong index in the hidden or visible conditionals)."""
+    table = _tiny_table([2, 3], [0.528])
+    inst = oracle.Instance.from_clauses(3, [[1, -2, 3], [-1, -3], [2, 3, -1]])
+    x0 = np.array([1, 0, 1], np.uint8)
+    B = 1 << 16
+    st = oracle.init_chains(3, B, seed=11)
+    st.x[:] = x0
+    oracle.gibbs(inst, table, st, 1, seed=11, n_temps=1)
+    idx = (st.x.astype(np.int64) << np.arange(3)).sum(axis=1)
+    emp = np.bincount(idx, minlength=8) / B
+    exact = _exact_one_step(inst, table, x0)
+    chi2 = (B * (emp - exact) ** 2 / np.maximum(exact, 1e-12)).sum()
+    assert chi2 < 30.0, (emp, exact)  # 7 dof: p ~ 1e-4
+
+
+def test_stationary_distribution():
+    """Block Gibbs leaves p(v) ~ exp(-F(v)) invariant (Sec. 3.1): the empirical
+    state frequencies over many chains and steps match it."""
+    table = _tiny_table([2, 3], [0.528])
+    inst = oracle.Instance.from_clauses(4, [[1, -2, 3], [-1, 4], [-3, -4, 2], [2, 4]])
+    X = oracle.all_assignments(4)
+    F = oracle.free_energy(inst, table, X, temp=0)
+    p = np.exp(-(F - F.min()))
+    p /= p.sum()
+    B = 4096
+    st = oracle.init_chains(4, B, seed=5)
+    oracle.gibbs(inst, table, st, 10, seed=5, n_temps=1)
+    counts = np.zeros(16)
+    for _ in range(40):
+        oracle.gibbs(inst, table, st, 1, seed=5, n_temps=1)
+        counts += np.bincount((st.x.astype(np.int64) << np.arange(4)).sum(axis=1), minlength=16)
+    emp = counts / counts.sum()
+    assert 0.5 * np.abs(emp - p).sum() < 0.01
+
+
+# --------------------------------------------------------------------------
+# Search: determinism, resume, best-keep, quality
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cfg1_table():
+    return _tiny_table([3], [0.068, 0.528], iters=20000)
+
+
+def test_init_contract():
+    st = oracle.init_chains(50, 64, seed=9)
+    assert abs(st.x.mean() - 0.5) < 0.03
+    assert np.all(st.nu == 0.25)
+    assert np.all(st.best_cost == np.iinfo(np.int64).max)
+    assert st.x[3, 17] == (oracle.draw16(9, 1, 0, 17, 0, 3) < 32768)
+
+
+def test_determinism_and_resume(cfg1_table):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    a = oracle.init_chains(50, 32, seed=4)
+    b = a.copy()
+    oracle.gibbs(inst, cfg1_table, a, 30, seed=4, n_temps=2)
+    oracle.gibbs(inst, cfg1_table, b, 12, seed=4, n_temps=2)
+    oracle.gibbs(inst, cfg1_table, b, 18, seed=4, n_temps=2)
+    for f in ["x", "nu", "best_cost", "best_x", "cost", "free_energy"]:
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_best_keep_invariants(cfg1_table):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    st = oracle.init_chains(50, 16, seed=1)
+    seen = np.full(16, np.iinfo(np.int64).max)
+    for _ in range(20):
+        oracle.gibbs(inst, cfg1_table, st, 1, seed=1, n_temps=2)
+        seen = np.minimum(seen, st.cost)
+    oracle.score_and_keep(inst, st)
+    seen = np.minimum(seen, st.cost)
+    assert np.array_equal(st.best_cost, seen)
+    assert np.array_equal(oracle.evaluate(inst, st.best_x), st.best_cost)
+
+
+def test_nu_update_range(cfg1_table):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    st = oracle.init_chains(50, 8, seed=2)
+    oracle.gibbs(inst, cfg1_table, st, 50, seed=2, n_temps=2, alpha=0.05)
+    assert st.nu.min() >= 0 and st.nu.max() <= 0.25
+
+
+def test_brute_force_twin_reaches_optimum(cfg1_table):
+    """n = 18, m = 77 (ratio 4.3): the best cost found is never below the
+    exact optimum, and 256 chains x 200 steps reach it."""
+    inst = inst_of(workloads.random_ksat(18, 77, 3, seed=0))
+    opt = oracle.brute_force_optimum(inst)
+    best, bx, st = oracle.solve(inst, cfg1_table, 256, 200, seed=0, n_temps=2, threads=4)
+    assert best >= opt
+    assert oracle.evaluate(inst, bx[None])[0] == best
+    assert best == opt
+
+
+def test_gibbs_beats_uniform_random(cfg1_table):
+    """Ablation idea of Table 2 (-Gibbs): at an equal number of evaluated
+    assignments, Gibbs sampling finds lower costs than uniform random ones."""
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    best, _, _ = oracle.solve(inst, cfg1_table, 64, 100, seed=3, n_temps=2, threads=4)
+    rng = np.random.default_rng(0)
+    X = rng.integers(0, 2, size=(64 * 101, 50)).astype(np.uint8)
+    assert best < oracle.evaluate(inst, X).min()
+
+
+def test_draw_decision_is_strict_below_threshold():
+    """The sampling contract's decision x = [u < P]: with no clauses every
+    visible logit is 0, so P = 65536 * sigma(0) = 32768 and x' must equal
+    [u < 32768] for every chain and variable (2^18 draws hit u == 32768)."""
+    inst = oracle.Instance.from_clauses(4, [])
+    B = 1 << 16
+    st = oracle.init_chains(4, B, seed=21)
+    oracle.gibbs(inst, oracle.RbmTable(), st, 1, seed=21, n_temps=1)
+    draws = np.array([[oracle.draw16(21, 3, 0, i, 0, b) for i in range(4)] for b in range(B)])
+    assert (draws == 32768).any()
+    assert np.array_equal(st.x, (draws < 32768).astype(np.uint8))
+    assert np.allclose(st.nu, 0.99 * 0.25 + 0.01 * 0.25)
