@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput benchmark of RbmSAT block Gibbs sampling on GB300.
+
+A step is one full Gibbs round over all chains: score (weighted unsatisfied
+cost + free energy), best-keep, hidden draws, scatter-sum of visible logits,
+visible draws and the nu update. Metric: clause-assignment evaluations per
+second = m * B * steps / seconds, summed over ranks (weak scaling: every rank
+runs its own B chains; no data-path collective).
+
+Default workload: weighted Max-3-SAT, n = 1000 variables, m = 6000 clauses,
+weights uniform in [1, 1000], B = 4096 chains, seeded synthetic instance.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on the
+host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "clause·assignment evals/s"
+UNIT = "evals/s"
+BAD_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="w3sat-n1000-m6000")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name, seed):
+    spec = workloads.WORKLOADS[name]
+    n, off, lits, w = spec["gen"](seed)
+    return n, off, lits, w, spec["B"]
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_rate(n, off, lits, w, B, seconds, seed, table=None, n_buckets=4):
+    """Times the oracle's Gibbs rounds on a sample of chains with every host
+    core; returns (evals/s, threads, sample description)."""
+    import oracle
+    inst = oracle.Instance(n, off, lits, w)
+    if table is None:
+        table = oracle.make_table(sorted(set(np.diff(off)) - {0}), [0.068, 0.528],
+                                  n_buckets=n_buckets, iters=2000)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    m = len(off) - 1
+    # calibrate on one round of `threads` chains, then size the sample
+    ids = np.linspace(0, B - 1, threads).astype(np.int32)
+    st = oracle.init_chains(n, 0, seed, chain_ids=ids, B_total=B)
+    t0 = time.perf_counter()
+    oracle.gibbs(inst, table, st, 1, seed, n_temps=2, n_buckets=n_buckets, threads=threads)
+    per_round = time.perf_counter() - t0
+    rounds = max(1, int(seconds / max(per_round, 1e-6)))
+    chains = threads * min(8, max(1, rounds // 4))
+    steps = max(1, int(rounds * threads / chains))
+    ids = np.linspace(0, B - 1, chains).astype(np.int32)
+    st = oracle.init_chains(n, 0, seed, chain_ids=ids, B_total=B)
+    t0 = time.perf_counter()
+    oracle.gibbs(inst, table, st, steps, seed, n_temps=2, n_buckets=n_buckets, threads=threads)
+    dt = time.perf_counter() - t0
+    sample = (f"{chains} of {B} chains x {steps} Gibbs rounds of the full formula "
+              f"(m = {m}), {dt:.1f} s on {threads} threads")
+    return m * chains * steps / dt, threads, sample, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n, off, lits, w, B = workload(args.workload, args.seed)
+    m = len(off) - 1
+    import oracle
+    table = oracle.make_table(sorted(set(np.diff(off)) - {0}), [0.068, 0.528], n_buckets=4,
+                              iters=2000)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    inst = oracle.Instance(n, off, lits, w)
+    chains = threads
+    ids = np.linspace(0, B - 1, chains).astype(np.int32)
+    st = oracle.init_chains(n, 0, args.seed, chain_ids=ids, B_total=B)
+    oracle.gibbs(inst, table, st, max(args.warmup, 0), args.seed, n_temps=2, n_buckets=4,
+                 threads=threads)
+    t0 = time.perf_counter()
+    oracle.gibbs(inst, table, st, args.steps, args.seed, n_temps=2, n_buckets=4, threads=threads)
+    dt = time.perf_counter() - t0
+    value = m * chains * args.steps / dt
+    sample = f"{chains} of {B} chains per step (full formula, m = {m})"
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=ws,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * dt / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", config=dict(workload=args.workload, n=n, m=m, B=B),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=threads, kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].strip() == "Active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0), "fallback"
+
+
+def algorithmic_bytes(kernel, n, m, nnz, B):
+    """Compulsory bytes one launch moves (sparse path): the state it must read
+    and write once, nothing re-read. Per clause and chain the hidden state is
+    one byte (up to 8 hidden units); per variable and chain the state is one
+    byte and nu four bytes."""
+    formula = 4 * (m + 1) + 4 * nnz + 4 * m + 8 * m
+    if kernel == "gather_hidden":
+        return n * B + m * B + formula
+    if kernel == "visible":
+        return m * B + 2 * n * B + 8 * n * B + 8 * nnz
+    if kernel == "best_keep":
+        return 12 * B
+    return None
+
+
+def run_mine(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_02101_gb300 as ms
+
+    n, off, lits, w, B = workload(args.workload, args.seed)
+    m, nnz = len(off) - 1, int(off[-1])
+    stream = torch.cuda.Stream()
+    params = ms.maxsat_default_params()
+    ctx = ms.maxsat_create(n, off, lits, w, params, stream)
+    seed = args.seed * 1000003 + rank
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, args.warmup)
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    ms.maxsat_step(ctx, args.steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms_total = start.elapsed_time(stop)
+    if ws > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = m * B * args.steps * ws / (ms_total / 1e3)
+
+    # per-kernel device times over a second region of the same length (plain
+    # launches, CUDA events around every launch on the library's stream)
+    ms.maxsat_set_profiling(ctx, True)
+    ms.maxsat_step(ctx, args.steps)
+    kt = ms.maxsat_kernel_times(ctx)
+    ms.maxsat_set_profiling(ctx, False)
+    top = max(kt, key=lambda k: kt[k][1])
+    launches, tot = kt[top]
+    avg_s = tot / launches / 1e3
+    peaks, peak_src = measured_peaks()
+    alg = algorithmic_bytes(top, n, m, nnz, B)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f).get(args.workload, {}).get(top)
+        if tr and tr.get("kernel_hash") == ms_kernel_hash():
+            traffic = tr.get("bytes_per_launch")
+    roofline = dict(kernel=top, bound="hbm", achieved=alg / avg_s / 1e9, peak=peaks["hbm_gbs"],
+                    unit="GB/s", frac=alg / avg_s / 1e9 / peaks["hbm_gbs"], traffic=traffic,
+                    algorithmic_bytes=alg, avg_launch_us=avg_s * 1e6,
+                    peak_source=f"{peak_src} (copy bandwidth)",
+                    kernels={k: dict(launches=v[0], avg_us=1e3 * v[1] / v[0])
+                             for k, v in kt.items()})
+
+    # end to end through the public API with host buffers: create from host
+    # arrays (pre-fitted parameters, so no fitting), solve, best assignment and
+    # cost back to the host
+    sets = []
+    for s in (ms_fitted_sets(ms, off, params)):
+        sets.append(s)
+    p2 = ms.maxsat_default_params(sets=sets)
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx2 = ms.maxsat_create(n, off, lits, w, p2, stream)
+    cost, assign = ms.maxsat_solve(ctx2, B, e2e_steps, seed)
+    ms.maxsat_destroy(ctx2)
+    e2e_s = time.perf_counter() - t0
+    e2e = dict(value=m * B * e2e_steps * ws / e2e_s, unit=UNIT,
+               h2d_bytes_per_step=(off.nbytes + lits.nbytes + w.nbytes) / e2e_steps,
+               d2h_bytes_per_step=(n + 8 * B) / e2e_steps, best_cost=int(cost))
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, threads, sample, _ = oracle_rate(n, off, lits, w, B, args.cpu_seconds, seed)
+        cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
+
+    S = params.steps_per_graph
+    launches_timed = 3 * args.steps + (args.steps // S if S else 0)
+    path = {1: "dense", 2: "sparse"}[ms.maxsat_get_path(ctx)]
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_total / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
+                config=dict(workload=args.workload, n=n, m=m, B=B, path=path,
+                            steps_per_graph=S, parallelism=f"replicas{ws}",
+                            l2="working set above L2 (no flush): G/hidden state, nu and "
+                               "x of 4096 chains; state carried step to step"),
+                roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
+                gpu_launches=launches_timed)
+    ms.maxsat_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def ms_kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2311_02101_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ms_fitted_sets(ms, off, params):
+    """The library's own fitted sets for this formula's clause lengths and
+    weight buckets (host fitting, outside the timed region)."""
+    lengths = sorted(set(np.diff(off).tolist()) - {0})
+    fstar = [0.068, 0.528]
+    out = []
+    for e, fs in enumerate(fstar):
+        for j in range(params.n_buckets):
+            for K in lengths:
+                L = 3 if K <= 3 else K + 1
+                W, b = ms.maxsat_fit_or_rbm(K, L, fs * (1 + j * params.bucket_gamma),
+                                            params.quant_bits, params.fit_iters)
+                out.append(dict(len=K, bucket=j, temp=e, W=W, b=b))
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * maxsat.h -- C ABI of the GB300 RbmSAT library (libmaxsat.so).
+ *
+ * RbmSAT ("Solving MaxSAT with Matrix Multiplication") turns a CNF formula into
+ * a Restricted Boltzmann Machine whose free energy falls with every satisfied
+ * clause (Sec. 4.1) and searches with block Gibbs sampling over many parallel
+ * chains (Sec. 4.2), keeping the best assignment seen. Each Gibbs round is:
+ *   - the "gather": every clause reads the truth of its literals for every
+ *     chain (Sec. 4.3), giving the weighted unsatisfied cost and the clause
+ *     free energy (Eq. 1);
+ *   - hidden units drawn from p(h | v) (Eq. 2, Eq. 6) after the negation
+ *     transform of the canonical OR-gate RBM (Eq. 4);
+ *   - the "scatter-add" of the hidden units' contributions into the visible
+ *     logits (Eq. 7) and new visible states drawn from p(v | h) (Eq. 3),
+ *     plus the moving average nu of the conditional variance (Sec. 4.4);
+ *   - best-so-far tracking (Sec. 4.2).
+ *
+ * Conventions (all entry points):
+ *   - Return MAXSAT_OK (0) or a negative MAXSAT_E* code; the message is then
+ *     available from maxsat_last_error(ctx) (or maxsat_last_error(NULL) when
+ *     maxsat_create itself failed).
+ *   - Assignments at the ABI are bytes, 1 = True, 0 = False, chain-major
+ *     (B rows of n bytes). Any nonzero byte reads as True.
+ *   - Pointers named *_dev are device pointers on the context's device; all
+ *     others are host pointers. The caller owns every buffer it passes; the
+ *     library copies what it keeps and never frees caller memory.
+ *   - All device work is ordered on the CUDA stream given to maxsat_create.
+ *     Calls that return results in host memory synchronise that stream.
+ *   - A context is not thread-safe: one thread at a time per context.
+ *   - There is no CPU fallback: without an sm_103 device every call that needs
+ *     one fails with MAXSAT_ENODEV.
+ */
+#ifndef MAXSAT_H_
+#define MAXSAT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAXSAT_OK 0
+#define MAXSAT_EINVAL (-1)    /* bad argument or an exactness precondition fails */
+#define MAXSAT_ENOMEM (-2)    /* device or host allocation failed */
+#define MAXSAT_ECUDA (-3)     /* a CUDA runtime call failed */
+#define MAXSAT_ENODEV (-4)    /* no sm_103 device */
+#define MAXSAT_ESTATE (-5)    /* call out of order (e.g. step before reset) */
+
+#define MAXSAT_MAX_LEN 12     /* longest clause with an OR-gate RBM */
+#define MAXSAT_MAX_HIDDEN 16  /* most hidden units per clause RBM */
+
+#define MAXSAT_PATH_AUTO 0
+#define MAXSAT_PATH_DENSE 1   /* tensor-core products over dense operands */
+#define MAXSAT_PATH_SPARSE 2  /* gather / pull-scatter over the literal lists */
+
+/* One canonical (un-negated) OR-gate clause RBM: Sec. 4.1 "OR gate as an
+ * RBM", general per-position weights W in R^{len x n_hidden} and hidden biases
+ * b, no visible bias. It serves clauses of length `len` in weight bucket
+ * `bucket` on chains of temperature `temp`. Every W entry must be a multiple
+ * of 2^-quant_bits and every b entry a multiple of 2^-24 below 2^20 in
+ * magnitude, so that every hidden logit is an exact double and every visible
+ * logit an exact multiple of 2^-quant_bits (maxsat_fit_or_rbm returns such
+ * values). The arrays are read during maxsat_create only. */
+typedef struct {
+  int32_t len;       /* 1 .. MAXSAT_MAX_LEN */
+  int32_t bucket;    /* 0 .. n_buckets - 1 */
+  int32_t temp;      /* 0 .. n_temps - 1 */
+  int32_t n_hidden;  /* 1 .. MAXSAT_MAX_HIDDEN */
+  const double* W;   /* len x n_hidden, row-major (row k = clause position k) */
+  const double* b;   /* n_hidden */
+} maxsat_rbm_set;
+
+/* Solver parameters; maxsat_default_params fills the defaults. */
+typedef struct {
+  int32_t n_temps;       /* temperature ensemble size E (Sec. 4.2); default 2 */
+  const double* fstar;   /* E targets F* (F_s = -F*); NULL = {0.068, 0.528}, the
+                            paper's 1-TPU condition (appendix "Pretraining") */
+  int32_t n_buckets;     /* weight buckets J (a reading: the paper is unweighted);
+                            clause c uses bucket min(J-1, floor(log2(w_c / w_min)));
+                            default 4 */
+  double bucket_gamma;   /* bucket j fits target F* (1 + j gamma); default 0.5 */
+  double alpha;          /* rate of the nu moving average (Sec. 4.4; the paper
+                            gives none); default 0.01 */
+  int32_t quant_bits;    /* Q: W on the 2^-Q grid; default 4 */
+  int32_t path;          /* MAXSAT_PATH_*; default AUTO */
+  int32_t fit_iters;     /* Adam iterations when fitting (lr 1e-3, appendix
+                            "Pretraining"; the paper gives no count);
+                            default 50000 */
+  int32_t n_sets;        /* 0 with sets == NULL: fit every needed set at create */
+  const maxsat_rbm_set* sets;
+  int32_t steps_per_graph; /* Gibbs rounds per CUDA-graph launch (the paper runs
+                              500 rounds per device dispatch); default 500;
+                              0 = plain launches */
+} maxsat_params;
+
+typedef struct maxsat_ctx maxsat_ctx;
+
+/* Fills *p with the defaults listed above. */
+void maxsat_default_params(maxsat_params* p);
+
+/* Builds a solver for one weighted CNF formula.
+ *   n_vars      number of variables n >= 1
+ *   n_clauses   number of clauses m >= 0
+ *   clause_off  m + 1 host int64 offsets into lits, clause_off[0] = 0,
+ *               non-decreasing; clause c holds lits[clause_off[c] ..
+ *               clause_off[c+1]) (at most MAXSAT_MAX_LEN literals)
+ *   lits        DIMACS literals: +v is variable v (1-based) true, -v false
+ *               (the signed index table T of Sec. 4.3); duplicates and x OR
+ *               NOT x are allowed; an empty clause is never satisfied
+ *   weights     m host int64 weights >= 1, or NULL for all 1
+ *   params      NULL for the defaults
+ *   cuda_stream cudaStream_t (as void*) all work is ordered on; NULL = legacy
+ *               default stream
+ * Fits any missing OR-gate RBM sets (Sec. 4.1), builds the probability and
+ * free-energy tables and copies the formula to the device. *out receives the
+ * context (NULL on failure). */
+int maxsat_create(maxsat_ctx** out, int32_t n_vars, int64_t n_clauses,
+                  const int64_t* clause_off, const int32_t* lits,
+                  const int64_t* weights, const maxsat_params* params,
+                  void* cuda_stream);
+
+/* Starts B fresh chains (Fig. code initialisation): every variable drawn
+ * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */
+int maxsat_reset(maxsat_ctx* ctx, int32_t restarts, uint64_t seed);
+
+/* Runs `steps` Gibbs rounds on the current chains. Round t scores the current
+ * state x_t (cost, free energy), keeps it if its cost is strictly below the
+ * chain's best, draws h ~ p(h | x_t) and x_{t+1} ~ p(v | h) and updates nu.
+ * Asynchronous on the context's stream. */
+int maxsat_step(maxsat_ctx* ctx, int64_t steps);
+
+/* Scores the current states and updates the best-so-far without drawing
+ * (the evaluation after the last round, so rounds 0..T-1 plus this score
+ * x_0 .. x_T). Asynchronous. */
+int maxsat_score(maxsat_ctx* ctx);
+
+/* Weighted unsatisfied cost of B arbitrary assignments (the MaxSAT objective,
+ * Sec. 1). assign_dev: B x n device bytes; cost_dev: B device int64.
+ * Independent of the chains. Asynchronous. */
+int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B,
+                int64_t* cost_dev);
+
+/* reset + `steps` rounds + score, then copies the best assignment over all
+ * chains (lowest cost, ties to the lowest chain index) to best_assign (n host
+ * bytes, may be NULL) and its cost to *best_cost. Synchronises. */
+int maxsat_solve(maxsat_ctx* ctx, int32_t restarts, int64_t steps, uint64_t seed,
+                 uint8_t* best_assign, int64_t* best_cost);
+
+/* Copies chain state to host buffers (each may be NULL): x and best_x are
+ * B x n bytes, nu is B x n float, best_cost / cost are B int64 (cost = last
+ * scored state), free_energy B float (last scored state, Eq. 1 summed over
+ * clauses), *t the next round's index. Synchronises. */
+int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
+                     uint8_t* best_x, int64_t* cost, float* free_energy,
+                     uint32_t* t);
+
+/* Restores chain state (checkpoint resume): B chains, the seed they were
+ * started with, x / nu / best_cost / best_x as returned by maxsat_get_state and
+ * the round index t. With the counter-based randomness, resuming continues
+ * the same trajectory bit for bit. Synchronises. */
+int maxsat_set_state(maxsat_ctx* ctx, int32_t restarts, uint64_t seed,
+                     const uint8_t* x, const float* nu, const int64_t* best_cost,
+                     const uint8_t* best_x, uint32_t t);
+
+/* Per-kernel timing. While profiling is on, maxsat_step and maxsat_score use
+ * plain launches (no CUDA graph) and bracket every kernel launch with CUDA
+ * events on the context's stream; maxsat_kernel_times then synchronises and
+ * reports, per kernel name, the number of launches and their total device
+ * time in milliseconds since profiling was switched on. names receives up to
+ * max_kernels NUL-terminated names of at most 31 characters (32 bytes each).
+ * Returns the number of kernels reported (>= 0) or a negative code. */
+int maxsat_set_profiling(maxsat_ctx* ctx, int32_t on);
+int maxsat_kernel_times(maxsat_ctx* ctx, int32_t max_kernels, char* names,
+                        int64_t* launches, double* total_ms);
+
+/* Which path the context runs (MAXSAT_PATH_DENSE or _SPARSE). */
+int maxsat_get_path(const maxsat_ctx* ctx);
+
+/* Frees the context and its device memory (NULL is a no-op). */
+void maxsat_destroy(maxsat_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed
+ * maxsat_create when ctx is NULL); "" when none. Valid until the next call. */
+const char* maxsat_last_error(const maxsat_ctx* ctx);
+
+/* Fits one canonical OR-gate RBM on the host (Sec. 4.1): minimises
+ * F(0)^2 + sum_{v != 0} (F(v) - F_s)^2 over all 2^len inputs with Adam at
+ * learning rate 1e-3, F_s = -fstar; then rounds W to the 2^-quant_bits grid,
+ * refits b with W fixed and rounds b to the 2^-24 grid. W_out: len x n_hidden
+ * row-major, b_out: n_hidden (host). No device needed. */
+int maxsat_fit_or_rbm(int32_t len, int32_t n_hidden, double fstar,
+                      int32_t quant_bits, int32_t iters, double* W_out,
+                      double* b_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAXSAT_H_ */

@@ -68,9 +68,9 @@ def lib():
         _lib.oracle_draw16.argtypes = [u64, u32, u32, u32, u32, u32]
         _lib.oracle_draw16.restype = u32
         _lib.oracle_eval.argtypes = [i32, i64, P, P, P, P, i32, P]
-        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P]
+        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P, P]
         _lib.oracle_gibbs.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32, i32,
-                                      f64, u64, i32, u32, i32, P, P, P, P, P, P, i32]
+                                      f64, u64, i32, P, i32, u32, i32, P, P, P, P, P, P, i32]
         _lib.oracle_free_energy.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32,
                                             i32, P, i32, P]
     return _lib
@@ -326,18 +326,27 @@ class ChainState:
     cost: np.ndarray  # B int64 (last scored state)
     free_energy: np.ndarray  # B float64 (last scored state)
     t: int = 0
+    chain_ids: np.ndarray | None = None  # global chain index of each row
+    B_total: int = 0  # ensemble size the temperatures are spread over
 
     def copy(self):
         return ChainState(self.x.copy(), self.nu.copy(), self.best_cost.copy(),
-                          self.best_x.copy(), self.cost.copy(), self.free_energy.copy(), self.t)
+                          self.best_x.copy(), self.cost.copy(), self.free_energy.copy(), self.t,
+                          None if self.chain_ids is None else self.chain_ids.copy(), self.B_total)
 
 
-def init_chains(n: int, B: int, seed: int) -> ChainState:
+def init_chains(n: int, B: int, seed: int, chain_ids=None, B_total=None) -> ChainState:
+    """B chains; with `chain_ids`, row r is chain chain_ids[r] of an ensemble
+    of B_total chains (so a sample of a large run can be reproduced)."""
+    if chain_ids is not None:
+        chain_ids = np.ascontiguousarray(chain_ids, np.int32)
+        B = len(chain_ids)
     x = np.zeros((B, n), np.uint8)
     nu = np.zeros((B, n), np.float64)
     best = np.zeros(B, np.int64)
-    lib().oracle_init(n, B, seed, _ptr(x), _ptr(nu), _ptr(best))
-    return ChainState(x, nu, best, x.copy(), np.zeros(B, np.int64), np.zeros(B), 0)
+    lib().oracle_init(n, B, seed, _ptr(chain_ids), _ptr(x), _ptr(nu), _ptr(best))
+    return ChainState(x, nu, best, x.copy(), np.zeros(B, np.int64), np.zeros(B), 0,
+                      chain_ids, int(B_total if B_total is not None else B))
 
 
 def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int,
@@ -348,7 +357,8 @@ def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int
     B = st.x.shape[0]
     rc = lib().oracle_gibbs(inst.n, inst.m, _ptr(inst.off), _ptr(inst.lits), _ptr(inst.w),
                             len(ln), _ptr(ln), _ptr(bk), _ptr(tp), _ptr(nh), _ptr(W), _ptr(b),
-                            n_temps, n_buckets, alpha, seed, B, st.t, steps,
+                            n_temps, n_buckets, alpha, seed, B, _ptr(st.chain_ids),
+                            st.B_total or B, st.t, steps,
                             _ptr(st.x), _ptr(st.nu), _ptr(st.best_cost), _ptr(st.best_x),
                             _ptr(st.cost), _ptr(st.free_energy), threads)
     if rc != 0:

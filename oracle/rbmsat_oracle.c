@@ -182,11 +182,12 @@ static void negation_transform(const rbm_table* t, int s, const int32_t* lits,
 /* Chain initialisation (Fig. code: v ~ Bernoulli(0.5), nu = 0.25,          */
 /* best-so-far empty).                                                      */
 /* ---------------------------------------------------------------------- */
-int oracle_init(int32_t n, int32_t B, uint64_t seed, uint8_t* x, double* nu,
-                int64_t* best_cost) {
+int oracle_init(int32_t n, int32_t B, uint64_t seed, const int32_t* chain_ids,
+                uint8_t* x, double* nu, int64_t* best_cost) {
   for (int32_t b = 0; b < B; ++b) {
+    uint32_t gb = (uint32_t)(chain_ids ? chain_ids[b] : b);
     for (int32_t i = 0; i < n; ++i) {
-      uint32_t u = oracle_draw16(seed, PH_INIT, 0u, (uint32_t)i, 0u, (uint32_t)b);
+      uint32_t u = oracle_draw16(seed, PH_INIT, 0u, (uint32_t)i, 0u, gb);
       x[(int64_t)b * n + i] = u < 32768u;
       nu[(int64_t)b * n + i] = 0.25;
     }
@@ -197,18 +198,20 @@ int oracle_init(int32_t n, int32_t B, uint64_t seed, uint8_t* x, double* nu,
 
 /* ---------------------------------------------------------------------- */
 /* T rounds of block Gibbs sampling on B chains, starting at step t0.       */
-/* State arrays are B x n, chain-major. cost/free_energy receive the score  */
-/* of the state scored in the last round. Returns 0, or -1 when a clause    */
-/* has no parameter set.                                                    */
+/* State arrays are B x n, chain-major. Row b is chain chain_ids[b] of an   */
+/* ensemble of B_total chains (identity when chain_ids is NULL): the index  */
+/* selects its draws and its temperature. cost/free_energy receive the      */
+/* score of the state scored in the last round. Returns 0, or -1 when a     */
+/* clause has no parameter set.                                             */
 /* ---------------------------------------------------------------------- */
 int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
                  const int64_t* w, int32_t n_sets, const int32_t* set_len,
                  const int32_t* set_bucket, const int32_t* set_temp,
                  const int32_t* set_nh, const double* W, const double* bias,
                  int32_t n_temps, int32_t n_buckets, double alpha, uint64_t seed,
-                 int32_t B, uint32_t t0, int32_t T, uint8_t* x, double* nu,
-                 int64_t* best_cost, uint8_t* best_x, int64_t* cost,
-                 double* free_energy, int32_t n_threads) {
+                 int32_t B, const int32_t* chain_ids, int32_t B_total, uint32_t t0,
+                 int32_t T, uint8_t* x, double* nu, int64_t* best_cost, uint8_t* best_x,
+                 int64_t* cost, double* free_energy, int32_t n_threads) {
   rbm_table tab = {n_sets, set_len, set_bucket, set_temp, set_nh, W, bias};
   int64_t wmin = INT64_MAX;
   for (int64_t c = 0; c < m; ++c) {
@@ -216,12 +219,14 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
     if (wc < wmin) wmin = wc;
   }
   int bad = 0;
+  if (!chain_ids) B_total = B;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
 #endif
   for (int32_t b = 0; b < B; ++b) {
-    int32_t e = (int32_t)(((int64_t)b * n_temps) / B);
+    uint32_t gb = (uint32_t)(chain_ids ? chain_ids[b] : b);
+    int32_t e = (int32_t)(((int64_t)gb * n_temps) / B_total);
     uint8_t* xb = x + (int64_t)b * n;
     double* nub = nu + (int64_t)b * n;
     double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -254,8 +259,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
             a += Wp[k][h] * (double)xb[v];
           }
           F -= softplus(a);
-          uint32_t u = oracle_draw16(seed, PH_HID, t, (uint32_t)c, (uint32_t)h,
-                                     (uint32_t)b);
+          uint32_t u = oracle_draw16(seed, PH_HID, t, (uint32_t)c, (uint32_t)h, gb);
           hid[c * OR_MAX_H + h] = u < prob16(a);
         }
       }
@@ -284,7 +288,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
         uint32_t P = prob16(z[i]);
         double rho = (double)P / 65536.0;
         nub[i] = (1.0 - alpha) * nub[i] + alpha * rho * (1.0 - rho);
-        uint32_t u = oracle_draw16(seed, PH_VIS, t, (uint32_t)i, 0u, (uint32_t)b);
+        uint32_t u = oracle_draw16(seed, PH_VIS, t, (uint32_t)i, 0u, gb);
         xb[i] = u < P;
       }
     }

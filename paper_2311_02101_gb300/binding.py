@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libmaxsat.so (include/maxsat.h): argument marshalling
+only. Every step of a Gibbs round runs in the library's CUDA kernels; PyTorch
+provides device buffers and streams. There is no CPU fallback: importing
+works without a GPU, but the library must have been built (``build()``), and
+calls that need the device fail with MaxsatError(MAXSAT_ENODEV) without one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXSAT_OK = 0
+MAXSAT_EINVAL = -1
+MAXSAT_ENOMEM = -2
+MAXSAT_ECUDA = -3
+MAXSAT_ENODEV = -4
+MAXSAT_ESTATE = -5
+MAXSAT_MAX_LEN = 12
+MAXSAT_MAX_HIDDEN = 16
+MAXSAT_PATH_AUTO = 0
+MAXSAT_PATH_DENSE = 1
+MAXSAT_PATH_SPARSE = 2
+
+LIB_PATH = _build.LIB
+
+
+class MaxsatError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class maxsat_rbm_set(ctypes.Structure):
+    _fields_ = [("len", ctypes.c_int32), ("bucket", ctypes.c_int32), ("temp", ctypes.c_int32),
+                ("n_hidden", ctypes.c_int32), ("W", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+class maxsat_params(ctypes.Structure):
+    _fields_ = [("n_temps", ctypes.c_int32), ("fstar", ctypes.c_void_p),
+                ("n_buckets", ctypes.c_int32), ("bucket_gamma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("quant_bits", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("fit_iters", ctypes.c_int32),
+                ("n_sets", ctypes.c_int32), ("sets", ctypes.POINTER(maxsat_rbm_set)),
+                ("steps_per_graph", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmaxsat.so is not built ({LIB_PATH}); run "
+                               "__graft_entry__.build() or paper_2311_02101_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u32, u64, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+        L.maxsat_default_params.argtypes = [ctypes.POINTER(maxsat_params)]
+        L.maxsat_default_params.restype = None
+        L.maxsat_create.argtypes = [ctypes.POINTER(P), i32, i64, P, P, P,
+                                    ctypes.POINTER(maxsat_params), P]
+        L.maxsat_reset.argtypes = [P, i32, u64]
+        L.maxsat_step.argtypes = [P, i64]
+        L.maxsat_score.argtypes = [P]
+        L.maxsat_eval.argtypes = [P, P, i32, P]
+        L.maxsat_solve.argtypes = [P, i32, i64, u64, P, P]
+        L.maxsat_get_state.argtypes = [P, P, P, P, P, P, P, P]
+        L.maxsat_set_state.argtypes = [P, i32, u64, P, P, P, P, u32]
+        L.maxsat_get_path.argtypes = [P]
+        L.maxsat_destroy.argtypes = [P]
+        L.maxsat_destroy.restype = None
+        L.maxsat_last_error.argtypes = [P]
+        L.maxsat_last_error.restype = ctypes.c_char_p
+        L.maxsat_fit_or_rbm.argtypes = [i32, i32, f64, i32, i32, P, P]
+        L.maxsat_set_profiling.argtypes = [P, i32]
+        L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
+        for name in ["maxsat_create", "maxsat_reset", "maxsat_step", "maxsat_score",
+                     "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
+                     "maxsat_get_path", "maxsat_fit_or_rbm", "maxsat_set_profiling",
+                     "maxsat_kernel_times"]:
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, ctx=None):
+    if rc != MAXSAT_OK:
+        raise MaxsatError(rc, maxsat_last_error(ctx))
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Context:
+    """Opaque solver handle (the C maxsat_ctx*) plus the few facts the binding
+    needs for marshalling."""
+
+    def __init__(self, handle, n, m):
+        self.handle = handle
+        self.n = n
+        self.m = m
+        self.B = 0
+
+    def __del__(self):
+        try:
+            maxsat_destroy(self)
+        except Exception:
+            pass
+
+
+def maxsat_default_params(**overrides):
+    """A maxsat_params with the library defaults, fields overridden by keyword;
+    `fstar` (list of floats) and `sets` (list of dicts with len, bucket, temp,
+    W, b) are converted; the returned object keeps their buffers alive."""
+    p = maxsat_params()
+    lib().maxsat_default_params(ctypes.byref(p))
+    keep = []
+    for k, v in overrides.items():
+        if k == "fstar":
+            arr = np.ascontiguousarray(v, np.float64)
+            keep.append(arr)
+            p.fstar = arr.ctypes.data
+            p.n_temps = len(arr)
+        elif k == "sets":
+            sets = list(v)
+            S = (maxsat_rbm_set * max(1, len(sets)))()
+            for i, s in enumerate(sets):
+                W = np.ascontiguousarray(s["W"], np.float64)
+                b = np.ascontiguousarray(s["b"], np.float64)
+                keep += [W, b]
+                S[i] = maxsat_rbm_set(int(s["len"]), int(s["bucket"]), int(s["temp"]),
+                                      int(W.shape[1]), W.ctypes.data, b.ctypes.data)
+            keep.append(S)
+            p.sets = ctypes.cast(S, ctypes.POINTER(maxsat_rbm_set))
+            p.n_sets = len(sets)
+        else:
+            setattr(p, k, v)
+    p._keep = keep
+    return p
+
+
+def maxsat_create(n, off, lits, weights=None, params=None, stream=None) -> Context:
+    off = np.ascontiguousarray(off, np.int64)
+    lits = np.ascontiguousarray(lits, np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, np.int64)
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    rc = lib().maxsat_create(ctypes.byref(h), int(n), len(off) - 1, _np_ptr(off), _np_ptr(lits),
+                             _np_ptr(w), pp, _stream_handle(stream))
+    _check(rc, None)
+    return Context(h.value, int(n), len(off) - 1)
+
+
+def maxsat_reset(ctx: Context, restarts: int, seed: int):
+    _check(lib().maxsat_reset(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1)), ctx)
+    ctx.B = int(restarts)
+
+
+def maxsat_step(ctx: Context, steps: int):
+    _check(lib().maxsat_step(ctx.handle, int(steps)), ctx)
+
+
+def maxsat_score(ctx: Context):
+    _check(lib().maxsat_score(ctx.handle), ctx)
+
+
+def maxsat_eval(ctx: Context, assign_dev, cost_dev):
+    """assign_dev: torch uint8 CUDA tensor (B x n, contiguous); cost_dev: torch
+    int64 CUDA tensor (B)."""
+    B = int(assign_dev.shape[0])
+    assert assign_dev.is_cuda and cost_dev.is_cuda and assign_dev.is_contiguous()
+    assert tuple(assign_dev.shape) == (B, ctx.n) and cost_dev.numel() >= B
+    _check(lib().maxsat_eval(ctx.handle, assign_dev.data_ptr(), B, cost_dev.data_ptr()), ctx)
+
+
+def maxsat_solve(ctx: Context, restarts: int, steps: int, seed: int):
+    """Returns (best cost, best assignment as n uint8)."""
+    best = np.zeros(ctx.n, np.uint8)
+    cost = ctypes.c_int64()
+    _check(lib().maxsat_solve(ctx.handle, int(restarts), int(steps), int(seed) & (2 ** 64 - 1),
+                              _np_ptr(best), ctypes.byref(cost)), ctx)
+    ctx.B = int(restarts)
+    return int(cost.value), best
+
+
+def maxsat_get_state(ctx: Context):
+    B, n = ctx.B, ctx.n
+    out = dict(x=np.zeros((B, n), np.uint8), nu=np.zeros((B, n), np.float32),
+               best_cost=np.zeros(B, np.int64), best_x=np.zeros((B, n), np.uint8),
+               cost=np.zeros(B, np.int64), free_energy=np.zeros(B, np.float32))
+    t = ctypes.c_uint32()
+    _check(lib().maxsat_get_state(ctx.handle, _np_ptr(out["x"]), _np_ptr(out["nu"]),
+                                  _np_ptr(out["best_cost"]), _np_ptr(out["best_x"]),
+                                  _np_ptr(out["cost"]), _np_ptr(out["free_energy"]),
+                                  ctypes.byref(t)), ctx)
+    out["t"] = int(t.value)
+    return out
+
+
+def maxsat_set_state(ctx: Context, restarts, seed, x, nu, best_cost, best_x, t):
+    x = np.ascontiguousarray(x, np.uint8)
+    nu = np.ascontiguousarray(nu, np.float32)
+    best_cost = np.ascontiguousarray(best_cost, np.int64)
+    best_x = np.ascontiguousarray(best_x, np.uint8)
+    _check(lib().maxsat_set_state(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1),
+                                  _np_ptr(x), _np_ptr(nu), _np_ptr(best_cost), _np_ptr(best_x),
+                                  int(t)), ctx)
+    ctx.B = int(restarts)
+
+
+def maxsat_set_profiling(ctx: Context, on: bool):
+    _check(lib().maxsat_set_profiling(ctx.handle, 1 if on else 0), ctx)
+
+
+def maxsat_kernel_times(ctx: Context, max_kernels: int = 32):
+    """{kernel name: (launches, total device ms)} since profiling was enabled."""
+    names = ctypes.create_string_buffer(32 * max_kernels)
+    cnt = np.zeros(max_kernels, np.int64)
+    ms = np.zeros(max_kernels, np.float64)
+    k = lib().maxsat_kernel_times(ctx.handle, max_kernels, names, _np_ptr(cnt), _np_ptr(ms))
+    if k < 0:
+        _check(k, ctx)
+    raw = names.raw
+    return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (int(cnt[i]), float(ms[i]))
+            for i in range(k)}
+
+
+def maxsat_get_path(ctx: Context) -> int:
+    return int(lib().maxsat_get_path(ctx.handle))
+
+
+def maxsat_destroy(ctx: Context):
+    if ctx is not None and ctx.handle:
+        lib().maxsat_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def maxsat_last_error(ctx: Context | None = None) -> str:
+    h = None if ctx is None else ctx.handle
+    return lib().maxsat_last_error(h).decode()
+
+
+def maxsat_fit_or_rbm(length, n_hidden, fstar, quant_bits=4, iters=20000):
+    W = np.zeros((length, n_hidden), np.float64)
+    b = np.zeros(n_hidden, np.float64)
+    _check(lib().maxsat_fit_or_rbm(int(length), int(n_hidden), float(fstar), int(quant_bits),
+                                   int(iters), _np_ptr(W), _np_ptr(b)))
+    return W, b

@@ -1,0 +1,686 @@
+// Host core of libmaxsat.so: the C ABI of include/maxsat.h.
+//
+// maxsat_create ingests the signed-literal formula (the index table T of
+// Sec. 4.3), assigns every clause to a group (length, weight bucket), fits or
+// accepts the OR-gate clause RBMs (Sec. 4.1), builds the probability and
+// free-energy tables and copies everything to the device. The Gibbs rounds
+// (Sec. 4.2-4.4) then run entirely in the kernels of sparse.cu / dense.cu,
+// launched on the caller's stream, optionally replayed from a CUDA graph of
+// `steps_per_graph` rounds (the paper dispatches 500 rounds at a time,
+// appendix "Batching operations").
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+using namespace rbmsat;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevAllocs {
+  std::vector<void*> ptrs;
+  ~DevAllocs() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <class T>
+  cudaError_t alloc(T** out, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return cudaSuccess;
+  }
+};
+
+}  // namespace
+
+struct maxsat_ctx {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  int path = MAXSAT_PATH_SPARSE;
+  int32_t n = 0, m = 0, nnz = 0;
+  maxsat_params prm{};
+  std::vector<double> fstar;
+  HostTables tabs;
+  int max_degree = 0;
+
+  DevAllocs formula_mem;  // formula + tables (lifetime of the context)
+  DevAllocs chain_mem;    // chain state (re-made when B changes)
+  DevAllocs eval_mem;     // eval scratch (grown on demand)
+  DevFormula F{};
+  DevTables T{};
+  DevChains C{};
+  bool have_chains = false;
+  uint32_t t = 0;
+  uint64_t seed = 0;
+  uint32_t* d_t = nullptr;  // round index read by graph-replayed kernels
+  bool d_t_synced = false;
+
+  uint8_t* ev_xt = nullptr;
+  int64_t* ev_part = nullptr;
+  int ev_Bp = 0;
+
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+
+  // per-kernel CUDA-event timing of plain launches
+  bool profiling = false;
+  struct Mark {
+    int kernel;  // index into prof_names
+    cudaEvent_t start, stop;
+  };
+  std::vector<Mark> marks;
+  std::vector<std::string> prof_names;
+  std::vector<double> prof_ms;
+  std::vector<int64_t> prof_count;
+
+  std::string err;
+};
+
+namespace {
+
+int fail(maxsat_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(maxsat_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? MAXSAT_ENOMEM : MAXSAT_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int check_device(maxsat_ctx* ctx) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ctx, MAXSAT_ENODEV, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  cudaDeviceProp prop{};
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail(ctx, MAXSAT_ENODEV, cudaGetErrorString(e));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(ctx, MAXSAT_ENODEV,
+                "libmaxsat is built for sm_103 (GB300); device is sm_" +
+                    std::to_string(prop.major) + std::to_string(prop.minor));
+  return MAXSAT_OK;
+}
+
+void destroy_graph(maxsat_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  ctx->graph_steps = 0;
+}
+
+int32_t weight_bucket(int64_t w, int64_t wmin, int32_t J) {
+  int32_t j = 0;
+  while (j + 1 < J && wmin <= (INT64_MAX >> (j + 1)) && (wmin << (j + 1)) <= w) ++j;
+  return j;
+}
+
+// Launches `body` on `st`, bracketed by CUDA events when profiling.
+template <class Fn>
+int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
+  if (!ctx->profiling) {
+    CK(ctx, body());
+    return MAXSAT_OK;
+  }
+  int k = 0;
+  while (k < (int)ctx->prof_names.size() && ctx->prof_names[k] != name) ++k;
+  if (k == (int)ctx->prof_names.size()) {
+    ctx->prof_names.push_back(name);
+    ctx->prof_ms.push_back(0.0);
+    ctx->prof_count.push_back(0);
+  }
+  maxsat_ctx::Mark mk{k, nullptr, nullptr};
+  CK(ctx, cudaEventCreate(&mk.start));
+  CK(ctx, cudaEventCreate(&mk.stop));
+  ctx->marks.push_back(mk);
+  CK(ctx, cudaEventRecord(mk.start, st));
+  CK(ctx, body());
+  CK(ctx, cudaEventRecord(mk.stop, st));
+  return MAXSAT_OK;
+}
+
+#define TIMED(ctx, st, name, expr)                                   \
+  do {                                                               \
+    int rc_ = timed(ctx, st, name, [&]() { return (expr); });        \
+    if (rc_ != MAXSAT_OK) return rc_;                                \
+  } while (0)
+
+// One Gibbs round: absolute index t = (tdev ? *tdev : 0) + t_rel.
+int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_t t_rel) {
+  TIMED(ctx, st, "gather_hidden",
+        launch_gather(ctx->F, ctx->T, ctx->C, ctx->C.xt, ctx->C.Bp, true, true, tdev, t_rel,
+                      ctx->C.cost_part, ctx->C.fe_part, st));
+  TIMED(ctx, st, "best_keep", launch_best_keep(ctx->F, ctx->C, st));
+  TIMED(ctx, st, "visible", launch_visible(ctx->F, ctx->T, ctx->C, (float)ctx->prm.alpha, tdev, t_rel, st));
+  return MAXSAT_OK;
+}
+
+int capture_graph(maxsat_ctx* ctx, int S) {
+  destroy_graph(ctx);
+  if (!ctx->cap_stream) CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  CK(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = MAXSAT_OK;
+  for (int s = 0; s < S && rc == MAXSAT_OK; ++s) rc = launch_round(ctx, ctx->cap_stream, ctx->d_t, (uint32_t)s);
+  if (rc == MAXSAT_OK) {
+    cudaError_t e = launch_advance(ctx->d_t, (uint32_t)S, ctx->cap_stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_advance");
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (rc != MAXSAT_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  ctx->graph_steps = S;
+  return MAXSAT_OK;
+}
+
+int alloc_chains(maxsat_ctx* ctx, int32_t B) {
+  if (ctx->have_chains && ctx->C.B == B) return MAXSAT_OK;
+  destroy_graph(ctx);
+  ctx->chain_mem.release();
+  ctx->have_chains = false;
+  const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
+  const size_t nB = (size_t)ctx->n * Bp;
+  const int nblk = clause_blocks_for(ctx->m);
+  DevChains& C = ctx->C;
+  C = DevChains{};
+  C.B = B;
+  C.Bp = Bp;
+  DevAllocs& A = ctx->chain_mem;
+  CK(ctx, A.alloc(&C.xt, nB));
+  CK(ctx, A.alloc(&C.nu, nB));
+  CK(ctx, A.alloc(&C.best, Bp));
+  CK(ctx, A.alloc(&C.best_xt, nB));
+  CK(ctx, A.alloc(&C.cost, Bp));
+  CK(ctx, A.alloc(&C.fe, Bp));
+  CK(ctx, A.alloc(&C.improved, Bp));
+  CK(ctx, A.alloc(&C.cost_part, (size_t)nblk * Bp));
+  CK(ctx, A.alloc(&C.fe_part, (size_t)nblk * Bp));
+  CK(ctx, A.alloc(&C.G, (size_t)ctx->nnz * Bp));
+  return MAXSAT_OK;
+}
+
+template <class T>
+int upload(maxsat_ctx* ctx, DevAllocs& A, const std::vector<T>& h, const T** out) {
+  T* d = nullptr;
+  CK(ctx, A.alloc(&d, h.size()));
+  if (!h.empty()) CK(ctx, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = d;
+  return MAXSAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void maxsat_default_params(maxsat_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_temps = 2;
+  p->fstar = nullptr;
+  p->n_buckets = 4;
+  p->bucket_gamma = 0.5;
+  p->alpha = 0.01;
+  p->quant_bits = 4;
+  p->path = MAXSAT_PATH_AUTO;
+  p->fit_iters = 50000;
+  p->n_sets = 0;
+  p->sets = nullptr;
+  p->steps_per_graph = 500;
+}
+
+const char* maxsat_last_error(const maxsat_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int maxsat_get_path(const maxsat_ctx* ctx) { return ctx ? ctx->path : MAXSAT_EINVAL; }
+
+int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
+                  const int32_t* lits, const int64_t* weights, const maxsat_params* params,
+                  void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1) return fail(nullptr, MAXSAT_EINVAL, "n_vars must be >= 1");
+  if (m < 0 || m > (int64_t)INT32_MAX / 2) return fail(nullptr, MAXSAT_EINVAL, "n_clauses out of range");
+  if (!off) return fail(nullptr, MAXSAT_EINVAL, "clause_off is NULL");
+  if (off[0] != 0) return fail(nullptr, MAXSAT_EINVAL, "clause_off[0] must be 0");
+  for (int64_t c = 0; c < m; ++c) {
+    const int64_t len = off[c + 1] - off[c];
+    if (len < 0) return fail(nullptr, MAXSAT_EINVAL, "clause_off must be non-decreasing");
+    if (len > MAXSAT_MAX_LEN)
+      return fail(nullptr, MAXSAT_EINVAL, "clause " + std::to_string(c) + " is longer than MAXSAT_MAX_LEN");
+  }
+  const int64_t nnz = off[m];
+  if (nnz > (int64_t)INT32_MAX / 2) return fail(nullptr, MAXSAT_EINVAL, "too many literals");
+  if (nnz > 0 && !lits) return fail(nullptr, MAXSAT_EINVAL, "lits is NULL");
+  for (int64_t j = 0; j < nnz; ++j)
+    if (lits[j] == 0 || lits[j] > n || lits[j] < -n)
+      return fail(nullptr, MAXSAT_EINVAL, "literal " + std::to_string(j) + " out of range");
+  int64_t wsum = 0, wmin = INT64_MAX;
+  for (int64_t c = 0; c < m; ++c) {
+    const int64_t w = weights ? weights[c] : 1;
+    if (w < 1) return fail(nullptr, MAXSAT_EINVAL, "weights must be >= 1");
+    if (w > ((int64_t)1 << 62) - wsum) return fail(nullptr, MAXSAT_EINVAL, "total weight exceeds 2^62");
+    wsum += w;
+    wmin = std::min(wmin, w);
+  }
+  maxsat_params prm;
+  if (params) prm = *params;
+  else maxsat_default_params(&prm);
+  if (prm.n_temps < 1 || prm.n_temps > 64) return fail(nullptr, MAXSAT_EINVAL, "n_temps must be in 1..64");
+  if (prm.n_buckets < 1 || prm.n_buckets > 16) return fail(nullptr, MAXSAT_EINVAL, "n_buckets must be in 1..16");
+  if (!(prm.alpha >= 0.0 && prm.alpha <= 1.0)) return fail(nullptr, MAXSAT_EINVAL, "alpha must be in [0, 1]");
+  if (prm.quant_bits < 0 || prm.quant_bits > 8) return fail(nullptr, MAXSAT_EINVAL, "quant_bits must be in 0..8");
+  if (prm.path < 0 || prm.path > 2) return fail(nullptr, MAXSAT_EINVAL, "unknown path");
+  if (prm.steps_per_graph < 0 || prm.steps_per_graph > 100000)
+    return fail(nullptr, MAXSAT_EINVAL, "steps_per_graph out of range");
+  if (prm.n_sets < 0 || (prm.n_sets > 0 && !prm.sets)) return fail(nullptr, MAXSAT_EINVAL, "sets is NULL");
+  if (prm.path == MAXSAT_PATH_DENSE)
+    return fail(nullptr, MAXSAT_EINVAL, "the dense path is not available in this build");
+
+  int rc = check_device(nullptr);
+  if (rc != MAXSAT_OK) return rc;
+
+  maxsat_ctx* ctx = new maxsat_ctx();
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->n = n;
+  ctx->m = (int32_t)m;
+  ctx->nnz = (int32_t)nnz;
+  ctx->prm = prm;
+  static const double kDefaultFstar[2] = {0.068, 0.528};
+  for (int e = 0; e < prm.n_temps; ++e) {
+    double f = prm.fstar ? prm.fstar[e] : (prm.n_temps == 2 ? kDefaultFstar[e] : 0.068 + (0.528 - 0.068) * e / std::max(1, prm.n_temps - 1));
+    ctx->fstar.push_back(f);
+  }
+  ctx->prm.fstar = nullptr;
+  ctx->prm.sets = nullptr;
+  ctx->path = MAXSAT_PATH_SPARSE;
+
+  // groups (length, bucket) in order of first appearance
+  std::vector<int32_t> cl_grp(m, -1), grp_len, grp_bucket;
+  std::map<std::pair<int, int>, int> gidx;
+  for (int64_t c = 0; c < m; ++c) {
+    const int len = (int)(off[c + 1] - off[c]);
+    if (len == 0) continue;
+    const int j = weight_bucket(weights ? weights[c] : 1, wmin, prm.n_buckets);
+    auto key = std::make_pair(len, j);
+    auto it = gidx.find(key);
+    if (it == gidx.end()) {
+      it = gidx.emplace(key, (int)grp_len.size()).first;
+      grp_len.push_back(len);
+      grp_bucket.push_back(j);
+    }
+    cl_grp[c] = it->second;
+  }
+
+  // clause RBM parameter sets: given, or fitted (Sec. 4.1)
+  std::vector<RbmSet> sets;
+  if (params && params->n_sets > 0) {
+    for (int s = 0; s < params->n_sets; ++s) {
+      const maxsat_rbm_set& u = params->sets[s];
+      if (u.len < 1 || u.len > MAXSAT_MAX_LEN || u.n_hidden < 1 || u.n_hidden > MAXSAT_MAX_HIDDEN ||
+          !u.W || !u.b) {
+        delete ctx;
+        return fail(nullptr, MAXSAT_EINVAL, "malformed RBM set " + std::to_string(s));
+      }
+      RbmSet r;
+      r.len = u.len;
+      r.bucket = u.bucket;
+      r.temp = u.temp;
+      r.nh = u.n_hidden;
+      r.W.assign(u.W, u.W + (size_t)u.len * u.n_hidden);
+      r.b.assign(u.b, u.b + u.n_hidden);
+      sets.push_back(std::move(r));
+    }
+  } else {
+    for (size_t g = 0; g < grp_len.size(); ++g)
+      for (int e = 0; e < prm.n_temps; ++e) {
+        RbmSet r;
+        r.len = grp_len[g];
+        r.bucket = grp_bucket[g];
+        r.temp = e;
+        r.nh = hidden_units_for(r.len);
+        r.W.resize((size_t)r.len * r.nh);
+        r.b.resize(r.nh);
+        sets.push_back(std::move(r));
+      }
+    // fitting cost grows as 2^len; beyond the paper's K <= 7 the iterations
+    // are scaled down by 2^(len - 7) (at least 2000)
+    std::vector<std::thread> pool;
+    std::vector<int> status(sets.size(), MAXSAT_OK);
+    const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::atomic<size_t> next{0};
+    for (unsigned w = 0; w < hw; ++w)
+      pool.emplace_back([&]() {
+        for (size_t i; (i = next.fetch_add(1)) < sets.size();) {
+          RbmSet& r = sets[i];
+          int iters = prm.fit_iters;
+          if (r.len > 7) iters = std::max(std::min(2000, iters), iters >> (r.len - 7));
+          const double target = ctx->fstar[r.temp] * (1.0 + r.bucket * prm.bucket_gamma);
+          status[i] = fit_or_rbm(r.len, r.nh, target, prm.quant_bits, iters, r.W.data(), r.b.data());
+        }
+      });
+    for (auto& th : pool) th.join();
+    for (int s : status)
+      if (s != MAXSAT_OK) {
+        delete ctx;
+        return fail(nullptr, s, "OR-gate RBM fit failed");
+      }
+  }
+  std::string terr = build_tables(sets, prm.n_temps, prm.quant_bits, grp_len, grp_bucket, &ctx->tabs);
+  if (!terr.empty()) {
+    delete ctx;
+    return fail(nullptr, MAXSAT_EINVAL, terr);
+  }
+
+  // host CSR in device form
+  std::vector<int32_t> cl_off(m + 1), lit_var(nnz), var_off(n + 1, 0), var_lit(nnz);
+  std::vector<int64_t> cl_w(m);
+  for (int64_t c = 0; c <= m; ++c) cl_off[c] = (int32_t)off[c];
+  for (int64_t c = 0; c < m; ++c) cl_w[c] = weights ? weights[c] : 1;
+  for (int64_t j = 0; j < nnz; ++j) {
+    const int32_t l = lits[j];
+    const int32_t v = (l > 0 ? l : -l) - 1;
+    lit_var[j] = v | (l < 0 ? (int32_t)0x80000000 : 0);
+    var_off[v + 1]++;
+  }
+  for (int i = 0; i < n; ++i) var_off[i + 1] += var_off[i];
+  {
+    std::vector<int32_t> fill(var_off.begin(), var_off.end() - 1);
+    for (int64_t j = 0; j < nnz; ++j) {
+      const int32_t l = lits[j];
+      const int32_t v = (l > 0 ? l : -l) - 1;
+      var_lit[fill[v]++] = (int32_t)j | (l < 0 ? (int32_t)0x80000000 : 0);
+    }
+  }
+  for (int i = 0; i < n; ++i) ctx->max_degree = std::max(ctx->max_degree, var_off[i + 1] - var_off[i]);
+  // exactness of the integer scatter-sum: |2^Q z| <= degree * max |2^Q G|
+  if ((int64_t)ctx->max_degree * ctx->tabs.gq_absmax >= ((int64_t)1 << 31)) {
+    delete ctx;
+    return fail(nullptr, MAXSAT_EINVAL, "visible logits could overflow int32");
+  }
+
+  DevAllocs& A = ctx->formula_mem;
+  DevFormula& F = ctx->F;
+  F.n = n;
+  F.m = (int32_t)m;
+  F.nnz = (int32_t)nnz;
+  DevTables& T = ctx->T;
+  T.n_temps = prm.n_temps;
+  T.qmax = ctx->tabs.qmax;
+#define UP(vec, dst)                                          \
+  do {                                                        \
+    int rc_ = upload(ctx, A, vec, &(dst));                    \
+    if (rc_ != MAXSAT_OK) {                                   \
+      std::string e_ = ctx->err;                              \
+      delete ctx;                                             \
+      return fail(nullptr, rc_, e_);                          \
+    }                                                         \
+  } while (0)
+  UP(cl_off, F.cl_off);
+  UP(lit_var, F.lit_var);
+  UP(cl_grp, F.cl_grp);
+  UP(cl_w, F.cl_w);
+  UP(var_off, F.var_off);
+  UP(var_lit, F.var_lit);
+  UP(ctx->tabs.grp_nh, T.grp_nh);
+  UP(ctx->tabs.phid_off, T.phid_off);
+  UP(ctx->tabs.fe_off, T.fe_off);
+  UP(ctx->tabs.gq_off, T.gq_off);
+  UP(ctx->tabs.phid, T.phid);
+  UP(ctx->tabs.fe, T.fe);
+  UP(ctx->tabs.gq, T.gq);
+  UP(ctx->tabs.pv, T.pv);
+#undef UP
+  {
+    cudaError_t e = A.alloc(&ctx->d_t, 1);
+    if (e != cudaSuccess) {
+      delete ctx;
+      return cuda_fail(nullptr, e, "cudaMalloc");
+    }
+  }
+  *out = ctx;
+  return MAXSAT_OK;
+}
+
+int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (B < 1 || B > (1 << 26)) return fail(ctx, MAXSAT_EINVAL, "restarts must be in 1..2^26");
+  int rc = alloc_chains(ctx, B);
+  if (rc != MAXSAT_OK) return rc;
+  if (ctx->C.key0 != (uint32_t)seed || ctx->C.key1 != (uint32_t)(seed >> 32)) destroy_graph(ctx);
+  ctx->C.key0 = (uint32_t)seed;
+  ctx->C.key1 = (uint32_t)(seed >> 32);
+  ctx->seed = seed;
+  ctx->t = 0;
+  ctx->d_t_synced = false;
+  CK(ctx, launch_init_sparse(ctx->C, ctx->n, ctx->stream));
+  ctx->have_chains = true;
+  return MAXSAT_OK;
+}
+
+int maxsat_step(maxsat_ctx* ctx, int64_t steps) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_step before maxsat_reset");
+  if (steps < 0) return fail(ctx, MAXSAT_EINVAL, "steps must be >= 0");
+  if ((uint64_t)ctx->t + (uint64_t)steps > 0xFFFFFFFFull) return fail(ctx, MAXSAT_EINVAL, "round index would exceed 2^32");
+  const int S = ctx->profiling ? 0 : ctx->prm.steps_per_graph;
+  while (steps > 0) {
+    if (S > 0 && steps >= S) {
+      if (!ctx->graph || ctx->graph_steps != S) {
+        int rc = capture_graph(ctx, S);
+        if (rc != MAXSAT_OK) return rc;
+      }
+      if (!ctx->d_t_synced) {
+        CK(ctx, launch_set_u32(ctx->d_t, ctx->t, ctx->stream));
+        ctx->d_t_synced = true;
+      }
+      CK(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+      ctx->t += (uint32_t)S;
+      steps -= S;
+    } else {
+      int rc = launch_round(ctx, ctx->stream, nullptr, ctx->t);
+      if (rc != MAXSAT_OK) return rc;
+      ctx->t += 1;
+      ctx->d_t_synced = false;
+      steps -= 1;
+    }
+  }
+  return MAXSAT_OK;
+}
+
+int maxsat_score(maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_score before maxsat_reset");
+  TIMED(ctx, ctx->stream, "gather_score",
+        launch_gather(ctx->F, ctx->T, ctx->C, ctx->C.xt, ctx->C.Bp, false, true, nullptr, 0,
+                      ctx->C.cost_part, ctx->C.fe_part, ctx->stream));
+  TIMED(ctx, ctx->stream, "best_keep", launch_best_keep(ctx->F, ctx->C, ctx->stream));
+  TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(ctx->C, ctx->n, ctx->stream));
+  return MAXSAT_OK;
+}
+
+static void drain_marks(maxsat_ctx* ctx) {
+  for (auto& mk : ctx->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, mk.start, mk.stop) == cudaSuccess) {
+      ctx->prof_ms[mk.kernel] += ms;
+      ctx->prof_count[mk.kernel] += 1;
+    }
+    cudaEventDestroy(mk.start);
+    cudaEventDestroy(mk.stop);
+  }
+  ctx->marks.clear();
+}
+
+int maxsat_set_profiling(maxsat_ctx* ctx, int32_t on) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->marks.empty()) {
+    cudaStreamSynchronize(ctx->stream);
+    drain_marks(ctx);
+  }
+  ctx->profiling = on != 0;
+  ctx->prof_names.clear();
+  ctx->prof_ms.clear();
+  ctx->prof_count.clear();
+  return MAXSAT_OK;
+}
+
+int maxsat_kernel_times(maxsat_ctx* ctx, int32_t max_kernels, char* names, int64_t* launches,
+                        double* total_ms) {
+  if (!ctx || max_kernels < 0) return MAXSAT_EINVAL;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  drain_marks(ctx);
+  const int k = std::min<int>(max_kernels, (int)ctx->prof_names.size());
+  for (int i = 0; i < k; ++i) {
+    if (names) {
+      std::memset(names + 32 * i, 0, 32);
+      std::strncpy(names + 32 * i, ctx->prof_names[i].c_str(), 31);
+    }
+    if (launches) launches[i] = ctx->prof_count[i];
+    if (total_ms) total_ms[i] = ctx->prof_ms[i];
+  }
+  return k;
+}
+
+int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* cost_dev) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
+  if (B == 0) return MAXSAT_OK;
+  const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
+  const int nblk = clause_blocks_for(ctx->m);
+  if (Bp > ctx->ev_Bp) {
+    ctx->eval_mem.release();
+    ctx->ev_Bp = 0;
+    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_xt, (size_t)ctx->n * Bp));
+    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_part, (size_t)nblk * Bp));
+    ctx->ev_Bp = Bp;
+  }
+  CK(ctx, launch_transpose_in(assign_dev, B, ctx->n, ctx->ev_xt, Bp, ctx->stream));
+  DevChains dummy{};
+  dummy.B = B;
+  dummy.Bp = Bp;
+  CK(ctx, launch_gather(ctx->F, ctx->T, dummy, ctx->ev_xt, Bp, false, false, nullptr, 0,
+                        ctx->ev_part, nullptr, ctx->stream));
+  CK(ctx, launch_reduce_cost(ctx->ev_part, nblk, Bp, B, cost_dev, ctx->stream));
+  return MAXSAT_OK;
+}
+
+int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
+                 uint8_t* best_assign, int64_t* best_cost) {
+  if (!ctx) return MAXSAT_EINVAL;
+  int rc = maxsat_reset(ctx, B, seed);
+  if (rc == MAXSAT_OK) rc = maxsat_step(ctx, steps);
+  if (rc == MAXSAT_OK) rc = maxsat_score(ctx);
+  if (rc != MAXSAT_OK) return rc;
+  std::vector<int64_t> best(B);
+  CK(ctx, cudaMemcpyAsync(best.data(), ctx->C.best, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  int bstar = 0;
+  for (int b = 1; b < B; ++b)
+    if (best[b] < best[bstar]) bstar = b;
+  if (best_cost) *best_cost = best[bstar];
+  if (best_assign) {
+    CK(ctx, cudaMemcpy2DAsync(best_assign, 1, ctx->C.best_xt + bstar, ctx->C.Bp, 1, ctx->n,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return MAXSAT_OK;
+}
+
+int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
+                     uint8_t* best_x, int64_t* cost, float* free_energy, uint32_t* t) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "no chains (call maxsat_reset)");
+  const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
+  const size_t nB = (size_t)n * Bp;
+  auto fetch_T = [&](const void* dsrc, size_t elem, void* dst) -> int {
+    std::vector<uint8_t> h(nB * elem);
+    CK(ctx, cudaMemcpyAsync(h.data(), dsrc, nB * elem, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    uint8_t* d = static_cast<uint8_t*>(dst);
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < n; ++i)
+        std::memcpy(d + ((size_t)b * n + i) * elem, h.data() + ((size_t)i * Bp + b) * elem, elem);
+    return MAXSAT_OK;
+  };
+  int rc;
+  if (x && (rc = fetch_T(ctx->C.xt, 1, x)) != MAXSAT_OK) return rc;
+  if (nu && (rc = fetch_T(ctx->C.nu, 4, nu)) != MAXSAT_OK) return rc;
+  if (best_x && (rc = fetch_T(ctx->C.best_xt, 1, best_x)) != MAXSAT_OK) return rc;
+  if (best_cost) CK(ctx, cudaMemcpyAsync(best_cost, ctx->C.best, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+  if (cost) CK(ctx, cudaMemcpyAsync(cost, ctx->C.cost, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+  if (free_energy) CK(ctx, cudaMemcpyAsync(free_energy, ctx->C.fe, 4 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (t) *t = ctx->t;
+  return MAXSAT_OK;
+}
+
+int maxsat_set_state(maxsat_ctx* ctx, int32_t B, uint64_t seed, const uint8_t* x,
+                     const float* nu, const int64_t* best_cost, const uint8_t* best_x,
+                     uint32_t t) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!x || !nu || !best_cost || !best_x) return fail(ctx, MAXSAT_EINVAL, "set_state needs x, nu, best_cost, best_x");
+  int rc = maxsat_reset(ctx, B, seed);  // allocates and fills the padding chains
+  if (rc != MAXSAT_OK) return rc;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  const int Bp = ctx->C.Bp, n = ctx->n;
+  const size_t nB = (size_t)n * Bp;
+  auto put_T = [&](void* ddst, size_t elem, const void* src) -> int {
+    std::vector<uint8_t> h(nB * elem);
+    CK(ctx, cudaMemcpy(h.data(), ddst, nB * elem, cudaMemcpyDeviceToHost));
+    const uint8_t* s = static_cast<const uint8_t*>(src);
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < n; ++i)
+        std::memcpy(h.data() + ((size_t)i * Bp + b) * elem, s + ((size_t)b * n + i) * elem, elem);
+    if (elem == 1)
+      for (int b = 0; b < B; ++b)
+        for (int i = 0; i < n; ++i) h[(size_t)i * Bp + b] = h[(size_t)i * Bp + b] != 0;
+    CK(ctx, cudaMemcpy(ddst, h.data(), nB * elem, cudaMemcpyHostToDevice));
+    return MAXSAT_OK;
+  };
+  if ((rc = put_T(ctx->C.xt, 1, x)) != MAXSAT_OK) return rc;
+  if ((rc = put_T(ctx->C.nu, 4, nu)) != MAXSAT_OK) return rc;
+  if ((rc = put_T(ctx->C.best_xt, 1, best_x)) != MAXSAT_OK) return rc;
+  CK(ctx, cudaMemcpy(ctx->C.best, best_cost, 8 * (size_t)B, cudaMemcpyHostToDevice));
+  ctx->t = t;
+  ctx->d_t_synced = false;
+  return MAXSAT_OK;
+}
+
+void maxsat_destroy(maxsat_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  drain_marks(ctx);
+  destroy_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Probability and free-energy tables of the clause RBMs.
+//
+// With the negation transform (Eq. 4), hidden unit h of a clause sees the
+// logit b'_h + sum_k W'_kh v_k = b_h + sum_k W_kh tau_k, where tau_k is the
+// truth of the clause's k-th literal. So one clause's hidden conditional
+// (Eq. 2 / Eq. 6) and free energy (Eq. 1) depend only on the pattern
+// p = sum_k tau_k 2^k of true literals, and its contribution to the visible
+// logits (Eq. 7) only on the pattern of sampled hidden units. For every set
+// s = (group g, temperature e) the tables hold
+//   phid[s][p][h] = rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))   (u32)
+//   fe[s][p]      = -sum_h softplus(b_h + sum_k W_kh tau_k(p))      (float)
+//   gq[s][hp][k]  = 2^Q sum_h W_kh [bit h of hp]                    (int16)
+// and the visible table pv[q] = rint(65536 sigma(q 2^-Q)) for |q| <= qmax.
+// A Bernoulli draw with a 16-bit uniform u is [u < P]. Beyond |z| >= 12 the
+// 16-bit probabilities are exactly 0 and 65536, so qmax = 12 * 2^Q clamps
+// without changing any draw.
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace rbmsat {
+
+namespace {
+double sigmoid(double a) { return 1.0 / (1.0 + std::exp(-a)); }
+double softplus(double a) { return a > 0 ? a + std::log1p(std::exp(-a)) : std::log1p(std::exp(a)); }
+uint32_t prob16(double a) { return (uint32_t)std::nearbyint(sigmoid(a) * 65536.0); }
+}  // namespace
+
+std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
+                         const std::vector<int32_t>& grp_len,
+                         const std::vector<int32_t>& grp_bucket, HostTables* T) {
+  const int G = (int)grp_len.size();
+  T->n_groups = G;
+  T->n_temps = E;
+  T->quant_bits = Q;
+  T->qmax = 12 << Q;
+  T->grp_len = grp_len;
+  T->grp_bucket = grp_bucket;
+  T->grp_nh.assign(G, 0);
+  T->phid_off.assign((size_t)G * E, 0);
+  T->fe_off.assign((size_t)G * E, 0);
+  T->gq_off.assign((size_t)G * E, 0);
+  T->phid.clear();
+  T->fe.clear();
+  T->gq.clear();
+  T->gq_absmax = 0;
+  const double scale = std::ldexp(1.0, Q);
+  for (int g = 0; g < G; ++g) {
+    for (int e = 0; e < E; ++e) {
+      const RbmSet* s = nullptr;
+      for (const auto& c : sets)
+        if (c.len == grp_len[g] && c.bucket == grp_bucket[g] && c.temp == e) s = &c;
+      if (!s)
+        return "no OR-gate RBM set for clause length " + std::to_string(grp_len[g]) +
+               ", bucket " + std::to_string(grp_bucket[g]) + ", temperature " +
+               std::to_string(e);
+      const int K = s->len, L = s->nh;
+      if (e == 0) T->grp_nh[g] = L;
+      if (T->grp_nh[g] != L)
+        return "sets of one length and bucket must share n_hidden across temperatures";
+      std::vector<int32_t> Wq((size_t)K * L);
+      for (int i = 0; i < K * L; ++i) {
+        const double v = s->W[i] * scale;
+        if (!std::isfinite(v) || v != std::nearbyint(v) || std::fabs(v) > 16384.0)
+          return "W entries must be multiples of 2^-quant_bits below 16384 * 2^-quant_bits";
+        Wq[i] = (int32_t)v;
+      }
+      for (int h = 0; h < L; ++h) {
+        const double v = std::ldexp(s->b[h], 24);
+        if (!std::isfinite(v) || v != std::nearbyint(v) || std::fabs(s->b[h]) > 1048576.0)
+          return "b entries must be multiples of 2^-24 below 2^20 in magnitude";
+      }
+      const size_t sidx = (size_t)g * E + e;
+      T->phid_off[sidx] = (int32_t)T->phid.size();
+      T->fe_off[sidx] = (int32_t)T->fe.size();
+      T->gq_off[sidx] = (int32_t)T->gq.size();
+      for (int p = 0; p < (1 << K); ++p) {
+        double F = 0.0;
+        for (int h = 0; h < L; ++h) {
+          int64_t acc = 0;
+          for (int k = 0; k < K; ++k)
+            if ((p >> k) & 1) acc += Wq[k * L + h];
+          const double a = s->b[h] + (double)acc / scale;
+          T->phid.push_back(prob16(a));
+          F -= softplus(a);
+        }
+        T->fe.push_back((float)F);
+      }
+      for (int hp = 0; hp < (1 << L); ++hp) {
+        for (int k = 0; k < K; ++k) {
+          int32_t acc = 0;
+          for (int h = 0; h < L; ++h)
+            if ((hp >> h) & 1) acc += Wq[k * L + h];
+          if (acc > 32767 || acc < -32767) return "2^Q G exceeds the int16 range";
+          T->gq.push_back((int16_t)acc);
+          if (std::abs(acc) > T->gq_absmax) T->gq_absmax = std::abs(acc);
+        }
+      }
+      if (T->phid.size() > (size_t)INT32_MAX / 2) return "tables too large";
+    }
+  }
+  T->pv.resize(2 * (size_t)T->qmax + 1);
+  for (int q = -T->qmax; q <= T->qmax; ++q) T->pv[q + T->qmax] = prob16((double)q / scale);
+  return "";
+}
+
+}  // namespace rbmsat

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs, the same clause-RBM parameters and the same seed.
+
+Bar: costs, best costs, chain states and best assignments bit-exact; the free
+energy within 1e-3 relative of the FP64 oracle; nu within the FP32 bound
+derived from the update nu <- (1 - alpha) nu + alpha rho (1 - rho): each round
+adds at most ~4 float32 rounding errors on a value <= 0.25 and shrinks older
+errors by (1 - alpha), so |nu_gpu - nu_oracle| <= 4 * 2^-24 * 0.25 *
+min(T, 1 / alpha) (plus the float32 rounding of alpha itself)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "or_rbm_params.txt")
+
+
+def nu_tol(T, alpha):
+    return 4 * 2.0 ** -24 * 0.25 * min(T, 1.0 / alpha) + 0.25 * abs(np.float32(alpha) - alpha) * T + 1e-9
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2311_02101_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def stream(ms):
+    import torch
+    return torch.cuda.Stream()
+
+
+@pytest.fixture(scope="module")
+def small_table():
+    """Lengths 1..4, one weight bucket, two temperatures (fitted by the oracle)."""
+    return oracle.make_table([1, 2, 3, 4], [0.068, 0.528], n_buckets=1, iters=5000)
+
+
+@pytest.fixture(scope="module")
+def table3():
+    """Length-3 sets fitted to convergence (20000 Adam iterations)."""
+    return oracle.make_table([3], [0.068, 0.528], n_buckets=1, iters=20000)
+
+
+@pytest.fixture(scope="module")
+def golden_table():
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden parameter file missing")
+    return oracle.RbmTable.load(GOLDEN)
+
+
+def inst_of(gen):
+    return oracle.Instance(*gen)
+
+
+def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0):
+    params = ms.maxsat_default_params(sets=table.sets, n_temps=n_temps, n_buckets=n_buckets,
+                                      alpha=alpha, steps_per_graph=spg, path=path)
+    params.fstar = None
+    return ms.maxsat_create(inst.n, inst.off, inst.lits, inst.w, params, stream)
+
+
+def run_gpu(ms, stream, inst, table, B, T, seed, **kw):
+    ctx = make_ctx(ms, stream, inst, table, **kw)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, T)
+    st = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    return st
+
+
+def run_oracle(inst, table, B, T, seed, n_temps=2, n_buckets=1, alpha=0.01, chain_ids=None,
+               B_total=None):
+    st = oracle.init_chains(inst.n, B, seed, chain_ids=chain_ids, B_total=B_total)
+    oracle.gibbs(inst, table, st, T, seed, n_temps=n_temps, n_buckets=n_buckets, alpha=alpha,
+                 threads=os.cpu_count() or 4)
+    return st
+
+
+def assert_same(gpu, ora, T, alpha, rows=None):
+    g = {k: (v if rows is None or np.ndim(v) == 0 else v[rows]) for k, v in gpu.items()}
+    assert np.array_equal(g["x"], ora.x), "chain states"
+    assert np.array_equal(g["best_cost"], ora.best_cost), "best costs"
+    assert np.array_equal(g["best_x"], ora.best_x), "best assignments"
+    assert np.array_equal(g["cost"], ora.cost), "costs"
+    np.testing.assert_allclose(g["free_energy"], ora.free_energy, rtol=1e-3, atol=1e-6)
+    assert np.max(np.abs(g["nu"] - ora.nu)) <= nu_tol(T, alpha)
+
+
+def edge_instance(seed=0):
+    """Random clauses of lengths 1..4 plus duplicates, a tautology, an empty
+    clause, a variable in no clause, and weights spanning several buckets."""
+    rng = np.random.default_rng(seed)
+    n = 37
+    lengths = rng.integers(1, 5, size=150)
+    _, off, lits, _ = workloads.from_lengths(n - 1, lengths, rng)
+    cl = [list(lits[off[c]:off[c + 1]]) for c in range(len(lengths))]
+    cl += [[3, 3, -5], [7, -7], [], [-2, -2, -2, 9], [12]]
+    w = list(rng.integers(1, 40, size=len(cl)))
+    return oracle.Instance.from_clauses(n, cl, w)
+
+
+# --------------------------------------------------------------------------
+# Exact cost evaluation (maxsat_eval)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [1, 7, 300])
+def test_eval_matches_oracle(ms, stream, small_table, B):
+    import torch
+    inst = edge_instance()
+    ctx = make_ctx(ms, stream, inst, small_table)
+    rng = np.random.default_rng(B)
+    X = rng.integers(0, 2, size=(B, inst.n)).astype(np.uint8)
+    X[0] *= 5  # any nonzero byte is True
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(X).cuda()
+        cd = torch.zeros(B, dtype=torch.int64, device="cuda")
+    ms.maxsat_eval(ctx, xd, cd)
+    stream.synchronize()
+    expect = oracle.evaluate(inst, (X != 0).astype(np.uint8))
+    assert np.array_equal(cd.cpu().numpy(), expect)
+    ms.maxsat_destroy(ctx)
+
+
+def test_eval_mixed_lengths_weighted(ms, stream, golden_table):
+    import torch
+    inst = inst_of(workloads.mixed_length(n=3000, m=15000, seed=3))
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4)
+    B = 513
+    X = np.random.default_rng(1).integers(0, 2, size=(B, inst.n)).astype(np.uint8)
+    xd = torch.from_numpy(X).cuda()
+    cd = torch.zeros(B, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    ms.maxsat_eval(ctx, xd, cd)
+    stream.synchronize()
+    assert np.array_equal(cd.cpu().numpy(), oracle.evaluate(inst, X))
+    ms.maxsat_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Gibbs trajectories
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [256, 300])
+def test_trajectory_3sat(ms, stream, small_table, B):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    T, seed = 30, 11
+    gpu = run_gpu(ms, stream, inst, small_table, B, T, seed)
+    assert gpu["t"] == T
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
+
+
+def test_trajectory_edge_cases(ms, stream, small_table):
+    inst = edge_instance(1)
+    T, seed, B = 25, 3, 40
+    gpu = run_gpu(ms, stream, inst, small_table, B, T, seed, alpha=0.05)
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed, alpha=0.05), T, 0.05)
+
+
+def test_trajectory_mixed_weighted_buckets(ms, stream, golden_table):
+    inst = inst_of(workloads.mixed_length(n=400, m=2000, seed=9))
+    T, seed, B = 12, 5, 64
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4)
+    assert_same(gpu, run_oracle(inst, golden_table, B, T, seed, n_buckets=4), T, 0.01)
+
+
+def test_graph_replay_matches_plain_launches(ms, stream, small_table):
+    inst = inst_of(workloads.random_ksat(60, 250, 3, seed=4, wmax=50))
+    a = run_gpu(ms, stream, inst, small_table, 256, 23, 9, spg=0)
+    b = run_gpu(ms, stream, inst, small_table, 256, 23, 9, spg=5)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_resume_is_bit_identical(ms, stream, small_table):
+    inst = inst_of(workloads.random_ksat(60, 250, 3, seed=4, wmax=50))
+    whole = run_gpu(ms, stream, inst, small_table, 256, 20, 13, spg=4)
+    ctx = make_ctx(ms, stream, inst, small_table, spg=4)
+    ms.maxsat_reset(ctx, 256, 13)
+    ms.maxsat_step(ctx, 9)
+    mid = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    ctx = make_ctx(ms, stream, inst, small_table, spg=4)
+    ms.maxsat_set_state(ctx, 256, 13, mid["x"], mid["nu"], mid["best_cost"], mid["best_x"], mid["t"])
+    ms.maxsat_step(ctx, 11)
+    end = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    for k in ["x", "nu", "best_cost", "best_x", "cost", "free_energy"]:
+        assert np.array_equal(whole[k], end[k]), k
+
+
+def test_solve_matches_oracle(ms, stream, small_table):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    ctx = make_ctx(ms, stream, inst, small_table, spg=16)
+    cost, assign = ms.maxsat_solve(ctx, 256, 40, 21)
+    st = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    ob, ox, ost = oracle.solve(inst, small_table, 256, 40, 21, n_temps=2,
+                               threads=os.cpu_count() or 4)
+    assert cost == ob and np.array_equal(assign, ox)
+    assert np.array_equal(st["best_cost"], ost.best_cost)
+    assert np.array_equal(st["best_x"], ost.best_x)
+    assert oracle.evaluate(inst, assign[None])[0] == cost
+
+
+def test_brute_force_twin(ms, stream, table3):
+    inst = inst_of(workloads.random_ksat(18, 77, 3, seed=0))
+    ctx = make_ctx(ms, stream, inst, table3, spg=50)
+    cost, assign = ms.maxsat_solve(ctx, 256, 200, 0)
+    ms.maxsat_destroy(ctx)
+    assert cost == oracle.brute_force_optimum(inst)
+    assert oracle.evaluate(inst, assign[None])[0] == cost
+
+
+def test_step_before_reset_is_an_error(ms, stream, small_table):
+    inst = inst_of(workloads.random_ksat(10, 20, 3, seed=0))
+    ctx = make_ctx(ms, stream, inst, small_table)
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_step(ctx, 1)
+    assert e.value.code == ms.MAXSAT_ESTATE
+    ms.maxsat_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Full sizes, in the launch configuration the benchmark times: sampled chains
+# recomputed by the oracle one by one (chains are independent)
+# --------------------------------------------------------------------------
+def test_full_size_weighted_3sat_sampled(ms, stream, golden_table):
+    inst = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0))
+    B, T, seed = 4096, 6, 1
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=3)
+    rows = np.array([0, 1, 7, 8, 2047, 2048, 3000, 4095])
+    ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows,
+                     B_total=B)
+    assert_same(gpu, ora, T, 0.01, rows=rows)
+
+
+def test_full_size_mixed_sampled(ms, stream, golden_table):
+    inst = inst_of(workloads.mixed_length(seed=0))
+    B, T, seed = 1024, 3, 2
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=0)
+    rows = np.array([0, 255, 511, 512, 1023])
+    ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows,
+                     B_total=B)
+    assert_same(gpu, ora, T, 0.01, rows=rows)
