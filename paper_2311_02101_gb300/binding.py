@@ -78,12 +78,13 @@ def lib():
         L.maxsat_last_error.argtypes = [P]
         L.maxsat_last_error.restype = ctypes.c_char_p
         L.maxsat_fit_or_rbm.argtypes = [i32, i32, f64, i32, i32, P, P]
+        L.maxsat_eval_noalloc.argtypes = [i32, i64, i64, P, P, P, P, i32, P, P]
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
         for name in ["maxsat_create", "maxsat_reset", "maxsat_step", "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
                      "maxsat_get_path", "maxsat_fit_or_rbm", "maxsat_set_profiling",
-                     "maxsat_kernel_times"]:
+                     "maxsat_kernel_times", "maxsat_eval_noalloc"]:
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -187,6 +188,20 @@ def maxsat_eval(ctx: Context, assign_dev, cost_dev):
     assert assign_dev.is_cuda and cost_dev.is_cuda and assign_dev.is_contiguous()
     assert tuple(assign_dev.shape) == (B, ctx.n) and cost_dev.numel() >= B
     _check(lib().maxsat_eval(ctx.handle, assign_dev.data_ptr(), B, cost_dev.data_ptr()), ctx)
+
+
+def maxsat_eval_noalloc(n, off_dev, lits_dev, weights_dev, assign_dev, cost_dev, stream=None):
+    """Allocation-free evaluation (no context): all arguments are torch CUDA
+    tensors (int64 offsets, int32 DIMACS literals, int64 weights or None,
+    uint8 B x n assignments, int64 B costs)."""
+    B = int(assign_dev.shape[0])
+    assert assign_dev.is_contiguous() and tuple(assign_dev.shape) == (B, n)
+    m = int(off_dev.numel()) - 1
+    _check(lib().maxsat_eval_noalloc(int(n), m, int(lits_dev.numel()), off_dev.data_ptr(),
+                                     lits_dev.data_ptr(),
+                                     None if weights_dev is None else weights_dev.data_ptr(),
+                                     assign_dev.data_ptr(), B, cost_dev.data_ptr(),
+                                     _stream_handle(stream)))
 
 
 def maxsat_solve(ctx: Context, restarts: int, steps: int, seed: int):

@@ -46,6 +46,10 @@ struct DevAllocs {
 
 }  // namespace
 
+namespace rbmsat {
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace rbmsat
+
 struct maxsat_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs

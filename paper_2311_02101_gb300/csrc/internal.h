@@ -93,6 +93,9 @@ std::string build_tables(const std::vector<RbmSet>& sets, int n_temps, int quant
                          const std::vector<int32_t>& grp_len,
                          const std::vector<int32_t>& grp_bucket, HostTables* out);
 
+// message returned by maxsat_last_error(NULL) (context-free calls)
+void set_context_free_error(const std::string& msg);
+
 // clause blocking of the sparse gather: clauses per block and block count
 int clause_block_for(int m);
 int clause_blocks_for(int m);
