@@ -281,7 +281,7 @@ def run_mine(args):
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
 
     S = params.steps_per_graph
-    launches_timed = 3 * args.steps + (args.steps // S if S else 0)
+    launches_timed = 2 * args.steps + (args.steps // S if S else 0)
     path = {1: "dense", 2: "sparse"}[ms.maxsat_get_path(ctx)]
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_total / args.steps, higher_is_better=True,

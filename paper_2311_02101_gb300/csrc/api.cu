@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "philox.cuh"
 
 using namespace rbmsat;
 
@@ -74,7 +75,9 @@ struct maxsat_ctx {
 
   uint8_t* ev_xt = nullptr;
   int64_t* ev_part = nullptr;
+  int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
+  bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
 
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -170,11 +173,12 @@ int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
 
 // One Gibbs round: absolute index t = (tdev ? *tdev : 0) + t_rel.
 int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_t t_rel) {
+  const DevChains& C = ctx->C;
   TIMED(ctx, st, "gather_hidden",
-        launch_gather(ctx->F, ctx->T, ctx->C, ctx->C.xt, ctx->C.Bp, true, true, tdev, t_rel,
-                      ctx->C.cost_part, ctx->C.fe_part, st));
-  TIMED(ctx, st, "best_keep", launch_best_keep(ctx->F, ctx->C, st));
-  TIMED(ctx, st, "visible", launch_visible(ctx->F, ctx->T, ctx->C, (float)ctx->prm.alpha, tdev, t_rel, st));
+        launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, tdev, t_rel, C.cost_part,
+                      C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
+  TIMED(ctx, st, "visible",
+        launch_visible(ctx->F, ctx->T, C, (float)ctx->prm.alpha, tdev, t_rel, ctx->wide_h, st));
   return MAXSAT_OK;
 }
 
@@ -224,15 +228,21 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   CK(ctx, A.alloc(&C.improved, Bp));
   CK(ctx, A.alloc(&C.cost_part, (size_t)nblk * Bp));
   CK(ctx, A.alloc(&C.fe_part, (size_t)nblk * Bp));
-  CK(ctx, A.alloc(&C.G, (size_t)ctx->nnz * Bp));
+  CK(ctx, A.alloc(&C.tickets, Bp / kChainTile));
+  uint8_t* H = nullptr;
+  CK(ctx, A.alloc(&H, (size_t)ctx->m * Bp * (ctx->wide_h ? 2 : 1)));
+  C.H = H;
   return MAXSAT_OK;
 }
 
+// Copies h to a new device buffer padded with zeros to a multiple of 16 bytes
+// (kernels stage tables into shared memory 16 bytes at a time).
 template <class T>
-int upload(maxsat_ctx* ctx, DevAllocs& A, const std::vector<T>& h, const T** out) {
+int upload(maxsat_ctx* ctx, DevAllocs& A, std::vector<T> h, const T** out) {
+  while ((h.size() * sizeof(T)) % 16 != 0 || h.empty()) h.push_back(T{});
   T* d = nullptr;
   CK(ctx, A.alloc(&d, h.size()));
-  if (!h.empty()) CK(ctx, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   *out = d;
   return MAXSAT_OK;
 }
@@ -403,7 +413,8 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   }
 
   // host CSR in device form
-  std::vector<int32_t> cl_off(m + 1), lit_var(nnz), var_off(n + 1, 0), var_lit(nnz);
+  std::vector<int32_t> cl_off(m + 1), lit_var(nnz), var_off(n + 1, 0);
+  std::vector<int4> var_inc(nnz);
   std::vector<int64_t> cl_w(m);
   for (int64_t c = 0; c <= m; ++c) cl_off[c] = (int32_t)off[c];
   for (int64_t c = 0; c < m; ++c) cl_w[c] = weights ? weights[c] : 1;
@@ -416,10 +427,16 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   for (int i = 0; i < n; ++i) var_off[i + 1] += var_off[i];
   {
     std::vector<int32_t> fill(var_off.begin(), var_off.end() - 1);
-    for (int64_t j = 0; j < nnz; ++j) {
-      const int32_t l = lits[j];
-      const int32_t v = (l > 0 ? l : -l) - 1;
-      var_lit[fill[v]++] = (int32_t)j | (l < 0 ? (int32_t)0x80000000 : 0);
+    for (int64_t c = 0; c < m; ++c) {
+      if (cl_grp[c] < 0) continue;
+      const GroupMeta& gm = ctx->tabs.meta[cl_grp[c]];
+      for (int64_t j = off[c]; j < off[c + 1]; ++j) {
+        const int32_t l = lits[j];
+        const int32_t v = (l > 0 ? l : -l) - 1;
+        const int32_t k = (int32_t)(j - off[c]);
+        var_inc[fill[v]++] = make_int4((int32_t)c, (gm.gq_off + k) | (l < 0 ? (int32_t)0x80000000 : 0),
+                                       gm.len, (1 << gm.nh) * gm.len);
+      }
     }
   }
   for (int i = 0; i < n; ++i) ctx->max_degree = std::max(ctx->max_degree, var_off[i + 1] - var_off[i]);
@@ -437,6 +454,12 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   DevTables& T = ctx->T;
   T.n_temps = prm.n_temps;
   T.qmax = ctx->tabs.qmax;
+  T.n_groups = ctx->tabs.n_groups;
+  T.hid_words = (int32_t)ctx->tabs.hid.size();
+  T.fe_len = (int32_t)ctx->tabs.fe.size();
+  T.gq_len = (int32_t)ctx->tabs.gq.size();
+  T.pv_len = (int32_t)ctx->tabs.pv.size();
+  ctx->wide_h = ctx->tabs.max_nh > 8;
 #define UP(vec, dst)                                          \
   do {                                                        \
     int rc_ = upload(ctx, A, vec, &(dst));                    \
@@ -451,12 +474,12 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   UP(cl_grp, F.cl_grp);
   UP(cl_w, F.cl_w);
   UP(var_off, F.var_off);
-  UP(var_lit, F.var_lit);
-  UP(ctx->tabs.grp_nh, T.grp_nh);
-  UP(ctx->tabs.phid_off, T.phid_off);
-  UP(ctx->tabs.fe_off, T.fe_off);
-  UP(ctx->tabs.gq_off, T.gq_off);
-  UP(ctx->tabs.phid, T.phid);
+  UP(var_inc, F.var_inc);
+  UP(ctx->tabs.meta, T.meta);
+  {
+    std::vector<unsigned long long> hid(ctx->tabs.hid.begin(), ctx->tabs.hid.end());
+    UP(hid, T.hid);
+  }
   UP(ctx->tabs.fe, T.fe);
   UP(ctx->tabs.gq, T.gq);
   UP(ctx->tabs.pv, T.pv);
@@ -480,6 +503,7 @@ int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
   if (ctx->C.key0 != (uint32_t)seed || ctx->C.key1 != (uint32_t)(seed >> 32)) destroy_graph(ctx);
   ctx->C.key0 = (uint32_t)seed;
   ctx->C.key1 = (uint32_t)(seed >> 32);
+  ctx->C.keys = philox_keys(ctx->C.key0, ctx->C.key1);
   ctx->seed = seed;
   ctx->t = 0;
   ctx->d_t_synced = false;
@@ -521,11 +545,11 @@ int maxsat_step(maxsat_ctx* ctx, int64_t steps) {
 int maxsat_score(maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_score before maxsat_reset");
+  const DevChains& C = ctx->C;
   TIMED(ctx, ctx->stream, "gather_score",
-        launch_gather(ctx->F, ctx->T, ctx->C, ctx->C.xt, ctx->C.Bp, false, true, nullptr, 0,
-                      ctx->C.cost_part, ctx->C.fe_part, ctx->stream));
-  TIMED(ctx, ctx->stream, "best_keep", launch_best_keep(ctx->F, ctx->C, ctx->stream));
-  TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(ctx->C, ctx->n, ctx->stream));
+        launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, nullptr, 0, C.cost_part,
+                      C.fe_part, C.tickets, nullptr, ctx->wide_h, ctx->stream));
+  TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(C, ctx->n, ctx->stream));
   return MAXSAT_OK;
 }
 
@@ -583,15 +607,13 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
     ctx->ev_Bp = 0;
     CK(ctx, ctx->eval_mem.alloc(&ctx->ev_xt, (size_t)ctx->n * Bp));
     CK(ctx, ctx->eval_mem.alloc(&ctx->ev_part, (size_t)nblk * Bp));
+    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_tickets, Bp / kChainTile));
+    CK(ctx, cudaMemsetAsync(ctx->ev_tickets, 0, sizeof(int32_t) * (Bp / kChainTile), ctx->stream));
     ctx->ev_Bp = Bp;
   }
   CK(ctx, launch_transpose_in(assign_dev, B, ctx->n, ctx->ev_xt, Bp, ctx->stream));
-  DevChains dummy{};
-  dummy.B = B;
-  dummy.Bp = Bp;
-  CK(ctx, launch_gather(ctx->F, ctx->T, dummy, ctx->ev_xt, Bp, false, false, nullptr, 0,
-                        ctx->ev_part, nullptr, ctx->stream));
-  CK(ctx, launch_reduce_cost(ctx->ev_part, nblk, Bp, B, cost_dev, ctx->stream));
+  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, nullptr, 0,
+                        ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h, ctx->stream));
   return MAXSAT_OK;
 }
 

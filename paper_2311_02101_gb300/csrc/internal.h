@@ -22,6 +22,19 @@ constexpr int kChainTile = 256;   // chains per block of the sparse kernels
 constexpr int kClauseBlock = 64;  // clauses per block of the sparse gather
 
 // ---------------------------------------------------------------------------
+// Per clause group (length, weight bucket): its table offsets.
+// ---------------------------------------------------------------------------
+struct GroupMeta {
+  int32_t len = 0;      // clause length K
+  int32_t nh = 0;       // hidden units L
+  int32_t words = 0;    // u64 threshold words per pattern, ceil(L / 3)
+  int32_t hid_off = 0;  // into hid (u64): + (e 2^K + p) words + w
+  int32_t fe_off = 0;   // into fe (float): + e 2^K + p
+  int32_t gq_off = 0;   // into gq (int16): + (e 2^L + hp) K + k
+  int32_t pad0 = 0, pad1 = 0;
+};
+
+// ---------------------------------------------------------------------------
 // Device views passed to kernels by value.
 // ---------------------------------------------------------------------------
 struct DevFormula {
@@ -30,27 +43,36 @@ struct DevFormula {
   const int32_t* lit_var;  // nnz: 0-based variable, bit 31 set when negated
   const int32_t* cl_grp;   // m: clause group (length, bucket); -1 = empty clause
   const int64_t* cl_w;     // m weights
-  const int32_t* var_off;  // n + 1 offsets into var_lit
-  const int32_t* var_lit;  // nnz: literal index, bit 31 set when negated
+  const int32_t* var_off;  // n + 1 offsets into var_inc
+  const int4* var_inc;     // incidence of a variable: {clause, gq_off + position
+                           // (bit 31 set when negated), clause length K,
+                           // per-temperature stride 2^L K of gq}
 };
 
 struct DevTables {
   int32_t n_temps;     // E
   int32_t qmax;        // visible logits clamp to [-qmax, qmax] (units 2^-Q)
-  const int32_t* grp_nh;    // per group: hidden units L
-  const int32_t* phid_off;  // per set s = g * E + e: offset into phid
-  const int32_t* fe_off;    // per set: offset into fe
-  const int32_t* gq_off;    // per set: offset into gq
-  const uint32_t* phid;     // [pattern][h]: 65536 sigma(b_h + sum_k W_kh tau_k), rint
-  const float* fe;          // [pattern]: clause free energy (Eq. 1)
-  const int16_t* gq;        // [hidden pattern][k]: 2^Q sum_h W_kh h_h
-  const uint32_t* pv;       // [q + qmax]: 65536 sigma(q 2^-Q), rint
+  int32_t n_groups;
+  int32_t hid_words, fe_len, gq_len, pv_len;  // element counts
+  int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
+  const GroupMeta* meta;
+  const unsigned long long* hid;
+  const float* fe;
+  const int16_t* gq;
+  const uint32_t* pv;
+};
+
+// Philox round keys of one seed (computed on the host, read by the kernels
+// from parameter space).
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
 };
 
 struct DevChains {
   int32_t B;      // chains reported
   int32_t Bp;     // chains allocated (multiple of kChainTile)
   uint32_t key0, key1;
+  RoundKeys keys;
   uint8_t* xt;        // sparse layout: n x Bp, 0/1
   float* nu;          // n x Bp
   int64_t* best;      // Bp
@@ -60,7 +82,8 @@ struct DevChains {
   uint8_t* improved;  // Bp flags of the last best-keep
   int64_t* cost_part; // [clause block][Bp]
   float* fe_part;     // [clause block][Bp]
-  int16_t* G;         // nnz x Bp: 2^Q G per literal and chain
+  void* H;            // m x Bp hidden patterns (uint8_t, or uint16_t when L > 8)
+  int32_t* tickets;   // Bp / kChainTile arrival counters of the gather blocks
 };
 
 // ---------------------------------------------------------------------------
@@ -73,10 +96,10 @@ struct RbmSet {
 };
 
 struct HostTables {
-  int32_t n_groups = 0, n_temps = 0, qmax = 0, quant_bits = 0;
+  int32_t n_groups = 0, n_temps = 0, qmax = 0, quant_bits = 0, max_nh = 0;
   std::vector<int32_t> grp_len, grp_bucket, grp_nh;
-  std::vector<int32_t> phid_off, fe_off, gq_off;
-  std::vector<uint32_t> phid;
+  std::vector<GroupMeta> meta;
+  std::vector<uint64_t> hid;
   std::vector<float> fe;
   std::vector<int16_t> gq;
   std::vector<uint32_t> pv;
@@ -101,21 +124,23 @@ int clause_block_for(int m);
 int clause_blocks_for(int m);
 
 // sparse.cu launchers (all asynchronous on `st`)
+enum GatherMode { kStep = 0, kScore = 1, kEval = 2 };
 cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st);
-cudaError_t launch_gather(const DevFormula& F, const DevTables& T, const DevChains& C,
-                          const uint8_t* xt, int Bp, bool sample, bool free_energy,
+// kStep: cost, free energy, hidden draws, then (last block of each chain tile)
+// best-keep; kScore: the same without draws; kEval: cost only, written to
+// eval_out. xt / Bp / B / tickets / partials may differ from C's (eval).
+cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
+                          const DevChains& C, const uint8_t* xt, int B, int Bp,
                           const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
-                          float* fe_part, cudaStream_t st);
-cudaError_t launch_best_keep(const DevFormula& F, const DevChains& C, cudaStream_t st);
+                          float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide_h,
+                          cudaStream_t st);
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
-                           float alpha, const uint32_t* tdev, uint32_t t_rel,
+                           float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide_h,
                            cudaStream_t st);
 cudaError_t launch_keep_copy(const DevChains& C, int n, cudaStream_t st);
 cudaError_t launch_advance(uint32_t* tdev, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t st);
 cudaError_t launch_transpose_in(const uint8_t* assign, int B, int n, uint8_t* xt, int Bp,
                                 cudaStream_t st);
-cudaError_t launch_reduce_cost(const int64_t* cost_part, int nblk, int Bp, int B,
-                               int64_t* cost_out, cudaStream_t st);
 
 }  // namespace rbmsat

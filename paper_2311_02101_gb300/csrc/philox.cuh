@@ -7,13 +7,11 @@
 
 #include <cstdint>
 
+#include "internal.h"
+
 namespace rbmsat {
 
-struct RoundKeys {
-  uint32_t k0[10], k1[10];
-};
-
-__device__ __forceinline__ RoundKeys philox_keys(uint32_t key0, uint32_t key1) {
+__host__ __device__ __forceinline__ RoundKeys philox_keys(uint32_t key0, uint32_t key1) {
   RoundKeys r;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {

@@ -6,19 +6,21 @@
 // directly on the literal lists, never on a dense clause-variable matrix:
 //   k_gather   one thread = one clause x 8 chains: reads the clause's literal
 //              truths for 8 chains at once (8 bytes per literal from the
-//              variable-major state), forms the truth pattern, adds the weight
-//              of unsatisfied clauses, the clause free energy (Eq. 1) and
-//              draws the hidden units (Eq. 2 / Eq. 6); writes each literal's
-//              scatter contribution G for the 8 chains (16 bytes).
-//   k_best_keep  reduces the per-block costs / free energies in a fixed order
-//              and keeps improving states (Sec. 4.2).
-//   k_visible  one thread = one variable x 8 chains: pull-based scatter-sum of
-//              G over the variable's literals (Eq. 7; no atomics, so the sums
-//              are exact and deterministic), draws the new visible states
+//              variable-major state), forms each chain's truth pattern, adds
+//              the weight of unsatisfied clauses and the clause free energy
+//              (Eq. 1), draws the hidden units (Eq. 2 / Eq. 6) and stores the
+//              hidden pattern (one byte per clause and chain). The last block
+//              to finish a tile of 256 chains reduces the per-block costs in a
+//              fixed order and keeps improving states (Sec. 4.2).
+//   k_visible  one thread = one variable x 8 chains: pull-based scatter-sum
+//              over the variable's literals of the contribution table entry
+//              selected by the clause's hidden pattern (Eq. 7; integer sums,
+//              no atomics, deterministic), draws the new visible states
 //              (Eq. 3), updates nu (Sec. 4.4) and copies improved states into
 //              the best-so-far before they are overwritten.
 // State layout: x and nu are variable-major (n x Bp) so 8 consecutive chains of
-// one variable are one 8-byte (x) or 32-byte (nu) access.
+// one variable are one 8-byte (x) or 32-byte (nu) access. The small
+// probability tables are staged in shared memory when they fit.
 #include <cstdint>
 
 #include "internal.h"
@@ -37,13 +39,21 @@ __device__ __forceinline__ int temp_of(int b, int E, int B) {
   return e < E - 1 ? e : E - 1;
 }
 
+// Copies `bytes` (multiple of 16) from global to shared memory, whole block.
+__device__ __forceinline__ void stage(void* dst, const void* src, int bytes) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+__host__ __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
+
 __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
   const int i = blockIdx.y * 8 + warp;
   if (i < n) {
-    const RoundKeys K = philox_keys(C.key0, C.key1);
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, 0u, kPhaseInit), K);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, 0u, kPhaseInit), C.keys);
     uint64_t x = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) x |= (uint64_t)(lane16(r, q) < 32768u) << (8 * q);
@@ -60,50 +70,68 @@ __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
       C.best[b0 + q] = INT64_MAX;
       C.improved[b0 + q] = 0;
     }
+    if (lane == 0) C.tickets[blockIdx.x] = 0;
   }
 }
 
-template <bool SAMPLE, bool FE>
+template <int MODE, bool SM, typename HT>
 __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevChains C,
-                                                const uint8_t* __restrict__ xt, int Bp,
-                                                int cblock, const uint32_t* tdev,
-                                                uint32_t t_rel, int64_t* cost_part,
-                                                float* fe_part) {
+                                                const uint8_t* __restrict__ xt, int B, int Bp,
+                                                int cblock, const uint32_t* tdev, uint32_t t_rel,
+                                                int64_t* cost_part, float* fe_part,
+                                                int32_t* tickets, int64_t* eval_out) {
+  constexpr bool FE = MODE != kEval;
+  constexpr bool SAMPLE = MODE == kStep;
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_cost[8][256];
   __shared__ float s_fe[8][256];
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
   const int c_begin = blockIdx.y * cblock;
   const int c_end = min(c_begin + cblock, F.m);
   const int E = T.n_temps;
 
-  int e[8];
+  const GroupMeta* meta = T.meta;
+  const unsigned long long* hid = T.hid;
+  const float* fe_tab = T.fe;
+  if (SM && FE) {
+    const int mb = align16(T.n_groups * (int)sizeof(GroupMeta));
+    const int hb = align16(T.hid_words * 8);
+    const int fb = align16(T.fe_len * 4);
+    stage(smem, T.meta, mb);
+    stage(smem + mb, T.hid, hb);
+    stage(smem + mb + hb, T.fe, fb);
+    __syncthreads();
+    meta = reinterpret_cast<const GroupMeta*>(smem);
+    hid = reinterpret_cast<const unsigned long long*>(smem + mb);
+    fe_tab = reinterpret_cast<const float*>(smem + mb + hb);
+  }
+
+  // temperature of the thread's 8 chains: one value unless a temperature
+  // block boundary falls inside them
+  const int e0 = FE ? temp_of(b0, E, B) : 0;
+  const bool e_uniform = !FE || e0 == temp_of(b0 + 7, E, B);
+  // the weighted unsat cost accumulates in this warp's shared-memory row
+  // (each entry is owned by one thread), the free energy in registers
+  int64_t* my_cost = &s_cost[warp][lane * 8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) e[q] = (SAMPLE || FE) ? temp_of(b0 + q, E, C.B) : 0;
-  int64_t cost[8];
+  for (int q = 0; q < 8; ++q) my_cost[q] = 0;
   float fe[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    cost[q] = 0;
-    fe[q] = 0.f;
-  }
-  RoundKeys K;
+  for (int q = 0; q < 8; ++q) fe[q] = 0.f;
   uint32_t t = 0;
-  if (SAMPLE) {
-    K = philox_keys(C.key0, C.key1);
-    t = step_index(tdev, t_rel);
-  }
+  if (SAMPLE) t = step_index(tdev, t_rel);
 
   for (int c = c_begin + warp; c < c_end; c += 8) {
     const int o = __ldg(F.cl_off + c);
     const int len = __ldg(F.cl_off + c + 1) - o;
-    // truth pattern of the clause's literals for 8 chains: byte q of plo holds
-    // bits 0..7 of chain q's pattern, byte q of phi bits 8..15
+    // byte q of plo: bits 0..7 of chain q's truth pattern; of phi: bits 8..15
     uint64_t plo = 0, phi = 0;
     for (int k = 0; k < len; ++k) {
       const int32_t lv = __ldg(F.lit_var + o + k);
-      const int v = lv & 0x7FFFFFFF;
-      uint64_t x8 = __ldg(reinterpret_cast<const unsigned long long*>(xt + (size_t)v * Bp + b0));
+      uint64_t x8 = __ldg(reinterpret_cast<const unsigned long long*>(
+          xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
       if (lv < 0) x8 ^= 0x0101010101010101ull;
       if (k < 8) plo |= x8 << k;
       else phi |= x8 << (k - 8);
@@ -115,52 +143,61 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
     const int64_t wc = __ldg(F.cl_w + c);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      if (p[q] == 0) cost[q] += wc;
-    if (!(SAMPLE || FE) || len == 0) continue;
+      if (p[q] == 0) my_cost[q] += wc;
+    if (!FE || len == 0) continue;
 
     const int grp = __ldg(F.cl_grp + c);
-    int s[8];
+    const GroupMeta gm = meta[grp];
+    int row[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[q] = grp * E + e[q];
-    if (FE) {
+    for (int q = 0; q < 8; ++q)
+      row[q] = ((e_uniform ? e0 : temp_of(b0 + q, E, B)) << len) + p[q];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) fe[q] += __ldg(T.fe + __ldg(T.fe_off + s[q]) + p[q]);
-    }
-    if (!SAMPLE) continue;
+    for (int q = 0; q < 8; ++q) fe[q] += fe_tab[gm.fe_off + row[q]];
+    if constexpr (SAMPLE) {
 
-    const int L = __ldg(T.grp_nh + grp);
-    int pbase[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pbase[q] = __ldg(T.phid_off + s[q]) + p[q] * L;
-    uint32_t hp[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) hp[q] = 0;
-    for (int h = 0; h < L; ++h) {
-      const uint4 r = philox4x32_10(
-          make_uint4((uint32_t)c, (uint32_t)g8 | ((uint32_t)h << 24), t, kPhaseHidden), K);
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        hp[q] |= (uint32_t)(lane16(r, q) < __ldg(T.phid + pbase[q] + h)) << h;
-    }
-    int gbase[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) gbase[q] = __ldg(T.gq_off + s[q]) + (int)hp[q] * len;
-    for (int k = 0; k < len; ++k) {
-      uint32_t w[4];
-#pragma unroll
-      for (int h2 = 0; h2 < 4; ++h2) {
-        const uint32_t lo = (uint16_t)__ldg(T.gq + gbase[2 * h2] + k);
-        const uint32_t hi = (uint16_t)__ldg(T.gq + gbase[2 * h2 + 1] + k);
-        w[h2] = lo | (hi << 16);
+      uint32_t hp[8];
+  #pragma unroll
+      for (int q = 0; q < 8; ++q) hp[q] = 0;
+      for (int w = 0; w < gm.words; ++w) {
+        uint64_t wd[8];
+  #pragma unroll
+        for (int q = 0; q < 8; ++q) wd[q] = hid[gm.hid_off + row[q] * gm.words + w];
+  #pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int h = 3 * w + r;
+          if (h >= gm.nh) break;
+          const uint4 R = philox4x32_10(
+              make_uint4((uint32_t)c, (uint32_t)g8 | ((uint32_t)h << 24), t, kPhaseHidden), C.keys);
+  #pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const uint32_t P = (uint32_t)(wd[q] >> (17 * r)) & 0x1FFFFu;
+            hp[q] |= (uint32_t)(lane16(R, q) < P) << h;
+          }
+        }
       }
-      *reinterpret_cast<uint4*>(C.G + (size_t)(o + k) * Bp + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+      HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
+      if (sizeof(HT) == 1) {
+        uint64_t v = 0;
+  #pragma unroll
+        for (int q = 0; q < 8; ++q) v |= (uint64_t)hp[q] << (8 * q);
+        *reinterpret_cast<uint64_t*>(H) = v;
+      } else {
+        uint4 v;
+        v.x = hp[0] | (hp[1] << 16);
+        v.y = hp[2] | (hp[3] << 16);
+        v.z = hp[4] | (hp[5] << 16);
+        v.w = hp[6] | (hp[7] << 16);
+        *reinterpret_cast<uint4*>(H) = v;
+      }
     }
   }
 
+  // per-block partial sums, then the block that arrives last for this tile of
+  // 256 chains reduces all partials in block order and keeps improvements
+  if (FE) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    s_cost[warp][lane * 8 + q] = cost[q];
-    s_fe[warp][lane * 8 + q] = fe[q];
+    for (int q = 0; q < 8; ++q) s_fe[warp][lane * 8 + q] = fe[q];
   }
   __syncthreads();
   const int tid = threadIdx.x;
@@ -169,42 +206,34 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
     tc += s_cost[w][tid];
-    tf += s_fe[w][tid];
+    if (FE) tf += s_fe[w][tid];
   }
   const size_t out = (size_t)blockIdx.y * Bp + (size_t)blockIdx.x * 256 + tid;
   cost_part[out] = tc;
   if (FE) fe_part[out] = tf;
-}
-
-// Block = 32 chains (lanes) x 8 warps over clause blocks; fixed summation order.
-__global__ void __launch_bounds__(256) k_best_keep(DevChains C, int nblk) {
-  __shared__ int64_t s_cost[8][32];
-  __shared__ float s_fe[8][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int b = blockIdx.x * 32 + lane;
-  int64_t c = 0;
-  float f = 0.f;
-  for (int k = warp; k < nblk; k += 8) {
-    c += C.cost_part[(size_t)k * C.Bp + b];
-    f += C.fe_part[(size_t)k * C.Bp + b];
-  }
-  s_cost[warp][lane] = c;
-  s_fe[warp][lane] = f;
+  __threadfence();
   __syncthreads();
-  if (warp == 0) {
-    int64_t tc = 0;
-    float tf = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      tc += s_cost[w][lane];
-      tf += s_fe[w][lane];
-    }
-    C.cost[b] = tc;
-    C.fe[b] = tf;
-    const bool imp = tc < C.best[b];
-    if (imp) C.best[b] = tc;
+  if (tid == 0) s_last = atomicAdd(tickets + blockIdx.x, 1) == (int)gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int b = blockIdx.x * 256 + tid;
+  int64_t csum = 0;
+  float fsum = 0.f;
+  for (int k = 0; k < (int)gridDim.y; ++k) {
+    csum += __ldcg(cost_part + (size_t)k * Bp + b);
+    if (FE) fsum += __ldcg(fe_part + (size_t)k * Bp + b);
+  }
+  if (MODE == kEval) {
+    if (b < B) eval_out[b] = csum;
+  } else {
+    C.cost[b] = csum;
+    C.fe[b] = fsum;
+    const bool imp = csum < C.best[b];
+    if (imp) C.best[b] = csum;
     C.improved[b] = imp ? 1 : 0;
   }
+  if (tid == 0) tickets[blockIdx.x] = 0;
 }
 
 __device__ __forceinline__ void keep_improved(const DevChains& C, size_t o, int b0,
@@ -217,45 +246,67 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, size_t o, int 
   }
 }
 
+template <bool SM, typename HT>
 __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
                                                  uint32_t t_rel) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
+  const int16_t* gq = T.gq;
+  const uint32_t* pv = T.pv;
+  if (SM) {
+    const int gb = align16(T.gq_len * 2);
+    stage(smem, T.gq, gb);
+    stage(smem + gb, T.pv, align16(T.pv_len * 4));
+    __syncthreads();
+    gq = reinterpret_cast<const int16_t*>(smem);
+    pv = reinterpret_cast<const uint32_t*>(smem + gb);
+  }
   const int i = blockIdx.y * 8 + warp;
   if (i >= F.n) return;
   const uint32_t t = step_index(tdev, t_rel);
+  int e[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) e[q] = temp_of(b0 + q, T.n_temps, C.B);
   int z[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) z[q] = 0;
+  const HT* H = static_cast<const HT*>(C.H);
   const int j_end = __ldg(F.var_off + i + 1);
   for (int jj = __ldg(F.var_off + i); jj < j_end; ++jj) {
-    const int32_t jl = __ldg(F.var_lit + jj);
-    const int j = jl & 0x7FFFFFFF;
-    const uint4 g = __ldg(reinterpret_cast<const uint4*>(C.G + (size_t)j * C.Bp + b0));
-    const uint32_t w[4] = {g.x, g.y, g.z, g.w};
+    const int4 inc = __ldg(F.var_inc + jj);
+    const int base = inc.y & 0x7FFFFFFF;
+    const int sgn = inc.y < 0 ? -1 : 1;
+    uint32_t hp[8];
+    if (sizeof(HT) == 1) {
+      const uint64_t v = __ldg(reinterpret_cast<const unsigned long long*>(H + (size_t)inc.x * C.Bp + b0));
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int v = (int)(int16_t)((q & 1) ? (w[q >> 1] >> 16) : (w[q >> 1] & 0xFFFFu));
-      z[q] += jl < 0 ? -v : v;
+      for (int q = 0; q < 8; ++q) hp[q] = (uint32_t)(v >> (8 * q)) & 0xFFu;
+    } else {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(H + (size_t)inc.x * C.Bp + b0));
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hp[q] = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
     }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) z[q] += sgn * (int)gq[base + e[q] * inc.w + (int)hp[q] * inc.z];
   }
   const size_t o = (size_t)i * C.Bp + b0;
   const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
   keep_improved(C, o, b0, xold);
 
-  const RoundKeys K = philox_keys(C.key0, C.key1);
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, t, kPhaseVisible), K);
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, t, kPhaseVisible), C.keys);
   float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
-  float4 n0 = nu4[0], n1 = nu4[1];
+  const float4 n0 = nu4[0], n1 = nu4[1];
   float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
   const float keep = 1.0f - alpha;
   uint64_t xnew = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int qq = max(-T.qmax, min(T.qmax, z[q]));
-    const uint32_t P = __ldg(T.pv + qq + T.qmax);
-    // rho (1 - rho) with rho = P / 65536: P (65536 - P) < 2^31, scaled by 2^-32
+    const uint32_t P = pv[qq + T.qmax];
+    // rho (1 - rho) with rho = P / 65536: P (65536 - P) <= 2^30, scaled by 2^-32
     const float var = (float)(P * (65536u - P)) * 2.3283064365386963e-10f;
     nu[q] = keep * nu[q] + alpha * var;
     xnew |= (uint64_t)(lane16(r, q) < P) << (8 * q);
@@ -294,13 +345,64 @@ __global__ void k_transpose_in(const uint8_t* __restrict__ assign, int B, int n,
   }
 }
 
-__global__ void k_reduce_cost(const int64_t* __restrict__ part, int nblk, int Bp, int B,
-                              int64_t* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  int64_t c = 0;
-  for (int k = 0; k < nblk; ++k) c += part[(size_t)k * Bp + b];
-  out[b] = c;
+int gather_smem_bytes(const DevTables& T) {
+  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.hid_words * 8) +
+         align16(T.fe_len * 4);
+}
+
+int visible_smem_bytes(const DevTables& T) {
+  return align16(T.gq_len * 2) + align16(T.pv_len * 4);
+}
+
+constexpr int kSmemLimit = 160 * 1024;
+
+template <int MODE, bool SM, typename HT>
+cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
+                           const DevTables& T, const DevChains& C, const uint8_t* xt, int B,
+                           int Bp, int cb, const uint32_t* tdev, uint32_t t_rel,
+                           int64_t* cost_part, float* fe_part, int32_t* tickets,
+                           int64_t* eval_out) {
+  auto kern = k_gather<MODE, SM, HT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, 256, smem, st>>>(F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part, fe_part, tickets,
+                                eval_out);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t gather_mode(dim3 grid, cudaStream_t st, bool wide, const DevFormula& F,
+                        const DevTables& T, const DevChains& C, const uint8_t* xt, int B, int Bp,
+                        int cb, const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
+                        float* fe_part, int32_t* tickets, int64_t* eval_out) {
+  const int sm = gather_smem_bytes(T);
+  const bool use_sm = MODE != kEval && sm <= kSmemLimit;
+  if (use_sm && !wide)
+    return gather_variant<MODE, true, uint8_t>(grid, sm, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+                                               cost_part, fe_part, tickets, eval_out);
+  if (use_sm)
+    return gather_variant<MODE, true, uint16_t>(grid, sm, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+                                                cost_part, fe_part, tickets, eval_out);
+  if (!wide)
+    return gather_variant<MODE, false, uint8_t>(grid, 0, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+                                                cost_part, fe_part, tickets, eval_out);
+  return gather_variant<MODE, false, uint16_t>(grid, 0, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+                                               cost_part, fe_part, tickets, eval_out);
+}
+
+template <bool SM, typename HT>
+cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
+                            const DevTables& T, const DevChains& C, float alpha,
+                            const uint32_t* tdev, uint32_t t_rel) {
+  auto kern = k_visible<SM, HT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, 256, smem, st>>>(F, T, C, alpha, tdev, t_rel);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -322,32 +424,36 @@ cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const DevFormula& F, const DevTables& T, const DevChains& C,
-                          const uint8_t* xt, int Bp, bool sample, bool fe,
+cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
+                          const DevChains& C, const uint8_t* xt, int B, int Bp,
                           const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
-                          float* fe_part, cudaStream_t st) {
+                          float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide,
+                          cudaStream_t st) {
   const int cb = clause_block_for(F.m);
   dim3 grid(Bp / kChainTile, clause_blocks_for(F.m));
-  if (sample)
-    k_gather<true, true><<<grid, 256, 0, st>>>(F, T, C, xt, Bp, cb, tdev, t_rel, cost_part, fe_part);
-  else if (fe)
-    k_gather<false, true><<<grid, 256, 0, st>>>(F, T, C, xt, Bp, cb, tdev, t_rel, cost_part, fe_part);
-  else
-    k_gather<false, false><<<grid, 256, 0, st>>>(F, T, C, xt, Bp, cb, tdev, t_rel, cost_part, fe_part);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_best_keep(const DevFormula& F, const DevChains& C, cudaStream_t st) {
-  k_best_keep<<<C.Bp / 32, 256, 0, st>>>(C, clause_blocks_for(F.m));
-  return cudaGetLastError();
+  switch (mode) {
+    case kStep:
+      return gather_mode<kStep>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+                                fe_part, tickets, eval_out);
+    case kScore:
+      return gather_mode<kScore>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+                                 fe_part, tickets, eval_out);
+    default:
+      return gather_mode<kEval>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+                                fe_part, tickets, eval_out);
+  }
 }
 
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
-                           float alpha, const uint32_t* tdev, uint32_t t_rel,
+                           float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide,
                            cudaStream_t st) {
   dim3 grid(C.Bp / kChainTile, (F.n + 7) / 8);
-  k_visible<<<grid, 256, 0, st>>>(F, T, C, alpha, tdev, t_rel);
-  return cudaGetLastError();
+  const int sm = visible_smem_bytes(T);
+  const bool use_sm = sm <= kSmemLimit;
+  if (use_sm && !wide) return visible_variant<true, uint8_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel);
+  if (use_sm) return visible_variant<true, uint16_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel);
+  if (!wide) return visible_variant<false, uint8_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel);
+  return visible_variant<false, uint16_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel);
 }
 
 cudaError_t launch_keep_copy(const DevChains& C, int n, cudaStream_t st) {
@@ -370,12 +476,6 @@ cudaError_t launch_transpose_in(const uint8_t* assign, int B, int n, uint8_t* xt
                                 cudaStream_t st) {
   dim3 grid((n + 31) / 32, Bp / 32);
   k_transpose_in<<<grid, dim3(32, 8), 0, st>>>(assign, B, n, xt, Bp);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_cost(const int64_t* part, int nblk, int Bp, int B,
-                               int64_t* out, cudaStream_t st) {
-  k_reduce_cost<<<(B + 255) / 256, 256, 0, st>>>(part, nblk, Bp, B, out);
   return cudaGetLastError();
 }
 

@@ -4,12 +4,15 @@
 // logit b'_h + sum_k W'_kh v_k = b_h + sum_k W_kh tau_k, where tau_k is the
 // truth of the clause's k-th literal. So one clause's hidden conditional
 // (Eq. 2 / Eq. 6) and free energy (Eq. 1) depend only on the pattern
-// p = sum_k tau_k 2^k of true literals, and its contribution to the visible
-// logits (Eq. 7) only on the pattern of sampled hidden units. For every set
-// s = (group g, temperature e) the tables hold
-//   phid[s][p][h] = rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))   (u32)
-//   fe[s][p]      = -sum_h softplus(b_h + sum_k W_kh tau_k(p))      (float)
-//   gq[s][hp][k]  = 2^Q sum_h W_kh [bit h of hp]                    (int16)
+// p = sum_k tau_k 2^k of true literals, and its contributions to the visible
+// logits (Eq. 7) only on the pattern hp = sum_h h_h 2^h of sampled hidden
+// units. Per group g (clause length K, weight bucket) with L hidden units and
+// per temperature e the tables hold
+//   hid[g][e][p][w]   u64 word w packs rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))
+//                     for h = 3w, 3w + 1, 3w + 2 in bits 0, 17, 34 (17 bits each,
+//                     values 0..65536); W = ceil(L / 3) words per pattern
+//   fe[g][e][p]       -sum_h softplus(b_h + sum_k W_kh tau_k(p))       (float)
+//   gq[g][e][hp][k]   2^Q sum_h W_kh [bit h of hp]                     (int16)
 // and the visible table pv[q] = rint(65536 sigma(q 2^-Q)) for |q| <= qmax.
 // A Bernoulli draw with a 16-bit uniform u is [u < P]. Beyond |z| >= 12 the
 // 16-bit probabilities are exactly 0 and 65536, so qmax = 12 * 2^Q clamps
@@ -40,25 +43,34 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
   T->grp_len = grp_len;
   T->grp_bucket = grp_bucket;
   T->grp_nh.assign(G, 0);
-  T->phid_off.assign((size_t)G * E, 0);
-  T->fe_off.assign((size_t)G * E, 0);
-  T->gq_off.assign((size_t)G * E, 0);
-  T->phid.clear();
+  T->meta.assign(G, GroupMeta{});
+  T->hid.clear();
   T->fe.clear();
   T->gq.clear();
   T->gq_absmax = 0;
+  T->max_nh = 0;
   const double scale = std::ldexp(1.0, Q);
   for (int g = 0; g < G; ++g) {
+    const int K = grp_len[g];
+    GroupMeta& gm = T->meta[g];
+    gm.len = K;
+    gm.hid_off = (int32_t)T->hid.size();
+    gm.fe_off = (int32_t)T->fe.size();
+    gm.gq_off = (int32_t)T->gq.size();
     for (int e = 0; e < E; ++e) {
       const RbmSet* s = nullptr;
       for (const auto& c : sets)
-        if (c.len == grp_len[g] && c.bucket == grp_bucket[g] && c.temp == e) s = &c;
+        if (c.len == K && c.bucket == grp_bucket[g] && c.temp == e) s = &c;
       if (!s)
-        return "no OR-gate RBM set for clause length " + std::to_string(grp_len[g]) +
-               ", bucket " + std::to_string(grp_bucket[g]) + ", temperature " +
-               std::to_string(e);
-      const int K = s->len, L = s->nh;
-      if (e == 0) T->grp_nh[g] = L;
+        return "no OR-gate RBM set for clause length " + std::to_string(K) + ", bucket " +
+               std::to_string(grp_bucket[g]) + ", temperature " + std::to_string(e);
+      const int L = s->nh;
+      if (e == 0) {
+        T->grp_nh[g] = L;
+        gm.nh = L;
+        gm.words = (L + 2) / 3;
+        T->max_nh = std::max(T->max_nh, L);
+      }
       if (T->grp_nh[g] != L)
         return "sets of one length and bucket must share n_hidden across temperatures";
       std::vector<int32_t> Wq((size_t)K * L);
@@ -73,20 +85,18 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
         if (!std::isfinite(v) || v != std::nearbyint(v) || std::fabs(s->b[h]) > 1048576.0)
           return "b entries must be multiples of 2^-24 below 2^20 in magnitude";
       }
-      const size_t sidx = (size_t)g * E + e;
-      T->phid_off[sidx] = (int32_t)T->phid.size();
-      T->fe_off[sidx] = (int32_t)T->fe.size();
-      T->gq_off[sidx] = (int32_t)T->gq.size();
       for (int p = 0; p < (1 << K); ++p) {
         double F = 0.0;
+        std::vector<uint64_t> words(gm.words, 0);
         for (int h = 0; h < L; ++h) {
           int64_t acc = 0;
           for (int k = 0; k < K; ++k)
             if ((p >> k) & 1) acc += Wq[k * L + h];
           const double a = s->b[h] + (double)acc / scale;
-          T->phid.push_back(prob16(a));
+          words[h / 3] |= (uint64_t)prob16(a) << (17 * (h % 3));
           F -= softplus(a);
         }
+        for (uint64_t w : words) T->hid.push_back(w);
         T->fe.push_back((float)F);
       }
       for (int hp = 0; hp < (1 << L); ++hp) {
@@ -99,7 +109,8 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
           if (std::abs(acc) > T->gq_absmax) T->gq_absmax = std::abs(acc);
         }
       }
-      if (T->phid.size() > (size_t)INT32_MAX / 2) return "tables too large";
+      if (T->hid.size() > (size_t)INT32_MAX / 4 || T->gq.size() > (size_t)INT32_MAX / 2)
+        return "tables too large";
     }
   }
   T->pv.resize(2 * (size_t)T->qmax + 1);
