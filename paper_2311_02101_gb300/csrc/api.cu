@@ -64,6 +64,7 @@ struct maxsat_ctx {
   DevAllocs formula_mem;  // formula + tables (lifetime of the context)
   DevAllocs chain_mem;    // chain state (re-made when B changes)
   DevAllocs eval_mem;     // eval scratch (grown on demand)
+  DevAllocs dense_eval_mem;  // dense eval scratch (grown on demand)
   DevFormula F{};
   DevTables T{};
   DevChains C{};
@@ -81,6 +82,21 @@ struct maxsat_ctx {
 
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+
+  // dense tensor-core path (built when requested)
+  bool dense = false;
+  bool e5m2 = false;
+  int n_pad = 0, m_pad = 0;
+  uint8_t* dA = nullptr;          // m_pad x n_pad FP8 pattern-encoding gather matrix
+  int32_t* d_row_len = nullptr;   // m_pad clause lengths (0 for padding rows)
+  int64_t* d_row_w = nullptr;     // m_pad weights (0 for padding rows)
+  CUtensorMap tmA{};
+  uint8_t* dXe = nullptr;         // eval scratch: Bp x n_pad FP8 states
+  int64_t* d_epart = nullptr;     // eval scratch: (m_pad / 128) x Bp partial costs
+  int32_t* d_etick = nullptr;     // eval scratch: Bp / 128 tickets
+  int dev_Bp = 0;
+  CUtensorMap tmXe{};
+  int* d_err = nullptr;           // device wait-timeout code (0 = none)
 
   // per-kernel CUDA-event timing of plain launches
   bool profiling = false;
@@ -271,7 +287,10 @@ const char* maxsat_last_error(const maxsat_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }
 
-int maxsat_get_path(const maxsat_ctx* ctx) { return ctx ? ctx->path : MAXSAT_EINVAL; }
+int maxsat_get_path(const maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  return ctx->dense ? MAXSAT_PATH_DENSE : ctx->path;
+}
 
 int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
                   const int32_t* lits, const int64_t* weights, const maxsat_params* params,
@@ -314,8 +333,6 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   if (prm.steps_per_graph < 0 || prm.steps_per_graph > 100000)
     return fail(nullptr, MAXSAT_EINVAL, "steps_per_graph out of range");
   if (prm.n_sets < 0 || (prm.n_sets > 0 && !prm.sets)) return fail(nullptr, MAXSAT_EINVAL, "sets is NULL");
-  if (prm.path == MAXSAT_PATH_DENSE)
-    return fail(nullptr, MAXSAT_EINVAL, "the dense path is not available in this build");
 
   int rc = check_device(nullptr);
   if (rc != MAXSAT_OK) return rc;
@@ -483,13 +500,59 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   UP(ctx->tabs.fe, T.fe);
   UP(ctx->tabs.gq, T.gq);
   UP(ctx->tabs.pv, T.pv);
-#undef UP
+#define UP2(vec, dst)                                         \
+  do {                                                        \
+    int rc_ = upload(ctx, A, vec, &(dst));                    \
+    if (rc_ != MAXSAT_OK) {                                   \
+      std::string e_ = ctx->err;                              \
+      delete ctx;                                             \
+      return fail(nullptr, rc_, e_);                          \
+    }                                                         \
+  } while (0)
   {
     cudaError_t e = A.alloc(&ctx->d_t, 1);
+    if (e == cudaSuccess) e = A.alloc(&ctx->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
       delete ctx;
       return cuda_fail(nullptr, e, "cudaMalloc");
     }
+  }
+  if (prm.path == MAXSAT_PATH_DENSE) {
+    int64_t wmax = 0;
+    for (int64_t c = 0; c < m; ++c) wmax = std::max<int64_t>(wmax, weights ? weights[c] : 1);
+    if (wmax >= ((int64_t)1 << 43)) {
+      delete ctx;
+      return fail(nullptr, MAXSAT_EINVAL, "the dense path needs weights below 2^43");
+    }
+    std::vector<uint8_t> Ah;
+    std::string derr = build_gather_matrix(n, (int)m, off, lits, &ctx->e5m2, &ctx->n_pad,
+                                           &ctx->m_pad, &Ah);
+    if (!derr.empty()) {
+      delete ctx;
+      return fail(nullptr, MAXSAT_EINVAL, derr);
+    }
+    std::vector<int32_t> rl(ctx->m_pad, 0);
+    std::vector<int64_t> rw(ctx->m_pad, 0);
+    for (int64_t c = 0; c < m; ++c) {
+      rl[c] = (int32_t)(off[c + 1] - off[c]);
+      rw[c] = weights ? weights[c] : 1;
+    }
+    const uint8_t* dA = nullptr;
+    const int32_t* drl = nullptr;
+    const int64_t* drw = nullptr;
+    UP2(Ah, dA);
+    UP2(rl, drl);
+    UP2(rw, drw);
+    ctx->dA = const_cast<uint8_t*>(dA);
+    ctx->d_row_len = const_cast<int32_t*>(drl);
+    ctx->d_row_w = const_cast<int64_t*>(drw);
+    derr = make_tmap_2d(&ctx->tmA, ctx->dA, ctx->n_pad, ctx->m_pad, ctx->n_pad, 128, 128, false);
+    if (!derr.empty()) {
+      delete ctx;
+      return fail(nullptr, MAXSAT_ECUDA, derr);
+    }
+    ctx->dense = true;
   }
   *out = ctx;
   return MAXSAT_OK;
@@ -600,6 +663,28 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
   if (B == 0) return MAXSAT_OK;
+  if (ctx->dense) {
+    const int Bp = (B + 127) / 128 * 128;
+    if (Bp > ctx->dev_Bp) {
+      // grow the eval scratch (cudaFree of the old one synchronises the device)
+      ctx->dense_eval_mem.release();
+      ctx->dev_Bp = 0;
+      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->dXe, (size_t)Bp * ctx->n_pad));
+      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_epart, (size_t)(ctx->m_pad / 128) * Bp));
+      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_etick, Bp / 128));
+      CK(ctx, cudaMemsetAsync(ctx->d_etick, 0, sizeof(int32_t) * (Bp / 128), ctx->stream));
+      std::string e = make_tmap_2d(&ctx->tmXe, ctx->dXe, ctx->n_pad, Bp, ctx->n_pad, 128, 128, false);
+      if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
+      ctx->dev_Bp = Bp;
+    }
+    const int Bt = ctx->dev_Bp;
+    CK(ctx, launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, ctx->stream));
+    TIMED(ctx, ctx->stream, "gemm1_eval",
+          launch_gemm1_eval(ctx->tmA, ctx->tmXe, ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
+                            ctx->d_row_len, ctx->d_row_w, ctx->d_epart, ctx->d_etick, cost_dev,
+                            ctx->d_err, ctx->stream));
+    return MAXSAT_OK;
+  }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
   const int nblk = clause_blocks_for(ctx->m);
   if (Bp > ctx->ev_Bp) {

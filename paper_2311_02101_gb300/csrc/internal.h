@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "maxsat.h"
@@ -142,5 +143,18 @@ cudaError_t launch_advance(uint32_t* tdev, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t st);
 cudaError_t launch_transpose_in(const uint8_t* assign, int B, int n, uint8_t* xt, int Bp,
                                 cudaStream_t st);
+
+// dense.cu: tensor-core path
+bool fp8_encode_int(int v, bool e5m2, uint8_t* out);
+std::string build_gather_matrix(int n, int m, const int64_t* off, const int32_t* lits,
+                                bool* e5m2, int* n_pad, int* m_pad, std::vector<uint8_t>* A);
+std::string make_tmap_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows,
+                         uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows, bool bf16);
+cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
+                              int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
+                              const int64_t* row_w, int64_t* part, int32_t* tickets,
+                              int64_t* out, int* err, cudaStream_t st);
+cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
+                              uint8_t* X, cudaStream_t st);
 
 }  // namespace rbmsat

@@ -147,6 +147,31 @@ def test_eval_mixed_lengths_weighted(ms, stream, golden_table):
     ms.maxsat_destroy(ctx)
 
 
+@pytest.mark.parametrize("which", ["edge", "mixed12", "w3sat"])
+def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which):
+    """FP8 tensor-core gather (pattern-encoding matrix, tcgen05) against the
+    literal-by-literal oracle: E4M3 operands up to length 9, E5M2 beyond."""
+    import torch
+    if which == "edge":
+        inst, table, J, B = edge_instance(2), small_table, 1, 200
+    elif which == "mixed12":
+        inst, table, J, B = inst_of(workloads.mixed_length(n=1500, m=7000, seed=4)), golden_table, 4, 300
+    else:
+        inst, table, J, B = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0)), golden_table, 4, 4096
+    ctx = make_ctx(ms, stream, inst, table, n_buckets=J, path=ms.MAXSAT_PATH_DENSE)
+    assert ms.maxsat_get_path(ctx) == ms.MAXSAT_PATH_DENSE
+    rng = np.random.default_rng(5)
+    for rep in range(2):
+        X = rng.integers(0, 2, size=(B, inst.n)).astype(np.uint8)
+        with torch.cuda.stream(stream):
+            xd = torch.from_numpy(X).cuda()
+            cd = torch.full((B,), -1, dtype=torch.int64, device="cuda")
+        ms.maxsat_eval(ctx, xd, cd)
+        stream.synchronize()
+        assert np.array_equal(cd.cpu().numpy(), oracle.evaluate(inst, X)), rep
+    ms.maxsat_destroy(ctx)
+
+
 # --------------------------------------------------------------------------
 # Gibbs trajectories
 # --------------------------------------------------------------------------
