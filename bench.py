@@ -280,6 +280,8 @@ def run_mine(args):
         v, threads, sample, _ = oracle_rate(n, off, lits, w, B, args.cpu_seconds, seed)
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
 
+    dense_eval = dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
+
     S = params.steps_per_graph
     launches_timed = 2 * args.steps + (args.steps // S if S else 0)
     path = {1: "dense", 2: "sparse"}[ms.maxsat_get_path(ctx)]
@@ -291,13 +293,49 @@ def run_mine(args):
                             l2="working set above L2 (no flush): G/hidden state, nu and "
                                "x of 4096 chains; state carried step to step"),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
-                gpu_launches=launches_timed)
+                gpu_launches=launches_timed, dense_eval=dense_eval)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args):
+    """Exact cost evaluation of B random assignments on the FP8 tensor-core
+    gather (maxsat_eval on the dense path): per-launch device time from CUDA
+    events, against the FP8 dense peak (measured BF16 peak x 2, the nominal
+    FP8 / BF16 ratio)."""
+    m = len(off) - 1
+    p = ms.maxsat_default_params(sets=sets, path=ms.MAXSAT_PATH_DENSE)
+    try:
+        ctx = ms.maxsat_create(n, off, lits, w, p, stream)
+    except ms.MaxsatError as e:
+        return dict(unavailable=str(e))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    with torch.cuda.stream(stream):
+        X = torch.randint(0, 2, (B, n), dtype=torch.uint8, device="cuda", generator=g)
+        cost = torch.zeros(B, dtype=torch.int64, device="cuda")
+    for _ in range(5):
+        ms.maxsat_eval(ctx, X, cost)
+    reps = max(20, min(500, args.steps))
+    ms.maxsat_set_profiling(ctx, True)
+    for _ in range(reps):
+        ms.maxsat_eval(ctx, X, cost)
+    kt = ms.maxsat_kernel_times(ctx)
+    ms.maxsat_set_profiling(ctx, False)
+    ms.maxsat_destroy(ctx)
+    launches, tot = kt["gemm1_eval"]
+    avg = tot / launches / 1e3
+    flops = 2.0 * m * n * B
+    peaks, src = measured_peaks()
+    fp8_peak = 2.0 * peaks["bf16_tflops"]
+    return dict(kernel="gemm1_eval (tcgen05 kind::f8f6f4)", avg_launch_us=avg * 1e6,
+                evals_per_s=m * B / avg, achieved_tflops=flops / avg / 1e12, peak_tflops=fp8_peak,
+                frac=flops / avg / 1e12 / fp8_peak, bound="tensor",
+                peak_source=f"{src} BF16 burst x 2 (nominal FP8/BF16 ratio)",
+                flops_per_launch=flops)
 
 
 def ms_kernel_hash():

@@ -90,6 +90,7 @@ struct maxsat_ctx {
   uint8_t* dA = nullptr;          // m_pad x n_pad FP8 pattern-encoding gather matrix
   int32_t* d_row_len = nullptr;   // m_pad clause lengths (0 for padding rows)
   int64_t* d_row_w = nullptr;     // m_pad weights (0 for padding rows)
+  uint8_t* d_grp_small = nullptr; // per 32-row group: 1 when its rows share one weight
   CUtensorMap tmA{};
   uint8_t* dXe = nullptr;         // eval scratch: Bp x n_pad FP8 states
   int64_t* d_epart = nullptr;     // eval scratch: (m_pad / 128) x Bp partial costs
@@ -538,12 +539,22 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
       rl[c] = (int32_t)(off[c + 1] - off[c]);
       rw[c] = weights ? weights[c] : 1;
     }
+    // per 32-row group: 1 when all its rows carry the same weight
+    std::vector<uint8_t> small(ctx->m_pad / 32, 0);
+    for (int g = 0; g < ctx->m_pad / 32; ++g) {
+      bool same = true;
+      for (int r = 1; r < 32; ++r) same = same && rw[g * 32 + r] == rw[g * 32];
+      small[g] = same ? 1 : 0;
+    }
     const uint8_t* dA = nullptr;
     const int32_t* drl = nullptr;
     const int64_t* drw = nullptr;
+    const uint8_t* dsm = nullptr;
     UP2(Ah, dA);
     UP2(rl, drl);
     UP2(rw, drw);
+    UP2(small, dsm);
+    ctx->d_grp_small = const_cast<uint8_t*>(dsm);
     ctx->dA = const_cast<uint8_t*>(dA);
     ctx->d_row_len = const_cast<int32_t*>(drl);
     ctx->d_row_w = const_cast<int64_t*>(drw);
@@ -664,16 +675,16 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
   if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
   if (B == 0) return MAXSAT_OK;
   if (ctx->dense) {
-    const int Bp = (B + 127) / 128 * 128;
+    const int Bp = (B + 255) / 256 * 256;
     if (Bp > ctx->dev_Bp) {
       // grow the eval scratch (cudaFree of the old one synchronises the device)
       ctx->dense_eval_mem.release();
       ctx->dev_Bp = 0;
       CK(ctx, ctx->dense_eval_mem.alloc(&ctx->dXe, (size_t)Bp * ctx->n_pad));
       CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_epart, (size_t)(ctx->m_pad / 128) * Bp));
-      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_etick, Bp / 128));
-      CK(ctx, cudaMemsetAsync(ctx->d_etick, 0, sizeof(int32_t) * (Bp / 128), ctx->stream));
-      std::string e = make_tmap_2d(&ctx->tmXe, ctx->dXe, ctx->n_pad, Bp, ctx->n_pad, 128, 128, false);
+      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_etick, Bp / 256));
+      CK(ctx, cudaMemsetAsync(ctx->d_etick, 0, sizeof(int32_t) * (Bp / 256), ctx->stream));
+      std::string e = make_tmap_2d(&ctx->tmXe, ctx->dXe, ctx->n_pad, Bp, ctx->n_pad, 128, 256, false);
       if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
       ctx->dev_Bp = Bp;
     }
@@ -681,8 +692,8 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
     CK(ctx, launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, ctx->stream));
     TIMED(ctx, ctx->stream, "gemm1_eval",
           launch_gemm1_eval(ctx->tmA, ctx->tmXe, ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
-                            ctx->d_row_len, ctx->d_row_w, ctx->d_epart, ctx->d_etick, cost_dev,
-                            ctx->d_err, ctx->stream));
+                            ctx->d_row_len, ctx->d_row_w, ctx->d_grp_small, ctx->d_epart,
+                            ctx->d_etick, cost_dev, ctx->d_err, ctx->stream));
     return MAXSAT_OK;
   }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;

@@ -29,6 +29,7 @@
 // host reads after the launch, and the kernel still releases its TMEM.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -41,35 +42,76 @@ namespace rbmsat {
 
 namespace {
 
-constexpr int kBM = 128;          // clauses per tile
-constexpr int kBN = 128;          // chains per tile
+constexpr int kBM = 128;          // clauses per tile (TMEM lanes)
+constexpr int kBN = 256;          // chains per tile (TMEM columns per accumulator)
 constexpr int kBK = 128;          // FP8 elements (bytes) per K-block: one 128-byte swizzle row
 constexpr int kStages = 4;
 constexpr int kStageA = kBM * kBK;  // 16 KB
-constexpr int kStageB = kBN * kBK;  // 16 KB
-constexpr int kThreads = 192;
+constexpr int kStageB = kBN * kBK;  // 32 KB
+constexpr int kEpiWarps = 8;  // epilogue warps (two per TMEM lane quarter)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct Gemm1Smem {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t accum;
+  uint64_t full[kStages];   // TMA -> MMA: stage loaded
+  uint64_t empty[kStages];  // MMA -> TMA: stage consumed
+  uint64_t tfull[2];        // MMA -> epilogue: accumulator buffer ready
+  uint64_t tempty[2];       // epilogue -> MMA: accumulator buffer drained
   uint32_t tmem_slot;
-  int last;
-  int64_t cost[4][kBN];
+  int64_t cost[2][4 * kBN];  // per tile parity and epilogue warp: its rows' column sums
+  int64_t w[8][32];       // per epilogue warp: the weights of its 32 rows
 };
 
 constexpr int kGemm1Smem = 1024 + kStages * (kStageA + kStageB) + (int)sizeof(Gemm1Smem);
 
+template <int EPI_THREADS>
 __device__ __forceinline__ void epi_bar() {
-  asm volatile("bar.sync 1, 128;" ::: "memory");
+  asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
 }
 
-// EVAL: weighted unsatisfied cost per chain.
-__global__ void __launch_bounds__(kThreads, 1)
+// 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit q =
+// column q); afterwards lane q holds column q (bit i = row i). Five stages
+// swap the off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int j = 16 >> st;
+    const uint32_t mk = masks[st];
+    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    x = (lane & j) ? ((x & ~mk) | ((other >> j) & mk)) : ((x & mk) | ((other & mk) << j));
+  }
+  return x;
+}
+
+// Warp transpose-reduce: lane l holds v[0..31] (one value per column of its
+// row); afterwards v[0] of lane l is the sum over the 32 lanes of column l.
+// Five halving levels, 31 shuffles in total.
+template <typename T>
+__device__ __forceinline__ T column_sums32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int level = 0; level < 5; ++level) {
+    const int half = 16 >> level;
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const T send = upper ? v[i] : v[i + half];
+      const T keep = upper ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, half);
+    }
+  }
+  return v[0];
+}
+
+// Persistent gather GEMM: each CTA walks the tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ... (chain tile fastest). EVAL epilogue: weighted unsatisfied
+// cost per chain. Two TMEM accumulators (2 x 256 columns) let the epilogue of
+// one tile overlap the MMAs of the next.
+template <int EPI>
+__global__ void __launch_bounds__(64 + 32 * EPI, 1)
     k_gemm1_eval(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 int m, int num_kb, int B, int Bp, uint32_t idesc, const int32_t* __restrict__ row_len,
-                 const int64_t* __restrict__ row_w, int64_t* __restrict__ part,
+                 int m, int num_kb, int tiles_m, int tiles_n, int B, int Bp, uint32_t idesc,
+                 const int32_t* __restrict__ row_len, const int64_t* __restrict__ row_w,
+                 const uint8_t* __restrict__ grp_small, int64_t* __restrict__ part,
                  int32_t* __restrict__ tickets, int64_t* __restrict__ out, int* err) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -78,21 +120,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sB = tiles + kStages * kStageA;
   Gemm1Smem& S = *reinterpret_cast<Gemm1Smem*>(tiles + kStages * (kStageA + kStageB));
 
+  static_assert(EPI == 4 || EPI == 8, "4 or 8 epilogue warps");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile_n = blockIdx.x, tile_m = blockIdx.y;
+  const int num_tiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&S.full[s], 1);
       tc::mbar_init(&S.empty[s], 1);
     }
-    tc::mbar_init(&S.accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&S.tfull[b], 1);
+      tc::mbar_init(&S.tempty[b], EPI);
+    }
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmA);
     tc::prefetch_tmap(&tmB);
   }
   if (warp == 1) {
-    tc::tmem_alloc(&S.tmem_slot, kBN);
+    tc::tmem_alloc(&S.tmem_slot, 2 * kBN);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -102,88 +148,136 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < num_kb; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-        if (!tc::mbar_wait(&S.empty[s], ph ^ 1u, err, 1, kWaitCycles)) break;
-        tc::mbar_arrive_expect_tx(&S.full[s], kStageA + kStageB);
-        tc::tma_load_2d(sA + s * kStageA, &tmA, &S.full[s], kb * kBK, tile_m * kBM);
-        tc::tma_load_2d(sB + s * kStageB, &tmB, &S.full[s], kb * kBK, tile_n * kBN);
+      uint32_t g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int tm = tile / tiles_n, tn = tile % tiles_n;
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t ph = (g / kStages) & 1u;
+          ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, err, 1, kWaitCycles);
+          if (!ok) break;
+          tc::mbar_arrive_expect_tx(&S.full[s], kStageA + kStageB);
+          tc::tma_load_2d(sA + s * kStageA, &tmA, &S.full[s], kb * kBK, tm * kBM);
+          tc::tma_load_2d(sB + s * kStageB, &tmB, &S.full[s], kb * kBK, tn * kBN);
+        }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
+      uint32_t g = 0;
       bool ok = true;
-      for (int kb = 0; kb < num_kb && ok; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
-        ok = tc::mbar_wait(&S.full[s], ph, err, 2, kWaitCycles);
+      int li = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++li) {
+        const int buf = li & 1;
+        const uint32_t use = (uint32_t)(li >> 1);
+        ok = tc::mbar_wait(&S.tempty[buf], (use & 1u) ^ 1u, err, 4, kWaitCycles);
         if (!ok) break;
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_u32(sA + s * kStageA), b0 = tc::smem_u32(sB + s * kStageB);
+        const uint32_t d = tmem + (uint32_t)(buf * kBN);
+        for (int kb = 0; kb < num_kb; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t ph = (g / kStages) & 1u;
+          ok = tc::mbar_wait(&S.full[s], ph, err, 2, kWaitCycles);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sA + s * kStageA), b0 = tc::smem_u32(sB + s * kStageB);
 #pragma unroll
-        for (int kk = 0; kk < kBK / 32; ++kk)
-          tc::mma<true>(tmem, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), idesc,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
-        tc::commit(&S.empty[s]);
+          for (int kk = 0; kk < kBK / 32; ++kk)
+            tc::mma<true>(d, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), idesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::commit(&S.empty[s]);
+        }
+        tc::commit(&S.tfull[buf]);
       }
-      tc::commit(&S.accum);
     }
     __syncwarp();
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps: TMEM lane quarter = warp % 4; with 8 warps the two
+    // warps of a quarter split the columns
+    constexpr int kCols = kBN * 4 / EPI;  // columns per epilogue warp
     const int quarter = warp & 3;
     const int ew = warp - 2;
-    const int row = quarter * 32 + lane;
-    const int c = tile_m * kBM + row;
-    const int len = c < m ? __ldg(row_len + c) : 0;
-    const int64_t w = c < m ? __ldg(row_w + c) : 0;
-    const int bias = (1 << len) - 1;
-    const uint32_t wlo = (uint32_t)(w & 0xFFFF), whi = (uint32_t)(w >> 16);
-    const bool ok = tc::mbar_wait(&S.accum, 0, err, 3, kWaitCycles);
-    tc::fence_after_sync();
-    for (int j = 0; j < kBN / 32; ++j) {
-      uint32_t r[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(j * 32), r);
-      tc::tmem_ld_wait();
+    const int half = ew / 4;              // 0, or 1 for the second warp of a quarter
+    const int t = threadIdx.x - 64;       // 0 .. 32 EPI - 1
+    int li = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
+      const int tm = tile / tiles_n, tn = tile % tiles_n;
+      const int buf = li & 1;
+      const int row = quarter * 32 + lane;
+      const int c = tm * kBM + row;
+      const int len = c < m ? __ldg(row_len + c) : 0;
+      const int64_t w = c < m ? __ldg(row_w + c) : 0;
+      const int bias = (1 << len) - 1;
+      // rows of one warp that share a weight let a popcount replace the sum
+      const bool uniform = __ldg(grp_small + tm * 4 + quarter) != 0;
+      const float unsat_d = -(float)bias;  // D of a clause with no true literal
+      S.w[ew][lane] = w;
+      __syncwarp();
+      const bool ok = tc::mbar_wait(&S.tfull[buf], (uint32_t)(li >> 1) & 1u, err, 3, kWaitCycles);
+      tc::fence_after_sync();
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                             (uint32_t)(buf * kBN + half * kCols);
+      for (int j = 0; j < kCols / 32; ++j) {
+        uint32_t r[32];
+        tc::tmem_ld32(taddr + (uint32_t)(j * 32), r);
+        tc::tmem_ld_wait();
+        uint32_t unsat = 0;  // bit q: column q unsatisfied for this row
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int d = __float2int_rn(__uint_as_float(r[q]));
-        const bool unsat = ok && ((d + bias) >> 1) == 0;
-        const uint32_t lo = __reduce_add_sync(0xFFFFFFFFu, unsat ? wlo : 0u);
-        const uint32_t hi = __reduce_add_sync(0xFFFFFFFFu, unsat ? whi : 0u);
-        if (lane == 0) S.cost[ew][j * 32 + q] = (int64_t)lo + ((int64_t)hi << 16);
+        for (int q = 0; q < 32; ++q) unsat |= (uint32_t)(__uint_as_float(r[q]) == unsat_d) << q;
+        if (!ok) unsat = 0;
+        uint32_t rows = transpose32(unsat, lane);  // lane = column: its unsatisfied rows
+        int64_t col;
+        if (uniform) {
+          col = (int64_t)__popc(rows) * S.w[ew][0];
+        } else {
+          col = 0;
+          while (rows) {
+            col += S.w[ew][__ffs(rows) - 1];
+            rows &= rows - 1;
+          }
+        }
+        S.cost[buf][ew * kCols + j * 32 + lane] = col;
       }
-    }
-    tc::fence_before_sync();
-    epi_bar();
-    const int t = threadIdx.x - 64;  // 0..127
-    const int64_t csum = S.cost[0][t] + S.cost[1][t] + S.cost[2][t] + S.cost[3][t];
-    part[(size_t)tile_m * Bp + (size_t)tile_n * kBN + t] = csum;
-    __threadfence();
-    epi_bar();
-    if (t == 0) S.last = atomicAdd(tickets + tile_n, 1) == (int)gridDim.y - 1;
-    epi_bar();
-    if (S.last) {
-      __threadfence();
-      const int b = tile_n * kBN + t;
-      int64_t tot = 0;
-      for (int k = 0; k < (int)gridDim.y; ++k) tot += __ldcg(part + (size_t)k * Bp + b);
-      if (b < B) out[b] = tot;
-      if (t == 0) tickets[tile_n] = 0;
+      // accumulator drained: hand the buffer back to the MMA warp
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&S.tempty[buf]))
+                     : "memory");
+      // one barrier per tile: the column sums are double-buffered by tile
+      // parity, so the next tile writes the other buffer while this one is read
+      epi_bar<32 * EPI>();
+      for (int col = t; col < kBN; col += 32 * EPI) {
+        const int h = col / kCols, cc = col % kCols;  // which warp of each quarter
+        int64_t csum = 0;
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) csum += S.cost[buf][(h * 4 + qd) * kCols + cc];
+        part[(size_t)tm * Bp + (size_t)tn * kBN + col] = csum;
+      }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, kBN);
+    tc::tmem_dealloc(tmem, 2 * kBN);
   }
 }
 
 // assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
 // variables, 0 for padding variables and padding chains.
+// Sum of the per-tile partial costs, in tile order (deterministic).
+__global__ void k_sum_tiles(const int64_t* __restrict__ part, int tiles_m, int Bp, int B,
+                            int64_t* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int64_t tot = 0;
+  for (int k = 0; k < tiles_m; ++k) tot += part[(size_t)k * Bp + b];
+  out[b] = tot;
+}
+
 __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, int Bp, int n_pad,
                              uint8_t one, uint8_t minus_one, uint8_t* __restrict__ X) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,20 +385,31 @@ std::string build_gather_matrix(int n, int m, const int64_t* off, const int32_t*
 
 cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
-                              const int64_t* row_w, int64_t* part, int32_t* tickets,
-                              int64_t* out, int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm1_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGemm1Smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+                              const int64_t* row_w, const uint8_t* grp_small, int64_t* part,
+                              int32_t* tickets, int64_t* out, int* err, cudaStream_t st) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gemm1_eval<kEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kGemm1Smem);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
   }
   const uint32_t fmt = e5m2 ? 1u : 0u;
   const uint32_t idesc = tc::instr_desc(kBM, kBN, fmt, fmt);
-  dim3 grid(Bp / kBN, m_pad / kBM);
-  k_gemm1_eval<<<grid, kThreads, kGemm1Smem, st>>>(tmA, tmB, m, n_pad / kBK, B, Bp, idesc, row_len,
-                                                   row_w, part, tickets, out, err);
+  const int tiles_m = m_pad / kBM, tiles_n = Bp / kBN;
+  const int grid = std::min(sms, tiles_m * tiles_n);
+  k_gemm1_eval<kEpiWarps><<<grid, 64 + 32 * kEpiWarps, kGemm1Smem, st>>>(tmA, tmB, m, n_pad / kBK, tiles_m, tiles_n, B,
+                                                   Bp, idesc, row_len, row_w, grp_small, part,
+                                                   tickets, out, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_tiles<<<(B + 255) / 256, 256, 0, st>>>(part, tiles_m, Bp, B, out);
   return cudaGetLastError();
 }
 

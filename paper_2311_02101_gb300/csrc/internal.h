@@ -152,8 +152,8 @@ std::string make_tmap_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint
                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows, bool bf16);
 cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
-                              const int64_t* row_w, int64_t* part, int32_t* tickets,
-                              int64_t* out, int* err, cudaStream_t st);
+                              const int64_t* row_w, const uint8_t* grp_small, int64_t* part,
+                              int32_t* tickets, int64_t* out, int* err, cudaStream_t st);
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
                               uint8_t* X, cudaStream_t st);
 

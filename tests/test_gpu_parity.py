@@ -147,7 +147,7 @@ def test_eval_mixed_lengths_weighted(ms, stream, golden_table):
     ms.maxsat_destroy(ctx)
 
 
-@pytest.mark.parametrize("which", ["edge", "mixed12", "w3sat"])
+@pytest.mark.parametrize("which", ["edge", "mixed12", "w3sat", "u3sat"])
 def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which):
     """FP8 tensor-core gather (pattern-encoding matrix, tcgen05) against the
     literal-by-literal oracle: E4M3 operands up to length 9, E5M2 beyond."""
@@ -156,8 +156,10 @@ def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which)
         inst, table, J, B = edge_instance(2), small_table, 1, 200
     elif which == "mixed12":
         inst, table, J, B = inst_of(workloads.mixed_length(n=1500, m=7000, seed=4)), golden_table, 4, 300
-    else:
+    elif which == "w3sat":
         inst, table, J, B = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0)), golden_table, 4, 4096
+    else:  # unweighted: every 32-row group shares one weight
+        inst, table, J, B = inst_of(workloads.random_ksat(300, 1290, 3, seed=8)), small_table, 1, 700
     ctx = make_ctx(ms, stream, inst, table, n_buckets=J, path=ms.MAXSAT_PATH_DENSE)
     assert ms.maxsat_get_path(ctx) == ms.MAXSAT_PATH_DENSE
     rng = np.random.default_rng(5)
