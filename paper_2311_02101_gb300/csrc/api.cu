@@ -98,6 +98,19 @@ struct maxsat_ctx {
   int dev_Bp = 0;
   CUtensorMap tmXe{};
   int* d_err = nullptr;           // device wait-timeout code (0 = none)
+  // dense scatter-add (GEMM2): block-diagonal variable x incidence matrix
+  int tiles_v = 0, kmax = 0;
+  bool g_bf16 = true;             // G operand BF16 (else FP16)
+  int32_t* d_kstart = nullptr;    // tiles_v + 1
+  int32_t* d_kblocks = nullptr;   // tiles_v
+  CUtensorMap tmA2{};
+  // dense chain state
+  uint8_t* dX = nullptr;          // Bp x n_pad FP8 +-1
+  float* dnu = nullptr;           // Bp x n_pad
+  uint8_t* dbest_x = nullptr;     // Bp x n_pad 0/1
+  int64_t* dcost_part = nullptr;  // tiles_m x Bp
+  float* dfe_part = nullptr;      // tiles_m x Bp
+  CUtensorMap tmX{};
 
   // per-kernel CUDA-event timing of plain launches
   bool profiling = false;
@@ -191,6 +204,20 @@ int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
 // One Gibbs round: absolute index t = (tdev ? *tdev : 0) + t_rel.
 int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_t t_rel) {
   const DevChains& C = ctx->C;
+  if (ctx->dense) {
+    TIMED(ctx, st, "gemm1_step",
+          launch_gemm1_step(true, ctx->tmA, ctx->tmX, ctx->m, ctx->m_pad, ctx->n_pad, C.B, C.Bp,
+                            ctx->e5m2, ctx->d_row_len, ctx->d_row_w, ctx->F.cl_grp,
+                            ctx->d_grp_small, ctx->dcost_part, ctx->dfe_part, C.H, ctx->wide_h,
+                            tdev, t_rel, ctx->d_err, ctx->T, C, st));
+    TIMED(ctx, st, "keep", launch_keep_dense(ctx->dcost_part, ctx->dfe_part, ctx->m_pad / 128, C, st));
+    TIMED(ctx, st, "gemm2",
+          launch_gemm2(ctx->tmA2, ctx->n, ctx->n_pad, C.B, C.Bp, ctx->tiles_v, ctx->d_kstart,
+                       ctx->d_kblocks, ctx->F.var_inc, C.H, ctx->wide_h, ctx->dX, ctx->dnu,
+                       ctx->dbest_x, ctx->e5m2, ctx->g_bf16, (float)ctx->prm.alpha, tdev, t_rel,
+                       ctx->d_err, ctx->T, C, st));
+    return MAXSAT_OK;
+  }
   TIMED(ctx, st, "gather_hidden",
         launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, tdev, t_rel, C.cost_part,
                       C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
@@ -236,6 +263,25 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   C.B = B;
   C.Bp = Bp;
   DevAllocs& A = ctx->chain_mem;
+  if (ctx->dense) {
+    const size_t nP = (size_t)ctx->n_pad * Bp;
+    const int tiles_m = ctx->m_pad / 128;
+    CK(ctx, A.alloc(&ctx->dX, nP));
+    CK(ctx, A.alloc(&ctx->dnu, nP));
+    CK(ctx, A.alloc(&ctx->dbest_x, nP));
+    CK(ctx, A.alloc(&ctx->dcost_part, (size_t)tiles_m * Bp));
+    CK(ctx, A.alloc(&ctx->dfe_part, (size_t)tiles_m * Bp));
+    CK(ctx, A.alloc(&C.best, Bp));
+    CK(ctx, A.alloc(&C.cost, Bp));
+    CK(ctx, A.alloc(&C.fe, Bp));
+    CK(ctx, A.alloc(&C.improved, Bp));
+    uint8_t* H = nullptr;
+    CK(ctx, A.alloc(&H, (size_t)std::max(ctx->m, 1) * Bp * (ctx->wide_h ? 2 : 1)));
+    C.H = H;
+    std::string e = make_tmap_2d(&ctx->tmX, ctx->dX, ctx->n_pad, Bp, ctx->n_pad, 128, 256, false);
+    if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
+    return MAXSAT_OK;
+  }
   CK(ctx, A.alloc(&C.xt, nB));
   CK(ctx, A.alloc(&C.nu, nB));
   CK(ctx, A.alloc(&C.best, Bp));
@@ -254,6 +300,16 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
 
 // Copies h to a new device buffer padded with zeros to a multiple of 16 bytes
 // (kernels stage tables into shared memory 16 bytes at a time).
+// Reads the kernels' wait-timeout code (call after synchronising the stream).
+int check_device_error(maxsat_ctx* ctx) {
+  int code = 0;
+  CK(ctx, cudaMemcpy(&code, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code != 0)
+    return fail(ctx, MAXSAT_ECUDA, "a tensor-core pipeline wait timed out (code " +
+                                       std::to_string(code) + "); results are invalid");
+  return MAXSAT_OK;
+}
+
 template <class T>
 int upload(maxsat_ctx* ctx, DevAllocs& A, std::vector<T> h, const T** out) {
   while ((h.size() * sizeof(T)) % 16 != 0 || h.empty()) h.push_back(T{});
@@ -563,6 +619,44 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
       delete ctx;
       return fail(nullptr, MAXSAT_ECUDA, derr);
     }
+    // scatter-add operands: G values exact in BF16 up to 256, in FP16 up to
+    // 2048; the FP32 accumulator exact while |2^Q z| < 2^24
+    const int gmax = ctx->tabs.gq_absmax;
+    if (gmax > 2048 || (int64_t)ctx->max_degree * gmax >= ((int64_t)1 << 24)) {
+      delete ctx;
+      return fail(nullptr, MAXSAT_EINVAL, "scatter-add contributions are not exact in FP16 / FP32");
+    }
+    ctx->g_bf16 = gmax <= 256;
+    ctx->tiles_v = ctx->n_pad / 128;
+    std::vector<int32_t> kst(ctx->tiles_v + 1), kbl(ctx->tiles_v);
+    for (int tv = 0; tv <= ctx->tiles_v; ++tv) kst[tv] = var_off[std::min(tv * 128, n)];
+    int kbmax = 1;
+    for (int tv = 0; tv < ctx->tiles_v; ++tv) {
+      kbl[tv] = std::max(1, (kst[tv + 1] - kst[tv] + 63) / 64);
+      kbmax = std::max(kbmax, kbl[tv]);
+    }
+    ctx->kmax = kbmax * 64;
+    const uint16_t plus = ctx->g_bf16 ? 0x3F80 : 0x3C00, minus = ctx->g_bf16 ? 0xBF80 : 0xBC00;
+    std::vector<uint16_t> A2((size_t)ctx->tiles_v * 128 * ctx->kmax, 0);
+    for (int i = 0; i < n; ++i) {
+      const int tv = i / 128;
+      for (int jj = var_off[i]; jj < var_off[i + 1]; ++jj)
+        A2[(size_t)i * ctx->kmax + (jj - kst[tv])] = var_inc[jj].y < 0 ? minus : plus;
+    }
+    const uint16_t* dA2 = nullptr;
+    const int32_t* dks = nullptr;
+    const int32_t* dkb = nullptr;
+    UP2(A2, dA2);
+    UP2(kst, dks);
+    UP2(kbl, dkb);
+    ctx->d_kstart = const_cast<int32_t*>(dks);
+    ctx->d_kblocks = const_cast<int32_t*>(dkb);
+    derr = make_tmap_2d(&ctx->tmA2, dA2, ctx->kmax, (uint64_t)ctx->tiles_v * 128,
+                        (uint64_t)ctx->kmax * 2, 64, 128, true);
+    if (!derr.empty()) {
+      delete ctx;
+      return fail(nullptr, MAXSAT_ECUDA, derr);
+    }
     ctx->dense = true;
   }
   *out = ctx;
@@ -581,7 +675,11 @@ int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
   ctx->seed = seed;
   ctx->t = 0;
   ctx->d_t_synced = false;
-  CK(ctx, launch_init_sparse(ctx->C, ctx->n, ctx->stream));
+  if (ctx->dense)
+    CK(ctx, launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n, ctx->n_pad,
+                              ctx->e5m2, ctx->stream));
+  else
+    CK(ctx, launch_init_sparse(ctx->C, ctx->n, ctx->stream));
   ctx->have_chains = true;
   return MAXSAT_OK;
 }
@@ -620,6 +718,18 @@ int maxsat_score(maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_score before maxsat_reset");
   const DevChains& C = ctx->C;
+  if (ctx->dense) {
+    cudaStream_t st = ctx->stream;
+    TIMED(ctx, st, "gemm1_score",
+          launch_gemm1_step(false, ctx->tmA, ctx->tmX, ctx->m, ctx->m_pad, ctx->n_pad, C.B, C.Bp,
+                            ctx->e5m2, ctx->d_row_len, ctx->d_row_w, ctx->F.cl_grp,
+                            ctx->d_grp_small, ctx->dcost_part, ctx->dfe_part, C.H, ctx->wide_h,
+                            nullptr, 0, ctx->d_err, ctx->T, C, st));
+    TIMED(ctx, st, "keep", launch_keep_dense(ctx->dcost_part, ctx->dfe_part, ctx->m_pad / 128, C, st));
+    TIMED(ctx, st, "keep_copy",
+          launch_keep_copy_dense(C, ctx->dX, ctx->dbest_x, ctx->n, ctx->n_pad, ctx->e5m2, st));
+    return MAXSAT_OK;
+  }
   TIMED(ctx, ctx->stream, "gather_score",
         launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, nullptr, 0, C.cost_part,
                       C.fe_part, C.tickets, nullptr, ctx->wide_h, ctx->stream));
@@ -728,10 +838,15 @@ int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
     if (best[b] < best[bstar]) bstar = b;
   if (best_cost) *best_cost = best[bstar];
   if (best_assign) {
-    CK(ctx, cudaMemcpy2DAsync(best_assign, 1, ctx->C.best_xt + bstar, ctx->C.Bp, 1, ctx->n,
+    if (ctx->dense)
+      CK(ctx, cudaMemcpyAsync(best_assign, ctx->dbest_x + (size_t)bstar * ctx->n_pad, ctx->n,
                               cudaMemcpyDeviceToHost, ctx->stream));
+    else
+      CK(ctx, cudaMemcpy2DAsync(best_assign, 1, ctx->C.best_xt + bstar, ctx->C.Bp, 1, ctx->n,
+                                cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
   }
+  if (ctx->dense) return check_device_error(ctx);
   return MAXSAT_OK;
 }
 
@@ -741,6 +856,34 @@ int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "no chains (call maxsat_reset)");
   const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
   const size_t nB = (size_t)n * Bp;
+  if (ctx->dense) {
+    const int np = ctx->n_pad;
+    uint8_t one;
+    fp8_encode_int(1, ctx->e5m2, &one);
+    auto fetch_rows = [&](const void* dsrc, size_t elem, void* dst, bool fp8) -> int {
+      std::vector<uint8_t> h((size_t)np * Bp * elem);
+      CK(ctx, cudaMemcpyAsync(h.data(), dsrc, h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(ctx, cudaStreamSynchronize(ctx->stream));
+      uint8_t* d = static_cast<uint8_t*>(dst);
+      for (int b = 0; b < B; ++b)
+        for (int i = 0; i < n; ++i) {
+          const uint8_t* src = h.data() + ((size_t)b * np + i) * elem;
+          if (fp8) d[(size_t)b * n + i] = *src == one ? 1 : 0;
+          else std::memcpy(d + ((size_t)b * n + i) * elem, src, elem);
+        }
+      return MAXSAT_OK;
+    };
+    int rc2;
+    if (x && (rc2 = fetch_rows(ctx->dX, 1, x, true)) != MAXSAT_OK) return rc2;
+    if (nu && (rc2 = fetch_rows(ctx->dnu, 4, nu, false)) != MAXSAT_OK) return rc2;
+    if (best_x && (rc2 = fetch_rows(ctx->dbest_x, 1, best_x, false)) != MAXSAT_OK) return rc2;
+    if (best_cost) CK(ctx, cudaMemcpyAsync(best_cost, ctx->C.best, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cost) CK(ctx, cudaMemcpyAsync(cost, ctx->C.cost, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+    if (free_energy) CK(ctx, cudaMemcpyAsync(free_energy, ctx->C.fe, 4 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (t) *t = ctx->t;
+    return check_device_error(ctx);
+  }
   auto fetch_T = [&](const void* dsrc, size_t elem, void* dst) -> int {
     std::vector<uint8_t> h(nB * elem);
     CK(ctx, cudaMemcpyAsync(h.data(), dsrc, nB * elem, cudaMemcpyDeviceToHost, ctx->stream));
@@ -773,6 +916,34 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t B, uint64_t seed, const uint8_t* x
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   const int Bp = ctx->C.Bp, n = ctx->n;
   const size_t nB = (size_t)n * Bp;
+  if (ctx->dense) {
+    const int np = ctx->n_pad;
+    uint8_t one, minus_one;
+    fp8_encode_int(1, ctx->e5m2, &one);
+    fp8_encode_int(-1, ctx->e5m2, &minus_one);
+    auto put_rows = [&](void* ddst, size_t elem, const void* src, int kind) -> int {
+      std::vector<uint8_t> h((size_t)np * Bp * elem);
+      CK(ctx, cudaMemcpy(h.data(), ddst, h.size(), cudaMemcpyDeviceToHost));
+      const uint8_t* sp = static_cast<const uint8_t*>(src);
+      for (int b = 0; b < B; ++b)
+        for (int i = 0; i < n; ++i) {
+          uint8_t* d = h.data() + ((size_t)b * np + i) * elem;
+          const uint8_t* v = sp + ((size_t)b * n + i) * elem;
+          if (kind == 1) *d = *v ? one : minus_one;      // FP8 state
+          else if (kind == 2) *d = *v ? 1 : 0;           // best assignment bytes
+          else std::memcpy(d, v, elem);                  // nu
+        }
+      CK(ctx, cudaMemcpy(ddst, h.data(), h.size(), cudaMemcpyHostToDevice));
+      return MAXSAT_OK;
+    };
+    if ((rc = put_rows(ctx->dX, 1, x, 1)) != MAXSAT_OK) return rc;
+    if ((rc = put_rows(ctx->dnu, 4, nu, 0)) != MAXSAT_OK) return rc;
+    if ((rc = put_rows(ctx->dbest_x, 1, best_x, 2)) != MAXSAT_OK) return rc;
+    CK(ctx, cudaMemcpy(ctx->C.best, best_cost, 8 * (size_t)B, cudaMemcpyHostToDevice));
+    ctx->t = t;
+    ctx->d_t_synced = false;
+    return MAXSAT_OK;
+  }
   auto put_T = [&](void* ddst, size_t elem, const void* src) -> int {
     std::vector<uint8_t> h(nB * elem);
     CK(ctx, cudaMemcpy(h.data(), ddst, nB * elem, cudaMemcpyDeviceToHost));

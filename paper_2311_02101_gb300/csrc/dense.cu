@@ -37,6 +37,7 @@
 
 #include "internal.h"
 #include "tc_ptx.cuh"
+#include "dense_common.cuh"
 
 namespace rbmsat {
 
@@ -62,45 +63,6 @@ struct Gemm1Smem {
 };
 
 constexpr int kGemm1Smem = 1024 + kStages * (kStageA + kStageB) + (int)sizeof(Gemm1Smem);
-
-template <int EPI_THREADS>
-__device__ __forceinline__ void epi_bar() {
-  asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-}
-
-// 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit q =
-// column q); afterwards lane q holds column q (bit i = row i). Five stages
-// swap the off-diagonal blocks of size 16, 8, 4, 2, 1.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int j = 16 >> st;
-    const uint32_t mk = masks[st];
-    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-    x = (lane & j) ? ((x & ~mk) | ((other >> j) & mk)) : ((x & mk) | ((other & mk) << j));
-  }
-  return x;
-}
-
-// Warp transpose-reduce: lane l holds v[0..31] (one value per column of its
-// row); afterwards v[0] of lane l is the sum over the 32 lanes of column l.
-// Five halving levels, 31 shuffles in total.
-template <typename T>
-__device__ __forceinline__ T column_sums32(T (&v)[32], int lane) {
-#pragma unroll
-  for (int level = 0; level < 5; ++level) {
-    const int half = 16 >> level;
-    const bool upper = (lane & half) != 0;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const T send = upper ? v[i] : v[i + half];
-      const T keep = upper ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, half);
-    }
-  }
-  return v[0];
-}
 
 // Persistent gather GEMM: each CTA walks the tiles blockIdx.x, blockIdx.x +
 // gridDim.x, ... (chain tile fastest). EVAL epilogue: weighted unsatisfied
@@ -227,7 +189,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
 #pragma unroll
         for (int q = 0; q < 32; ++q) unsat |= (uint32_t)(__uint_as_float(r[q]) == unsat_d) << q;
         if (!ok) unsat = 0;
-        uint32_t rows = transpose32(unsat, lane);  // lane = column: its unsatisfied rows
+        uint32_t rows = tc::transpose32(unsat, lane);  // lane = column: its unsatisfied rows
         int64_t col;
         if (uniform) {
           col = (int64_t)__popc(rows) * S.w[ew][0];
@@ -248,7 +210,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
                      : "memory");
       // one barrier per tile: the column sums are double-buffered by tile
       // parity, so the next tile writes the other buffer while this one is read
-      epi_bar<32 * EPI>();
+      tc::epi_bar<32 * EPI>();
       for (int col = t; col < kBN; col += 32 * EPI) {
         const int h = col / kCols, cc = col % kCols;  // which warp of each quarter
         int64_t csum = 0;

@@ -1,0 +1,759 @@
+// Dense tensor-core path of one Gibbs round (Sec. 4.3 "gather" and
+// "scatter-add" as matrix products).
+//
+//   k_gemm1_step  gather: the FP8 pattern-encoding clause matrix times the
+//                 +-1 chain states (tcgen05 kind::f8f6f4, see dense.cu); the
+//                 epilogue decodes each clause x chain truth pattern, sums
+//                 the weighted unsatisfied cost and the clause free energy
+//                 (Eq. 1) per chain over its 128 rows, draws the hidden units
+//                 (Eq. 2 / Eq. 6) and stores the hidden pattern (one byte per
+//                 clause and chain, as the sparse path).
+//   k_keep_dense  per chain: sums the per-tile partials in tile order and
+//                 keeps improvements (Sec. 4.2).
+//   k_gemm2       scatter-add: Z = P^T G, the variable x literal-incidence
+//                 matrix P^T (+-1, BF16 or FP16) times the per-literal
+//                 contributions G of the hidden patterns (Eq. 7). Incidences
+//                 are sorted by variable, so a tile of 128 variables only
+//                 spans its own incidence range: the product is
+//                 block-diagonal and each tile loops over its own K-blocks.
+//                 TMA loads P^T; 8 builder warps expand the hidden patterns
+//                 into the 128-byte-swizzled G tile in shared memory (table
+//                 lookups, no HBM round trip); one thread issues
+//                 tcgen05.mma kind::f16; 8 epilogue warps draw the new states
+//                 (Eq. 3), update nu (Sec. 4.4) and copy improved states into
+//                 the best-so-far.
+// State (dense layout): x as FP8 +-1, chains x n_pad (the B operand of the
+// gather); nu float and best x bytes in the same layout.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dense_common.cuh"
+#include "internal.h"
+#include "philox.cuh"
+#include "tc_ptx.cuh"
+
+namespace rbmsat {
+
+namespace {
+
+constexpr int kBM = 128;   // TMEM lanes: clauses (GEMM1) or variables (GEMM2) per tile
+constexpr int kBN = 256;   // chains per tile
+constexpr int kBK1 = 128;  // GEMM1 K-block: 128 FP8
+constexpr int kBK2 = 64;   // GEMM2 K-block: 64 16-bit elements
+constexpr int kS1 = 3;     // GEMM1 ring stages (step mode)
+constexpr int kS2 = 4;     // GEMM2 ring stages
+constexpr int kStage1A = kBM * kBK1, kStage1B = kBN * kBK1;        // 16 KB, 32 KB
+constexpr int kStage2A = kBM * kBK2 * 2, kStage2B = kBN * kBK2 * 2;  // 16 KB, 32 KB
+constexpr int kEpi1 = 16;  // GEMM1 epilogue warps (4 per TMEM lane quarter)
+constexpr int kBld = 8;    // GEMM2 builder warps (one chain per thread)
+constexpr int kEpi2 = 8;   // GEMM2 epilogue warps (2 per lane quarter)
+constexpr long long kWait = 4000000000LL;
+
+__device__ __forceinline__ uint32_t step_index(const uint32_t* tdev, uint32_t t_rel) {
+  return (tdev ? *tdev : 0u) + t_rel;
+}
+
+__device__ __forceinline__ int temp_of(int b, int E, int B) {
+  const int e = (int)(((int64_t)b * E) / B);
+  return e < E - 1 ? e : E - 1;
+}
+
+__host__ __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
+
+__device__ __forceinline__ void stage16(void* dst, const void* src, int bytes, int tid, int nthr) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = tid; i < bytes / 16; i += nthr) d[i] = __ldg(s + i);
+}
+
+// ---------------------------------------------------------------- GEMM1 step
+struct G1Smem {
+  uint64_t full[kS1];
+  uint64_t empty[kS1];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint32_t tmem_slot;
+  int64_t cost[2][4 * kBN];
+  float fe[2][4 * kBN];
+  int64_t w[kEpi1][32];
+};
+
+constexpr int kTabOff1 =
+    (kS1 * (kStage1A + kStage1B) + (int)sizeof(G1Smem) + 127) / 128 * 128;
+
+struct G1Args {
+  int m, num_kb, tiles_m, tiles_n, B, Bp;
+  uint32_t idesc;
+  const int32_t* row_len;   // m_pad
+  const int64_t* row_w;     // m_pad
+  const int32_t* cl_grp;    // m
+  const uint8_t* grp_same;  // m_pad / 32: rows of a 32-row group share one weight
+  int64_t* cost_part;       // tiles_m x Bp
+  float* fe_part;           // tiles_m x Bp
+  void* H;                  // m x Bp hidden patterns
+  const uint32_t* tdev;
+  uint32_t t_rel;
+  int* err;
+};
+
+template <bool SAMPLE, bool SM, typename HT>
+__global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
+    k_gemm1_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const G1Args a, const DevTables T, const DevChains C) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* ring = smem_raw + (base - tc::smem_u32(smem_raw));
+  uint8_t* sA = ring;
+  uint8_t* sB = ring + kS1 * kStage1A;
+  G1Smem& S = *reinterpret_cast<G1Smem*>(ring + kS1 * (kStage1A + kStage1B));
+  // staged tables start on a 128-byte boundary (16-byte vector stores)
+  uint8_t* tabs = ring + kTabOff1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int num_tiles = a.tiles_m * a.tiles_n;
+
+  // clause-RBM tables: staged in shared memory when small
+  const GroupMeta* meta = T.meta;
+  const unsigned long long* hid = T.hid;
+  const float* fe_tab = T.fe;
+  if (SM) {
+    const int mb = align16(T.n_groups * (int)sizeof(GroupMeta));
+    const int hb = align16(T.hid_words * 8);
+    const int fb = align16(T.fe_len * 4);
+    stage16(tabs, T.meta, mb, threadIdx.x, blockDim.x);
+    stage16(tabs + mb, T.hid, hb, threadIdx.x, blockDim.x);
+    stage16(tabs + mb + hb, T.fe, fb, threadIdx.x, blockDim.x);
+    meta = reinterpret_cast<const GroupMeta*>(tabs);
+    hid = reinterpret_cast<const unsigned long long*>(tabs + mb);
+    fe_tab = reinterpret_cast<const float*>(tabs + mb + hb);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kS1; ++s) {
+      tc::mbar_init(&S.full[s], 1);
+      tc::mbar_init(&S.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&S.tfull[b], 1);
+      tc::mbar_init(&S.tempty[b], kEpi1);
+    }
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&S.tmem_slot, 2 * kBN);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int tm = tile / a.tiles_n, tn = tile % a.tiles_n;
+        for (int kb = 0; kb < a.num_kb; ++kb, ++g) {
+          const int s = (int)(g % kS1);
+          const uint32_t ph = (g / kS1) & 1u;
+          ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, a.err, 11, kWait);
+          if (!ok) break;
+          tc::mbar_arrive_expect_tx(&S.full[s], kStage1A + kStage1B);
+          tc::tma_load_2d(sA + s * kStage1A, &tmA, &S.full[s], kb * kBK1, tm * kBM);
+          tc::tma_load_2d(sB + s * kStage1B, &tmB, &S.full[s], kb * kBK1, tn * kBN);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      int li = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++li) {
+        const int buf = li & 1;
+        ok = tc::mbar_wait(&S.tempty[buf], ((uint32_t)(li >> 1) & 1u) ^ 1u, a.err, 14, kWait);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(buf * kBN);
+        for (int kb = 0; kb < a.num_kb; ++kb, ++g) {
+          const int s = (int)(g % kS1);
+          const uint32_t ph = (g / kS1) & 1u;
+          ok = tc::mbar_wait(&S.full[s], ph, a.err, 12, kWait);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sA + s * kStage1A), b0 = tc::smem_u32(sB + s * kStage1B);
+#pragma unroll
+          for (int kk = 0; kk < kBK1 / 32; ++kk)
+            tc::mma<true>(d, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), a.idesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::commit(&S.empty[s]);
+        }
+        tc::commit(&S.tfull[buf]);
+      }
+    }
+    __syncwarp();
+  } else {
+    constexpr int kCols = kBN * 4 / kEpi1;  // 64 columns per epilogue warp
+    const int quarter = warp & 3;
+    const int ew = warp - 2;
+    const int cgrp = ew / 4;
+    const int t = threadIdx.x - 64;
+    const int E = T.n_temps;
+    uint32_t tround = 0;
+    if (SAMPLE) tround = step_index(a.tdev, a.t_rel);
+    int li = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
+      const int tm = tile / a.tiles_n, tn = tile % a.tiles_n;
+      const int buf = li & 1;
+      const int c = tm * kBM + quarter * 32 + lane;
+      const int len = c < a.m ? __ldg(a.row_len + c) : 0;
+      const int grp = c < a.m ? __ldg(a.cl_grp + c) : -1;
+      const int64_t w = c < a.m ? __ldg(a.row_w + c) : 0;
+      const int bias = (1 << len) - 1;
+      const float unsat_d = -(float)bias;
+      const bool same_w = __ldg(a.grp_same + tm * 4 + quarter) != 0;
+      GroupMeta gm{};
+      if (grp >= 0) gm = meta[grp];
+      S.w[ew][lane] = w;
+      __syncwarp();
+      const bool ok = tc::mbar_wait(&S.tfull[buf], (uint32_t)(li >> 1) & 1u, a.err, 13, kWait);
+      tc::fence_after_sync();
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                             (uint32_t)(buf * kBN + cgrp * kCols);
+      for (int j = 0; j < kCols / 32; ++j) {
+        uint32_t r[32];
+        tc::tmem_ld32(taddr + (uint32_t)(j * 32), r);
+        tc::tmem_ld_wait();
+        // weighted unsatisfied cost of the 32 columns over the warp's rows
+        uint32_t unsat = 0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) unsat |= (uint32_t)(__uint_as_float(r[q]) == unsat_d) << q;
+        if (!ok) unsat = 0;
+        uint32_t rows = tc::transpose32(unsat, lane);
+        int64_t col = 0;
+        if (same_w) {
+          col = (int64_t)__popc(rows) * S.w[ew][0];
+        } else {
+          while (rows) {
+            col += S.w[ew][__ffs(rows) - 1];
+            rows &= rows - 1;
+          }
+        }
+        S.cost[buf][ew * kCols + j * 32 + lane] = col;
+        // per 8 chains: free energy, hidden draws, hidden patterns
+#pragma unroll
+        for (int sub = 0; sub < 4; ++sub) {
+          const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
+          const int e0 = temp_of(b0, E, a.B);
+          const bool e_uni = e0 == temp_of(b0 + 7, E, a.B);
+          int row[8];
+          float f[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            // truth pattern; the mask keeps table rows in range even if the
+            // accumulator is invalid after a timed-out wait
+            const int p = ((__float2int_rn(__uint_as_float(r[sub * 8 + q])) + bias) >> 1) & bias;
+            row[q] = ((e_uni ? e0 : temp_of(b0 + q, E, a.B)) << len) + p;
+            f[q] = grp >= 0 ? fe_tab[gm.fe_off + row[q]] : 0.f;
+          }
+          const float fs = tc::column_sums8(f, lane);
+          if (lane < 8) S.fe[buf][ew * kCols + j * 32 + sub * 8 + lane] = fs;
+          if (SAMPLE && grp >= 0) {
+            uint32_t hp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) hp[q] = 0;
+            for (int wd = 0; wd < gm.words; ++wd) {
+              uint64_t words[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) words[q] = hid[gm.hid_off + row[q] * gm.words + wd];
+#pragma unroll
+              for (int rr = 0; rr < 3; ++rr) {
+                const int h = 3 * wd + rr;
+                if (h >= gm.nh) break;
+                const uint4 R = philox4x32_10(
+                    make_uint4((uint32_t)c, (uint32_t)(b0 >> 3) | ((uint32_t)h << 24), tround,
+                               kPhaseHidden),
+                    C.keys);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const uint32_t P = (uint32_t)(words[q] >> (17 * rr)) & 0x1FFFFu;
+                  hp[q] |= (uint32_t)(lane16(R, q) < P) << h;
+                }
+              }
+            }
+            HT* H = static_cast<HT*>(a.H) + (size_t)c * a.Bp + b0;
+            if (sizeof(HT) == 1) {
+              uint64_t v = 0;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v |= (uint64_t)hp[q] << (8 * q);
+              *reinterpret_cast<uint64_t*>(H) = v;
+            } else {
+              *reinterpret_cast<uint4*>(H) = make_uint4(hp[0] | (hp[1] << 16), hp[2] | (hp[3] << 16),
+                                                        hp[4] | (hp[5] << 16), hp[6] | (hp[7] << 16));
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&S.tempty[buf]);
+      tc::epi_bar<32 * kEpi1>();
+      for (int colx = t; colx < kBN; colx += 32 * kEpi1) {
+        const int h = colx / kCols, cc = colx % kCols;
+        int64_t cs = 0;
+        float fsum = 0.f;
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+          cs += S.cost[buf][(h * 4 + qd) * kCols + cc];
+          fsum += S.fe[buf][(h * 4 + qd) * kCols + cc];
+        }
+        const size_t o = (size_t)tm * a.Bp + (size_t)tn * kBN + colx;
+        a.cost_part[o] = cs;
+        a.fe_part[o] = fsum;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kBN);
+  }
+}
+
+// ---------------------------------------------------------------- keep
+__global__ void k_keep_dense(const int64_t* __restrict__ cost_part, const float* __restrict__ fe_part,
+                             int tiles_m, DevChains C) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= C.Bp) return;
+  int64_t cs = 0;
+  float fs = 0.f;
+  for (int k = 0; k < tiles_m; ++k) {
+    cs += cost_part[(size_t)k * C.Bp + b];
+    fs += fe_part[(size_t)k * C.Bp + b];
+  }
+  C.cost[b] = cs;
+  C.fe[b] = fs;
+  const bool imp = cs < C.best[b];
+  if (imp) C.best[b] = cs;
+  C.improved[b] = imp ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- GEMM2
+struct G2Smem {
+  uint64_t full[kS2];
+  uint64_t empty[kS2];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint32_t tmem_slot;
+};
+
+constexpr int kTabOff2 =
+    (kS2 * (kStage2A + kStage2B) + (int)sizeof(G2Smem) + 127) / 128 * 128;
+
+struct G2Args {
+  int n, n_pad, B, Bp, tiles_v, tiles_n;
+  uint32_t idesc;
+  const int32_t* kstart;   // tiles_v + 1: incidence range of each variable tile
+  const int32_t* kblocks;  // tiles_v: K-blocks of each variable tile (>= 1)
+  const int4* var_inc;     // incidences sorted by variable
+  const void* H;           // m x Bp hidden patterns
+  uint8_t* X;              // Bp x n_pad FP8 states
+  float* nu;               // Bp x n_pad
+  uint8_t* best_x;         // Bp x n_pad (0 / 1)
+  uint8_t one, minus_one;  // FP8 encodings of +1 / -1
+  bool bf16;               // G operand type (else FP16)
+  float alpha;
+  const uint32_t* tdev;
+  uint32_t t_rel;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t to16(int v, bool bf16) {
+  if (bf16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)v));
+  return (uint32_t)__half_as_ushort(__float2half_rn((float)v));
+}
+
+template <bool SM, typename HT>
+__global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
+    k_gemm2(const __grid_constant__ CUtensorMap tmA2, const G2Args a, const DevTables T,
+            const DevChains C) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t* ring = smem_raw + (base - tc::smem_u32(smem_raw));
+  uint8_t* sA = ring;
+  uint8_t* sB = ring + kS2 * kStage2A;
+  G2Smem& S = *reinterpret_cast<G2Smem*>(ring + kS2 * (kStage2A + kStage2B));
+  // staged tables start on a 128-byte boundary (16-byte vector stores)
+  uint8_t* tabs = ring + kTabOff2;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int num_tiles = a.tiles_v * a.tiles_n;
+
+  const int16_t* gq = T.gq;
+  const uint32_t* pv = T.pv;
+  if (SM) {
+    const int gb = align16(T.gq_len * 2);
+    stage16(tabs, T.gq, gb, threadIdx.x, blockDim.x);
+    stage16(tabs + gb, T.pv, align16(T.pv_len * 4), threadIdx.x, blockDim.x);
+    gq = reinterpret_cast<const int16_t*>(tabs);
+    pv = reinterpret_cast<const uint32_t*>(tabs + gb);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kS2; ++s) {
+      tc::mbar_init(&S.full[s], 1 + kBld);
+      tc::mbar_init(&S.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&S.tfull[b], 1);
+      tc::mbar_init(&S.tempty[b], kEpi2);
+    }
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA2);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&S.tmem_slot, 2 * kBN);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.tmem_slot;
+
+  if (warp == 0) {
+    // TMA producer of the P^T slabs
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int tv = tile / a.tiles_n;
+        const int nkb = __ldg(a.kblocks + tv);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % kS2);
+          const uint32_t ph = (g / kS2) & 1u;
+          ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, a.err, 21, kWait);
+          if (!ok) break;
+          tc::mbar_arrive_expect_tx(&S.full[s], kStage2A);
+          tc::tma_load_2d(sA + s * kStage2A, &tmA2, &S.full[s], kb * kBK2, tv * kBM);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      int li = 0;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++li) {
+        const int tv = tile / a.tiles_n;
+        const int nkb = __ldg(a.kblocks + tv);
+        const int buf = li & 1;
+        ok = tc::mbar_wait(&S.tempty[buf], ((uint32_t)(li >> 1) & 1u) ^ 1u, a.err, 24, kWait);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(buf * kBN);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % kS2);
+          const uint32_t ph = (g / kS2) & 1u;
+          ok = tc::mbar_wait(&S.full[s], ph, a.err, 22, kWait);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sA + s * kStage2A), b0 = tc::smem_u32(sB + s * kStage2B);
+#pragma unroll
+          for (int kk = 0; kk < kBK2 / 16; ++kk)
+            tc::mma<false>(d, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), a.idesc,
+                           (kb > 0 || kk > 0) ? 1u : 0u);
+          tc::commit(&S.empty[s]);
+        }
+        tc::commit(&S.tfull[buf]);
+      }
+    }
+    __syncwarp();
+  } else if (warp < 2 + kBld) {
+    // builders: thread = one chain of the tile; writes its 128-byte row of
+    // the G tile (64 incidences) in the 128-byte swizzle
+    const int bt = threadIdx.x - 64;  // 0..255
+    const HT* H = static_cast<const HT*>(a.H);
+    uint32_t g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
+      const int b = tn * kBN + bt;
+      const int e = temp_of(b, T.n_temps, a.B);
+      const int k0 = __ldg(a.kstart + tv), k1 = __ldg(a.kstart + tv + 1);
+      const int nkb = __ldg(a.kblocks + tv);
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = (int)(g % kS2);
+        const uint32_t ph = (g / kS2) & 1u;
+        ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, a.err, 23, kWait);
+        if (!ok) break;
+        uint8_t* rowp = sB + s * kStage2B + bt * 128;
+        const int jj0 = k0 + kb * kBK2;
+#pragma unroll 1
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t pk[4];
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            uint32_t two = 0;
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+              const int jj = jj0 + ch * 8 + e2 * 2 + hf;
+              int v = 0;
+              if (jj < k1) {
+                const int4 inc = __ldg(a.var_inc + jj);
+                const int hp = (int)H[(size_t)inc.x * a.Bp + b];
+                v = gq[(inc.y & 0x7FFFFFFF) + e * inc.w + hp * inc.z];
+              }
+              two |= to16(v, a.bf16) << (16 * hf);
+            }
+            pk[e2] = two;
+          }
+          *reinterpret_cast<uint4*>(rowp + ((ch ^ (bt & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&S.full[s]);
+      }
+    }
+  } else {
+    // epilogue: row = variable; two warps per TMEM lane quarter split the chains
+    constexpr int kCols = kBN * 4 / kEpi2;  // 128
+    const int quarter = warp & 3;
+    const int ew = warp - 2 - kBld;
+    const int cgrp = ew / 4;
+    const uint32_t tround = step_index(a.tdev, a.t_rel);
+    const float keep = 1.0f - a.alpha;
+    int li = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
+      const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
+      const int buf = li & 1;
+      const int i = tv * kBM + quarter * 32 + lane;
+      const bool valid = i < a.n;
+      tc::mbar_wait(&S.tfull[buf], (uint32_t)(li >> 1) & 1u, a.err, 25, kWait);
+      tc::fence_after_sync();
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
+                             (uint32_t)(buf * kBN + cgrp * kCols);
+      for (int j = 0; j < kCols / 32; ++j) {
+        uint32_t r[32];
+        tc::tmem_ld32(taddr + (uint32_t)(j * 32), r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int sub = 0; sub < 4; ++sub) {
+          const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
+          const uint4 R = philox4x32_10(
+              make_uint4((uint32_t)i, (uint32_t)(b0 >> 3), tround, kPhaseVisible), C.keys);
+          if (!valid) continue;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int b = b0 + q;
+            const int z = __float2int_rn(__uint_as_float(r[sub * 8 + q]));
+            const int qq = max(-T.qmax, min(T.qmax, z));
+            const uint32_t P = pv[qq + T.qmax];
+            const float var = (float)(P * (65536u - P)) * 2.3283064365386963e-10f;
+            const size_t o = (size_t)b * a.n_pad + i;
+            const uint8_t xold = a.X[o];
+            if (C.improved[b]) a.best_x[o] = xold == a.one ? 1 : 0;
+            a.nu[o] = keep * a.nu[o] + a.alpha * var;
+            a.X[o] = lane16(R, q) < P ? a.one : a.minus_one;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&S.tempty[buf]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kBN);
+  }
+}
+
+// ---------------------------------------------------------------- state
+__global__ void k_init_dense(DevChains C, uint8_t* X, float* nu, uint8_t* best_x, int n,
+                             int n_pad, uint8_t one, uint8_t minus_one) {
+  const int g8 = blockIdx.x, b0 = g8 * 8;
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i < n_pad) {
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (i < n) r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, 0u, kPhaseInit), C.keys);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const size_t o = (size_t)(b0 + q) * n_pad + i;
+      const bool bit = lane16(r, q) < 32768u;
+      X[o] = i < n ? (bit ? one : minus_one) : 0;
+      nu[o] = i < n ? 0.25f : 0.f;
+      best_x[o] = i < n && bit ? 1 : 0;
+    }
+  }
+  if (blockIdx.y == 0 && threadIdx.x < 8) {
+    C.best[b0 + threadIdx.x] = INT64_MAX;
+    C.improved[b0 + threadIdx.x] = 0;
+  }
+}
+
+__global__ void k_keep_copy_dense(const DevChains C, const uint8_t* X, uint8_t* best_x, int n,
+                                  int n_pad, uint8_t one) {
+  const int b = blockIdx.y;
+  if (!C.improved[b]) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const size_t o = (size_t)b * n_pad + i;
+    best_x[o] = X[o] == one ? 1 : 0;
+  }
+}
+
+template <bool SAMPLE, bool SM, typename HT>
+cudaError_t g1_variant(int grid, int smem, cudaStream_t st, const CUtensorMap& tmA,
+                       const CUtensorMap& tmB, const G1Args& a, const DevTables& T,
+                       const DevChains& C) {
+  auto kern = k_gemm1_step<SAMPLE, SM, HT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 64 + 32 * kEpi1, smem, st>>>(tmA, tmB, a, T, C);
+  return cudaGetLastError();
+}
+
+template <bool SM, typename HT>
+cudaError_t g2_variant(int grid, int smem, cudaStream_t st, const CUtensorMap& tmA2,
+                       const G2Args& a, const DevTables& T, const DevChains& C) {
+  auto kern = k_gemm2<SM, HT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 64 + 32 * (kBld + kEpi2), smem, st>>>(tmA2, a, T, C);
+  return cudaGetLastError();
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  return sms;
+}
+
+constexpr int kSmemMax = 227 * 1024;
+
+}  // namespace
+
+int dense_g1_table_bytes(const DevTables& T) {
+  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.hid_words * 8) +
+         align16(T.fe_len * 4);
+}
+
+cudaError_t launch_gemm1_step(bool sample, const CUtensorMap& tmA, const CUtensorMap& tmB, int m,
+                              int m_pad, int n_pad, int B, int Bp, bool e5m2,
+                              const int32_t* row_len, const int64_t* row_w, const int32_t* cl_grp,
+                              const uint8_t* grp_same, int64_t* cost_part, float* fe_part, void* H,
+                              bool wide, const uint32_t* tdev, uint32_t t_rel, int* err,
+                              const DevTables& T, const DevChains& C, cudaStream_t st) {
+  G1Args a;
+  a.m = m;
+  a.num_kb = n_pad / kBK1;
+  a.tiles_m = m_pad / kBM;
+  a.tiles_n = Bp / kBN;
+  a.B = B;
+  a.Bp = Bp;
+  const uint32_t fmt = e5m2 ? 1u : 0u;
+  a.idesc = tc::instr_desc(kBM, kBN, fmt, fmt);
+  a.row_len = row_len;
+  a.row_w = row_w;
+  a.cl_grp = cl_grp;
+  a.grp_same = grp_same;
+  a.cost_part = cost_part;
+  a.fe_part = fe_part;
+  a.H = H;
+  a.tdev = tdev;
+  a.t_rel = t_rel;
+  a.err = err;
+  const int base_smem = 1024 + kTabOff1;
+  const int tb = dense_g1_table_bytes(T);
+  const bool sm = base_smem + tb <= kSmemMax;
+  const int smem = base_smem + (sm ? tb : 0);
+  const int grid = std::min(sm_count(), a.tiles_m * a.tiles_n);
+  if (sample) {
+    if (sm) return wide ? g1_variant<true, true, uint16_t>(grid, smem, st, tmA, tmB, a, T, C)
+                        : g1_variant<true, true, uint8_t>(grid, smem, st, tmA, tmB, a, T, C);
+    return wide ? g1_variant<true, false, uint16_t>(grid, smem, st, tmA, tmB, a, T, C)
+                : g1_variant<true, false, uint8_t>(grid, smem, st, tmA, tmB, a, T, C);
+  }
+  if (sm) return g1_variant<false, true, uint8_t>(grid, smem, st, tmA, tmB, a, T, C);
+  return g1_variant<false, false, uint8_t>(grid, smem, st, tmA, tmB, a, T, C);
+}
+
+cudaError_t launch_keep_dense(const int64_t* cost_part, const float* fe_part, int tiles_m,
+                              const DevChains& C, cudaStream_t st) {
+  k_keep_dense<<<(C.Bp + 255) / 256, 256, 0, st>>>(cost_part, fe_part, tiles_m, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int Bp, int tiles_v,
+                         const int32_t* kstart, const int32_t* kblocks, const int4* var_inc,
+                         const void* H, bool wide, uint8_t* X, float* nu, uint8_t* best_x,
+                         bool e5m2, bool bf16, float alpha, const uint32_t* tdev, uint32_t t_rel,
+                         int* err, const DevTables& T, const DevChains& C, cudaStream_t st) {
+  G2Args a;
+  a.n = n;
+  a.n_pad = n_pad;
+  a.B = B;
+  a.Bp = Bp;
+  a.tiles_v = tiles_v;
+  a.tiles_n = Bp / kBN;
+  const uint32_t fmt = bf16 ? 1u : 0u;
+  a.idesc = tc::instr_desc(kBM, kBN, fmt, fmt);
+  a.kstart = kstart;
+  a.kblocks = kblocks;
+  a.var_inc = var_inc;
+  a.H = H;
+  a.X = X;
+  a.nu = nu;
+  a.best_x = best_x;
+  fp8_encode_int(1, e5m2, &a.one);
+  fp8_encode_int(-1, e5m2, &a.minus_one);
+  a.bf16 = bf16;
+  a.alpha = alpha;
+  a.tdev = tdev;
+  a.t_rel = t_rel;
+  a.err = err;
+  const int base_smem = 1024 + kTabOff2;
+  const int tb = align16(T.gq_len * 2) + align16(T.pv_len * 4);
+  const bool sm = base_smem + tb <= kSmemMax;
+  const int smem = base_smem + (sm ? tb : 0);
+  const int grid = std::min(sm_count(), a.tiles_v * a.tiles_n);
+  if (sm) return wide ? g2_variant<true, uint16_t>(grid, smem, st, tmA2, a, T, C)
+                      : g2_variant<true, uint8_t>(grid, smem, st, tmA2, a, T, C);
+  return wide ? g2_variant<false, uint16_t>(grid, smem, st, tmA2, a, T, C)
+              : g2_variant<false, uint8_t>(grid, smem, st, tmA2, a, T, C);
+}
+
+cudaError_t launch_init_dense(const DevChains& C, uint8_t* X, float* nu, uint8_t* best_x, int n,
+                              int n_pad, bool e5m2, cudaStream_t st) {
+  uint8_t one, minus_one;
+  fp8_encode_int(1, e5m2, &one);
+  fp8_encode_int(-1, e5m2, &minus_one);
+  dim3 grid(C.Bp / 8, (n_pad + 127) / 128);
+  k_init_dense<<<grid, 128, 0, st>>>(C, X, nu, best_x, n, n_pad, one, minus_one);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keep_copy_dense(const DevChains& C, const uint8_t* X, uint8_t* best_x, int n,
+                                   int n_pad, bool e5m2, cudaStream_t st) {
+  uint8_t one;
+  fp8_encode_int(1, e5m2, &one);
+  dim3 grid((n + 255) / 256, C.Bp);
+  k_keep_copy_dense<<<grid, 256, 0, st>>>(C, X, best_x, n, n_pad, one);
+  return cudaGetLastError();
+}
+
+}  // namespace rbmsat

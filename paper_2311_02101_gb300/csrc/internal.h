@@ -157,4 +157,23 @@ cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, in
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
                               uint8_t* X, cudaStream_t st);
 
+// dense_step.cu: the dense Gibbs round
+cudaError_t launch_gemm1_step(bool sample, const CUtensorMap& tmA, const CUtensorMap& tmB, int m,
+                              int m_pad, int n_pad, int B, int Bp, bool e5m2,
+                              const int32_t* row_len, const int64_t* row_w, const int32_t* cl_grp,
+                              const uint8_t* grp_same, int64_t* cost_part, float* fe_part, void* H,
+                              bool wide, const uint32_t* tdev, uint32_t t_rel, int* err,
+                              const DevTables& T, const DevChains& C, cudaStream_t st);
+cudaError_t launch_keep_dense(const int64_t* cost_part, const float* fe_part, int tiles_m,
+                              const DevChains& C, cudaStream_t st);
+cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int Bp, int tiles_v,
+                         const int32_t* kstart, const int32_t* kblocks, const int4* var_inc,
+                         const void* H, bool wide, uint8_t* X, float* nu, uint8_t* best_x,
+                         bool e5m2, bool bf16, float alpha, const uint32_t* tdev, uint32_t t_rel,
+                         int* err, const DevTables& T, const DevChains& C, cudaStream_t st);
+cudaError_t launch_init_dense(const DevChains& C, uint8_t* X, float* nu, uint8_t* best_x, int n,
+                              int n_pad, bool e5m2, cudaStream_t st);
+cudaError_t launch_keep_copy_dense(const DevChains& C, const uint8_t* X, uint8_t* best_x, int n,
+                                   int n_pad, bool e5m2, cudaStream_t st);
+
 }  // namespace rbmsat

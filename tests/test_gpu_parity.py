@@ -279,3 +279,62 @@ def test_full_size_mixed_sampled(ms, stream, golden_table):
     ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows,
                      B_total=B)
     assert_same(gpu, ora, T, 0.01, rows=rows)
+
+
+# --------------------------------------------------------------------------
+# Dense tensor-core Gibbs round: the same contract, so the same trajectory
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [256, 300])
+def test_dense_trajectory_3sat(ms, stream, small_table, B):
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    T, seed = 20, 11
+    gpu = run_gpu(ms, stream, inst, small_table, B, T, seed, path=ms.MAXSAT_PATH_DENSE)
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
+
+
+def test_dense_trajectory_mixed_weighted(ms, stream, golden_table):
+    """Lengths up to 12: E5M2 gather operands, 13 hidden units (16-bit hidden
+    patterns), four weight buckets."""
+    inst = inst_of(workloads.mixed_length(n=400, m=2000, seed=9))
+    T, seed, B = 8, 5, 64
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4,
+                  path=ms.MAXSAT_PATH_DENSE)
+    assert_same(gpu, run_oracle(inst, golden_table, B, T, seed, n_buckets=4), T, 0.01)
+
+
+def test_dense_equals_sparse_full_size(ms, stream, golden_table):
+    inst = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0))
+    B, T, seed = 4096, 6, 3
+    d = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=3,
+                path=ms.MAXSAT_PATH_DENSE)
+    s = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=3,
+                path=ms.MAXSAT_PATH_SPARSE)
+    for k in ["x", "best_cost", "best_x", "cost"]:
+        assert np.array_equal(d[k], s[k]), k
+    np.testing.assert_allclose(d["free_energy"], s["free_energy"], rtol=1e-3)
+    assert np.max(np.abs(d["nu"] - s["nu"])) <= nu_tol(T, 0.01)
+    rows = np.array([0, 9, 2047, 2048, 4095])
+    ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows, B_total=B)
+    assert_same(d, ora, T, 0.01, rows=rows)
+
+
+def test_dense_solve_and_resume(ms, stream, small_table):
+    inst = inst_of(workloads.random_ksat(60, 250, 3, seed=4, wmax=50))
+    ctx = make_ctx(ms, stream, inst, small_table, spg=8, path=ms.MAXSAT_PATH_DENSE)
+    cost, assign = ms.maxsat_solve(ctx, 256, 30, 21)
+    ms.maxsat_destroy(ctx)
+    ob, ox, _ = oracle.solve(inst, small_table, 256, 30, 21, n_temps=2, threads=os.cpu_count() or 4)
+    assert cost == ob and np.array_equal(assign, ox)
+    whole = run_gpu(ms, stream, inst, small_table, 256, 20, 13, spg=4, path=ms.MAXSAT_PATH_DENSE)
+    ctx = make_ctx(ms, stream, inst, small_table, spg=4, path=ms.MAXSAT_PATH_DENSE)
+    ms.maxsat_reset(ctx, 256, 13)
+    ms.maxsat_step(ctx, 9)
+    mid = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    ctx = make_ctx(ms, stream, inst, small_table, spg=4, path=ms.MAXSAT_PATH_DENSE)
+    ms.maxsat_set_state(ctx, 256, 13, mid["x"], mid["nu"], mid["best_cost"], mid["best_x"], mid["t"])
+    ms.maxsat_step(ctx, 11)
+    end = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    for k in ["x", "nu", "best_cost", "best_x", "cost", "free_energy"]:
+        assert np.array_equal(whole[k], end[k]), k
