@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--path", default="auto", choices=["auto", "sparse", "dense"])
     return ap.parse_args()
 
 
@@ -175,6 +176,34 @@ def measured_peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0), "fallback"
 
 
+def dense_block_work(n, off, lits):
+    """Executed dense work of the scatter-add per chain: each 128-variable tile
+    spans its own incidence range (incidences sorted by variable), padded to
+    64."""
+    var = np.abs(lits.astype(np.int64)) - 1
+    deg = np.bincount(var, minlength=n)
+    vo = np.concatenate([[0], np.cumsum(deg)])
+    n_pad = (n + 127) // 128 * 128
+    tot = 0
+    for tv in range(n_pad // 128):
+        k0, k1 = vo[min(tv * 128, n)], vo[min((tv + 1) * 128, n)]
+        tot += 128 * max(1, -(-(k1 - k0) // 64)) * 64
+    return tot
+
+
+def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks):
+    """(bound, algorithmic amount per launch, unit, peak) of one kernel.
+    Sparse kernels: compulsory bytes against the copy bandwidth. Dense
+    kernels: tensor-core FLOPs (the dense gather product C x states, 2 m n B;
+    the block-diagonal scatter-add, 2 B sum over variable tiles of 128 x its
+    incidence range) against the FP8 / BF16 dense peak."""
+    if kernel in ("gemm1_step", "gemm1_score", "gemm1_eval"):
+        return "tensor", 2.0 * m * n * B, "TFLOP/s", 2.0 * peaks["bf16_tflops_sustained"]
+    if kernel == "gemm2":
+        return "tensor", 2.0 * B * dense_block_work(n, off, lits), "TFLOP/s", peaks["bf16_tflops_sustained"]
+    return "hbm", algorithmic_bytes(kernel, n, m, nnz, B), "GB/s", peaks["hbm_gbs"]
+
+
 def algorithmic_bytes(kernel, n, m, nnz, B):
     """Compulsory bytes one launch moves (sparse path): the state it must read
     and write once, nothing re-read. Per clause and chain the hidden state is
@@ -204,7 +233,9 @@ def run_mine(args):
     n, off, lits, w, B = workload(args.workload, args.seed)
     m, nnz = len(off) - 1, int(off[-1])
     stream = torch.cuda.Stream()
-    params = ms.maxsat_default_params()
+    path_code = {"auto": ms.MAXSAT_PATH_AUTO, "sparse": ms.MAXSAT_PATH_SPARSE,
+                 "dense": ms.MAXSAT_PATH_DENSE}[args.path]
+    params = ms.maxsat_default_params(path=path_code)
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
     seed = args.seed * 1000003 + rank
     ms.maxsat_reset(ctx, B, seed)
@@ -242,7 +273,8 @@ def run_mine(args):
     launches, tot = kt[top]
     avg_s = tot / launches / 1e3
     peaks, peak_src = measured_peaks()
-    alg = algorithmic_bytes(top, n, m, nnz, B)
+    bound, alg, unit, peak = kernel_roofline(top, n, m, nnz, B, off, lits, peaks)
+    scale = 1e9 if unit == "GB/s" else 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -250,10 +282,12 @@ def run_mine(args):
             tr = json.load(f).get(args.workload, {}).get(top)
         if tr and tr.get("kernel_hash") == ms_kernel_hash():
             traffic = tr.get("bytes_per_launch")
-    roofline = dict(kernel=top, bound="hbm", achieved=alg / avg_s / 1e9, peak=peaks["hbm_gbs"],
-                    unit="GB/s", frac=alg / avg_s / 1e9 / peaks["hbm_gbs"], traffic=traffic,
-                    algorithmic_bytes=alg, avg_launch_us=avg_s * 1e6,
-                    peak_source=f"{peak_src} (copy bandwidth)",
+    roofline = dict(kernel=top, bound=bound, achieved=alg / avg_s / scale, peak=peak, unit=unit,
+                    frac=alg / avg_s / scale / peak, traffic=traffic,
+                    algorithmic=alg, avg_launch_us=avg_s * 1e6,
+                    peak_source=(f"{peak_src} copy bandwidth" if unit == "GB/s" else
+                                 f"{peak_src} BF16 sustained" + (" x 2 (nominal FP8/BF16)"
+                                                                 if "gemm1" in top else "")),
                     kernels={k: dict(launches=v[0], avg_us=1e3 * v[1] / v[0])
                              for k, v in kt.items()})
 
@@ -263,7 +297,7 @@ def run_mine(args):
     sets = []
     for s in (ms_fitted_sets(ms, off, params)):
         sets.append(s)
-    p2 = ms.maxsat_default_params(sets=sets)
+    p2 = ms.maxsat_default_params(sets=sets, path=path_code)
     e2e_steps = args.steps
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -281,19 +315,22 @@ def run_mine(args):
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
 
     dense_eval = dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
+    paths = compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
 
     S = params.steps_per_graph
-    launches_timed = 2 * args.steps + (args.steps // S if S else 0)
+    per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
+    launches_timed = per_round * args.steps + (args.steps // S if S else 0)
     path = {1: "dense", 2: "sparse"}[ms.maxsat_get_path(ctx)]
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_total / args.steps, higher_is_better=True,
-                scaling="weak", vs_baseline=None, dtype="int32", data="synthetic",
-                config=dict(workload=args.workload, n=n, m=m, B=B, path=path,
+                scaling="weak", vs_baseline=None, dtype="fp8" if path == "dense" else "int32",
+                data="synthetic",
+                config=dict(workload=args.workload, n=n, m=m, B=B, path=path, path_requested=args.path,
                             steps_per_graph=S, parallelism=f"replicas{ws}",
                             l2="working set above L2 (no flush): G/hidden state, nu and "
                                "x of 4096 chains; state carried step to step"),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
-                gpu_launches=launches_timed, dense_eval=dense_eval)
+                gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -336,6 +373,39 @@ def dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args):
                 frac=flops / avg / 1e12 / fp8_peak, bound="tensor",
                 peak_source=f"{src} BF16 burst x 2 (nominal FP8/BF16 ratio)",
                 flops_per_launch=flops)
+
+
+def compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args):
+    """Device time per Gibbs round of both paths on the same workload (CUDA
+    graphs, CUDA events), with the per-kernel split from a profiled region."""
+    out = {}
+    K = max(20, min(200, args.steps))
+    for name, code in [("sparse", ms.MAXSAT_PATH_SPARSE), ("dense", ms.MAXSAT_PATH_DENSE)]:
+        try:
+            ctx = ms.maxsat_create(n, off, lits, w, ms.maxsat_default_params(sets=sets, path=code,
+                                                                             steps_per_graph=K),
+                                   stream)
+        except ms.MaxsatError as e:
+            out[name] = dict(unavailable=str(e))
+            continue
+        ms.maxsat_reset(ctx, B, seed)
+        ms.maxsat_step(ctx, K)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ms.maxsat_step(ctx, K)
+        b.record(stream)
+        b.synchronize()
+        ms_round = a.elapsed_time(b) / K
+        ms.maxsat_set_profiling(ctx, True)
+        ms.maxsat_step(ctx, min(K, 50))
+        kt = ms.maxsat_kernel_times(ctx)
+        ms.maxsat_set_profiling(ctx, False)
+        ms.maxsat_get_state(ctx)  # surfaces a device-side wait timeout, if any
+        ms.maxsat_destroy(ctx)
+        out[name] = dict(ms_per_round=ms_round, evals_per_s=(len(off) - 1) * B / (ms_round / 1e3),
+                         kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()})
+    return out
 
 
 def ms_kernel_hash():

@@ -103,6 +103,7 @@ struct maxsat_ctx {
   bool g_bf16 = true;             // G operand BF16 (else FP16)
   int32_t* d_kstart = nullptr;    // tiles_v + 1
   int32_t* d_kblocks = nullptr;   // tiles_v
+  uint16_t* d_gq16 = nullptr;     // contribution table as BF16 / FP16 bits
   CUtensorMap tmA2{};
   // dense chain state
   uint8_t* dX = nullptr;          // Bp x n_pad FP8 +-1
@@ -213,7 +214,7 @@ int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_
     TIMED(ctx, st, "keep", launch_keep_dense(ctx->dcost_part, ctx->dfe_part, ctx->m_pad / 128, C, st));
     TIMED(ctx, st, "gemm2",
           launch_gemm2(ctx->tmA2, ctx->n, ctx->n_pad, C.B, C.Bp, ctx->tiles_v, ctx->d_kstart,
-                       ctx->d_kblocks, ctx->F.var_inc, C.H, ctx->wide_h, ctx->dX, ctx->dnu,
+                       ctx->d_kblocks, ctx->F.var_inc, ctx->d_gq16, C.H, ctx->wide_h, ctx->dX, ctx->dnu,
                        ctx->dbest_x, ctx->e5m2, ctx->g_bf16, (float)ctx->prm.alpha, tdev, t_rel,
                        ctx->d_err, ctx->T, C, st));
     return MAXSAT_OK;
@@ -643,12 +644,31 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
       for (int jj = var_off[i]; jj < var_off[i + 1]; ++jj)
         A2[(size_t)i * ctx->kmax + (jj - kst[tv])] = var_inc[jj].y < 0 ? minus : plus;
     }
+    // contributions as 16-bit floating-point bit patterns (exact: integers
+    // below 2^8 in BF16, below 2^11 in FP16)
+    std::vector<uint16_t> gq16(ctx->tabs.gq.size());
+    for (size_t k = 0; k < gq16.size(); ++k) {
+      const int v = ctx->tabs.gq[k];
+      uint16_t bits = 0;
+      if (v != 0) {
+        const unsigned av = (unsigned)(v < 0 ? -v : v);
+        const int e2 = 31 - __builtin_clz(av);
+        const int mb = ctx->g_bf16 ? 7 : 10;  // mantissa bits
+        const unsigned mant = (e2 <= mb ? (av << (mb - e2)) : (av >> (e2 - mb))) & ((1u << mb) - 1u);
+        bits = (uint16_t)(((unsigned)(e2 + (ctx->g_bf16 ? 127 : 15)) << mb) | mant);
+        if (v < 0) bits |= 0x8000;
+      }
+      gq16[k] = bits;
+    }
     const uint16_t* dA2 = nullptr;
     const int32_t* dks = nullptr;
     const int32_t* dkb = nullptr;
+    const uint16_t* dg16 = nullptr;
     UP2(A2, dA2);
     UP2(kst, dks);
     UP2(kbl, dkb);
+    UP2(gq16, dg16);
+    ctx->d_gq16 = const_cast<uint16_t*>(dg16);
     ctx->d_kstart = const_cast<int32_t*>(dks);
     ctx->d_kblocks = const_cast<int32_t*>(dkb);
     derr = make_tmap_2d(&ctx->tmA2, dA2, ctx->kmax, (uint64_t)ctx->tiles_v * 128,

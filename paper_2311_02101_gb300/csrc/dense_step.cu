@@ -45,11 +45,11 @@ constexpr int kBN = 256;   // chains per tile
 constexpr int kBK1 = 128;  // GEMM1 K-block: 128 FP8
 constexpr int kBK2 = 64;   // GEMM2 K-block: 64 16-bit elements
 constexpr int kS1 = 3;     // GEMM1 ring stages (step mode)
-constexpr int kS2 = 4;     // GEMM2 ring stages
+constexpr int kS2 = 3;     // GEMM2 ring stages (at most)
 constexpr int kStage1A = kBM * kBK1, kStage1B = kBN * kBK1;        // 16 KB, 32 KB
 constexpr int kStage2A = kBM * kBK2 * 2, kStage2B = kBN * kBK2 * 2;  // 16 KB, 32 KB
 constexpr int kEpi1 = 16;  // GEMM1 epilogue warps (4 per TMEM lane quarter)
-constexpr int kBld = 8;    // GEMM2 builder warps (one chain per thread)
+constexpr int kBld = 16;   // GEMM2 builder warps (a chain and half a K-block per thread)
 constexpr int kEpi2 = 8;   // GEMM2 epilogue warps (2 per lane quarter)
 constexpr long long kWait = 4000000000LL;
 
@@ -348,15 +348,28 @@ __global__ void k_keep_dense(const int64_t* __restrict__ cost_part, const float*
 
 // ---------------------------------------------------------------- GEMM2
 struct G2Smem {
-  uint64_t full[kS2];
-  uint64_t empty[kS2];
+  uint64_t loaded[kS2];  // TMA / bulk copies -> builders: P^T, hidden rows, records
+  uint64_t hready[kS2];  // builders' cp.async copies of the hidden patterns landed
+  uint64_t built[kS2];   // builders -> MMA: G tile written
+  uint64_t empty[kS2];   // MMA -> producer and builders: stage consumed
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint32_t tmem_slot;
 };
 
-constexpr int kTabOff2 =
-    (kS2 * (kStage2A + kStage2B) + (int)sizeof(G2Smem) + 127) / 128 * 128;
+// GEMM2 ring stage: P^T tile, G tile, the K-block's staged hidden patterns
+// (64 incidences x 256 chains) and its 64 incidence records.
+template <typename HT>
+struct G2Stage {
+  static constexpr int kA = kStage2A;
+  static constexpr int kB = kStage2B;
+  static constexpr int kH = kBK2 * kBN * (int)sizeof(HT);  // staged hidden patterns [u][chain]
+  static constexpr int kInc = 1024;
+  static constexpr int kBytes = kA + kB + kH + kInc;  // multiple of 1024
+  static constexpr int kStages = sizeof(HT) == 1 ? 3 : 2;
+  static constexpr int kTabOff =
+      (kStages * kBytes + (int)sizeof(G2Smem) + 127) / 128 * 128;
+};
 
 struct G2Args {
   int n, n_pad, B, Bp, tiles_v, tiles_n;
@@ -364,6 +377,7 @@ struct G2Args {
   const int32_t* kstart;   // tiles_v + 1: incidence range of each variable tile
   const int32_t* kblocks;  // tiles_v: K-blocks of each variable tile (>= 1)
   const int4* var_inc;     // incidences sorted by variable
+  const uint16_t* gq16;    // contribution table as BF16 / FP16 bits (layout of T.gq)
   const void* H;           // m x Bp hidden patterns
   uint8_t* X;              // Bp x n_pad FP8 states
   float* nu;               // Bp x n_pad
@@ -376,39 +390,43 @@ struct G2Args {
   int* err;
 };
 
-__device__ __forceinline__ uint32_t to16(int v, bool bf16) {
-  if (bf16) return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)v));
-  return (uint32_t)__half_as_ushort(__float2half_rn((float)v));
-}
 
 template <bool SM, typename HT>
 __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
     k_gemm2(const __grid_constant__ CUtensorMap tmA2, const G2Args a, const DevTables T,
             const DevChains C) {
+  using St = G2Stage<HT>;
+  constexpr int NS = St::kStages;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* ring = smem_raw + (base - tc::smem_u32(smem_raw));
-  uint8_t* sA = ring;
-  uint8_t* sB = ring + kS2 * kStage2A;
-  G2Smem& S = *reinterpret_cast<G2Smem*>(ring + kS2 * (kStage2A + kStage2B));
+  G2Smem& S = *reinterpret_cast<G2Smem*>(ring + NS * St::kBytes);
   // staged tables start on a 128-byte boundary (16-byte vector stores)
-  uint8_t* tabs = ring + kTabOff2;
+  uint8_t* tabs = ring + St::kTabOff;
+  auto stA = [&](int s) { return ring + s * St::kBytes; };
+  auto stB = [&](int s) { return ring + s * St::kBytes + St::kA; };
+  auto stH = [&](int s) { return reinterpret_cast<HT*>(ring + s * St::kBytes + St::kA + St::kB); };
+  auto stI = [&](int s) {
+    return reinterpret_cast<int4*>(ring + s * St::kBytes + St::kA + St::kB + St::kH);
+  };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_tiles = a.tiles_v * a.tiles_n;
 
-  const int16_t* gq = T.gq;
+  const uint16_t* gq = a.gq16;
   const uint32_t* pv = T.pv;
   if (SM) {
     const int gb = align16(T.gq_len * 2);
-    stage16(tabs, T.gq, gb, threadIdx.x, blockDim.x);
+    stage16(tabs, a.gq16, gb, threadIdx.x, blockDim.x);
     stage16(tabs + gb, T.pv, align16(T.pv_len * 4), threadIdx.x, blockDim.x);
-    gq = reinterpret_cast<const int16_t*>(tabs);
+    gq = reinterpret_cast<const uint16_t*>(tabs);
     pv = reinterpret_cast<const uint32_t*>(tabs + gb);
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kS2; ++s) {
-      tc::mbar_init(&S.full[s], 1 + kBld);
+    for (int s = 0; s < NS; ++s) {
+      tc::mbar_init(&S.loaded[s], 1);
+      tc::mbar_init(&S.built[s], kBld);
+      tc::mbar_init(&S.hready[s], 32 * kBld);
       tc::mbar_init(&S.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -428,21 +446,30 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
   const uint32_t tmem = S.tmem_slot;
 
   if (warp == 0) {
-    // TMA producer of the P^T slabs
-    if (lane == 0) {
-      uint32_t g = 0;
-      bool ok = true;
-      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-        const int tv = tile / a.tiles_n;
-        const int nkb = __ldg(a.kblocks + tv);
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
-          const int s = (int)(g % kS2);
-          const uint32_t ph = (g / kS2) & 1u;
+    // producer warp: P^T tile by TMA and the K-block's incidence records by
+    // one bulk copy
+    uint32_t g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int tv = tile / a.tiles_n;
+      const int k0 = __ldg(a.kstart + tv), k1 = __ldg(a.kstart + tv + 1);
+      const int nkb = __ldg(a.kblocks + tv);
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int s = (int)(g % NS);
+        const uint32_t ph = (g / NS) & 1u;
+        if (lane == 0) {
           ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, a.err, 21, kWait);
-          if (!ok) break;
-          tc::mbar_arrive_expect_tx(&S.full[s], kStage2A);
-          tc::tma_load_2d(sA + s * kStage2A, &tmA2, &S.full[s], kb * kBK2, tv * kBM);
+          if (ok) {
+            const int jj0 = k0 + kb * kBK2;
+            const int nvalid = max(0, min(kBK2, k1 - jj0));
+            tc::mbar_arrive_expect_tx(&S.loaded[s], (uint32_t)(St::kA + nvalid * 16));
+            tc::tma_load_2d(stA(s), &tmA2, &S.loaded[s], kb * kBK2, tv * kBM);
+            if (nvalid > 0)
+              tc::bulk_load(stI(s), a.var_inc + jj0, (uint32_t)(nvalid * 16), &S.loaded[s]);
+          }
         }
+        ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        if (!ok) break;
       }
     }
     __syncwarp();
@@ -460,12 +487,12 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
         tc::fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(buf * kBN);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
-          const int s = (int)(g % kS2);
-          const uint32_t ph = (g / kS2) & 1u;
-          ok = tc::mbar_wait(&S.full[s], ph, a.err, 22, kWait);
+          const int s = (int)(g % NS);
+          const uint32_t ph = (g / NS) & 1u;
+          ok = tc::mbar_wait(&S.built[s], ph, a.err, 22, kWait);
           if (!ok) break;
           tc::fence_after_sync();
-          const uint32_t a0 = tc::smem_u32(sA + s * kStage2A), b0 = tc::smem_u32(sB + s * kStage2B);
+          const uint32_t a0 = tc::smem_u32(stA(s)), b0 = tc::smem_u32(stB(s));
 #pragma unroll
           for (int kk = 0; kk < kBK2 / 16; ++kk)
             tc::mma<false>(d, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), a.idesc,
@@ -477,56 +504,121 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
     }
     __syncwarp();
   } else if (warp < 2 + kBld) {
-    // builders: thread = one chain of the tile; writes its 128-byte row of
-    // the G tile (64 incidences) in the 128-byte swizzle
-    const int bt = threadIdx.x - 64;  // 0..255
+    // builders. Copy phase: thread = 2 items (incidence u, 16 consecutive
+    // chains), cp.async of their hidden-pattern bytes into the stage's staging
+    // area one K-block ahead. Build phase: thread = (chain, 8 incidences) x 4,
+    // reads the staged bytes, looks the contributions up and writes 16-byte
+    // chunks of the G tile (row = chain, 128-byte swizzle).
+    const int bt = threadIdx.x - 64;  // 0 .. 511
     const HT* H = static_cast<const HT*>(a.H);
+    auto issue_copies = [&](int s, int jk0, int jk1, int ttn) {
+      const int4* inc = stI(s);
+      HT* hs = stH(s);
+      const int cq = bt & 15, u0 = bt >> 4;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int u = u0 + 32 * it;
+        if (jk0 + u < jk1) {
+          const HT* src = H + (size_t)inc[u].x * a.Bp + (size_t)ttn * kBN + cq * 16;
+#pragma unroll
+          for (int v = 0; v < (int)sizeof(HT); ++v)
+            tc::cp_async16(hs + u * kBN + cq * 16 + v * (16 / sizeof(HT)), src + v * (16 / sizeof(HT)));
+        }
+      }
+      tc::cp_async_arrive(&S.hready[s]);
+    };
+    // flat walk over (tile, K-block) in the producer's order
+    int tile = blockIdx.x, kb = 0;
+    int tn = 0, k0 = 0, k1 = 0, nkb = 0;
+    if (tile < num_tiles) {
+      const int tv = tile / a.tiles_n;
+      tn = tile % a.tiles_n;
+      k0 = __ldg(a.kstart + tv);
+      k1 = __ldg(a.kstart + tv + 1);
+      nkb = __ldg(a.kblocks + tv);
+    }
     uint32_t g = 0;
-    bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
-      const int b = tn * kBN + bt;
-      const int e = temp_of(b, T.n_temps, a.B);
-      const int k0 = __ldg(a.kstart + tv), k1 = __ldg(a.kstart + tv + 1);
-      const int nkb = __ldg(a.kblocks + tv);
-      for (int kb = 0; kb < nkb; ++kb, ++g) {
-        const int s = (int)(g % kS2);
-        const uint32_t ph = (g / kS2) & 1u;
-        ok = tc::mbar_wait(&S.empty[s], ph ^ 1u, a.err, 23, kWait);
+    bool ok = tile < num_tiles;
+    if (ok) {
+      ok = tc::mbar_wait(&S.loaded[0], 0u, a.err, 23, kWait);
+      if (ok) issue_copies(0, k0, k1, tn);
+    }
+    const int chain = bt & (kBN - 1);
+    const int hk = bt / kBN;  // which half of the K-block (32 incidences)
+    while (ok) {
+      const int s = (int)(g % NS);
+      const uint32_t ph = (g / NS) & 1u;
+      // next K-block (possibly of the next tile): records, then its copies
+      int ntile = tile, nkb_i = kb + 1;
+      if (nkb_i >= nkb) {
+        ntile = tile + gridDim.x;
+        nkb_i = 0;
+      }
+      int ntn = tn, nk0 = k0, nk1 = k1, nnkb = nkb;
+      if (ntile < num_tiles) {
+        if (ntile != tile) {
+          const int ntv = ntile / a.tiles_n;
+          ntn = ntile % a.tiles_n;
+          nk0 = __ldg(a.kstart + ntv);
+          nk1 = __ldg(a.kstart + ntv + 1);
+          nnkb = __ldg(a.kblocks + ntv);
+        }
+        const int ns = (int)((g + 1) % NS);
+        const uint32_t nph = ((g + 1) / NS) & 1u;
+        ok = tc::mbar_wait(&S.loaded[ns], nph, a.err, 23, kWait);
         if (!ok) break;
-        uint8_t* rowp = sB + s * kStage2B + bt * 128;
+        issue_copies(ns, nk0 + nkb_i * kBK2, nk1, ntn);
+      }
+      // build the current K-block once every builder's copies have landed
+      ok = tc::mbar_wait(&S.hready[s], ph, a.err, 26, kWait);
+      if (!ok) break;
+      {
         const int jj0 = k0 + kb * kBK2;
-#pragma unroll 1
-        for (int ch = 0; ch < 8; ++ch) {
+        const int4* inc = stI(s);
+        const HT* hs = stH(s);
+        uint8_t* rowp = stB(s) + chain * 128;
+        const int e = temp_of(tn * kBN + chain, T.n_temps, a.B);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          const int chunk = hk * 4 + ch;
           uint32_t pk[4];
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
+          for (int u2 = 0; u2 < 4; ++u2) {
             uint32_t two = 0;
 #pragma unroll
             for (int hf = 0; hf < 2; ++hf) {
-              const int jj = jj0 + ch * 8 + e2 * 2 + hf;
-              int v = 0;
-              if (jj < k1) {
-                const int4 inc = __ldg(a.var_inc + jj);
-                const int hp = (int)H[(size_t)inc.x * a.Bp + b];
-                v = gq[(inc.y & 0x7FFFFFFF) + e * inc.w + hp * inc.z];
+              const int u = chunk * 8 + u2 * 2 + hf;
+              uint32_t v = 0;  // 16-bit pattern of the contribution (0 = +0.0)
+              if (jj0 + u < k1) {
+                const int4 m = inc[u];
+                const int hp = (int)hs[u * kBN + chain];
+                v = gq[(m.y & 0x7FFFFFFF) + e * m.w + hp * m.z];
               }
-              two |= to16(v, a.bf16) << (16 * hf);
+              two |= v << (16 * hf);
             }
-            pk[e2] = two;
+            pk[u2] = two;
           }
-          *reinterpret_cast<uint4*>(rowp + ((ch ^ (bt & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(rowp + ((chunk ^ (chain & 7)) << 4)) =
+              make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
         tc::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&S.full[s]);
+        if (lane == 0) tc::mbar_arrive(&S.built[s]);
       }
+      ++g;
+      if (ntile >= num_tiles) break;
+      tile = ntile;
+      kb = nkb_i;
+      tn = ntn;
+      k0 = nk0;
+      k1 = nk1;
+      nkb = nnkb;
     }
   } else {
     // epilogue: row = variable; two warps per TMEM lane quarter split the chains
     constexpr int kCols = kBN * 4 / kEpi2;  // 128
     const int quarter = warp & 3;
-    const int ew = warp - 2 - kBld;
+    const int ew = warp - 2 - kBld;  // 0 .. kEpi2 - 1
     const int cgrp = ew / 4;
     const uint32_t tround = step_index(a.tdev, a.t_rel);
     const float keep = 1.0f - a.alpha;
@@ -700,7 +792,8 @@ cudaError_t launch_keep_dense(const int64_t* cost_part, const float* fe_part, in
 
 cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int Bp, int tiles_v,
                          const int32_t* kstart, const int32_t* kblocks, const int4* var_inc,
-                         const void* H, bool wide, uint8_t* X, float* nu, uint8_t* best_x,
+                         const uint16_t* gq16, const void* H, bool wide, uint8_t* X, float* nu,
+                         uint8_t* best_x,
                          bool e5m2, bool bf16, float alpha, const uint32_t* tdev, uint32_t t_rel,
                          int* err, const DevTables& T, const DevChains& C, cudaStream_t st) {
   G2Args a;
@@ -715,6 +808,7 @@ cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int B
   a.kstart = kstart;
   a.kblocks = kblocks;
   a.var_inc = var_inc;
+  a.gq16 = gq16;
   a.H = H;
   a.X = X;
   a.nu = nu;
@@ -726,15 +820,18 @@ cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int B
   a.tdev = tdev;
   a.t_rel = t_rel;
   a.err = err;
-  const int base_smem = 1024 + kTabOff2;
   const int tb = align16(T.gq_len * 2) + align16(T.pv_len * 4);
-  const bool sm = base_smem + tb <= kSmemMax;
-  const int smem = base_smem + (sm ? tb : 0);
   const int grid = std::min(sm_count(), a.tiles_v * a.tiles_n);
-  if (sm) return wide ? g2_variant<true, uint16_t>(grid, smem, st, tmA2, a, T, C)
-                      : g2_variant<true, uint8_t>(grid, smem, st, tmA2, a, T, C);
-  return wide ? g2_variant<false, uint16_t>(grid, smem, st, tmA2, a, T, C)
-              : g2_variant<false, uint8_t>(grid, smem, st, tmA2, a, T, C);
+  if (wide) {
+    const int base_smem = 1024 + G2Stage<uint16_t>::kTabOff;
+    const bool sm = base_smem + tb <= kSmemMax;
+    return sm ? g2_variant<true, uint16_t>(grid, base_smem + tb, st, tmA2, a, T, C)
+              : g2_variant<false, uint16_t>(grid, base_smem, st, tmA2, a, T, C);
+  }
+  const int base_smem = 1024 + G2Stage<uint8_t>::kTabOff;
+  const bool sm = base_smem + tb <= kSmemMax;
+  return sm ? g2_variant<true, uint8_t>(grid, base_smem + tb, st, tmA2, a, T, C)
+            : g2_variant<false, uint8_t>(grid, base_smem, st, tmA2, a, T, C);
 }
 
 cudaError_t launch_init_dense(const DevChains& C, uint8_t* X, float* nu, uint8_t* best_x, int n,

@@ -168,7 +168,8 @@ cudaError_t launch_keep_dense(const int64_t* cost_part, const float* fe_part, in
                               const DevChains& C, cudaStream_t st);
 cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int Bp, int tiles_v,
                          const int32_t* kstart, const int32_t* kblocks, const int4* var_inc,
-                         const void* H, bool wide, uint8_t* X, float* nu, uint8_t* best_x,
+                         const uint16_t* gq16, const void* H, bool wide, uint8_t* X, float* nu,
+                         uint8_t* best_x,
                          bool e5m2, bool bf16, float alpha, const uint32_t* tdev, uint32_t t_rel,
                          int* err, const DevTables& T, const DevChains& C, cudaStream_t st);
 cudaError_t launch_init_dense(const DevChains& C, uint8_t* X, float* nu, uint8_t* best_x, int n,
