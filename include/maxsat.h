@@ -49,7 +49,10 @@ extern "C" {
 #define MAXSAT_MAX_LEN 12     /* longest clause with an OR-gate RBM */
 #define MAXSAT_MAX_HIDDEN 16  /* most hidden units per clause RBM */
 
-#define MAXSAT_PATH_AUTO 0
+#define MAXSAT_PATH_AUTO 0    /* measured choice: the first maxsat_reset for a
+                                 given B times a few rounds of each path (when
+                                 the dense operands are exact and fit) and
+                                 keeps the faster */
 #define MAXSAT_PATH_DENSE 1   /* tensor-core products over dense operands */
 #define MAXSAT_PATH_SPARSE 2  /* gather / pull-scatter over the literal lists */
 
@@ -173,7 +176,8 @@ int maxsat_set_profiling(maxsat_ctx* ctx, int32_t on);
 int maxsat_kernel_times(maxsat_ctx* ctx, int32_t max_kernels, char* names,
                         int64_t* launches, double* total_ms);
 
-/* Which path the context runs (MAXSAT_PATH_DENSE or _SPARSE). */
+/* Which path the Gibbs rounds run on (MAXSAT_PATH_DENSE or _SPARSE); with
+ * MAXSAT_PATH_AUTO the choice is made by the first maxsat_reset for each B. */
 int maxsat_get_path(const maxsat_ctx* ctx);
 
 /* Allocation-free cost evaluation (the paper has no counterpart: it is an

@@ -83,8 +83,13 @@ struct maxsat_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
 
-  // dense tensor-core path (built when requested)
-  bool dense = false;
+  // dense tensor-core path (built when requested or for the measured choice)
+  DevAllocs dense_mem;
+  bool dense_built = false;  // dense operands exist
+  bool dense = false;        // Gibbs rounds run on the dense path
+  bool chains_dense = false; // layout of the allocated chain state
+  int auto_B = 0;            // B of the last measured choice (AUTO)
+  float auto_ms[2] = {0, 0}; // measured ms per round: sparse, dense
   bool e5m2 = false;
   int n_pad = 0, m_pad = 0;
   uint8_t* dA = nullptr;          // m_pad x n_pad FP8 pattern-encoding gather matrix
@@ -252,7 +257,7 @@ int capture_graph(maxsat_ctx* ctx, int S) {
 }
 
 int alloc_chains(maxsat_ctx* ctx, int32_t B) {
-  if (ctx->have_chains && ctx->C.B == B) return MAXSAT_OK;
+  if (ctx->have_chains && ctx->C.B == B && ctx->chains_dense == ctx->dense) return MAXSAT_OK;
   destroy_graph(ctx);
   ctx->chain_mem.release();
   ctx->have_chains = false;
@@ -263,6 +268,7 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   C = DevChains{};
   C.B = B;
   C.Bp = Bp;
+  ctx->chains_dense = ctx->dense;
   DevAllocs& A = ctx->chain_mem;
   if (ctx->dense) {
     const size_t nP = (size_t)ctx->n_pad * Bp;
@@ -322,6 +328,178 @@ int upload(maxsat_ctx* ctx, DevAllocs& A, std::vector<T> h, const T** out) {
 }
 
 }  // namespace
+
+// Measured path choice (MAXSAT_PATH_AUTO): times a few Gibbs rounds of B
+// chains on each path with CUDA events and keeps the faster one.
+int choose_path(maxsat_ctx* ctx, int32_t B) {
+  cudaEvent_t e0, e1;
+  CK(ctx, cudaEventCreate(&e0));
+  CK(ctx, cudaEventCreate(&e1));
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  int rc = MAXSAT_OK;
+  for (int d = 0; d < 2 && rc == MAXSAT_OK; ++d) {
+    ctx->dense = d == 1;
+    rc = alloc_chains(ctx, B);
+    if (rc != MAXSAT_OK) break;
+    ctx->C.keys = philox_keys(0x5EEDu, 0u);
+    cudaError_t e = ctx->dense ? launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n,
+                                                   ctx->n_pad, ctx->e5m2, ctx->stream)
+                               : launch_init_sparse(ctx->C, ctx->n, ctx->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "init");
+      break;
+    }
+    constexpr int kRounds = 3;
+    for (int r = 0; r <= kRounds && rc == MAXSAT_OK; ++r) {
+      if (r == 1) cudaEventRecord(e0, ctx->stream);
+      rc = launch_round(ctx, ctx->stream, nullptr, (uint32_t)r);
+    }
+    if (rc != MAXSAT_OK) break;
+    cudaEventRecord(e1, ctx->stream);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "cudaEventSynchronize");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->auto_ms[d] = ms / kRounds;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->profiling = prof;
+  if (rc != MAXSAT_OK) return rc;
+  ctx->dense = ctx->auto_ms[1] < ctx->auto_ms[0];
+  ctx->auto_B = B;
+  ctx->have_chains = false;  // the timing runs left no valid chains
+  return MAXSAT_OK;
+}
+
+// Builds the dense (tensor-core) operands: the FP8 pattern-encoding gather
+// matrix, the block-diagonal variable x incidence matrix and their TMA maps.
+// Returns MAXSAT_OK, or an error code with *why (the context stays usable on
+// the sparse path).
+int build_dense(maxsat_ctx* ctx, int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
+                const int64_t* weights, const std::vector<int32_t>& var_off,
+                const std::vector<int4>& var_inc, std::string* why) {
+  DevAllocs& A = ctx->dense_mem;
+#define UPD(vec, dst)                                  \
+  do {                                                 \
+    int rc_ = upload(ctx, A, vec, &(dst));             \
+    if (rc_ != MAXSAT_OK) {                            \
+      *why = ctx->err;                                 \
+      return rc_;                                      \
+    }                                                  \
+  } while (0)
+  const int64_t cells = (int64_t)((n + 127) / 128 * 128) * (int64_t)((m + 127) / 128 * 128);
+  if (cells > ((int64_t)1 << 33)) {
+    *why = "the dense gather matrix would exceed 8 GB";
+    return MAXSAT_EINVAL;
+  }
+  int64_t wmax = 0;
+  for (int64_t c = 0; c < m; ++c) wmax = std::max<int64_t>(wmax, weights ? weights[c] : 1);
+  if (wmax >= ((int64_t)1 << 43)) {
+    *why = "the dense path needs weights below 2^43";
+    return MAXSAT_EINVAL;
+  }
+  std::vector<uint8_t> Ah;
+  std::string derr = build_gather_matrix(n, (int)m, off, lits, &ctx->e5m2, &ctx->n_pad,
+                                         &ctx->m_pad, &Ah);
+  if (!derr.empty()) {
+    *why = derr;
+    return MAXSAT_EINVAL;
+  }
+  std::vector<int32_t> rl(ctx->m_pad, 0);
+  std::vector<int64_t> rw(ctx->m_pad, 0);
+  for (int64_t c = 0; c < m; ++c) {
+    rl[c] = (int32_t)(off[c + 1] - off[c]);
+    rw[c] = weights ? weights[c] : 1;
+  }
+  // per 32-row group: 1 when all its rows carry the same weight
+  std::vector<uint8_t> small(ctx->m_pad / 32, 0);
+  for (int g = 0; g < ctx->m_pad / 32; ++g) {
+    bool same = true;
+    for (int r = 1; r < 32; ++r) same = same && rw[g * 32 + r] == rw[g * 32];
+    small[g] = same ? 1 : 0;
+  }
+  const uint8_t* dA = nullptr;
+  const int32_t* drl = nullptr;
+  const int64_t* drw = nullptr;
+  const uint8_t* dsm = nullptr;
+  UPD(Ah, dA);
+  UPD(rl, drl);
+  UPD(rw, drw);
+  UPD(small, dsm);
+  ctx->d_grp_small = const_cast<uint8_t*>(dsm);
+  ctx->dA = const_cast<uint8_t*>(dA);
+  ctx->d_row_len = const_cast<int32_t*>(drl);
+  ctx->d_row_w = const_cast<int64_t*>(drw);
+  derr = make_tmap_2d(&ctx->tmA, ctx->dA, ctx->n_pad, ctx->m_pad, ctx->n_pad, 128, 128, false);
+  if (!derr.empty()) {
+    *why = derr;
+    return MAXSAT_ECUDA;
+  }
+  // scatter-add operands: G values exact in BF16 up to 256, in FP16 up to
+  // 2048; the FP32 accumulator exact while |2^Q z| < 2^24
+  const int gmax = ctx->tabs.gq_absmax;
+  if (gmax > 2048 || (int64_t)ctx->max_degree * gmax >= ((int64_t)1 << 24)) {
+    *why = "scatter-add contributions are not exact in FP16 / FP32";
+    return MAXSAT_EINVAL;
+  }
+  ctx->g_bf16 = gmax <= 256;
+  ctx->tiles_v = ctx->n_pad / 128;
+  std::vector<int32_t> kst(ctx->tiles_v + 1), kbl(ctx->tiles_v);
+  for (int tv = 0; tv <= ctx->tiles_v; ++tv) kst[tv] = var_off[std::min(tv * 128, n)];
+  int kbmax = 1;
+  for (int tv = 0; tv < ctx->tiles_v; ++tv) {
+    kbl[tv] = std::max(1, (kst[tv + 1] - kst[tv] + 63) / 64);
+    kbmax = std::max(kbmax, kbl[tv]);
+  }
+  ctx->kmax = kbmax * 64;
+  const uint16_t plus = ctx->g_bf16 ? 0x3F80 : 0x3C00, minus = ctx->g_bf16 ? 0xBF80 : 0xBC00;
+  std::vector<uint16_t> A2((size_t)ctx->tiles_v * 128 * ctx->kmax, 0);
+  for (int i = 0; i < n; ++i) {
+    const int tv = i / 128;
+    for (int jj = var_off[i]; jj < var_off[i + 1]; ++jj)
+      A2[(size_t)i * ctx->kmax + (jj - kst[tv])] = var_inc[jj].y < 0 ? minus : plus;
+  }
+  // contributions as 16-bit floating-point bit patterns (exact: integers
+  // below 2^8 in BF16, below 2^11 in FP16)
+  std::vector<uint16_t> gq16(ctx->tabs.gq.size());
+  for (size_t k = 0; k < gq16.size(); ++k) {
+    const int v = ctx->tabs.gq[k];
+    uint16_t bits = 0;
+    if (v != 0) {
+      const unsigned av = (unsigned)(v < 0 ? -v : v);
+      const int e2 = 31 - __builtin_clz(av);
+      const int mb = ctx->g_bf16 ? 7 : 10;  // mantissa bits
+      const unsigned mant = (e2 <= mb ? (av << (mb - e2)) : (av >> (e2 - mb))) & ((1u << mb) - 1u);
+      bits = (uint16_t)(((unsigned)(e2 + (ctx->g_bf16 ? 127 : 15)) << mb) | mant);
+      if (v < 0) bits |= 0x8000;
+    }
+    gq16[k] = bits;
+  }
+  const uint16_t* dA2 = nullptr;
+  const int32_t* dks = nullptr;
+  const int32_t* dkb = nullptr;
+  const uint16_t* dg16 = nullptr;
+  UPD(A2, dA2);
+  UPD(kst, dks);
+  UPD(kbl, dkb);
+  UPD(gq16, dg16);
+  ctx->d_gq16 = const_cast<uint16_t*>(dg16);
+  ctx->d_kstart = const_cast<int32_t*>(dks);
+  ctx->d_kblocks = const_cast<int32_t*>(dkb);
+  derr = make_tmap_2d(&ctx->tmA2, dA2, ctx->kmax, (uint64_t)ctx->tiles_v * 128,
+                      (uint64_t)ctx->kmax * 2, 64, 128, true);
+  if (!derr.empty()) {
+    *why = derr;
+    return MAXSAT_ECUDA;
+  }
+  return MAXSAT_OK;
+#undef UPD
+}
 
 extern "C" {
 
@@ -576,108 +754,19 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
       return cuda_fail(nullptr, e, "cudaMalloc");
     }
   }
-  if (prm.path == MAXSAT_PATH_DENSE) {
-    int64_t wmax = 0;
-    for (int64_t c = 0; c < m; ++c) wmax = std::max<int64_t>(wmax, weights ? weights[c] : 1);
-    if (wmax >= ((int64_t)1 << 43)) {
-      delete ctx;
-      return fail(nullptr, MAXSAT_EINVAL, "the dense path needs weights below 2^43");
-    }
-    std::vector<uint8_t> Ah;
-    std::string derr = build_gather_matrix(n, (int)m, off, lits, &ctx->e5m2, &ctx->n_pad,
-                                           &ctx->m_pad, &Ah);
-    if (!derr.empty()) {
-      delete ctx;
-      return fail(nullptr, MAXSAT_EINVAL, derr);
-    }
-    std::vector<int32_t> rl(ctx->m_pad, 0);
-    std::vector<int64_t> rw(ctx->m_pad, 0);
-    for (int64_t c = 0; c < m; ++c) {
-      rl[c] = (int32_t)(off[c + 1] - off[c]);
-      rw[c] = weights ? weights[c] : 1;
-    }
-    // per 32-row group: 1 when all its rows carry the same weight
-    std::vector<uint8_t> small(ctx->m_pad / 32, 0);
-    for (int g = 0; g < ctx->m_pad / 32; ++g) {
-      bool same = true;
-      for (int r = 1; r < 32; ++r) same = same && rw[g * 32 + r] == rw[g * 32];
-      small[g] = same ? 1 : 0;
-    }
-    const uint8_t* dA = nullptr;
-    const int32_t* drl = nullptr;
-    const int64_t* drw = nullptr;
-    const uint8_t* dsm = nullptr;
-    UP2(Ah, dA);
-    UP2(rl, drl);
-    UP2(rw, drw);
-    UP2(small, dsm);
-    ctx->d_grp_small = const_cast<uint8_t*>(dsm);
-    ctx->dA = const_cast<uint8_t*>(dA);
-    ctx->d_row_len = const_cast<int32_t*>(drl);
-    ctx->d_row_w = const_cast<int64_t*>(drw);
-    derr = make_tmap_2d(&ctx->tmA, ctx->dA, ctx->n_pad, ctx->m_pad, ctx->n_pad, 128, 128, false);
-    if (!derr.empty()) {
-      delete ctx;
-      return fail(nullptr, MAXSAT_ECUDA, derr);
-    }
-    // scatter-add operands: G values exact in BF16 up to 256, in FP16 up to
-    // 2048; the FP32 accumulator exact while |2^Q z| < 2^24
-    const int gmax = ctx->tabs.gq_absmax;
-    if (gmax > 2048 || (int64_t)ctx->max_degree * gmax >= ((int64_t)1 << 24)) {
-      delete ctx;
-      return fail(nullptr, MAXSAT_EINVAL, "scatter-add contributions are not exact in FP16 / FP32");
-    }
-    ctx->g_bf16 = gmax <= 256;
-    ctx->tiles_v = ctx->n_pad / 128;
-    std::vector<int32_t> kst(ctx->tiles_v + 1), kbl(ctx->tiles_v);
-    for (int tv = 0; tv <= ctx->tiles_v; ++tv) kst[tv] = var_off[std::min(tv * 128, n)];
-    int kbmax = 1;
-    for (int tv = 0; tv < ctx->tiles_v; ++tv) {
-      kbl[tv] = std::max(1, (kst[tv + 1] - kst[tv] + 63) / 64);
-      kbmax = std::max(kbmax, kbl[tv]);
-    }
-    ctx->kmax = kbmax * 64;
-    const uint16_t plus = ctx->g_bf16 ? 0x3F80 : 0x3C00, minus = ctx->g_bf16 ? 0xBF80 : 0xBC00;
-    std::vector<uint16_t> A2((size_t)ctx->tiles_v * 128 * ctx->kmax, 0);
-    for (int i = 0; i < n; ++i) {
-      const int tv = i / 128;
-      for (int jj = var_off[i]; jj < var_off[i + 1]; ++jj)
-        A2[(size_t)i * ctx->kmax + (jj - kst[tv])] = var_inc[jj].y < 0 ? minus : plus;
-    }
-    // contributions as 16-bit floating-point bit patterns (exact: integers
-    // below 2^8 in BF16, below 2^11 in FP16)
-    std::vector<uint16_t> gq16(ctx->tabs.gq.size());
-    for (size_t k = 0; k < gq16.size(); ++k) {
-      const int v = ctx->tabs.gq[k];
-      uint16_t bits = 0;
-      if (v != 0) {
-        const unsigned av = (unsigned)(v < 0 ? -v : v);
-        const int e2 = 31 - __builtin_clz(av);
-        const int mb = ctx->g_bf16 ? 7 : 10;  // mantissa bits
-        const unsigned mant = (e2 <= mb ? (av << (mb - e2)) : (av >> (e2 - mb))) & ((1u << mb) - 1u);
-        bits = (uint16_t)(((unsigned)(e2 + (ctx->g_bf16 ? 127 : 15)) << mb) | mant);
-        if (v < 0) bits |= 0x8000;
+  if (prm.path != MAXSAT_PATH_SPARSE) {
+    std::string why;
+    const int drc = build_dense(ctx, n, m, off, lits, weights, var_off, var_inc, &why);
+    if (drc == MAXSAT_OK) {
+      ctx->dense_built = true;
+      ctx->dense = prm.path == MAXSAT_PATH_DENSE;
+    } else {
+      ctx->dense_mem.release();
+      if (prm.path == MAXSAT_PATH_DENSE) {
+        delete ctx;
+        return fail(nullptr, drc, why);
       }
-      gq16[k] = bits;
     }
-    const uint16_t* dA2 = nullptr;
-    const int32_t* dks = nullptr;
-    const int32_t* dkb = nullptr;
-    const uint16_t* dg16 = nullptr;
-    UP2(A2, dA2);
-    UP2(kst, dks);
-    UP2(kbl, dkb);
-    UP2(gq16, dg16);
-    ctx->d_gq16 = const_cast<uint16_t*>(dg16);
-    ctx->d_kstart = const_cast<int32_t*>(dks);
-    ctx->d_kblocks = const_cast<int32_t*>(dkb);
-    derr = make_tmap_2d(&ctx->tmA2, dA2, ctx->kmax, (uint64_t)ctx->tiles_v * 128,
-                        (uint64_t)ctx->kmax * 2, 64, 128, true);
-    if (!derr.empty()) {
-      delete ctx;
-      return fail(nullptr, MAXSAT_ECUDA, derr);
-    }
-    ctx->dense = true;
   }
   *out = ctx;
   return MAXSAT_OK;
@@ -686,6 +775,10 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
 int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 1 || B > (1 << 26)) return fail(ctx, MAXSAT_EINVAL, "restarts must be in 1..2^26");
+  if (ctx->prm.path == MAXSAT_PATH_AUTO && ctx->dense_built && ctx->auto_B != B) {
+    int rc0 = choose_path(ctx, B);
+    if (rc0 != MAXSAT_OK) return rc0;
+  }
   int rc = alloc_chains(ctx, B);
   if (rc != MAXSAT_OK) return rc;
   if (ctx->C.key0 != (uint32_t)seed || ctx->C.key1 != (uint32_t)(seed >> 32)) destroy_graph(ctx);
@@ -804,7 +897,7 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
   if (B == 0) return MAXSAT_OK;
-  if (ctx->dense) {
+  if (ctx->dense_built) {
     const int Bp = (B + 255) / 256 * 256;
     if (Bp > ctx->dev_Bp) {
       // grow the eval scratch (cudaFree of the old one synchronises the device)

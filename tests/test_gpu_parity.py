@@ -338,3 +338,19 @@ def test_dense_solve_and_resume(ms, stream, small_table):
     ms.maxsat_destroy(ctx)
     for k in ["x", "nu", "best_cost", "best_x", "cost", "free_energy"]:
         assert np.array_equal(whole[k], end[k]), k
+
+
+def test_auto_path_choice_is_measured_and_consistent(ms, stream, golden_table):
+    """MAXSAT_PATH_AUTO: the reset times both paths and keeps one; the chains
+    it then runs follow the same contract (sampled chains vs the oracle)."""
+    inst = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0))
+    B, T, seed = 1024, 4, 8
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=2,
+                  path=ms.MAXSAT_PATH_AUTO)
+    rows = np.array([0, 511, 512, 1023])
+    ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows, B_total=B)
+    assert_same(gpu, ora, T, 0.01, rows=rows)
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=ms.MAXSAT_PATH_AUTO)
+    ms.maxsat_reset(ctx, B, seed)
+    assert ms.maxsat_get_path(ctx) in (ms.MAXSAT_PATH_DENSE, ms.MAXSAT_PATH_SPARSE)
+    ms.maxsat_destroy(ctx)
