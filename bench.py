@@ -191,16 +191,37 @@ def dense_block_work(n, off, lits):
     return tot
 
 
-def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks):
+def alu_peak(clock_mhz):
+    """Instruction-issue peak: 152 SMs x 4 sub-partitions x 32 lanes, one
+    instruction per sub-partition per clock, at the SM clock seen."""
+    return 152 * 4 * 32 * clock_mhz * 1e6 / 1e12
+
+
+def sampling_ops(off):
+    """Algorithmic integer operations of the hidden sampling per chain: per
+    clause with L hidden units, L/8 Philox4x32-10 calls (10 rounds x (2
+    multiplies + 2 three-way XORs) = 40 operations for 8 draws, i.e. 5 per
+    draw), one threshold compare per unit, one truth test per literal."""
+    lens = np.diff(off)
+    L = np.where(lens <= 3, 3, lens + 1)
+    L = np.where(lens == 0, 0, L)
+    return float((6 * L + lens).sum())
+
+
+def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks, clock_mhz):
     """(bound, algorithmic amount per launch, unit, peak) of one kernel.
-    Sparse kernels: compulsory bytes against the copy bandwidth. Dense
-    kernels: tensor-core FLOPs (the dense gather product C x states, 2 m n B;
-    the block-diagonal scatter-add, 2 B sum over variable tiles of 128 x its
-    incidence range) against the FP8 / BF16 dense peak."""
+    Sparse gather: integer operations of the hidden sampling against the
+    instruction-issue peak. Sparse visible update: compulsory bytes against
+    the copy bandwidth. Dense kernels: tensor-core FLOPs (the dense gather
+    product C x states, 2 m n B; the block-diagonal scatter-add, 2 B sum over
+    variable tiles of 128 x its incidence range) against the FP8 / BF16 dense
+    peak."""
     if kernel in ("gemm1_step", "gemm1_score", "gemm1_eval"):
         return "tensor", 2.0 * m * n * B, "TFLOP/s", 2.0 * peaks["bf16_tflops_sustained"]
     if kernel == "gemm2":
         return "tensor", 2.0 * B * dense_block_work(n, off, lits), "TFLOP/s", peaks["bf16_tflops_sustained"]
+    if kernel == "gather_hidden":
+        return "alu", B * sampling_ops(off), "Tops/s", alu_peak(clock_mhz)
     return "hbm", algorithmic_bytes(kernel, n, m, nnz, B), "GB/s", peaks["hbm_gbs"]
 
 
@@ -237,8 +258,11 @@ def run_mine(args):
                  "dense": ms.MAXSAT_PATH_DENSE}[args.path]
     params = ms.maxsat_default_params(path=path_code)
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
-    seed = args.seed * 1000003 + rank
-    ms.maxsat_reset(ctx, B, seed)
+    # every rank runs its own shard of one ensemble of ws * B chains (weak
+    # scaling): global chains rank * B .. rank * B + B - 1
+    seed = args.seed * 1000003
+    offset, total = rank * B, ws * B
+    ms.maxsat_reset_shard(ctx, B, seed, offset, total)
     ms.maxsat_step(ctx, args.warmup)
     stream.synchronize()
 
@@ -273,19 +297,22 @@ def run_mine(args):
     launches, tot = kt[top]
     avg_s = tot / launches / 1e3
     peaks, peak_src = measured_peaks()
-    bound, alg, unit, peak = kernel_roofline(top, n, m, nnz, B, off, lits, peaks)
+    clock = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    bound, alg, unit, peak = kernel_roofline(top, n, m, nnz, B, off, lits, peaks, clock)
     scale = 1e9 if unit == "GB/s" else 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f).get(args.workload, {}).get(top)
-        if tr and tr.get("kernel_hash") == ms_kernel_hash():
+        if tr and tr.get("source_hash") == kernel_source_hash(top):
             traffic = tr.get("bytes_per_launch")
     roofline = dict(kernel=top, bound=bound, achieved=alg / avg_s / scale, peak=peak, unit=unit,
                     frac=alg / avg_s / scale / peak, traffic=traffic,
                     algorithmic=alg, avg_launch_us=avg_s * 1e6,
                     peak_source=(f"{peak_src} copy bandwidth" if unit == "GB/s" else
+                                 f"issue peak 152 SM x 4 x 32 lanes at {clock:.0f} MHz (SM clock "
+                                 "seen in the timed region)" if unit == "Tops/s" else
                                  f"{peak_src} BF16 sustained" + (" x 2 (nominal FP8/BF16)"
                                                                  if "gemm1" in top else "")),
                     kernels={k: dict(launches=v[0], avg_us=1e3 * v[1] / v[0])
@@ -314,6 +341,16 @@ def run_mine(args):
         v, threads, sample, _ = oracle_rate(n, off, lits, w, B, args.cpu_seconds, seed)
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
 
+    # the one exchange of the multi-rank path: best cost and assignment
+    ms.maxsat_score(ctx)
+    stt = ms.maxsat_get_state(ctx)
+    lb = int(np.argmin(stt["best_cost"]))
+    gbest = (int(stt["best_cost"][lb]), offset + lb)
+    if ws > 1:
+        from paper_2311_02101_gb300 import distributed as dd
+        c_, ch_, _ = dd.reduce_best(gbest[0], gbest[1], stt["best_x"][lb])
+        gbest = (c_, ch_)
+
     dense_eval = dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
     paths = compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
 
@@ -326,11 +363,13 @@ def run_mine(args):
                 scaling="weak", vs_baseline=None, dtype="fp8" if path == "dense" else "int32",
                 data="synthetic",
                 config=dict(workload=args.workload, n=n, m=m, B=B, path=path, path_requested=args.path,
-                            steps_per_graph=S, parallelism=f"replicas{ws}",
+                            steps_per_graph=S, parallelism=f"chain-shards{ws}",
                             l2="working set above L2 (no flush): G/hidden state, nu and "
                                "x of 4096 chains; state carried step to step"),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
-                gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths)
+                gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
+                best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
+                          chains=ws * B))
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -408,13 +447,23 @@ def compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args):
     return out
 
 
-def ms_kernel_hash():
+KERNEL_SOURCES = {
+    "gather_hidden": ["sparse.cu", "philox.cuh", "internal.h"],
+    "visible": ["sparse.cu", "philox.cuh", "internal.h"],
+    "gemm1_step": ["dense_step.cu", "dense_common.cuh", "tc_ptx.cuh", "philox.cuh", "internal.h"],
+    "gemm2": ["dense_step.cu", "dense_common.cuh", "tc_ptx.cuh", "philox.cuh", "internal.h"],
+    "gemm1_eval": ["dense.cu", "dense_common.cuh", "tc_ptx.cuh", "internal.h"],
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a kernel is built from: a recorded DRAM traffic
+    figure is used only while it matches."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2311_02101_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
 

@@ -126,6 +126,15 @@ int maxsat_create(maxsat_ctx** out, int32_t n_vars, int64_t n_clauses,
  * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */
 int maxsat_reset(maxsat_ctx* ctx, int32_t restarts, uint64_t seed);
 
+/* maxsat_reset for one shard of a larger ensemble (chains are independent,
+ * Sec. 4.2): the local chains are chains chain_offset .. chain_offset + B - 1
+ * of an ensemble of total_chains. Every draw and the temperature block of a
+ * chain follow its global index, so shards on several GPUs together run
+ * exactly the chains of one total_chains run. chain_offset must be a
+ * multiple of 8; maxsat_reset(ctx, B, seed) is the shard (0, B). */
+int maxsat_reset_shard(maxsat_ctx* ctx, int32_t restarts, uint64_t seed,
+                       int32_t chain_offset, int32_t total_chains);
+
 /* Runs `steps` Gibbs rounds on the current chains. Round t scores the current
  * state x_t (cost, free energy), keeps it if its cost is strictly below the
  * chain's best, draws h ~ p(h | x_t) and x_{t+1} ~ p(v | h) and updates nu.

@@ -66,6 +66,7 @@ def lib():
         L.maxsat_create.argtypes = [ctypes.POINTER(P), i32, i64, P, P, P,
                                     ctypes.POINTER(maxsat_params), P]
         L.maxsat_reset.argtypes = [P, i32, u64]
+        L.maxsat_reset_shard.argtypes = [P, i32, u64, i32, i32]
         L.maxsat_step.argtypes = [P, i64]
         L.maxsat_score.argtypes = [P]
         L.maxsat_eval.argtypes = [P, P, i32, P]
@@ -81,7 +82,8 @@ def lib():
         L.maxsat_eval_noalloc.argtypes = [i32, i64, i64, P, P, P, P, i32, P, P]
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
-        for name in ["maxsat_create", "maxsat_reset", "maxsat_step", "maxsat_score",
+        for name in ["maxsat_create", "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
+                     "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
                      "maxsat_get_path", "maxsat_fit_or_rbm", "maxsat_set_profiling",
                      "maxsat_kernel_times", "maxsat_eval_noalloc"]:
@@ -170,6 +172,13 @@ def maxsat_create(n, off, lits, weights=None, params=None, stream=None) -> Conte
 
 def maxsat_reset(ctx: Context, restarts: int, seed: int):
     _check(lib().maxsat_reset(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1)), ctx)
+    ctx.B = int(restarts)
+
+
+def maxsat_reset_shard(ctx: Context, restarts: int, seed: int, chain_offset: int,
+                       total_chains: int):
+    _check(lib().maxsat_reset_shard(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1),
+                                    int(chain_offset), int(total_chains)), ctx)
     ctx.B = int(restarts)
 
 

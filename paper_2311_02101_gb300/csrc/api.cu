@@ -343,6 +343,8 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
     rc = alloc_chains(ctx, B);
     if (rc != MAXSAT_OK) break;
     ctx->C.keys = philox_keys(0x5EEDu, 0u);
+    ctx->C.g8_off = 0;
+    ctx->C.B_total = B;
     cudaError_t e = ctx->dense ? launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n,
                                                    ctx->n_pad, ctx->e5m2, ctx->stream)
                                : launch_init_sparse(ctx->C, ctx->n, ctx->stream);
@@ -773,18 +775,32 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
 }
 
 int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
+  return maxsat_reset_shard(ctx, B, seed, 0, B);
+}
+
+int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_offset,
+                       int32_t total_chains) {
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 1 || B > (1 << 26)) return fail(ctx, MAXSAT_EINVAL, "restarts must be in 1..2^26");
+  if (chain_offset < 0 || chain_offset % 8 != 0 || total_chains < chain_offset + B ||
+      (int64_t)total_chains + kChainTile > ((int64_t)1 << 26))
+    return fail(ctx, MAXSAT_EINVAL,
+                "chain_offset must be a non-negative multiple of 8 and chain_offset + restarts "
+                "<= total_chains < 2^26 - 256");
   if (ctx->prm.path == MAXSAT_PATH_AUTO && ctx->dense_built && ctx->auto_B != B) {
     int rc0 = choose_path(ctx, B);
     if (rc0 != MAXSAT_OK) return rc0;
   }
   int rc = alloc_chains(ctx, B);
   if (rc != MAXSAT_OK) return rc;
-  if (ctx->C.key0 != (uint32_t)seed || ctx->C.key1 != (uint32_t)(seed >> 32)) destroy_graph(ctx);
+  if (ctx->C.key0 != (uint32_t)seed || ctx->C.key1 != (uint32_t)(seed >> 32) ||
+      ctx->C.g8_off != chain_offset / 8 || ctx->C.B_total != total_chains)
+    destroy_graph(ctx);
   ctx->C.key0 = (uint32_t)seed;
   ctx->C.key1 = (uint32_t)(seed >> 32);
   ctx->C.keys = philox_keys(ctx->C.key0, ctx->C.key1);
+  ctx->C.g8_off = chain_offset / 8;
+  ctx->C.B_total = total_chains;
   ctx->seed = seed;
   ctx->t = 0;
   ctx->d_t_synced = false;

@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
 #pragma unroll
         for (int sub = 0; sub < 4; ++sub) {
           const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
-          const int e0 = temp_of(b0, E, a.B);
-          const bool e_uni = e0 == temp_of(b0 + 7, E, a.B);
+          const int gb0 = C.g8_off * 8 + b0;  // global chain index
+          const int e0 = temp_of(gb0, E, C.B_total);
+          const bool e_uni = e0 == temp_of(gb0 + 7, E, C.B_total);
           int row[8];
           float f[8];
 #pragma unroll
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
             // truth pattern; the mask keeps table rows in range even if the
             // accumulator is invalid after a timed-out wait
             const int p = ((__float2int_rn(__uint_as_float(r[sub * 8 + q])) + bias) >> 1) & bias;
-            row[q] = ((e_uni ? e0 : temp_of(b0 + q, E, a.B)) << len) + p;
+            row[q] = ((e_uni ? e0 : temp_of(gb0 + q, E, C.B_total)) << len) + p;
             f[q] = grp >= 0 ? fe_tab[gm.fe_off + row[q]] : 0.f;
           }
           const float fs = tc::column_sums8(f, lane);
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
                 const int h = 3 * wd + rr;
                 if (h >= gm.nh) break;
                 const uint4 R = philox4x32_10(
-                    make_uint4((uint32_t)c, (uint32_t)(b0 >> 3) | ((uint32_t)h << 24), tround,
+                    make_uint4((uint32_t)c, (uint32_t)(gb0 >> 3) | ((uint32_t)h << 24), tround,
                                kPhaseHidden),
                     C.keys);
 #pragma unroll
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
         const int4* inc = stI(s);
         const HT* hs = stH(s);
         uint8_t* rowp = stB(s) + chain * 128;
-        const int e = temp_of(tn * kBN + chain, T.n_temps, a.B);
+        const int e = temp_of(C.g8_off * 8 + tn * kBN + chain, T.n_temps, C.B_total);
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
           const int chunk = hk * 4 + ch;
@@ -640,7 +641,8 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
         for (int sub = 0; sub < 4; ++sub) {
           const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
           const uint4 R = philox4x32_10(
-              make_uint4((uint32_t)i, (uint32_t)(b0 >> 3), tround, kPhaseVisible), C.keys);
+              make_uint4((uint32_t)i, (uint32_t)(C.g8_off + (b0 >> 3)), tround, kPhaseVisible),
+              C.keys);
           if (!valid) continue;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -677,7 +679,8 @@ __global__ void k_init_dense(DevChains C, uint8_t* X, float* nu, uint8_t* best_x
   const int i = blockIdx.y * blockDim.x + threadIdx.x;
   if (i < n_pad) {
     uint4 r = make_uint4(0, 0, 0, 0);
-    if (i < n) r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, 0u, kPhaseInit), C.keys);
+    if (i < n)
+      r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), 0u, kPhaseInit), C.keys);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const size_t o = (size_t)(b0 + q) * n_pad + i;

@@ -72,6 +72,8 @@ struct RoundKeys {
 struct DevChains {
   int32_t B;      // chains reported
   int32_t Bp;     // chains allocated (multiple of kChainTile)
+  int32_t g8_off;   // global index of local chain 0, divided by 8 (chain shards)
+  int32_t B_total;  // chains of the whole ensemble (temperature blocks)
   uint32_t key0, key1;
   RoundKeys keys;
   uint8_t* xt;        // sparse layout: n x Bp, 0/1

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
   const int i = blockIdx.y * 8 + warp;
   if (i < n) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, 0u, kPhaseInit), C.keys);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), 0u, kPhaseInit), C.keys);
     uint64_t x = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) x |= (uint64_t)(lane16(r, q) < 32768u) << (8 * q);
@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
 
   // temperature of the thread's 8 chains: one value unless a temperature
   // block boundary falls inside them
-  const int e0 = FE ? temp_of(b0, E, B) : 0;
-  const bool e_uniform = !FE || e0 == temp_of(b0 + 7, E, B);
+  // global chain index: draws and temperatures follow it (chain shards)
+  const int gb0 = C.g8_off * 8 + b0;
+  const int e0 = FE ? temp_of(gb0, E, C.B_total) : 0;
+  const bool e_uniform = !FE || e0 == temp_of(gb0 + 7, E, C.B_total);
   // the weighted unsat cost accumulates in this warp's shared-memory row
   // (each entry is owned by one thread), the free energy in registers
   int64_t* my_cost = &s_cost[warp][lane * 8];
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
     int row[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      row[q] = ((e_uniform ? e0 : temp_of(b0 + q, E, B)) << len) + p[q];
+      row[q] = ((e_uniform ? e0 : temp_of(gb0 + q, E, C.B_total)) << len) + p[q];
 #pragma unroll
     for (int q = 0; q < 8; ++q) fe[q] += fe_tab[gm.fe_off + row[q]];
     if constexpr (SAMPLE) {
@@ -168,7 +170,9 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
           const int h = 3 * w + r;
           if (h >= gm.nh) break;
           const uint4 R = philox4x32_10(
-              make_uint4((uint32_t)c, (uint32_t)g8 | ((uint32_t)h << 24), t, kPhaseHidden), C.keys);
+              make_uint4((uint32_t)c, (uint32_t)(g8 + C.g8_off) | ((uint32_t)h << 24), t,
+                         kPhaseHidden),
+              C.keys);
   #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const uint32_t P = (uint32_t)(wd[q] >> (17 * r)) & 0x1FFFFu;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevC
   const uint32_t t = step_index(tdev, t_rel);
   int e[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) e[q] = temp_of(b0 + q, T.n_temps, C.B);
+  for (int q = 0; q < 8; ++q) e[q] = temp_of(C.g8_off * 8 + b0 + q, T.n_temps, C.B_total);
   int z[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) z[q] = 0;
@@ -296,7 +300,8 @@ __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevC
   const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
   keep_improved(C, o, b0, xold);
 
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)g8, t, kPhaseVisible), C.keys);
+  const uint4 r =
+      philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), t, kPhaseVisible), C.keys);
   float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
   const float4 n0 = nu4[0], n1 = nu4[1];
   float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};

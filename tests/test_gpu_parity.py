@@ -354,3 +354,23 @@ def test_auto_path_choice_is_measured_and_consistent(ms, stream, golden_table):
     ms.maxsat_reset(ctx, B, seed)
     assert ms.maxsat_get_path(ctx) in (ms.MAXSAT_PATH_DENSE, ms.MAXSAT_PATH_SPARSE)
     ms.maxsat_destroy(ctx)
+
+
+@pytest.mark.parametrize("path", ["sparse", "dense"])
+def test_chain_shards_reproduce_one_run(ms, stream, small_table, path):
+    """Two shards of 256 chains (global chains 0..255 and 256..511 of 512) run
+    exactly the chains of one 512-chain run: draws and temperature blocks
+    follow the global chain index."""
+    code = ms.MAXSAT_PATH_DENSE if path == "dense" else ms.MAXSAT_PATH_SPARSE
+    inst = inst_of(workloads.random_ksat(80, 340, 3, seed=6, wmax=20))
+    T, seed = 12, 77
+    whole = run_gpu(ms, stream, inst, small_table, 512, T, seed, spg=4, path=code)
+    for r in range(2):
+        ctx = make_ctx(ms, stream, inst, small_table, spg=4, path=code)
+        ms.maxsat_reset_shard(ctx, 256, seed, 256 * r, 512)
+        ms.maxsat_step(ctx, T)
+        part = ms.maxsat_get_state(ctx)
+        ms.maxsat_destroy(ctx)
+        sl = slice(256 * r, 256 * r + 256)
+        for k in ["x", "best_cost", "best_x", "cost", "nu", "free_energy"]:
+            assert np.array_equal(part[k], whole[k][sl]), (k, r)
