@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--path", default="auto", choices=["auto", "sparse", "dense"])
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--fixed-seconds", type=float, default=3.0,
+                    help="wall time of the equal-time best-cost comparison")
     return ap.parse_args()
 
 
@@ -353,6 +356,8 @@ def run_mine(args):
 
     dense_eval = dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
     paths = compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
+    fp32 = fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args,
+                           ms_total / args.steps) if not args.no_fp32 else None
 
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
@@ -369,13 +374,143 @@ def run_mine(args):
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
-                          chains=ws * B))
+                          chains=ws * B),
+                fp32_form=fp32)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+class Fp32Form:
+    """The plain FP32 form of one Gibbs round (the comparator): the same
+    clause RBMs and tables, the gather and the scatter-add as FP32 matrix
+    products in PyTorch (TF32 off), lookups and Bernoulli draws as tensor
+    ops with torch's generator. Uniform clause length only (k-SAT)."""
+
+    def __init__(self, torch, n, off, lits, w, B, sets, fstar=(0.068, 0.528), J=4, Q=4):
+        torch.backends.cuda.matmul.allow_tf32 = False
+        lens = np.diff(off)
+        K = int(lens[0])
+        assert (lens == K).all()
+        m = len(off) - 1
+        E = len(fstar)
+        self.t, self.n, self.m, self.B, self.K, self.E = torch, n, m, B, K, E
+        dev = "cuda"
+        lit = lits.reshape(m, K).astype(np.int64)
+        var, lam = np.abs(lit) - 1, np.sign(lit)
+        A = np.zeros((m, n), np.float32)
+        for k in range(K):
+            np.add.at(A, (np.arange(m), var[:, k]), lam[:, k] * float(2 ** k))
+        self.A = torch.tensor(A, device=dev)
+        Pm = np.zeros((m * K, n), np.float32)  # literal x variable, +-1
+        Pm[np.arange(m * K), var.reshape(-1)] = lam.reshape(-1)
+        self.P = torch.tensor(Pm, device=dev)
+        wmin = int(w.min())
+        bucket = np.zeros(m, np.int64)
+        for j in range(1, J):
+            bucket[w >= wmin * 2 ** j] = j
+        self.bucket = torch.tensor(bucket, device=dev)
+        self.w = torch.tensor(w, device=dev)
+        self.e = torch.tensor(np.minimum(np.arange(B) * E // B, E - 1), device=dev)
+        # tables per set s = bucket * E + e: thresholds [s][p][h], free energy
+        # [s][p], contributions 2^Q G [s][hp][k], visible thresholds [q]
+        L = None
+        ph, fe, gq = [], [], []
+        for j in range(J):
+            for e in range(E):
+                st = [x for x in sets if x["len"] == K and x["bucket"] == j and x["temp"] == e][0]
+                W, b = np.asarray(st["W"]), np.asarray(st["b"])
+                L = W.shape[1]
+                V = np.array([[(p >> k) & 1 for k in range(K)] for p in range(2 ** K)], float)
+                a = V @ W + b
+                ph.append(np.rint(65536.0 / (1.0 + np.exp(-a))))
+                fe.append(-np.logaddexp(0, a).sum(1))
+                Hp = np.array([[(hp >> h) & 1 for h in range(L)] for hp in range(2 ** L)], float)
+                gq.append(np.rint(Hp @ W.T * 2 ** Q))
+        self.L, self.Q = L, Q
+        self.ph = torch.tensor(np.stack(ph), dtype=torch.float32, device=dev)
+        self.fe = torch.tensor(np.stack(fe), dtype=torch.float32, device=dev)
+        self.gq = torch.tensor(np.stack(gq), dtype=torch.float32, device=dev)
+        qmax = 12 << Q
+        qs = np.arange(-qmax, qmax + 1)
+        self.qmax = qmax
+        self.pv = torch.tensor(np.rint(65536.0 / (1.0 + np.exp(-qs / 2.0 ** Q))), dtype=torch.float32,
+                               device=dev)
+        self.sidx = self.bucket[None, :] * E + self.e[:, None]  # B x m
+        self.gen = torch.Generator(device=dev).manual_seed(0)
+        self.x = (torch.rand(B, n, device=dev, generator=self.gen) < 0.5).float()
+        self.nu = torch.full((B, n), 0.25, device=dev)
+        self.best = torch.full((B,), 2 ** 62, dtype=torch.int64, device=dev)
+
+    def round(self, alpha=0.01):
+        t = self.t
+        D = (2.0 * self.x - 1.0) @ self.A.T  # B x m: 2 p - (2^K - 1)
+        p = ((D + (2 ** self.K - 1)) * 0.5).round().long()
+        cost = ((p == 0).long() * self.w[None, :]).sum(1)
+        self.best = t.minimum(self.best, cost)
+        Fb = self.fe[self.sidx, p].sum(1)
+        thr = self.ph[self.sidx, p]  # B x m x L
+        h = (t.rand(thr.shape, device="cuda", generator=self.gen) * 65536.0 < thr).long()
+        hp = (h << t.arange(self.L, device="cuda")).sum(-1)
+        G = self.gq[self.sidx, hp].reshape(self.B, self.m * self.K)  # 2^Q G per literal
+        z = G @ self.P  # B x n, units of 2^-Q
+        q = z.round().long().clamp(-self.qmax, self.qmax) + self.qmax
+        P = self.pv[q]
+        rho = P / 65536.0
+        self.nu = (1 - alpha) * self.nu + alpha * rho * (1 - rho)
+        self.x = (t.rand(P.shape, device="cuda", generator=self.gen) * 65536.0 < P).float()
+        return Fb
+
+
+def fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args, ours_ms_round):
+    """Device time per round of the plain FP32 form, and the best exact cost
+    each implementation reaches in the same wall time."""
+    lens = np.diff(off)
+    if not (lens == lens[0]).all():
+        return dict(unavailable="plain FP32 form written for uniform clause length")
+    f = Fp32Form(torch, n, off, lits, w, B, sets)
+    for _ in range(3):
+        f.round()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R = 20
+    a.record()
+    for _ in range(R):
+        f.round()
+    b.record()
+    b.synchronize()
+    ms_round = a.elapsed_time(b) / R
+    # equal wall time (seconds of rounds on each side, fresh chains, same seed)
+    budget = float(args.fixed_seconds)
+    f = Fp32Form(torch, n, off, lits, w, B, sets)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rounds_fp32 = 0
+    while time.perf_counter() - t0 < budget:
+        for _ in range(10):
+            f.round()
+        torch.cuda.synchronize()
+        rounds_fp32 += 10
+    best_fp32 = int(f.best.min())
+    ctx = ms.maxsat_create(n, off, lits, w, ms.maxsat_default_params(sets=sets), stream)
+    ms.maxsat_reset(ctx, B, seed)
+    rounds_ours = 0
+    chunk = max(10, int(0.05 / max(ours_ms_round / 1e3, 1e-6)))
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget:
+        ms.maxsat_step(ctx, chunk)
+        stream.synchronize()
+        rounds_ours += chunk
+    ms.maxsat_score(ctx)
+    best_ours = int(ms.maxsat_get_state(ctx)["best_cost"].min())
+    ms.maxsat_destroy(ctx)
+    return dict(ms_per_round=ms_round, speedup=ms_round / ours_ms_round,
+                fixed_time_s=budget, rounds_fp32=rounds_fp32, rounds_ours=rounds_ours,
+                best_cost_fp32=best_fp32, best_cost_ours=best_ours,
+                note="FP32 torch matmuls (TF32 off) + lookups, torch generator draws")
 
 
 def dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args):

@@ -282,11 +282,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
                     make_uint4((uint32_t)c, (uint32_t)(gb0 >> 3) | ((uint32_t)h << 24), tround,
                                kPhaseHidden),
                     C.keys);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  const uint32_t P = (uint32_t)(words[q] >> (17 * rr)) & 0x1FFFFu;
-                  hp[q] |= (uint32_t)(lane16(R, q) < P) << h;
-                }
+                hidden_bits(R, words, rr, h, hp);
               }
             }
             HT* H = static_cast<HT*>(a.H) + (size_t)c * a.Bp + b0;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
 }
 
 template <int MODE, bool SM, typename HT>
-__global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevChains C,
+__global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, DevChains C,
                                                 const uint8_t* __restrict__ xt, int B, int Bp,
                                                 int cblock, const uint32_t* tdev, uint32_t t_rel,
                                                 int64_t* cost_part, float* fe_part,
@@ -128,20 +128,29 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
   for (int c = c_begin + warp; c < c_end; c += 8) {
     const int o = __ldg(F.cl_off + c);
     const int len = __ldg(F.cl_off + c + 1) - o;
-    // byte q of plo: bits 0..7 of chain q's truth pattern; of phi: bits 8..15
-    uint64_t plo = 0, phi = 0;
+    // byte q of lo0|lo1 (chains 0..3 | 4..7): bits 0..7 of chain q's truth
+    // pattern; of hi0|hi1: bits 8..15
+    uint32_t lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
     for (int k = 0; k < len; ++k) {
       const int32_t lv = __ldg(F.lit_var + o + k);
-      uint64_t x8 = __ldg(reinterpret_cast<const unsigned long long*>(
-          xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
-      if (lv < 0) x8 ^= 0x0101010101010101ull;
-      if (k < 8) plo |= x8 << k;
-      else phi |= x8 << (k - 8);
+      const uint2 x8 =
+          __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
+      const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
+      if (k < 8) {
+        lo0 |= (x8.x ^ flip) << k;
+        lo1 |= (x8.y ^ flip) << k;
+      } else {
+        hi0 |= (x8.x ^ flip) << (k - 8);
+        hi1 |= (x8.y ^ flip) << (k - 8);
+      }
     }
     int p[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      p[q] = (int)((plo >> (8 * q)) & 0xFFu) | ((int)((phi >> (8 * q)) & 0xFFu) << 8);
+    for (int q = 0; q < 4; ++q) {
+      // result byte 0 = byte q of the low word, byte 1 = byte q of the high word
+      p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
+      p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
+    }
     const int64_t wc = __ldg(F.cl_w + c);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
@@ -173,11 +182,7 @@ __global__ void __launch_bounds__(256) k_gather(DevFormula F, DevTables T, DevCh
               make_uint4((uint32_t)c, (uint32_t)(g8 + C.g8_off) | ((uint32_t)h << 24), t,
                          kPhaseHidden),
               C.keys);
-  #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const uint32_t P = (uint32_t)(wd[q] >> (17 * r)) & 0x1FFFFu;
-            hp[q] |= (uint32_t)(lane16(R, q) < P) << h;
-          }
+          hidden_bits(R, wd, r, h, hp);
         }
       }
       HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;

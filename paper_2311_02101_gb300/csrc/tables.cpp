@@ -8,9 +8,11 @@
 // logits (Eq. 7) only on the pattern hp = sum_h h_h 2^h of sampled hidden
 // units. Per group g (clause length K, weight bucket) with L hidden units and
 // per temperature e the tables hold
-//   hid[g][e][p][w]   u64 word w packs rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))
-//                     for h = 3w, 3w + 1, 3w + 2 in bits 0, 17, 34 (17 bits each,
-//                     values 0..65536); W = ceil(L / 3) words per pattern
+//   hid[g][e][p][w]   u64 word w packs, for h = 3w + r (r = 0, 1, 2), the
+//                     threshold P = rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))
+//                     as min(P, 65535) in bits 16 r .. 16 r + 15 and [P == 65536]
+//                     in bit 48 + r (a draw u in 0..65535 gives 1 iff u < P, i.e.
+//                     iff u < min(P, 65535) or P == 65536); W = ceil(L / 3)
 //   fe[g][e][p]       -sum_h softplus(b_h + sum_k W_kh tau_k(p))       (float)
 //   gq[g][e][hp][k]   2^Q sum_h W_kh [bit h of hp]                     (int16)
 // and the visible table pv[q] = rint(65536 sigma(q 2^-Q)) for |q| <= qmax.
@@ -93,7 +95,9 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
           for (int k = 0; k < K; ++k)
             if ((p >> k) & 1) acc += Wq[k * L + h];
           const double a = s->b[h] + (double)acc / scale;
-          words[h / 3] |= (uint64_t)prob16(a) << (17 * (h % 3));
+          const uint32_t P = prob16(a);
+          words[h / 3] |= (uint64_t)(P < 65535u ? P : 65535u) << (16 * (h % 3));
+          if (P == 65536u) words[h / 3] |= (uint64_t)1 << (48 + h % 3);
           F -= softplus(a);
         }
         for (uint64_t w : words) T->hid.push_back(w);
