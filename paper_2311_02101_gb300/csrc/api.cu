@@ -78,6 +78,8 @@ struct maxsat_ctx {
   int64_t* ev_part = nullptr;
   int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
+  int gather_slots = 0;  // SMs x resident gather blocks per SM
+  int gather_cb = 0;     // clauses per gather block for the chains' Bp
   bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
 
   cudaGraphExec_t graph = nullptr;
@@ -225,8 +227,8 @@ int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_
     return MAXSAT_OK;
   }
   TIMED(ctx, st, "gather_hidden",
-        launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, tdev, t_rel, C.cost_part,
-                      C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
+        launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->gather_cb, tdev, t_rel,
+                      C.cost_part, C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
   TIMED(ctx, st, "visible",
         launch_visible(ctx->F, ctx->T, C, (float)ctx->prm.alpha, tdev, t_rel, ctx->wide_h, st));
   return MAXSAT_OK;
@@ -263,7 +265,14 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   ctx->have_chains = false;
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
   const size_t nB = (size_t)ctx->n * Bp;
-  const int nblk = clause_blocks_for(ctx->m);
+  if (ctx->gather_slots == 0) {
+    int dev = 0, sms = 0;
+    CK(ctx, cudaGetDevice(&dev));
+    CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ctx->gather_slots = std::max(sms, 1) * gather_blocks_per_sm(ctx->T, ctx->wide_h);
+  }
+  ctx->gather_cb = gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
+  const int nblk = ctx->m > 0 ? (ctx->m + ctx->gather_cb - 1) / ctx->gather_cb : 1;
   DevChains& C = ctx->C;
   C = DevChains{};
   C.B = B;
@@ -345,6 +354,7 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
     ctx->C.keys = philox_keys(0x5EEDu, 0u);
     ctx->C.g8_off = 0;
     ctx->C.B_total = B;
+    ctx->C.inv_B_total = 1.0f / (float)B;
     cudaError_t e = ctx->dense ? launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n,
                                                    ctx->n_pad, ctx->e5m2, ctx->stream)
                                : launch_init_sparse(ctx->C, ctx->n, ctx->stream);
@@ -801,6 +811,7 @@ int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_
   ctx->C.keys = philox_keys(ctx->C.key0, ctx->C.key1);
   ctx->C.g8_off = chain_offset / 8;
   ctx->C.B_total = total_chains;
+  ctx->C.inv_B_total = 1.0f / (float)total_chains;
   ctx->seed = seed;
   ctx->t = 0;
   ctx->d_t_synced = false;
@@ -860,8 +871,8 @@ int maxsat_score(maxsat_ctx* ctx) {
     return MAXSAT_OK;
   }
   TIMED(ctx, ctx->stream, "gather_score",
-        launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, nullptr, 0, C.cost_part,
-                      C.fe_part, C.tickets, nullptr, ctx->wide_h, ctx->stream));
+        launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->gather_cb, nullptr, 0,
+                      C.cost_part, C.fe_part, C.tickets, nullptr, ctx->wide_h, ctx->stream));
   TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(C, ctx->n, ctx->stream));
   return MAXSAT_OK;
 }
@@ -947,8 +958,9 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
     ctx->ev_Bp = Bp;
   }
   CK(ctx, launch_transpose_in(assign_dev, B, ctx->n, ctx->ev_xt, Bp, ctx->stream));
-  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, nullptr, 0,
-                        ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h, ctx->stream));
+  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, clause_block_for(ctx->m),
+                        nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h,
+                        ctx->stream));
   return MAXSAT_OK;
 }
 

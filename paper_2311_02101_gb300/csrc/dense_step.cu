@@ -57,11 +57,6 @@ __device__ __forceinline__ uint32_t step_index(const uint32_t* tdev, uint32_t t_
   return (tdev ? *tdev : 0u) + t_rel;
 }
 
-__device__ __forceinline__ int temp_of(int b, int E, int B) {
-  const int e = (int)(((int64_t)b * E) / B);
-  return e < E - 1 ? e : E - 1;
-}
-
 __host__ __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
 __device__ __forceinline__ void stage16(void* dst, const void* src, int bytes, int tid, int nthr) {
@@ -252,8 +247,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
         for (int sub = 0; sub < 4; ++sub) {
           const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
           const int gb0 = C.g8_off * 8 + b0;  // global chain index
-          const int e0 = temp_of(gb0, E, C.B_total);
-          const bool e_uni = e0 == temp_of(gb0 + 7, E, C.B_total);
+          const int e0 = temp_of(gb0, E, C.B_total, C.inv_B_total);
+          const bool e_uni = e0 == temp_of(gb0 + 7, E, C.B_total, C.inv_B_total);
           int row[8];
           float f[8];
 #pragma unroll
@@ -261,7 +256,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
             // truth pattern; the mask keeps table rows in range even if the
             // accumulator is invalid after a timed-out wait
             const int p = ((__float2int_rn(__uint_as_float(r[sub * 8 + q])) + bias) >> 1) & bias;
-            row[q] = ((e_uni ? e0 : temp_of(gb0 + q, E, C.B_total)) << len) + p;
+            row[q] = ((e_uni ? e0 : temp_of(gb0 + q, E, C.B_total, C.inv_B_total)) << len) + p;
             f[q] = grp >= 0 ? fe_tab[gm.fe_off + row[q]] : 0.f;
           }
           const float fs = tc::column_sums8(f, lane);
@@ -271,19 +266,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) hp[q] = 0;
             for (int wd = 0; wd < gm.words; ++wd) {
-              uint64_t words[8];
-#pragma unroll
-              for (int q = 0; q < 8; ++q) words[q] = hid[gm.hid_off + row[q] * gm.words + wd];
-#pragma unroll
-              for (int rr = 0; rr < 3; ++rr) {
-                const int h = 3 * wd + rr;
-                if (h >= gm.nh) break;
-                const uint4 R = philox4x32_10(
-                    make_uint4((uint32_t)c, (uint32_t)(gb0 >> 3) | ((uint32_t)h << 24), tround,
-                               kPhaseHidden),
-                    C.keys);
-                hidden_bits(R, words, rr, h, hp);
-              }
+              hidden_word(hid + gm.hid_off, row, gm.words, wd, gm.nh, (uint32_t)c,
+                          (uint32_t)(gb0 >> 3), tround, C.keys, hp);
             }
             HT* H = static_cast<HT*>(a.H) + (size_t)c * a.Bp + b0;
             if (sizeof(HT) == 1) {
@@ -574,7 +558,7 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
         const int4* inc = stI(s);
         const HT* hs = stH(s);
         uint8_t* rowp = stB(s) + chain * 128;
-        const int e = temp_of(C.g8_off * 8 + tn * kBN + chain, T.n_temps, C.B_total);
+        const int e = temp_of(C.g8_off * 8 + tn * kBN + chain, T.n_temps, C.B_total, C.inv_B_total);
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
           const int chunk = hk * 4 + ch;

@@ -74,6 +74,7 @@ struct DevChains {
   int32_t Bp;     // chains allocated (multiple of kChainTile)
   int32_t g8_off;   // global index of local chain 0, divided by 8 (chain shards)
   int32_t B_total;  // chains of the whole ensemble (temperature blocks)
+  float inv_B_total;  // 1 / B_total (first guess of the temperature index)
   uint32_t key0, key1;
   RoundKeys keys;
   uint8_t* xt;        // sparse layout: n x Bp, 0/1
@@ -125,6 +126,12 @@ void set_context_free_error(const std::string& msg);
 // clause blocking of the sparse gather: clauses per block and block count
 int clause_block_for(int m);
 int clause_blocks_for(int m);
+// clauses per block for the step / score gathers over `tiles` chain tiles:
+// the block count tiles * ceil(m / cb) is fitted to whole waves of `slots`
+// resident blocks (SMs x blocks per SM)
+int gather_clause_block(int m, int tiles, int slots);
+// resident gather blocks per SM for the tables' shared-memory footprint
+int gather_blocks_per_sm(const DevTables& T, bool wide_h);
 
 // sparse.cu launchers (all asynchronous on `st`)
 enum GatherMode { kStep = 0, kScore = 1, kEval = 2 };
@@ -133,7 +140,7 @@ cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st);
 // best-keep; kScore: the same without draws; kEval: cost only, written to
 // eval_out. xt / Bp / B / tickets / partials may differ from C's (eval).
 cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
-                          const DevChains& C, const uint8_t* xt, int B, int Bp,
+                          const DevChains& C, const uint8_t* xt, int B, int Bp, int cb,
                           const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
                           float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide_h,
                           cudaStream_t st);
@@ -178,5 +185,18 @@ cudaError_t launch_init_dense(const DevChains& C, uint8_t* X, float* nu, uint8_t
                               int n_pad, bool e5m2, cudaStream_t st);
 cudaError_t launch_keep_copy_dense(const DevChains& C, const uint8_t* X, uint8_t* best_x, int n,
                                    int n_pad, bool e5m2, cudaStream_t st);
+
+#ifdef __CUDACC__
+// Temperature of global chain b among E contiguous blocks of B chains:
+// floor(b E / B) (capped at E - 1). A float product gives the quotient to
+// within one; exact 64-bit products correct it.
+__device__ __forceinline__ int temp_of(int b, int E, int B, float inv_B) {
+  int e = __float2int_rz((float)b * (float)E * inv_B);
+  const long long num = (long long)b * E;
+  if ((long long)(e + 1) * B <= num) ++e;
+  else if ((long long)e * B > num) --e;
+  return e < E - 1 ? e : E - 1;
+}
+#endif
 
 }  // namespace rbmsat

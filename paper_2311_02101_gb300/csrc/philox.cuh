@@ -31,19 +31,43 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& K) {
   return c;
 }
 
-// Hidden unit bits of 8 chains from one Philox block and the chains' packed
-// threshold words (16-bit thresholds, "always on" bits 48..50): bit h of
-// hp[q] |= [u_q < T_q,r] | sat_q,r for unit h = 3 w + r.
-__device__ __forceinline__ void hidden_bits(const uint4& R, const uint64_t (&wd)[8], int r, int h,
+// Samples the hidden units h = 3 w .. min(3 w + 3, nh) - 1 of one clause for
+// 8 chains (Eq. 2 / Eq. 6 with the negation transform). Unit h draws from the
+// Philox block at counter (clause, chain-octet | h << 24, round, hidden phase),
+// chain q taking its 16-bit lane q; the threshold word w of chain q is
+// tab[row[q] * words + w] (thresholds min(P, 65535) in bits 16 r .. 16 r + 15,
+// [P == 65536] in bit 48 + r), and bit h of hp[q] becomes [u < P]. A full word
+// computes its three Philox blocks in straight-line code so that their
+// multiply chains interleave, and reads the words only after them.
+__device__ __forceinline__ void hidden_word(const unsigned long long* tab, const int (&row)[8],
+                                            int words, int w, int nh, uint32_t clause,
+                                            uint32_t octet, uint32_t t, const RoundKeys& K,
                                             uint32_t (&hp)[8]) {
-  const uint32_t rw[4] = {R.x, R.y, R.z, R.w};
+  const int h0 = 3 * w;
+  const int nr = nh - h0 < 3 ? nh - h0 : 3;
+  uint4 R0, R1 = make_uint4(0, 0, 0, 0), R2 = make_uint4(0, 0, 0, 0);
+  const uint32_t cy = octet | ((uint32_t)h0 << 24);
+  if (nr == 3) {
+    R0 = philox4x32_10(make_uint4(clause, cy, t, kPhaseHidden), K);
+    R1 = philox4x32_10(make_uint4(clause, cy + (1u << 24), t, kPhaseHidden), K);
+    R2 = philox4x32_10(make_uint4(clause, cy + (2u << 24), t, kPhaseHidden), K);
+  } else {
+    R0 = philox4x32_10(make_uint4(clause, cy, t, kPhaseHidden), K);
+    if (nr == 2) R1 = philox4x32_10(make_uint4(clause, cy + (1u << 24), t, kPhaseHidden), K);
+  }
+  const uint32_t keep = (1u << nr) - 1u;
+  const uint32_t r0[4] = {R0.x, R0.y, R0.z, R0.w}, r1[4] = {R1.x, R1.y, R1.z, R1.w},
+                 r2[4] = {R2.x, R2.y, R2.z, R2.w};
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const uint32_t lo = (uint32_t)wd[q], hi = (uint32_t)(wd[q] >> 32);
-    const uint32_t T = r == 0 ? (lo & 0xFFFFu) : r == 1 ? (lo >> 16) : (hi & 0xFFFFu);
-    const uint32_t sat = (hi >> (16 + r)) & 1u;
-    const uint32_t u = (q & 1) ? (rw[q >> 1] >> 16) : (rw[q >> 1] & 0xFFFFu);
-    hp[q] |= ((uint32_t)(u < T) | sat) << h;
+    const unsigned long long wq = tab[row[q] * words + w];
+    const uint32_t lo = (uint32_t)wq, hi = (uint32_t)(wq >> 32);
+    const int sh = 16 * (q & 1);
+    const uint32_t u0 = (r0[q >> 1] >> sh) & 0xFFFFu, u1 = (r1[q >> 1] >> sh) & 0xFFFFu,
+                   u2 = (r2[q >> 1] >> sh) & 0xFFFFu;
+    const uint32_t bits = (uint32_t)(u0 < (lo & 0xFFFFu)) | ((uint32_t)(u1 < (lo >> 16)) << 1) |
+                          ((uint32_t)(u2 < (hi & 0xFFFFu)) << 2) | ((hi >> 16) & 7u);
+    hp[q] |= (bits & keep) << h0;
   }
 }
 

@@ -21,7 +21,9 @@
 // State layout: x and nu are variable-major (n x Bp) so 8 consecutive chains of
 // one variable are one 8-byte (x) or 32-byte (nu) access. The small
 // probability tables are staged in shared memory when they fit.
+#include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "philox.cuh"
@@ -32,11 +34,6 @@ namespace {
 
 __device__ __forceinline__ uint32_t step_index(const uint32_t* tdev, uint32_t t_rel) {
   return (tdev ? *tdev : 0u) + t_rel;
-}
-
-__device__ __forceinline__ int temp_of(int b, int E, int B) {
-  const int e = (int)(((int64_t)b * E) / B);
-  return e < E - 1 ? e : E - 1;
 }
 
 // Copies `bytes` (multiple of 16) from global to shared memory, whole block.
@@ -112,8 +109,15 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   // block boundary falls inside them
   // global chain index: draws and temperatures follow it (chain shards)
   const int gb0 = C.g8_off * 8 + b0;
-  const int e0 = FE ? temp_of(gb0, E, C.B_total) : 0;
-  const bool e_uniform = !FE || e0 == temp_of(gb0 + 7, E, C.B_total);
+  const int e0 = FE ? temp_of(gb0, E, C.B_total, C.inv_B_total) : 0;
+  const bool e_uniform = !FE || e0 == temp_of(gb0 + 7, E, C.B_total, C.inv_B_total);
+  // the 8 chains' temperatures, 6 bits each (E <= 64)
+  uint64_t epack = 0;
+  if (FE && !e_uniform) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      epack |= (uint64_t)temp_of(gb0 + q, E, C.B_total, C.inv_B_total) << (6 * q);
+  }
   // the weighted unsat cost accumulates in this warp's shared-memory row
   // (each entry is owned by one thread), the free energy in registers
   int64_t* my_cost = &s_cost[warp][lane * 8];
@@ -131,17 +135,36 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
     // byte q of lo0|lo1 (chains 0..3 | 4..7): bits 0..7 of chain q's truth
     // pattern; of hi0|hi1: bits 8..15
     uint32_t lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
-    for (int k = 0; k < len; ++k) {
-      const int32_t lv = __ldg(F.lit_var + o + k);
-      const uint2 x8 =
-          __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
-      const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
-      if (k < 8) {
-        lo0 |= (x8.x ^ flip) << k;
-        lo1 |= (x8.y ^ flip) << k;
-      } else {
-        hi0 |= (x8.x ^ flip) << (k - 8);
-        hi1 |= (x8.y ^ flip) << (k - 8);
+    if (len <= 4) {
+      // short clause: all literal and state loads in flight together
+      int32_t lv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lv[k] = k < len ? __ldg(F.lit_var + o + k) : 0;
+      uint2 x8[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
+                              xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
+                        : make_uint2(0u, 0u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
+        lo0 |= (x8[k].x ^ flip) << k;
+        lo1 |= (x8[k].y ^ flip) << k;
+      }
+    } else {
+      for (int k = 0; k < len; ++k) {
+        const int32_t lv = __ldg(F.lit_var + o + k);
+        const uint2 x8 =
+            __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
+        const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
+        if (k < 8) {
+          lo0 |= (x8.x ^ flip) << k;
+          lo1 |= (x8.y ^ flip) << k;
+        } else {
+          hi0 |= (x8.x ^ flip) << (k - 8);
+          hi1 |= (x8.y ^ flip) << (k - 8);
+        }
       }
     }
     int p[8];
@@ -151,10 +174,17 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
       p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
       p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
     }
-    const int64_t wc = __ldg(F.cl_w + c);
+    // unsatisfied clauses are rare once chains settle: touch the cost rows
+    // only when one of the 8 chains has p == 0
+    uint32_t unsat = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (p[q] == 0) my_cost[q] += wc;
+    for (int q = 0; q < 8; ++q) unsat |= (uint32_t)(p[q] == 0) << q;
+    if (unsat) {
+      const int64_t wc = __ldg(F.cl_w + c);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if ((unsat >> q) & 1u) my_cost[q] += wc;
+    }
     if (!FE || len == 0) continue;
 
     const int grp = __ldg(F.cl_grp + c);
@@ -162,7 +192,7 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
     int row[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      row[q] = ((e_uniform ? e0 : temp_of(gb0 + q, E, C.B_total)) << len) + p[q];
+      row[q] = ((e_uniform ? e0 : (int)((epack >> (6 * q)) & 63u)) << len) + p[q];
 #pragma unroll
     for (int q = 0; q < 8; ++q) fe[q] += fe_tab[gm.fe_off + row[q]];
     if constexpr (SAMPLE) {
@@ -171,19 +201,8 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   #pragma unroll
       for (int q = 0; q < 8; ++q) hp[q] = 0;
       for (int w = 0; w < gm.words; ++w) {
-        uint64_t wd[8];
-  #pragma unroll
-        for (int q = 0; q < 8; ++q) wd[q] = hid[gm.hid_off + row[q] * gm.words + w];
-  #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int h = 3 * w + r;
-          if (h >= gm.nh) break;
-          const uint4 R = philox4x32_10(
-              make_uint4((uint32_t)c, (uint32_t)(g8 + C.g8_off) | ((uint32_t)h << 24), t,
-                         kPhaseHidden),
-              C.keys);
-          hidden_bits(R, wd, r, h, hp);
-        }
+        hidden_word(hid + gm.hid_off, row, gm.words, w, gm.nh, (uint32_t)c,
+                    (uint32_t)(g8 + C.g8_off), t, C.keys, hp);
       }
       HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
       if (sizeof(HT) == 1) {
@@ -255,6 +274,8 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, size_t o, int 
   }
 }
 
+constexpr int kVisBatch = 8;
+
 template <bool SM, typename HT>
 __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
@@ -277,38 +298,58 @@ __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevC
   const uint32_t t = step_index(tdev, t_rel);
   int e[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) e[q] = temp_of(C.g8_off * 8 + b0 + q, T.n_temps, C.B_total);
+  for (int q = 0; q < 8; ++q) e[q] = temp_of(C.g8_off * 8 + b0 + q, T.n_temps, C.B_total, C.inv_B_total);
   int z[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) z[q] = 0;
   const HT* H = static_cast<const HT*>(C.H);
-  const int j_end = __ldg(F.var_off + i + 1);
-  for (int jj = __ldg(F.var_off + i); jj < j_end; ++jj) {
-    const int4 inc = __ldg(F.var_inc + jj);
+  using HV = typename std::conditional<sizeof(HT) == 1, unsigned long long, uint4>::type;
+  // this thread's state loads go out first; they are used after the sums
+  const size_t o = (size_t)i * C.Bp + b0;
+  const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
+  float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
+  const float4 n0 = nu4[0], n1 = nu4[1];
+  // z += sgn * 2^Q G[pattern] for one incidence (clause inc.x, literal slot)
+  auto add = [&](const int4& inc, const HV& v) {
     const int base = inc.y & 0x7FFFFFFF;
     const int sgn = inc.y < 0 ? -1 : 1;
     uint32_t hp[8];
-    if (sizeof(HT) == 1) {
-      const uint64_t v = __ldg(reinterpret_cast<const unsigned long long*>(H + (size_t)inc.x * C.Bp + b0));
+    if constexpr (sizeof(HT) == 1) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) hp[q] = (uint32_t)(v >> (8 * q)) & 0xFFu;
     } else {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(H + (size_t)inc.x * C.Bp + b0));
       const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int q = 0; q < 8; ++q) hp[q] = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) z[q] += sgn * (int)gq[base + e[q] * inc.w + (int)hp[q] * inc.z];
+  };
+  auto load = [&](int clause) {
+    return __ldg(reinterpret_cast<const HV*>(H + (size_t)clause * C.Bp + b0));
+  };
+  const int j_end = __ldg(F.var_off + i + 1);
+  int jj = __ldg(F.var_off + i);
+  // kVisBatch incidences per pass: their record and pattern loads are in
+  // flight together
+  for (; jj + kVisBatch <= j_end; jj += kVisBatch) {
+    int4 inc[kVisBatch];
+#pragma unroll
+    for (int u = 0; u < kVisBatch; ++u) inc[u] = __ldg(F.var_inc + jj + u);
+    HV v[kVisBatch];
+#pragma unroll
+    for (int u = 0; u < kVisBatch; ++u) v[u] = load(inc[u].x);
+#pragma unroll
+    for (int u = 0; u < kVisBatch; ++u) add(inc[u], v[u]);
   }
-  const size_t o = (size_t)i * C.Bp + b0;
-  const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
+  for (; jj < j_end; ++jj) {
+    const int4 inc = __ldg(F.var_inc + jj);
+    add(inc, load(inc.x));
+  }
   keep_improved(C, o, b0, xold);
 
   const uint4 r =
       philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), t, kPhaseVisible), C.keys);
-  float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
-  const float4 n0 = nu4[0], n1 = nu4[1];
   float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
   const float keep = 1.0f - alpha;
   uint64_t xnew = 0;
@@ -382,6 +423,17 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
   return cudaGetLastError();
 }
 
+template <bool SM, typename HT>
+int gather_occupancy(int smem) {
+  auto kern = k_gather<kStep, SM, HT>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 1;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem) != cudaSuccess) return 1;
+  return nb > 0 ? nb : 1;
+}
+
 template <int MODE>
 cudaError_t gather_mode(dim3 grid, cudaStream_t st, bool wide, const DevFormula& F,
                         const DevTables& T, const DevChains& C, const uint8_t* xt, int B, int Bp,
@@ -428,6 +480,42 @@ int clause_blocks_for(int m) {
   return nb > 0 ? nb : 1;
 }
 
+// below this many clauses per block, the per-block table staging dominates
+constexpr int kMinClauseBlock = 16;
+
+int gather_clause_block(int m, int tiles, int slots) {
+  int best = clause_block_for(m);
+  if (m <= 0 || tiles <= 0 || slots <= 0) return best;
+  auto fill = [&](int cb) {
+    const long long items = (long long)tiles * ((m + cb - 1) / cb);
+    const long long waves = (items + slots - 1) / slots;
+    return (double)items / (double)(waves * slots);
+  };
+  double best_fill = fill(best);
+  // fewest waves first: a later candidate must fill clearly better
+  for (int waves = 1; waves <= 64; ++waves) {
+    const long long y = (long long)waves * slots / tiles;
+    if (y < 1) continue;
+    const int cb = std::max((int)((m + y - 1) / y), kMinClauseBlock);
+    const double f = fill(cb);
+    if (f > best_fill + 0.01) {
+      best_fill = f;
+      best = cb;
+    }
+    if (cb == kMinClauseBlock) break;
+  }
+  return best;
+}
+
+int gather_blocks_per_sm(const DevTables& T, bool wide) {
+  const int sm = gather_smem_bytes(T);
+  const bool use_sm = sm <= kSmemLimit;
+  if (use_sm && !wide) return gather_occupancy<true, uint8_t>(sm);
+  if (use_sm) return gather_occupancy<true, uint16_t>(sm);
+  if (!wide) return gather_occupancy<false, uint8_t>(0);
+  return gather_occupancy<false, uint16_t>(0);
+}
+
 cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st) {
   dim3 grid(C.Bp / kChainTile, (n + 7) / 8);
   k_init<<<grid, 256, 0, st>>>(C, n);
@@ -435,12 +523,12 @@ cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st) {
 }
 
 cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
-                          const DevChains& C, const uint8_t* xt, int B, int Bp,
+                          const DevChains& C, const uint8_t* xt, int B, int Bp, int cb,
                           const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
                           float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide,
                           cudaStream_t st) {
-  const int cb = clause_block_for(F.m);
-  dim3 grid(Bp / kChainTile, clause_blocks_for(F.m));
+  if (cb < 1) return cudaErrorInvalidValue;
+  dim3 grid(Bp / kChainTile, F.m > 0 ? (F.m + cb - 1) / cb : 1);
   switch (mode) {
     case kStep:
       return gather_mode<kStep>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
