@@ -78,6 +78,7 @@ struct maxsat_ctx {
   int64_t* ev_part = nullptr;
   int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
+  std::vector<int64_t> h_w;  // clause weights (host copy)
   int gather_slots = 0;  // SMs x resident gather blocks per SM
   int gather_cb = 0;     // clauses per gather block for the chains' Bp
   bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
@@ -273,8 +274,17 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   }
   ctx->gather_cb = gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
   const int nblk = ctx->m > 0 ? (ctx->m + ctx->gather_cb - 1) / ctx->gather_cb : 1;
+  // 32-bit per-block cost rows when no clause block's weight sum reaches 2^31
+  int64_t wmax_block = 0;
+  for (int bl = 0; bl < nblk; ++bl) {
+    int64_t sum = 0;
+    const int c1 = std::min(ctx->m, (bl + 1) * ctx->gather_cb);
+    for (int c = bl * ctx->gather_cb; c < c1; ++c) sum += ctx->h_w[c];
+    wmax_block = std::max(wmax_block, sum);
+  }
   DevChains& C = ctx->C;
   C = DevChains{};
+  C.cost32 = wmax_block < ((int64_t)1 << 31) ? 1 : 0;
   C.B = B;
   C.Bp = Bp;
   ctx->chains_dense = ctx->dense;
@@ -683,6 +693,7 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   std::vector<int64_t> cl_w(m);
   for (int64_t c = 0; c <= m; ++c) cl_off[c] = (int32_t)off[c];
   for (int64_t c = 0; c < m; ++c) cl_w[c] = weights ? weights[c] : 1;
+  ctx->h_w = cl_w;
   for (int64_t j = 0; j < nnz; ++j) {
     const int32_t l = lits[j];
     const int32_t v = (l > 0 ? l : -l) - 1;
@@ -720,8 +731,8 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   T.n_temps = prm.n_temps;
   T.qmax = ctx->tabs.qmax;
   T.n_groups = ctx->tabs.n_groups;
-  T.hid_words = (int32_t)ctx->tabs.hid.size();
-  T.fe_len = (int32_t)ctx->tabs.fe.size();
+  T.rec_len = (int32_t)ctx->tabs.rec.size();
+  T.one_chunk = ctx->tabs.max_nh <= 3 ? 1 : 0;
   T.gq_len = (int32_t)ctx->tabs.gq.size();
   T.pv_len = (int32_t)ctx->tabs.pv.size();
   ctx->wide_h = ctx->tabs.max_nh > 8;
@@ -741,11 +752,7 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   UP(var_off, F.var_off);
   UP(var_inc, F.var_inc);
   UP(ctx->tabs.meta, T.meta);
-  {
-    std::vector<unsigned long long> hid(ctx->tabs.hid.begin(), ctx->tabs.hid.end());
-    UP(hid, T.hid);
-  }
-  UP(ctx->tabs.fe, T.fe);
+  UP(ctx->tabs.rec, T.rec);
   UP(ctx->tabs.gq, T.gq);
   UP(ctx->tabs.pv, T.pv);
 #define UP2(vec, dst)                                         \

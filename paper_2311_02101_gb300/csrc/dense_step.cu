@@ -95,7 +95,7 @@ struct G1Args {
   int* err;
 };
 
-template <bool SAMPLE, bool SM, typename HT>
+template <bool SAMPLE, bool SM, typename HT, bool ONE>
 __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
     k_gemm1_step(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const G1Args a, const DevTables T, const DevChains C) {
@@ -113,18 +113,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
 
   // clause-RBM tables: staged in shared memory when small
   const GroupMeta* meta = T.meta;
-  const unsigned long long* hid = T.hid;
-  const float* fe_tab = T.fe;
+  const uint32_t* rec = T.rec;
   if (SM) {
     const int mb = align16(T.n_groups * (int)sizeof(GroupMeta));
-    const int hb = align16(T.hid_words * 8);
-    const int fb = align16(T.fe_len * 4);
     stage16(tabs, T.meta, mb, threadIdx.x, blockDim.x);
-    stage16(tabs + mb, T.hid, hb, threadIdx.x, blockDim.x);
-    stage16(tabs + mb + hb, T.fe, fb, threadIdx.x, blockDim.x);
+    stage16(tabs + mb, T.rec, align16(T.rec_len * 4), threadIdx.x, blockDim.x);
     meta = reinterpret_cast<const GroupMeta*>(tabs);
-    hid = reinterpret_cast<const unsigned long long*>(tabs + mb);
-    fe_tab = reinterpret_cast<const float*>(tabs + mb + hb);
+    rec = reinterpret_cast<const uint32_t*>(tabs + mb);
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kS1; ++s) {
@@ -257,18 +252,27 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
             // accumulator is invalid after a timed-out wait
             const int p = ((__float2int_rn(__uint_as_float(r[sub * 8 + q])) + bias) >> 1) & bias;
             row[q] = ((e_uni ? e0 : temp_of(gb0 + q, E, C.B_total, C.inv_B_total)) << len) + p;
-            f[q] = grp >= 0 ? fe_tab[gm.fe_off + row[q]] : 0.f;
+            f[q] = 0.f;
           }
-          const float fs = tc::column_sums8(f, lane);
-          if (lane < 8) S.fe[buf][ew * kCols + j * 32 + sub * 8 + lane] = fs;
+          if (!SAMPLE && grp >= 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) f[q] = __uint_as_float(rec[gm.rec_off + row[q] * gm.stride]);
+          }
           if (SAMPLE && grp >= 0) {
+            // free energy (record word 0) and hidden draws from the records
+            const uint4* tab = reinterpret_cast<const uint4*>(rec + gm.rec_off);
+            int row4[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) row4[q] = row[q] * (gm.stride >> 2);
             uint32_t hp[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) hp[q] = 0;
-            for (int wd = 0; wd < gm.words; ++wd) {
-              hidden_word(hid + gm.hid_off, row, gm.words, wd, gm.nh, (uint32_t)c,
-                          (uint32_t)(gb0 >> 3), tround, C.keys, hp);
-            }
+            const uint32_t octet = (uint32_t)(gb0 >> 3);
+            const int chunks = gm.stride >> 2;
+            if (!gm.sat)
+              hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, C.keys, hp, f);
+            else
+              hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, C.keys, hp, f);
             HT* H = static_cast<HT*>(a.H) + (size_t)c * a.Bp + b0;
             if (sizeof(HT) == 1) {
               uint64_t v = 0;
@@ -280,6 +284,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
                                                         hp[4] | (hp[5] << 16), hp[6] | (hp[7] << 16));
             }
           }
+          const float fs = tc::column_sums8(f, lane);
+          if (lane < 8) S.fe[buf][ew * kCols + j * 32 + sub * 8 + lane] = fs;
         }
       }
       tc::fence_before_sync();
@@ -690,7 +696,10 @@ template <bool SAMPLE, bool SM, typename HT>
 cudaError_t g1_variant(int grid, int smem, cudaStream_t st, const CUtensorMap& tmA,
                        const CUtensorMap& tmB, const G1Args& a, const DevTables& T,
                        const DevChains& C) {
-  auto kern = k_gemm1_step<SAMPLE, SM, HT>;
+  // one-chunk records (L <= 3 everywhere): the sampling has no chunk loop
+  auto kern = k_gemm1_step<SAMPLE, SM, HT, false>;
+  if constexpr (SAMPLE && sizeof(HT) == 1)
+    if (T.one_chunk) kern = k_gemm1_step<SAMPLE, SM, HT, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, 64 + 32 * kEpi1, smem, st>>>(tmA, tmB, a, T, C);
@@ -723,8 +732,7 @@ constexpr int kSmemMax = 227 * 1024;
 }  // namespace
 
 int dense_g1_table_bytes(const DevTables& T) {
-  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.hid_words * 8) +
-         align16(T.fe_len * 4);
+  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.rec_len * 4);
 }
 
 cudaError_t launch_gemm1_step(bool sample, const CUtensorMap& tmA, const CUtensorMap& tmB, int m,

@@ -28,10 +28,10 @@ constexpr int kClauseBlock = 64;  // clauses per block of the sparse gather
 struct GroupMeta {
   int32_t len = 0;      // clause length K
   int32_t nh = 0;       // hidden units L
-  int32_t words = 0;    // u64 threshold words per pattern, ceil(L / 3)
-  int32_t hid_off = 0;  // into hid (u64): + (e 2^K + p) words + w
-  int32_t fe_off = 0;   // into fe (float): + e 2^K + p
+  int32_t rec_off = 0;  // into rec (u32, a multiple of 4): + (e 2^K + p) stride
+  int32_t stride = 0;   // u32 words per pattern record: 4 ceil((L + 1) / 4)
   int32_t gq_off = 0;   // into gq (int16): + (e 2^L + hp) K + k
+  int32_t sat = 0;      // 1 when some hidden probability of the group is 65536 / 65536
   int32_t pad0 = 0, pad1 = 0;
 };
 
@@ -54,11 +54,11 @@ struct DevTables {
   int32_t n_temps;     // E
   int32_t qmax;        // visible logits clamp to [-qmax, qmax] (units 2^-Q)
   int32_t n_groups;
-  int32_t hid_words, fe_len, gq_len, pv_len;  // element counts
+  int32_t rec_len, gq_len, pv_len;  // element counts
+  int32_t one_chunk;   // every group's pattern record is 16 bytes (L <= 3)
   int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
   const GroupMeta* meta;
-  const unsigned long long* hid;
-  const float* fe;
+  const uint32_t* rec;
   const int16_t* gq;
   const uint32_t* pv;
 };
@@ -75,6 +75,7 @@ struct DevChains {
   int32_t g8_off;   // global index of local chain 0, divided by 8 (chain shards)
   int32_t B_total;  // chains of the whole ensemble (temperature blocks)
   float inv_B_total;  // 1 / B_total (first guess of the temperature index)
+  int32_t cost32;     // sparse gather: every clause block's weight sum < 2^31
   uint32_t key0, key1;
   RoundKeys keys;
   uint8_t* xt;        // sparse layout: n x Bp, 0/1
@@ -103,8 +104,7 @@ struct HostTables {
   int32_t n_groups = 0, n_temps = 0, qmax = 0, quant_bits = 0, max_nh = 0;
   std::vector<int32_t> grp_len, grp_bucket, grp_nh;
   std::vector<GroupMeta> meta;
-  std::vector<uint64_t> hid;
-  std::vector<float> fe;
+  std::vector<uint32_t> rec;
   std::vector<int16_t> gq;
   std::vector<uint32_t> pv;
   int32_t gq_absmax = 0;  // largest |2^Q G|

@@ -31,43 +31,76 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& K) {
   return c;
 }
 
-// Samples the hidden units h = 3 w .. min(3 w + 3, nh) - 1 of one clause for
-// 8 chains (Eq. 2 / Eq. 6 with the negation transform). Unit h draws from the
-// Philox block at counter (clause, chain-octet | h << 24, round, hidden phase),
-// chain q taking its 16-bit lane q; the threshold word w of chain q is
-// tab[row[q] * words + w] (thresholds min(P, 65535) in bits 16 r .. 16 r + 15,
-// [P == 65536] in bit 48 + r), and bit h of hp[q] becomes [u < P]. A full word
-// computes its three Philox blocks in straight-line code so that their
-// multiply chains interleave, and reads the words only after them.
-__device__ __forceinline__ void hidden_word(const unsigned long long* tab, const int (&row)[8],
-                                            int words, int w, int nh, uint32_t clause,
-                                            uint32_t octet, uint32_t t, const RoundKeys& K,
-                                            uint32_t (&hp)[8]) {
-  const int h0 = 3 * w;
-  const int nr = nh - h0 < 3 ? nh - h0 : 3;
-  uint4 R0, R1 = make_uint4(0, 0, 0, 0), R2 = make_uint4(0, 0, 0, 0);
-  const uint32_t cy = octet | ((uint32_t)h0 << 24);
-  if (nr == 3) {
-    R0 = philox4x32_10(make_uint4(clause, cy, t, kPhaseHidden), K);
-    R1 = philox4x32_10(make_uint4(clause, cy + (1u << 24), t, kPhaseHidden), K);
-    R2 = philox4x32_10(make_uint4(clause, cy + (2u << 24), t, kPhaseHidden), K);
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Hidden draws of one clause for 8 chains (Eq. 2 / Eq. 6 with the negation
+// transform) from the chains' pattern records. Unit h draws from the Philox
+// block at counter (clause, chain-octet | h << 24, round, hidden phase),
+// chain q taking 16-bit lane q (low half of word q / 2 for even q, high half
+// for odd q), and bit h of hp[q] becomes [u < P]. Record word 1 + h holds
+// (min(P, 65535) << 16) | [P == 65536]: with u moved into the high half of
+// a 32-bit word x, the draw is [x < word] (| bit 0 when the group has a
+// saturated unit). tab points at the group's records as 16-byte chunks and
+// row4[q] is chain q's record in chunks; chunk j holds words 4j .. 4j + 3,
+// i.e. units 4j - 1 .. 4j + 2 (word 0 of chunk 0 is the free energy).
+// hidden_words draws words I0 .. I0 + NW - 1 of chunk j (those below hi);
+// its NW Philox blocks run as straight-line code so that their multiply
+// chains interleave. With FE it also adds the free energy to fe[q].
+template <bool SAT, int I0, int NW, bool FE>
+__device__ __forceinline__ void hidden_words(const uint4* tab, const int (&row4)[8], int j, int hi,
+                                             uint32_t clause, uint32_t cy, uint32_t t,
+                                             const RoundKeys& K, uint32_t (&hp)[8],
+                                             float (&fe)[8]) {
+  uint4 R[NW];
+  if (I0 + NW <= hi) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i)
+      R[i] = philox4x32_10(make_uint4(clause, cy + ((uint32_t)(I0 + i) << 24), t, kPhaseHidden), K);
   } else {
-    R0 = philox4x32_10(make_uint4(clause, cy, t, kPhaseHidden), K);
-    if (nr == 2) R1 = philox4x32_10(make_uint4(clause, cy + (1u << 24), t, kPhaseHidden), K);
+#pragma unroll
+    for (int i = 0; i < NW; ++i)
+      R[i] = I0 + i < hi ? philox4x32_10(make_uint4(clause, cy + ((uint32_t)(I0 + i) << 24), t,
+                                                    kPhaseHidden),
+                                         K)
+                         : make_uint4(0u, 0u, 0u, 0u);
   }
-  const uint32_t keep = (1u << nr) - 1u;
-  const uint32_t r0[4] = {R0.x, R0.y, R0.z, R0.w}, r1[4] = {R1.x, R1.y, R1.z, R1.w},
-                 r2[4] = {R2.x, R2.y, R2.z, R2.w};
+  const uint32_t vm = ((hi >= 4 ? 0xFu : (1u << hi) - 1u) >> I0) & ((1u << NW) - 1u);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const unsigned long long wq = tab[row[q] * words + w];
-    const uint32_t lo = (uint32_t)wq, hi = (uint32_t)(wq >> 32);
-    const int sh = 16 * (q & 1);
-    const uint32_t u0 = (r0[q >> 1] >> sh) & 0xFFFFu, u1 = (r1[q >> 1] >> sh) & 0xFFFFu,
-                   u2 = (r2[q >> 1] >> sh) & 0xFFFFu;
-    const uint32_t bits = (uint32_t)(u0 < (lo & 0xFFFFu)) | ((uint32_t)(u1 < (lo >> 16)) << 1) |
-                          ((uint32_t)(u2 < (hi & 0xFFFFu)) << 2) | ((hi >> 16) & 7u);
-    hp[q] |= (bits & keep) << h0;
+    const uint4 r = tab[row4[q] + j];
+    if (FE) fe[q] += __uint_as_float(r.x);
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      uint32_t x = word_of(R[i], q >> 1);
+      if (!(q & 1)) x = __byte_perm(x, 0u, 0x1032);  // the low-half draw moves up
+      const uint32_t w = word_of(r, I0 + i);
+      bits |= (uint32_t)(x < w) << i;
+      if (SAT) bits |= (w & 1u) << i;
+    }
+    hp[q] |= ((bits & vm) << (4 * j + I0)) >> 1;
+  }
+}
+
+// All hidden draws (and the free energy) of one clause for 8 chains. ONE:
+// every group's record is one chunk (L <= 3), so no later chunk exists.
+template <bool SAT, bool ONE>
+__device__ __forceinline__ void hidden_draws(const uint4* tab, const int (&row4)[8], int chunks,
+                                             int nh, uint32_t clause, uint32_t octet, uint32_t t,
+                                             const RoundKeys& K, uint32_t (&hp)[8],
+                                             float (&fe)[8]) {
+  // chunk 0: free energy and units 0..2
+  const uint32_t cy0 = octet | (0xFFu << 24);  // unit of word 0 is -1
+  hidden_words<SAT, 1, 3, true>(tab, row4, 0, nh + 1 < 4 ? nh + 1 : 4, clause, cy0, t, K, hp, fe);
+  if (ONE) return;
+  for (int j = 1; j < chunks; ++j) {
+    const int h0 = 4 * j - 1;
+    const int hi = nh - h0 < 4 ? nh - h0 : 4;
+    const uint32_t cy = octet | ((uint32_t)h0 << 24);
+    hidden_words<SAT, 0, 2, false>(tab, row4, j, hi, clause, cy, t, K, hp, fe);
+    if (hi > 2) hidden_words<SAT, 2, 2, false>(tab, row4, j, hi, clause, cy, t, K, hp, fe);
   }
 }
 

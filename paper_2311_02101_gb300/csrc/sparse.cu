@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
   }
 }
 
-template <int MODE, bool SM, typename HT>
+template <int MODE, bool SM, typename HT, bool ONE>
 __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, DevChains C,
                                                 const uint8_t* __restrict__ xt, int B, int Bp,
                                                 int cblock, const uint32_t* tdev, uint32_t t_rel,
@@ -90,19 +90,14 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   const int E = T.n_temps;
 
   const GroupMeta* meta = T.meta;
-  const unsigned long long* hid = T.hid;
-  const float* fe_tab = T.fe;
+  const uint32_t* rec = T.rec;
   if (SM && FE) {
     const int mb = align16(T.n_groups * (int)sizeof(GroupMeta));
-    const int hb = align16(T.hid_words * 8);
-    const int fb = align16(T.fe_len * 4);
     stage(smem, T.meta, mb);
-    stage(smem + mb, T.hid, hb);
-    stage(smem + mb + hb, T.fe, fb);
+    stage(smem + mb, T.rec, align16(T.rec_len * 4));
     __syncthreads();
     meta = reinterpret_cast<const GroupMeta*>(smem);
-    hid = reinterpret_cast<const unsigned long long*>(smem + mb);
-    fe_tab = reinterpret_cast<const float*>(smem + mb + hb);
+    rec = reinterpret_cast<const uint32_t*>(smem + mb);
   }
 
   // temperature of the thread's 8 chains: one value unless a temperature
@@ -120,9 +115,17 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   }
   // the weighted unsat cost accumulates in this warp's shared-memory row
   // (each entry is owned by one thread), the free energy in registers
+  // (32-bit rows when every block's weight sum fits: C.cost32). Each thread
+  // zeroes only the entries it owns in the view in use.
   int64_t* my_cost = &s_cost[warp][lane * 8];
+  int32_t* my_cost32 = reinterpret_cast<int32_t*>(&s_cost[0][0]) + warp * 256 + lane * 8;
+  if (MODE != kEval && C.cost32) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) my_cost[q] = 0;
+    for (int q = 0; q < 8; ++q) my_cost32[q] = 0;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) my_cost[q] = 0;
+  }
   float fe[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) fe[q] = 0.f;
@@ -181,9 +184,16 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
     for (int q = 0; q < 8; ++q) unsat |= (uint32_t)(p[q] == 0) << q;
     if (unsat) {
       const int64_t wc = __ldg(F.cl_w + c);
+      if (MODE != kEval && C.cost32) {
+        // each entry has one owner: the atomic is a one-instruction add
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if ((unsat >> q) & 1u) my_cost[q] += wc;
+        for (int q = 0; q < 8; ++q)
+          if ((unsat >> q) & 1u) atomicAdd(my_cost32 + q, (int)wc);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if ((unsat >> q) & 1u) my_cost[q] += wc;
+      }
     }
     if (!FE || len == 0) continue;
 
@@ -193,21 +203,28 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       row[q] = ((e_uniform ? e0 : (int)((epack >> (6 * q)) & 63u)) << len) + p[q];
+    if constexpr (!SAMPLE) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) fe[q] += fe_tab[gm.fe_off + row[q]];
-    if constexpr (SAMPLE) {
-
+      for (int q = 0; q < 8; ++q) fe[q] += __uint_as_float(rec[gm.rec_off + row[q] * gm.stride]);
+    } else {
+      // free energy (record word 0) and hidden draws from the records
+      const uint4* tab = reinterpret_cast<const uint4*>(rec + gm.rec_off);
+      int row4[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) row4[q] = row[q] * (gm.stride >> 2);
       uint32_t hp[8];
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < 8; ++q) hp[q] = 0;
-      for (int w = 0; w < gm.words; ++w) {
-        hidden_word(hid + gm.hid_off, row, gm.words, w, gm.nh, (uint32_t)c,
-                    (uint32_t)(g8 + C.g8_off), t, C.keys, hp);
-      }
+      const uint32_t octet = (uint32_t)(g8 + C.g8_off);
+      const int chunks = gm.stride >> 2;
+      if (!gm.sat)
+        hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, t, C.keys, hp, fe);
+      else
+        hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, t, C.keys, hp, fe);
       HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
       if (sizeof(HT) == 1) {
         uint64_t v = 0;
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < 8; ++q) v |= (uint64_t)hp[q] << (8 * q);
         *reinterpret_cast<uint64_t*>(H) = v;
       } else {
@@ -231,9 +248,11 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   const int tid = threadIdx.x;
   int64_t tc = 0;
   float tf = 0.f;
+  const bool c32 = MODE != kEval && C.cost32;
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    tc += s_cost[w][tid];
+    tc += c32 ? (int64_t)reinterpret_cast<const int32_t*>(&s_cost[0][0])[w * 256 + tid]
+              : s_cost[w][tid];
     if (FE) tf += s_fe[w][tid];
   }
   const size_t out = (size_t)blockIdx.y * Bp + (size_t)blockIdx.x * 256 + tid;
@@ -397,8 +416,7 @@ __global__ void k_transpose_in(const uint8_t* __restrict__ assign, int B, int n,
 }
 
 int gather_smem_bytes(const DevTables& T) {
-  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.hid_words * 8) +
-         align16(T.fe_len * 4);
+  return align16(T.n_groups * (int)sizeof(GroupMeta)) + align16(T.rec_len * 4);
 }
 
 int visible_smem_bytes(const DevTables& T) {
@@ -413,7 +431,10 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
                            int Bp, int cb, const uint32_t* tdev, uint32_t t_rel,
                            int64_t* cost_part, float* fe_part, int32_t* tickets,
                            int64_t* eval_out) {
-  auto kern = k_gather<MODE, SM, HT>;
+  // one-chunk records (L <= 3 everywhere): the sampling has no chunk loop
+  auto kern = k_gather<MODE, SM, HT, false>;
+  if constexpr (MODE == kStep && sizeof(HT) == 1)
+    if (T.one_chunk) kern = k_gather<MODE, SM, HT, true>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -425,7 +446,7 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
 
 template <bool SM, typename HT>
 int gather_occupancy(int smem) {
-  auto kern = k_gather<kStep, SM, HT>;
+  auto kern = k_gather<kStep, SM, HT, false>;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 1;

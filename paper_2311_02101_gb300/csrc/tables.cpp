@@ -8,19 +8,23 @@
 // logits (Eq. 7) only on the pattern hp = sum_h h_h 2^h of sampled hidden
 // units. Per group g (clause length K, weight bucket) with L hidden units and
 // per temperature e the tables hold
-//   hid[g][e][p][w]   u64 word w packs, for h = 3w + r (r = 0, 1, 2), the
-//                     threshold P = rint(65536 sigma(b_h + sum_k W_kh tau_k(p)))
-//                     as min(P, 65535) in bits 16 r .. 16 r + 15 and [P == 65536]
-//                     in bit 48 + r (a draw u in 0..65535 gives 1 iff u < P, i.e.
-//                     iff u < min(P, 65535) or P == 65536); W = ceil(L / 3)
-//   fe[g][e][p]       -sum_h softplus(b_h + sum_k W_kh tau_k(p))       (float)
+//   rec[g][e][p][.]   one record of 4 ceil((L + 1) / 4) u32 words per
+//                     pattern: word 0 the clause free energy
+//                     -sum_h softplus(b_h + sum_k W_kh tau_k(p)) (float bits),
+//                     word 1 + h hidden unit h's threshold
+//                     P = rint(65536 sigma(b_h + sum_k W_kh tau_k(p))) as
+//                     (min(P, 65535) << 16) | [P == 65536], then zeros
 //   gq[g][e][hp][k]   2^Q sum_h W_kh [bit h of hp]                     (int16)
+// A 16-bit draw u gives 1 iff u < P. With a threshold word t, u in the high
+// half of a 32-bit word x (any low half) gives x < t iff u < min(P, 65535),
+// so the draw is [x < t] | (t & 1): no field needs extracting.
 // and the visible table pv[q] = rint(65536 sigma(q 2^-Q)) for |q| <= qmax.
 // A Bernoulli draw with a 16-bit uniform u is [u < P]. Beyond |z| >= 12 the
 // 16-bit probabilities are exactly 0 and 65536, so qmax = 12 * 2^Q clamps
 // without changing any draw.
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -46,8 +50,7 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
   T->grp_bucket = grp_bucket;
   T->grp_nh.assign(G, 0);
   T->meta.assign(G, GroupMeta{});
-  T->hid.clear();
-  T->fe.clear();
+  T->rec.clear();
   T->gq.clear();
   T->gq_absmax = 0;
   T->max_nh = 0;
@@ -56,8 +59,7 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
     const int K = grp_len[g];
     GroupMeta& gm = T->meta[g];
     gm.len = K;
-    gm.hid_off = (int32_t)T->hid.size();
-    gm.fe_off = (int32_t)T->fe.size();
+    gm.rec_off = (int32_t)T->rec.size();
     gm.gq_off = (int32_t)T->gq.size();
     for (int e = 0; e < E; ++e) {
       const RbmSet* s = nullptr;
@@ -70,7 +72,7 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
       if (e == 0) {
         T->grp_nh[g] = L;
         gm.nh = L;
-        gm.words = (L + 2) / 3;
+        gm.stride = 4 * ((L + 1 + 3) / 4);
         T->max_nh = std::max(T->max_nh, L);
       }
       if (T->grp_nh[g] != L)
@@ -89,19 +91,20 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
       }
       for (int p = 0; p < (1 << K); ++p) {
         double F = 0.0;
-        std::vector<uint64_t> words(gm.words, 0);
+        std::vector<uint32_t> words(gm.stride, 0);
         for (int h = 0; h < L; ++h) {
           int64_t acc = 0;
           for (int k = 0; k < K; ++k)
             if ((p >> k) & 1) acc += Wq[k * L + h];
           const double a = s->b[h] + (double)acc / scale;
           const uint32_t P = prob16(a);
-          words[h / 3] |= (uint64_t)(P < 65535u ? P : 65535u) << (16 * (h % 3));
-          if (P == 65536u) words[h / 3] |= (uint64_t)1 << (48 + h % 3);
+          words[1 + h] = ((P < 65535u ? P : 65535u) << 16) | (P == 65536u ? 1u : 0u);
+          if (P == 65536u) gm.sat = 1;
           F -= softplus(a);
         }
-        for (uint64_t w : words) T->hid.push_back(w);
-        T->fe.push_back((float)F);
+        const float Ff = (float)F;
+        std::memcpy(&words[0], &Ff, 4);
+        for (uint32_t w : words) T->rec.push_back(w);
       }
       for (int hp = 0; hp < (1 << L); ++hp) {
         for (int k = 0; k < K; ++k) {
@@ -113,7 +116,7 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
           if (std::abs(acc) > T->gq_absmax) T->gq_absmax = std::abs(acc);
         }
       }
-      if (T->hid.size() > (size_t)INT32_MAX / 4 || T->gq.size() > (size_t)INT32_MAX / 2)
+      if (T->rec.size() > (size_t)INT32_MAX / 4 || T->gq.size() > (size_t)INT32_MAX / 2)
         return "tables too large";
     }
   }

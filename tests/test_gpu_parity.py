@@ -200,6 +200,39 @@ def test_trajectory_mixed_weighted_buckets(ms, stream, golden_table):
     assert_same(gpu, run_oracle(inst, golden_table, B, T, seed, n_buckets=4), T, 0.01)
 
 
+@pytest.fixture(scope="module")
+def sat_table():
+    """Lengths 3 (L = 3, one record chunk) and 5 (L = 6, two chunks) with unit
+    0 forced on (b = 20: P = 65536 for every pattern) and the last unit
+    forced off (b = -20: P = 0), so the saturated-threshold branch and the
+    zero threshold both run."""
+    base = oracle.make_table([3, 5], [0.068, 0.528], n_buckets=1, iters=3000)
+    t = oracle.RbmTable()
+    for s in base.sets:
+        b = s["b"].copy()
+        b[0], b[-1] = 20.0, -20.0
+        t.add(s["len"], s["bucket"], s["temp"], s["W"], b, s["target"])
+    return t
+
+
+@pytest.mark.parametrize("path", [2, 1])
+def test_saturated_hidden_units(ms, stream, sat_table, path):
+    rng = np.random.default_rng(4)
+    lengths = rng.choice([3, 5], size=400)
+    n, off, lits, w = workloads.from_lengths(120, lengths, rng)
+    inst = oracle.Instance(n, off, lits, w)
+    # the tables really hold P = 65536 and P = 0
+    for s in sat_table.sets:
+        a_on = s["b"][0] + np.minimum(s["W"][:, 0], 0).sum()
+        a_off = s["b"][-1] + np.maximum(s["W"][:, -1], 0).sum()
+        assert np.rint(65536 / (1 + np.exp(-a_on))) == 65536
+        assert np.rint(65536 / (1 + np.exp(-a_off))) == 0
+    T, seed, B = 15, 9, 256
+    gpu = run_gpu(ms, stream, inst, sat_table, B, T, seed, path=path)
+    assert ms.MAXSAT_PATH_DENSE == 1 and ms.MAXSAT_PATH_SPARSE == 2
+    assert_same(gpu, run_oracle(inst, sat_table, B, T, seed), T, 0.01)
+
+
 def test_graph_replay_matches_plain_launches(ms, stream, small_table):
     inst = inst_of(workloads.random_ksat(60, 250, 3, seed=4, wmax=50))
     a = run_gpu(ms, stream, inst, small_table, 256, 23, 9, spg=0)
