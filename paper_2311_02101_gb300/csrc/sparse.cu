@@ -293,10 +293,10 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, size_t o, int 
   }
 }
 
-constexpr int kVisBatch = 8;
+constexpr int kVisBatch = 4;
 
 template <bool SM, typename HT>
-__global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevChains C,
+__global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
                                                  uint32_t t_rel) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -315,9 +315,9 @@ __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevC
   const int i = blockIdx.y * 8 + warp;
   if (i >= F.n) return;
   const uint32_t t = step_index(tdev, t_rel);
-  int e[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) e[q] = temp_of(C.g8_off * 8 + b0 + q, T.n_temps, C.B_total, C.inv_B_total);
+  const int gb0 = C.g8_off * 8 + b0;  // global chain index
+  const int e0 = temp_of(gb0, T.n_temps, C.B_total, C.inv_B_total);
+  const bool e_uni = e0 == temp_of(gb0 + 7, T.n_temps, C.B_total, C.inv_B_total);
   int z[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) z[q] = 0;
@@ -328,43 +328,57 @@ __global__ void __launch_bounds__(256) k_visible(DevFormula F, DevTables T, DevC
   const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
   float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
   const float4 n0 = nu4[0], n1 = nu4[1];
-  // z += sgn * 2^Q G[pattern] for one incidence (clause inc.x, literal slot)
-  auto add = [&](const int4& inc, const HV& v) {
-    const int base = inc.y & 0x7FFFFFFF;
-    const int sgn = inc.y < 0 ? -1 : 1;
-    uint32_t hp[8];
-    if constexpr (sizeof(HT) == 1) {
+  const int j_begin = __ldg(F.var_off + i), j_end = __ldg(F.var_off + i + 1);
+  // z += sgn * 2^Q G[e][pattern][slot] over the variable's incidences
+  // (clause inc.x, table base | sign inc.y, stride K inc.z, per-temperature
+  // stride 2^L K inc.w). UNI: the 8 chains share temperature e0.
+  auto sums = [&](auto uni) {
+    constexpr bool UNI = decltype(uni)::value;
+    int e[8];
+    if constexpr (!UNI) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) hp[q] = (uint32_t)(v >> (8 * q)) & 0xFFu;
-    } else {
-      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int q = 0; q < 8; ++q) hp[q] = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+      for (int q = 0; q < 8; ++q) e[q] = temp_of(gb0 + q, T.n_temps, C.B_total, C.inv_B_total);
     }
+    // kVisBatch incidences per pass, their record and pattern loads in
+    // flight together; the last pass is predicated (warp-uniform)
+    for (int jj = j_begin; jj < j_end; jj += kVisBatch) {
+      int4 inc[kVisBatch];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) z[q] += sgn * (int)gq[base + e[q] * inc.w + (int)hp[q] * inc.z];
+      for (int u = 0; u < kVisBatch; ++u)
+        inc[u] = jj + u < j_end ? __ldg(F.var_inc + jj + u) : make_int4(0, 0, 0, 0);
+      HV v[kVisBatch];
+#pragma unroll
+      for (int u = 0; u < kVisBatch; ++u)
+        if (jj + u < j_end)
+          v[u] = __ldg(reinterpret_cast<const HV*>(H + (size_t)inc[u].x * C.Bp + b0));
+#pragma unroll
+      for (int u = 0; u < kVisBatch; ++u) {
+        if (jj + u >= j_end) break;
+        const int base = inc[u].y & 0x7FFFFFFF;
+        const int sgn = inc[u].y < 0 ? -1 : 1;
+        uint32_t hp[8];
+        if constexpr (sizeof(HT) == 1) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) hp[q] = (uint32_t)(v[u] >> (8 * q)) & 0xFFu;
+        } else {
+          const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) hp[q] = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+        }
+        if constexpr (UNI) {
+          const int bo = base + e0 * inc[u].w;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) z[q] += sgn * (int)gq[bo + (int)hp[q] * inc[u].z];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            z[q] += sgn * (int)gq[base + e[q] * inc[u].w + (int)hp[q] * inc[u].z];
+        }
+      }
+    }
   };
-  auto load = [&](int clause) {
-    return __ldg(reinterpret_cast<const HV*>(H + (size_t)clause * C.Bp + b0));
-  };
-  const int j_end = __ldg(F.var_off + i + 1);
-  int jj = __ldg(F.var_off + i);
-  // kVisBatch incidences per pass: their record and pattern loads are in
-  // flight together
-  for (; jj + kVisBatch <= j_end; jj += kVisBatch) {
-    int4 inc[kVisBatch];
-#pragma unroll
-    for (int u = 0; u < kVisBatch; ++u) inc[u] = __ldg(F.var_inc + jj + u);
-    HV v[kVisBatch];
-#pragma unroll
-    for (int u = 0; u < kVisBatch; ++u) v[u] = load(inc[u].x);
-#pragma unroll
-    for (int u = 0; u < kVisBatch; ++u) add(inc[u], v[u]);
-  }
-  for (; jj < j_end; ++jj) {
-    const int4 inc = __ldg(F.var_inc + jj);
-    add(inc, load(inc.x));
-  }
+  if (e_uni) sums(std::true_type{});
+  else sums(std::false_type{});
   keep_improved(C, o, b0, xold);
 
   const uint4 r =
