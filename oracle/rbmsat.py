@@ -68,9 +68,10 @@ def lib():
         _lib.oracle_draw16.argtypes = [u64, u32, u32, u32, u32, u32]
         _lib.oracle_draw16.restype = u32
         _lib.oracle_eval.argtypes = [i32, i64, P, P, P, P, i32, P]
-        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P, P]
+        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P, P, u32]
         _lib.oracle_gibbs.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32, i32,
-                                      f64, u64, i32, P, i32, u32, i32, P, P, P, P, P, P, i32]
+                                      f64, u64, i32, P, i32, u32, i32, P, P, P, P, P, P, i32,
+                                      u32]
         _lib.oracle_free_energy.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32,
                                             i32, P, i32, P]
     return _lib
@@ -328,25 +329,30 @@ class ChainState:
     t: int = 0
     chain_ids: np.ndarray | None = None  # global chain index of each row
     B_total: int = 0  # ensemble size the temperatures are spread over
+    instance: int = 0  # index of the formula in a batch (draws carry it)
 
     def copy(self):
         return ChainState(self.x.copy(), self.nu.copy(), self.best_cost.copy(),
                           self.best_x.copy(), self.cost.copy(), self.free_energy.copy(), self.t,
-                          None if self.chain_ids is None else self.chain_ids.copy(), self.B_total)
+                          None if self.chain_ids is None else self.chain_ids.copy(), self.B_total,
+                          self.instance)
 
 
-def init_chains(n: int, B: int, seed: int, chain_ids=None, B_total=None) -> ChainState:
+def init_chains(n: int, B: int, seed: int, chain_ids=None, B_total=None,
+                instance: int = 0) -> ChainState:
     """B chains; with `chain_ids`, row r is chain chain_ids[r] of an ensemble
-    of B_total chains (so a sample of a large run can be reproduced)."""
+    of B_total chains (so a sample of a large run can be reproduced).
+    `instance` is the formula's index in a batch: its draws carry it in the
+    high 24 bits of the phase word."""
     if chain_ids is not None:
         chain_ids = np.ascontiguousarray(chain_ids, np.int32)
         B = len(chain_ids)
     x = np.zeros((B, n), np.uint8)
     nu = np.zeros((B, n), np.float64)
     best = np.zeros(B, np.int64)
-    lib().oracle_init(n, B, seed, _ptr(chain_ids), _ptr(x), _ptr(nu), _ptr(best))
+    lib().oracle_init(n, B, seed, _ptr(chain_ids), _ptr(x), _ptr(nu), _ptr(best), instance)
     return ChainState(x, nu, best, x.copy(), np.zeros(B, np.int64), np.zeros(B), 0,
-                      chain_ids, int(B_total if B_total is not None else B))
+                      chain_ids, int(B_total if B_total is not None else B), int(instance))
 
 
 def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int,
@@ -360,7 +366,7 @@ def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int
                             n_temps, n_buckets, alpha, seed, B, _ptr(st.chain_ids),
                             st.B_total or B, st.t, steps,
                             _ptr(st.x), _ptr(st.nu), _ptr(st.best_cost), _ptr(st.best_x),
-                            _ptr(st.cost), _ptr(st.free_energy), threads)
+                            _ptr(st.cost), _ptr(st.free_energy), threads, st.instance)
     if rc != 0:
         raise ValueError("a clause has no RBM parameter set")
     st.t += steps
@@ -378,10 +384,11 @@ def score_and_keep(inst: Instance, st: ChainState) -> ChainState:
     return st
 
 
-def solve(inst, table, B, steps, seed, n_temps, n_buckets=1, alpha=0.01, threads=1):
+def solve(inst, table, B, steps, seed, n_temps, n_buckets=1, alpha=0.01, threads=1,
+          instance=0):
     """reset + `steps` rounds + final score; returns (best cost, best
     assignment, chain state). Ties go to the lowest chain index."""
-    st = init_chains(inst.n, B, seed)
+    st = init_chains(inst.n, B, seed, instance=instance)
     gibbs(inst, table, st, steps, seed, n_temps, n_buckets, alpha, threads)
     score_and_keep(inst, st)
     b = int(np.argmin(st.best_cost))

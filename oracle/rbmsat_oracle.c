@@ -31,7 +31,9 @@
  *     temperature of the chain); chains are split into contiguous temperature
  *     blocks e_b = floor(b * E / B);
  *   - the assignment is scored before each update and once more after the
- *     last step (by the caller), so steps t = 0..T score x_0..x_T.
+ *     last step (by the caller), so steps t = 0..T score x_0..x_T;
+ *   - a batch of formulas: instance i's draws carry i in the high 24 bits of
+ *     the phase word, with its own clause and variable indices.
  */
 #include <math.h>
 #include <stdint.h>
@@ -183,11 +185,11 @@ static void negation_transform(const rbm_table* t, int s, const int32_t* lits,
 /* best-so-far empty).                                                      */
 /* ---------------------------------------------------------------------- */
 int oracle_init(int32_t n, int32_t B, uint64_t seed, const int32_t* chain_ids,
-                uint8_t* x, double* nu, int64_t* best_cost) {
+                uint8_t* x, double* nu, int64_t* best_cost, uint32_t inst) {
   for (int32_t b = 0; b < B; ++b) {
     uint32_t gb = (uint32_t)(chain_ids ? chain_ids[b] : b);
     for (int32_t i = 0; i < n; ++i) {
-      uint32_t u = oracle_draw16(seed, PH_INIT, 0u, (uint32_t)i, 0u, gb);
+      uint32_t u = oracle_draw16(seed, PH_INIT | (inst << 8), 0u, (uint32_t)i, 0u, gb);
       x[(int64_t)b * n + i] = u < 32768u;
       nu[(int64_t)b * n + i] = 0.25;
     }
@@ -198,6 +200,10 @@ int oracle_init(int32_t n, int32_t B, uint64_t seed, const int32_t* chain_ids,
 
 /* ---------------------------------------------------------------------- */
 /* T rounds of block Gibbs sampling on B chains, starting at step t0.       */
+/* inst: the instance's index when many formulas are solved as one batch;  */
+/* it fills the high 24 bits of every draw's phase word (0 for a single     */
+/* formula), so each instance's chains draw exactly as if run alone with    */
+/* that index.                                                              */
 /* State arrays are B x n, chain-major. Row b is chain chain_ids[b] of an   */
 /* ensemble of B_total chains (identity when chain_ids is NULL): the index  */
 /* selects its draws and its temperature. cost/free_energy receive the      */
@@ -211,7 +217,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
                  int32_t n_temps, int32_t n_buckets, double alpha, uint64_t seed,
                  int32_t B, const int32_t* chain_ids, int32_t B_total, uint32_t t0,
                  int32_t T, uint8_t* x, double* nu, int64_t* best_cost, uint8_t* best_x,
-                 int64_t* cost, double* free_energy, int32_t n_threads) {
+                 int64_t* cost, double* free_energy, int32_t n_threads, uint32_t inst) {
   rbm_table tab = {n_sets, set_len, set_bucket, set_temp, set_nh, W, bias};
   int64_t wmin = INT64_MAX;
   for (int64_t c = 0; c < m; ++c) {
@@ -259,7 +265,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
             a += Wp[k][h] * (double)xb[v];
           }
           F -= softplus(a);
-          uint32_t u = oracle_draw16(seed, PH_HID, t, (uint32_t)c, (uint32_t)h, gb);
+          uint32_t u = oracle_draw16(seed, PH_HID | (inst << 8), t, (uint32_t)c, (uint32_t)h, gb);
           hid[c * OR_MAX_H + h] = u < prob16(a);
         }
       }
@@ -288,7 +294,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
         uint32_t P = prob16(z[i]);
         double rho = (double)P / 65536.0;
         nub[i] = (1.0 - alpha) * nub[i] + alpha * rho * (1.0 - rho);
-        uint32_t u = oracle_draw16(seed, PH_VIS, t, (uint32_t)i, 0u, gb);
+        uint32_t u = oracle_draw16(seed, PH_VIS | (inst << 8), t, (uint32_t)i, 0u, gb);
         xb[i] = u < P;
       }
     }

@@ -283,6 +283,24 @@ def test_init_contract():
     assert st.x[3, 17] == (oracle.draw16(9, 1, 0, 17, 0, 3) < 32768)
 
 
+def test_instance_index_enters_only_the_phase_word(cfg1_table):
+    """A formula solved as instance 5 of a batch draws from phase words
+    phase | 5 << 8: its initial state is those draws, and one round of Gibbs
+    from a common state differs from instance 0 only through its draws (the
+    scores of the common state agree)."""
+    st = oracle.init_chains(50, 16, seed=9, instance=5)
+    assert st.x[3, 17] == (oracle.draw16(9, 1 | (5 << 8), 0, 17, 0, 3) < 32768)
+    assert not np.array_equal(st.x, oracle.init_chains(50, 16, seed=9).x)
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    a = oracle.init_chains(50, 16, seed=9)
+    b = a.copy()
+    b.instance = 5
+    oracle.gibbs(inst, cfg1_table, a, 1, seed=9, n_temps=2)
+    oracle.gibbs(inst, cfg1_table, b, 1, seed=9, n_temps=2)
+    assert np.array_equal(a.cost, b.cost) and np.array_equal(a.best_cost, b.best_cost)
+    assert not np.array_equal(a.x, b.x)
+
+
 def test_determinism_and_resume(cfg1_table):
     inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
     a = oracle.init_chains(50, 32, seed=4)
