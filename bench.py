@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--path", default="auto", choices=["auto", "sparse", "dense"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the batched ragged-instance probe (512 formulas)")
     ap.add_argument("--fixed-seconds", type=float, default=3.0,
                     help="wall time of the equal-time best-cost comparison")
     return ap.parse_args()
@@ -358,6 +360,7 @@ def run_mine(args):
     paths = compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
     fp32 = fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args,
                            ms_total / args.steps) if not args.no_fp32 else None
+    ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
 
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
@@ -375,7 +378,7 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32)
+                fp32_form=fp32, ragged=ragged)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -511,6 +514,45 @@ def fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args, our
                 fixed_time_s=budget, rounds_fp32=rounds_fp32, rounds_ours=rounds_ours,
                 best_cost_fp32=best_fp32, best_cost_ours=best_ours,
                 note="FP32 torch matmuls (TF32 off) + lookups, torch generator draws")
+
+
+def ragged_probe(ms, torch, stream, sets, args):
+    """Batched ragged instances: 512 weighted 3-SAT formulas (n log-uniform
+    in [100, 5000], m / n uniform in [4, 8]) with 256 restarts each, all in
+    every launch of one context (maxsat_create_batch). Device time of K
+    graph-replayed rounds with CUDA events on the library's stream, then the
+    per-kernel split from a profiled region."""
+    spec = workloads.WORKLOADS["ragged-512"]
+    insts = spec["gen"](args.seed)
+    B = spec["B"]
+    m_tot = sum(len(i[1]) - 1 for i in insts)
+    p = ms.maxsat_default_params(sets=sets)
+    try:
+        ctx = ms.maxsat_create_batch(insts, p, stream)
+    except ms.MaxsatError as e:
+        return dict(unavailable=str(e))
+    K = max(20, min(200, args.steps))
+    ms.maxsat_reset(ctx, B, 7)
+    ms.maxsat_step(ctx, max(3, min(args.warmup, 20)))
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    ms.maxsat_step(ctx, K)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms_round = start.elapsed_time(stop) / K
+    ms.maxsat_set_profiling(ctx, True)
+    ms.maxsat_step(ctx, max(10, K // 4))
+    kt = ms.maxsat_kernel_times(ctx)
+    ms.maxsat_set_profiling(ctx, False)
+    best, _ = ms.maxsat_solve(ctx, B, 50, 7)
+    ms.maxsat_destroy(ctx)
+    return dict(workload="ragged-512", instances=len(insts), clauses=m_tot,
+                variables=int(sum(i[0] for i in insts)), B=B, rounds=K, ms_per_round=ms_round,
+                evals_per_s=m_tot * B / (ms_round / 1e3), unit="evals/s",
+                kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()},
+                launches_per_round=sum(v[0] for k, v in kt.items()) / max(10, K // 4),
+                best_cost_sum_50_rounds=int(np.sum(best)))
 
 
 def dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args):

@@ -122,6 +122,43 @@ int maxsat_create(maxsat_ctx** out, int32_t n_vars, int64_t n_clauses,
                   const int64_t* weights, const maxsat_params* params,
                   void* cuda_stream);
 
+/* Builds one solver for a batch of n_inst independent weighted CNF formulas
+ * of uneven size, run together in every launch. The paper runs independent
+ * chains side by side and suggests clustering clauses by size (Sec. 4.2,
+ * Sec. 5 "Datasets"); a batch extends this to many formulas.
+ *   n_inst      number of formulas, 1 .. 65535
+ *   n_vars      n_inst host int32: variables of each formula (>= 1)
+ *   n_clauses   n_inst host int64: clauses of each formula (>= 0)
+ *   clause_off  (sum of n_clauses) + 1 host int64 offsets into lits over the
+ *               formulas' clauses concatenated in order, clause_off[0] = 0
+ *   lits        DIMACS literals local to each formula (1 .. n_vars[k])
+ *   weights     per clause as in maxsat_create (concatenated), or NULL
+ * The context then behaves as one formula over the union of the variables
+ * (formula k's variables follow those of formulas 0 .. k-1), except that
+ * costs and the best-so-far are kept per formula: with B restarts, formula
+ * k has its own B chains, and
+ *   maxsat_eval       cost_dev is n_inst x B (row k: formula k's cost of
+ *                     each assignment; assign_dev is B x total variables),
+ *   maxsat_solve      best_assign gets every formula's best assignment
+ *                     (total variables bytes) and best_cost n_inst values,
+ *   maxsat_get_state / maxsat_set_state
+ *                     best_cost, cost, free_energy are n_inst x B.
+ * Draws of formula k use its own clause and variable indices with k in bits
+ * 8..31 of the Philox phase word, so each formula follows exactly the
+ * trajectory it would follow alone under that index. Weight buckets are
+ * relative to each formula's lightest clause. Sparse path only
+ * (MAXSAT_PATH_DENSE fails with MAXSAT_EINVAL; AUTO uses the sparse path).
+ * Errors: MAXSAT_EINVAL for a bad count, offset or literal (the message
+ * names the formula), MAXSAT_ENOMEM, MAXSAT_ECUDA, MAXSAT_ENODEV. */
+int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
+                        const int64_t* n_clauses, const int64_t* clause_off,
+                        const int32_t* lits, const int64_t* weights,
+                        const maxsat_params* params, void* cuda_stream);
+
+/* Number of formulas of the context (1 unless made by maxsat_create_batch),
+ * or a negative code. */
+int maxsat_get_n_instances(const maxsat_ctx* ctx);
+
 /* Starts B fresh chains (Fig. code initialisation): every variable drawn
  * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */
 int maxsat_reset(maxsat_ctx* ctx, int32_t restarts, uint64_t seed);
@@ -147,21 +184,23 @@ int maxsat_step(maxsat_ctx* ctx, int64_t steps);
 int maxsat_score(maxsat_ctx* ctx);
 
 /* Weighted unsatisfied cost of B arbitrary assignments (the MaxSAT objective,
- * Sec. 1). assign_dev: B x n device bytes; cost_dev: B device int64.
- * Independent of the chains. Asynchronous. */
+ * Sec. 1). assign_dev: B x n device bytes; cost_dev: B device int64 (n_inst x
+ * B for a batch). Independent of the chains. Asynchronous. */
 int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B,
                 int64_t* cost_dev);
 
 /* reset + `steps` rounds + score, then copies the best assignment over all
  * chains (lowest cost, ties to the lowest chain index) to best_assign (n host
- * bytes, may be NULL) and its cost to *best_cost. Synchronises. */
+ * bytes, may be NULL) and its cost to *best_cost (a batch: per formula, see
+ * maxsat_create_batch). Synchronises. */
 int maxsat_solve(maxsat_ctx* ctx, int32_t restarts, int64_t steps, uint64_t seed,
                  uint8_t* best_assign, int64_t* best_cost);
 
 /* Copies chain state to host buffers (each may be NULL): x and best_x are
  * B x n bytes, nu is B x n float, best_cost / cost are B int64 (cost = last
  * scored state), free_energy B float (last scored state, Eq. 1 summed over
- * clauses), *t the next round's index. Synchronises. */
+ * clauses), *t the next round's index; for a batch best_cost, cost and
+ * free_energy are n_inst x B. Synchronises. */
 int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
                      uint8_t* best_x, int64_t* cost, float* free_energy,
                      uint32_t* t);

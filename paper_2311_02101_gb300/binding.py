@@ -65,6 +65,9 @@ def lib():
         L.maxsat_default_params.restype = None
         L.maxsat_create.argtypes = [ctypes.POINTER(P), i32, i64, P, P, P,
                                     ctypes.POINTER(maxsat_params), P]
+        L.maxsat_create_batch.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, P,
+                                          ctypes.POINTER(maxsat_params), P]
+        L.maxsat_get_n_instances.argtypes = [P]
         L.maxsat_reset.argtypes = [P, i32, u64]
         L.maxsat_reset_shard.argtypes = [P, i32, u64, i32, i32]
         L.maxsat_step.argtypes = [P, i64]
@@ -82,7 +85,8 @@ def lib():
         L.maxsat_eval_noalloc.argtypes = [i32, i64, i64, P, P, P, P, i32, P, P]
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
-        for name in ["maxsat_create", "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
+        for name in ["maxsat_create", "maxsat_create_batch", "maxsat_get_n_instances",
+                     "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
                      "maxsat_get_path", "maxsat_fit_or_rbm", "maxsat_set_profiling",
@@ -114,10 +118,12 @@ class Context:
     """Opaque solver handle (the C maxsat_ctx*) plus the few facts the binding
     needs for marshalling."""
 
-    def __init__(self, handle, n, m):
+    def __init__(self, handle, n, m, n_inst=1, var_base=None):
         self.handle = handle
-        self.n = n
+        self.n = n          # variables (of all formulas of a batch)
         self.m = m
+        self.n_inst = n_inst
+        self.var_base = var_base if var_base is not None else np.array([0, n], np.int64)
         self.B = 0
 
     def __del__(self):
@@ -170,6 +176,36 @@ def maxsat_create(n, off, lits, weights=None, params=None, stream=None) -> Conte
     return Context(h.value, int(n), len(off) - 1)
 
 
+def maxsat_create_batch(instances, params=None, stream=None) -> Context:
+    """instances: sequence of (n, off, lits, weights-or-None), literals local
+    to each formula. One context runs all of them (maxsat_create_batch)."""
+    nv = np.array([int(i[0]) for i in instances], np.int32)
+    offs = [np.ascontiguousarray(i[1], np.int64) for i in instances]
+    nc = np.array([len(o) - 1 for o in offs], np.int64)
+    base = np.concatenate([[0], np.cumsum([o[-1] for o in offs])]).astype(np.int64)
+    off = np.concatenate([[0]] + [o[1:] + base[k] for k, o in enumerate(offs)]).astype(np.int64)
+    lits = np.ascontiguousarray(np.concatenate([np.asarray(i[2], np.int32) for i in instances]),
+                                np.int32)
+    if all(i[3] is None for i in instances):
+        w = None
+    else:
+        w = np.ascontiguousarray(np.concatenate(
+            [np.ones(len(o) - 1, np.int64) if i[3] is None else np.asarray(i[3], np.int64)
+             for i, o in zip(instances, offs)]), np.int64)
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(params) if params is not None else None
+    rc = lib().maxsat_create_batch(ctypes.byref(h), len(instances), _np_ptr(nv), _np_ptr(nc),
+                                   _np_ptr(off), _np_ptr(lits), _np_ptr(w), pp,
+                                   _stream_handle(stream))
+    _check(rc, None)
+    var_base = np.concatenate([[0], np.cumsum(nv)]).astype(np.int64)
+    return Context(h.value, int(var_base[-1]), int(nc.sum()), len(instances), var_base)
+
+
+def maxsat_get_n_instances(ctx: Context) -> int:
+    return int(lib().maxsat_get_n_instances(ctx.handle))
+
+
 def maxsat_reset(ctx: Context, restarts: int, seed: int):
     _check(lib().maxsat_reset(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1)), ctx)
     ctx.B = int(restarts)
@@ -192,10 +228,10 @@ def maxsat_score(ctx: Context):
 
 def maxsat_eval(ctx: Context, assign_dev, cost_dev):
     """assign_dev: torch uint8 CUDA tensor (B x n, contiguous); cost_dev: torch
-    int64 CUDA tensor (B)."""
+    int64 CUDA tensor (B; n_inst x B for a batch)."""
     B = int(assign_dev.shape[0])
     assert assign_dev.is_cuda and cost_dev.is_cuda and assign_dev.is_contiguous()
-    assert tuple(assign_dev.shape) == (B, ctx.n) and cost_dev.numel() >= B
+    assert tuple(assign_dev.shape) == (B, ctx.n) and cost_dev.numel() >= B * ctx.n_inst
     _check(lib().maxsat_eval(ctx.handle, assign_dev.data_ptr(), B, cost_dev.data_ptr()), ctx)
 
 
@@ -214,20 +250,26 @@ def maxsat_eval_noalloc(n, off_dev, lits_dev, weights_dev, assign_dev, cost_dev,
 
 
 def maxsat_solve(ctx: Context, restarts: int, steps: int, seed: int):
-    """Returns (best cost, best assignment as n uint8)."""
+    """Returns (best cost, best assignment as n uint8); for a batch, (n_inst
+    best costs, every formula's best assignment over all variables)."""
     best = np.zeros(ctx.n, np.uint8)
-    cost = ctypes.c_int64()
+    cost = np.zeros(ctx.n_inst, np.int64)
     _check(lib().maxsat_solve(ctx.handle, int(restarts), int(steps), int(seed) & (2 ** 64 - 1),
-                              _np_ptr(best), ctypes.byref(cost)), ctx)
+                              _np_ptr(best), _np_ptr(cost)), ctx)
     ctx.B = int(restarts)
-    return int(cost.value), best
+    if ctx.n_inst == 1:
+        return int(cost[0]), best
+    return cost, best
 
 
 def maxsat_get_state(ctx: Context):
-    B, n = ctx.B, ctx.n
+    """Chain state; best_cost, cost and free_energy are (B,) for one formula
+    and (n_inst, B) for a batch."""
+    B, n, K = ctx.B, ctx.n, ctx.n_inst
+    shp = (B,) if K == 1 else (K, B)
     out = dict(x=np.zeros((B, n), np.uint8), nu=np.zeros((B, n), np.float32),
-               best_cost=np.zeros(B, np.int64), best_x=np.zeros((B, n), np.uint8),
-               cost=np.zeros(B, np.int64), free_energy=np.zeros(B, np.float32))
+               best_cost=np.zeros(shp, np.int64), best_x=np.zeros((B, n), np.uint8),
+               cost=np.zeros(shp, np.int64), free_energy=np.zeros(shp, np.float32))
     t = ctypes.c_uint32()
     _check(lib().maxsat_get_state(ctx.handle, _np_ptr(out["x"]), _np_ptr(out["nu"]),
                                   _np_ptr(out["best_cost"]), _np_ptr(out["best_x"]),

@@ -79,6 +79,11 @@ struct maxsat_ctx {
   int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
   std::vector<int64_t> h_w;  // clause weights (host copy)
+  int n_inst = 1;                      // formulas in the batch
+  std::vector<int32_t> inst_var_base;  // n_inst + 1 first variable of each formula
+  std::vector<int32_t> inst_cl_base;   // n_inst + 1 first clause of each formula
+  GatherPlan plan{};                   // clause blocks of the step / score gathers
+  GatherPlan ev_plan{};                // clause blocks of the sparse eval
   int gather_slots = 0;  // SMs x resident gather blocks per SM
   int gather_cb = 0;     // clauses per gather block for the chains' Bp
   bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
@@ -228,7 +233,7 @@ int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_
     return MAXSAT_OK;
   }
   TIMED(ctx, st, "gather_hidden",
-        launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->gather_cb, tdev, t_rel,
+        launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->plan, tdev, t_rel,
                       C.cost_part, C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
   TIMED(ctx, st, "visible",
         launch_visible(ctx->F, ctx->T, C, (float)ctx->prm.alpha, tdev, t_rel, ctx->wide_h, st));
@@ -259,6 +264,49 @@ int capture_graph(maxsat_ctx* ctx, int S) {
   return MAXSAT_OK;
 }
 
+// Clause blocks of at most cb clauses that never straddle two formulas of
+// the batch (a formula without clauses still gets one empty block, so its
+// costs are written); uploaded into A. *wmax receives the largest weight sum
+// of a block.
+int plan_blocks(const maxsat_ctx* ctx, int cb) {
+  int64_t nb = 0;
+  for (int in = 0; in < ctx->n_inst; ++in)
+    nb += std::max<int64_t>(1, (ctx->inst_cl_base[in + 1] - ctx->inst_cl_base[in] + cb - 1) / cb);
+  return (int)std::min<int64_t>(nb, INT32_MAX);
+}
+
+int upload_plan(maxsat_ctx* ctx, DevAllocs& A, int cb, GatherPlan* P, int64_t* wmax) {
+  // one grid row per block: at most 65535 blocks
+  while (plan_blocks(ctx, cb) > 65535 && cb < (1 << 29)) cb *= 2;
+  if (plan_blocks(ctx, cb) > 65535) return fail(ctx, MAXSAT_EINVAL, "too many clause blocks");
+  std::vector<int4> blk;
+  std::vector<int32_t> ib(1, 0);
+  *wmax = 0;
+  for (int in = 0; in < ctx->n_inst; ++in) {
+    const int c0 = ctx->inst_cl_base[in], c1 = ctx->inst_cl_base[in + 1];
+    int c = c0;
+    do {
+      const int e = std::min(c1, c + cb);
+      blk.push_back(make_int4(in, c, e, c0));
+      int64_t sum = 0;
+      for (int k = c; k < e; ++k) sum += ctx->h_w[k];
+      *wmax = std::max(*wmax, sum);
+      c = e;
+    } while (c < c1);
+    ib.push_back((int32_t)blk.size());
+  }
+  int4* dblk = nullptr;
+  int32_t* dib = nullptr;
+  CK(ctx, A.alloc(&dblk, blk.size()));
+  CK(ctx, A.alloc(&dib, ib.size()));
+  CK(ctx, cudaMemcpy(dblk, blk.data(), sizeof(int4) * blk.size(), cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy(dib, ib.data(), sizeof(int32_t) * ib.size(), cudaMemcpyHostToDevice));
+  P->blk = dblk;
+  P->inst_blk = dib;
+  P->n_blk = (int32_t)blk.size();
+  return MAXSAT_OK;
+}
+
 int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   if (ctx->have_chains && ctx->C.B == B && ctx->chains_dense == ctx->dense) return MAXSAT_OK;
   destroy_graph(ctx);
@@ -273,22 +321,20 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
     ctx->gather_slots = std::max(sms, 1) * gather_blocks_per_sm(ctx->T, ctx->wide_h);
   }
   ctx->gather_cb = gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
-  const int nblk = ctx->m > 0 ? (ctx->m + ctx->gather_cb - 1) / ctx->gather_cb : 1;
-  // 32-bit per-block cost rows when no clause block's weight sum reaches 2^31
+  DevAllocs& A = ctx->chain_mem;
   int64_t wmax_block = 0;
-  for (int bl = 0; bl < nblk; ++bl) {
-    int64_t sum = 0;
-    const int c1 = std::min(ctx->m, (bl + 1) * ctx->gather_cb);
-    for (int c = bl * ctx->gather_cb; c < c1; ++c) sum += ctx->h_w[c];
-    wmax_block = std::max(wmax_block, sum);
-  }
+  int rcp = upload_plan(ctx, A, ctx->gather_cb, &ctx->plan, &wmax_block);
+  if (rcp != MAXSAT_OK) return rcp;
+  const int nblk = ctx->plan.n_blk;
+  const size_t nI = (size_t)ctx->n_inst * Bp;
   DevChains& C = ctx->C;
   C = DevChains{};
+  // 32-bit per-block cost rows when no clause block's weight sum reaches 2^31
   C.cost32 = wmax_block < ((int64_t)1 << 31) ? 1 : 0;
+  C.n_inst = ctx->n_inst;
   C.B = B;
   C.Bp = Bp;
   ctx->chains_dense = ctx->dense;
-  DevAllocs& A = ctx->chain_mem;
   if (ctx->dense) {
     const size_t nP = (size_t)ctx->n_pad * Bp;
     const int tiles_m = ctx->m_pad / 128;
@@ -310,14 +356,14 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   }
   CK(ctx, A.alloc(&C.xt, nB));
   CK(ctx, A.alloc(&C.nu, nB));
-  CK(ctx, A.alloc(&C.best, Bp));
+  CK(ctx, A.alloc(&C.best, nI));
   CK(ctx, A.alloc(&C.best_xt, nB));
-  CK(ctx, A.alloc(&C.cost, Bp));
-  CK(ctx, A.alloc(&C.fe, Bp));
-  CK(ctx, A.alloc(&C.improved, Bp));
+  CK(ctx, A.alloc(&C.cost, nI));
+  CK(ctx, A.alloc(&C.fe, nI));
+  CK(ctx, A.alloc(&C.improved, nI));
   CK(ctx, A.alloc(&C.cost_part, (size_t)nblk * Bp));
   CK(ctx, A.alloc(&C.fe_part, (size_t)nblk * Bp));
-  CK(ctx, A.alloc(&C.tickets, Bp / kChainTile));
+  CK(ctx, A.alloc(&C.tickets, (size_t)ctx->n_inst * (Bp / kChainTile)));
   uint8_t* H = nullptr;
   CK(ctx, A.alloc(&H, (size_t)ctx->m * Bp * (ctx->wide_h ? 2 : 1)));
   C.H = H;
@@ -367,7 +413,7 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
     ctx->C.inv_B_total = 1.0f / (float)B;
     cudaError_t e = ctx->dense ? launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n,
                                                    ctx->n_pad, ctx->e5m2, ctx->stream)
-                               : launch_init_sparse(ctx->C, ctx->n, ctx->stream);
+                               : launch_init_sparse(ctx->F, ctx->C, ctx->n, ctx->stream);
     if (e != cudaSuccess) {
       rc = cuda_fail(ctx, e, "init");
       break;
@@ -550,10 +596,15 @@ int maxsat_get_path(const maxsat_ctx* ctx) {
   return ctx->dense ? MAXSAT_PATH_DENSE : ctx->path;
 }
 
-int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
-                  const int32_t* lits, const int64_t* weights, const maxsat_params* params,
-                  void* cuda_stream) {
-  g_create_error.clear();
+// Creates a context for the disjoint union of formulas: formula k owns
+// variables var_base[k] .. var_base[k + 1] - 1 and clauses cl_base[k] ..
+// cl_base[k + 1] - 1 (one formula: {0, n} and {0, m}); lits use the union's
+// variable numbering.
+static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
+                       const int32_t* lits, const int64_t* weights, const maxsat_params* params,
+                       void* cuda_stream, const std::vector<int32_t>& var_base,
+                       const std::vector<int32_t>& cl_base) {
+  const int n_inst = (int)var_base.size() - 1;
   if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1) return fail(nullptr, MAXSAT_EINVAL, "n_vars must be >= 1");
@@ -572,13 +623,17 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   for (int64_t j = 0; j < nnz; ++j)
     if (lits[j] == 0 || lits[j] > n || lits[j] < -n)
       return fail(nullptr, MAXSAT_EINVAL, "literal " + std::to_string(j) + " out of range");
-  int64_t wsum = 0, wmin = INT64_MAX;
-  for (int64_t c = 0; c < m; ++c) {
-    const int64_t w = weights ? weights[c] : 1;
-    if (w < 1) return fail(nullptr, MAXSAT_EINVAL, "weights must be >= 1");
-    if (w > ((int64_t)1 << 62) - wsum) return fail(nullptr, MAXSAT_EINVAL, "total weight exceeds 2^62");
-    wsum += w;
-    wmin = std::min(wmin, w);
+  // weight buckets are relative to the lightest clause of each formula
+  std::vector<int64_t> wmin(n_inst, INT64_MAX);
+  for (int k = 0; k < n_inst; ++k) {
+    int64_t wsum = 0;
+    for (int64_t c = cl_base[k]; c < cl_base[k + 1]; ++c) {
+      const int64_t w = weights ? weights[c] : 1;
+      if (w < 1) return fail(nullptr, MAXSAT_EINVAL, "weights must be >= 1");
+      if (w > ((int64_t)1 << 62) - wsum) return fail(nullptr, MAXSAT_EINVAL, "total weight exceeds 2^62");
+      wsum += w;
+      wmin[k] = std::min(wmin[k], w);
+    }
   }
   maxsat_params prm;
   if (params) prm = *params;
@@ -592,11 +647,17 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
     return fail(nullptr, MAXSAT_EINVAL, "steps_per_graph out of range");
   if (prm.n_sets < 0 || (prm.n_sets > 0 && !prm.sets)) return fail(nullptr, MAXSAT_EINVAL, "sets is NULL");
 
+  if (n_inst > 1 && prm.path == MAXSAT_PATH_DENSE)
+    return fail(nullptr, MAXSAT_EINVAL, "a batch of formulas runs on the sparse path only");
+
   int rc = check_device(nullptr);
   if (rc != MAXSAT_OK) return rc;
 
   maxsat_ctx* ctx = new maxsat_ctx();
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->n_inst = n_inst;
+  ctx->inst_var_base = var_base;
+  ctx->inst_cl_base = cl_base;
   ctx->n = n;
   ctx->m = (int32_t)m;
   ctx->nnz = (int32_t)nnz;
@@ -613,10 +674,12 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   // groups (length, bucket) in order of first appearance
   std::vector<int32_t> cl_grp(m, -1), grp_len, grp_bucket;
   std::map<std::pair<int, int>, int> gidx;
+  int inst_of_c = 0;
   for (int64_t c = 0; c < m; ++c) {
+    while (c >= cl_base[inst_of_c + 1]) ++inst_of_c;
     const int len = (int)(off[c + 1] - off[c]);
     if (len == 0) continue;
-    const int j = weight_bucket(weights ? weights[c] : 1, wmin, prm.n_buckets);
+    const int j = weight_bucket(weights ? weights[c] : 1, wmin[inst_of_c], prm.n_buckets);
     auto key = std::make_pair(len, j);
     auto it = gidx.find(key);
     if (it == gidx.end()) {
@@ -751,6 +814,14 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   UP(cl_w, F.cl_w);
   UP(var_off, F.var_off);
   UP(var_inc, F.var_inc);
+  F.n_inst = n_inst;
+  F.var_inst = nullptr;
+  if (n_inst > 1) {
+    std::vector<int2> vi(n);
+    for (int k = 0; k < n_inst; ++k)
+      for (int v = var_base[k]; v < var_base[k + 1]; ++v) vi[v] = make_int2(k, v - var_base[k]);
+    UP(vi, F.var_inst);
+  }
   UP(ctx->tabs.meta, T.meta);
   UP(ctx->tabs.rec, T.rec);
   UP(ctx->tabs.gq, T.gq);
@@ -773,7 +844,17 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
       return cuda_fail(nullptr, e, "cudaMalloc");
     }
   }
-  if (prm.path != MAXSAT_PATH_SPARSE) {
+  {
+    int64_t wmax_ev = 0;
+    const int rcp = upload_plan(ctx, ctx->formula_mem, clause_block_for(ctx->m), &ctx->ev_plan,
+                                &wmax_ev);
+    if (rcp != MAXSAT_OK) {
+      std::string e_ = ctx->err;
+      delete ctx;
+      return fail(nullptr, rcp, e_);
+    }
+  }
+  if (prm.path != MAXSAT_PATH_SPARSE && n_inst == 1) {
     std::string why;
     const int drc = build_dense(ctx, n, m, off, lits, weights, var_off, var_inc, &why);
     if (drc == MAXSAT_OK) {
@@ -789,6 +870,64 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
   }
   *out = ctx;
   return MAXSAT_OK;
+}
+
+int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
+                  const int32_t* lits, const int64_t* weights, const maxsat_params* params,
+                  void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1) return fail(nullptr, MAXSAT_EINVAL, "n_vars must be >= 1");
+  if (m < 0 || m > (int64_t)INT32_MAX / 2) return fail(nullptr, MAXSAT_EINVAL, "n_clauses out of range");
+  return create_impl(out, n, m, off, lits, weights, params, cuda_stream, {0, n}, {0, (int32_t)m});
+}
+
+int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
+                        const int64_t* n_clauses, const int64_t* clause_off, const int32_t* lits,
+                        const int64_t* weights, const maxsat_params* params, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_inst < 1 || n_inst > 65535) return fail(nullptr, MAXSAT_EINVAL, "n_inst must be in 1..65535");
+  if (!n_vars || !n_clauses) return fail(nullptr, MAXSAT_EINVAL, "n_vars / n_clauses is NULL");
+  std::vector<int32_t> var_base(n_inst + 1, 0), cl_base(n_inst + 1, 0);
+  for (int k = 0; k < n_inst; ++k) {
+    if (n_vars[k] < 1) return fail(nullptr, MAXSAT_EINVAL, "every instance needs n_vars >= 1");
+    if (n_clauses[k] < 0) return fail(nullptr, MAXSAT_EINVAL, "n_clauses must be >= 0");
+    if ((int64_t)var_base[k] + n_vars[k] > INT32_MAX / 2 ||
+        (int64_t)cl_base[k] + n_clauses[k] > INT32_MAX / 2)
+      return fail(nullptr, MAXSAT_EINVAL, "batch too large");
+    var_base[k + 1] = var_base[k] + n_vars[k];
+    cl_base[k + 1] = cl_base[k] + (int32_t)n_clauses[k];
+  }
+  const int32_t n = var_base[n_inst];
+  const int64_t m = cl_base[n_inst];
+  if (!clause_off) return fail(nullptr, MAXSAT_EINVAL, "clause_off is NULL");
+  if (clause_off[0] != 0) return fail(nullptr, MAXSAT_EINVAL, "clause_off[0] must be 0");
+  for (int64_t c = 0; c < m; ++c)
+    if (clause_off[c + 1] < clause_off[c] || clause_off[c + 1] - clause_off[c] > MAXSAT_MAX_LEN)
+      return fail(nullptr, MAXSAT_EINVAL, "clause_off must be non-decreasing with lengths <= MAXSAT_MAX_LEN");
+  const int64_t nnz = clause_off[m];
+  if (nnz > (int64_t)INT32_MAX / 2) return fail(nullptr, MAXSAT_EINVAL, "too many literals");
+  if (nnz > 0 && !lits) return fail(nullptr, MAXSAT_EINVAL, "lits is NULL");
+  // instance-local DIMACS literals -> the union's numbering
+  std::vector<int32_t> glits((size_t)nnz);
+  for (int k = 0; k < n_inst; ++k)
+    for (int64_t j = clause_off[cl_base[k]]; j < clause_off[cl_base[k + 1]]; ++j) {
+      const int32_t l = lits[j];
+      if (l == 0 || l > n_vars[k] || l < -n_vars[k])
+        return fail(nullptr, MAXSAT_EINVAL, "instance " + std::to_string(k) + ": literal " +
+                                                std::to_string(j) + " out of range");
+      glits[j] = l > 0 ? l + var_base[k] : l - var_base[k];
+    }
+  return create_impl(out, n, m, clause_off, glits.data(), weights, params, cuda_stream, var_base,
+                     cl_base);
+}
+
+int maxsat_get_n_instances(const maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  return ctx->n_inst;
 }
 
 int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
@@ -826,7 +965,7 @@ int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_
     CK(ctx, launch_init_dense(ctx->C, ctx->dX, ctx->dnu, ctx->dbest_x, ctx->n, ctx->n_pad,
                               ctx->e5m2, ctx->stream));
   else
-    CK(ctx, launch_init_sparse(ctx->C, ctx->n, ctx->stream));
+    CK(ctx, launch_init_sparse(ctx->F, ctx->C, ctx->n, ctx->stream));
   ctx->have_chains = true;
   return MAXSAT_OK;
 }
@@ -878,9 +1017,9 @@ int maxsat_score(maxsat_ctx* ctx) {
     return MAXSAT_OK;
   }
   TIMED(ctx, ctx->stream, "gather_score",
-        launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->gather_cb, nullptr, 0,
+        launch_gather(kScore, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->plan, nullptr, 0,
                       C.cost_part, C.fe_part, C.tickets, nullptr, ctx->wide_h, ctx->stream));
-  TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(C, ctx->n, ctx->stream));
+  TIMED(ctx, ctx->stream, "keep_copy", launch_keep_copy(ctx->F, C, ctx->n, ctx->stream));
   return MAXSAT_OK;
 }
 
@@ -954,19 +1093,20 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
     return MAXSAT_OK;
   }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
-  const int nblk = clause_blocks_for(ctx->m);
+  const int nblk = ctx->ev_plan.n_blk;
   if (Bp > ctx->ev_Bp) {
     ctx->eval_mem.release();
     ctx->ev_Bp = 0;
+    const size_t ntk = (size_t)ctx->n_inst * (Bp / kChainTile);
     CK(ctx, ctx->eval_mem.alloc(&ctx->ev_xt, (size_t)ctx->n * Bp));
     CK(ctx, ctx->eval_mem.alloc(&ctx->ev_part, (size_t)nblk * Bp));
-    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_tickets, Bp / kChainTile));
-    CK(ctx, cudaMemsetAsync(ctx->ev_tickets, 0, sizeof(int32_t) * (Bp / kChainTile), ctx->stream));
+    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_tickets, ntk));
+    CK(ctx, cudaMemsetAsync(ctx->ev_tickets, 0, sizeof(int32_t) * ntk, ctx->stream));
     ctx->ev_Bp = Bp;
   }
   CK(ctx, launch_transpose_in(assign_dev, B, ctx->n, ctx->ev_xt, Bp, ctx->stream));
-  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, clause_block_for(ctx->m),
-                        nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h,
+  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, ctx->ev_plan, nullptr, 0,
+                        ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h,
                         ctx->stream));
   return MAXSAT_OK;
 }
@@ -978,22 +1118,29 @@ int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
   if (rc == MAXSAT_OK) rc = maxsat_step(ctx, steps);
   if (rc == MAXSAT_OK) rc = maxsat_score(ctx);
   if (rc != MAXSAT_OK) return rc;
-  std::vector<int64_t> best(B);
-  CK(ctx, cudaMemcpyAsync(best.data(), ctx->C.best, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, ctx->stream));
+  // per formula: its lowest best cost, ties to the lowest chain
+  const int K = ctx->n_inst, Bp = ctx->C.Bp;
+  std::vector<int64_t> best((size_t)K * B);
+  CK(ctx, cudaMemcpy2DAsync(best.data(), sizeof(int64_t) * B, ctx->C.best, sizeof(int64_t) * Bp,
+                            sizeof(int64_t) * B, K, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
-  int bstar = 0;
-  for (int b = 1; b < B; ++b)
-    if (best[b] < best[bstar]) bstar = b;
-  if (best_cost) *best_cost = best[bstar];
-  if (best_assign) {
-    if (ctx->dense)
-      CK(ctx, cudaMemcpyAsync(best_assign, ctx->dbest_x + (size_t)bstar * ctx->n_pad, ctx->n,
-                              cudaMemcpyDeviceToHost, ctx->stream));
-    else
-      CK(ctx, cudaMemcpy2DAsync(best_assign, 1, ctx->C.best_xt + bstar, ctx->C.Bp, 1, ctx->n,
+  for (int k = 0; k < K; ++k) {
+    const int64_t* bk = best.data() + (size_t)k * B;
+    int bstar = 0;
+    for (int b = 1; b < B; ++b)
+      if (bk[b] < bk[bstar]) bstar = b;
+    if (best_cost) best_cost[k] = bk[bstar];
+    if (best_assign) {
+      const int v0 = ctx->inst_var_base[k], nk = ctx->inst_var_base[k + 1] - v0;
+      if (ctx->dense)
+        CK(ctx, cudaMemcpyAsync(best_assign, ctx->dbest_x + (size_t)bstar * ctx->n_pad, ctx->n,
                                 cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
+      else
+        CK(ctx, cudaMemcpy2DAsync(best_assign + v0, 1, ctx->C.best_xt + (size_t)v0 * Bp + bstar, Bp,
+                                  1, nk, cudaMemcpyDeviceToHost, ctx->stream));
+    }
   }
+  if (best_assign) CK(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->dense) return check_device_error(ctx);
   return MAXSAT_OK;
 }
@@ -1046,9 +1193,17 @@ int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
   if (x && (rc = fetch_T(ctx->C.xt, 1, x)) != MAXSAT_OK) return rc;
   if (nu && (rc = fetch_T(ctx->C.nu, 4, nu)) != MAXSAT_OK) return rc;
   if (best_x && (rc = fetch_T(ctx->C.best_xt, 1, best_x)) != MAXSAT_OK) return rc;
-  if (best_cost) CK(ctx, cudaMemcpyAsync(best_cost, ctx->C.best, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
-  if (cost) CK(ctx, cudaMemcpyAsync(cost, ctx->C.cost, 8 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
-  if (free_energy) CK(ctx, cudaMemcpyAsync(free_energy, ctx->C.fe, 4 * (size_t)B, cudaMemcpyDeviceToHost, ctx->stream));
+  // per-formula rows of B chains (Bp apart on the device)
+  const int K = ctx->n_inst;
+  if (best_cost)
+    CK(ctx, cudaMemcpy2DAsync(best_cost, 8 * (size_t)B, ctx->C.best, 8 * (size_t)Bp, 8 * (size_t)B,
+                              K, cudaMemcpyDeviceToHost, ctx->stream));
+  if (cost)
+    CK(ctx, cudaMemcpy2DAsync(cost, 8 * (size_t)B, ctx->C.cost, 8 * (size_t)Bp, 8 * (size_t)B, K,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+  if (free_energy)
+    CK(ctx, cudaMemcpy2DAsync(free_energy, 4 * (size_t)B, ctx->C.fe, 4 * (size_t)Bp, 4 * (size_t)B,
+                              K, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   if (t) *t = ctx->t;
   return MAXSAT_OK;
@@ -1108,7 +1263,8 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t B, uint64_t seed, const uint8_t* x
   if ((rc = put_T(ctx->C.xt, 1, x)) != MAXSAT_OK) return rc;
   if ((rc = put_T(ctx->C.nu, 4, nu)) != MAXSAT_OK) return rc;
   if ((rc = put_T(ctx->C.best_xt, 1, best_x)) != MAXSAT_OK) return rc;
-  CK(ctx, cudaMemcpy(ctx->C.best, best_cost, 8 * (size_t)B, cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy2D(ctx->C.best, 8 * (size_t)Bp, best_cost, 8 * (size_t)B, 8 * (size_t)B,
+                       ctx->n_inst, cudaMemcpyHostToDevice));
   ctx->t = t;
   ctx->d_t_synced = false;
   return MAXSAT_OK;

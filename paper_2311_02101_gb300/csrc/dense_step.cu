@@ -270,9 +270,11 @@ __global__ void __launch_bounds__(64 + 32 * kEpi1, 1)
             const uint32_t octet = (uint32_t)(gb0 >> 3);
             const int chunks = gm.stride >> 2;
             if (!gm.sat)
-              hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, C.keys, hp, f);
+              hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, kPhaseHidden,
+                                        C.keys, hp, f);
             else
-              hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, C.keys, hp, f);
+              hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, tround, kPhaseHidden,
+                                       C.keys, hp, f);
             HT* H = static_cast<HT*>(a.H) + (size_t)c * a.Bp + b0;
             if (sizeof(HT) == 1) {
               uint64_t v = 0;

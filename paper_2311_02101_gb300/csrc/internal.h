@@ -45,9 +45,20 @@ struct DevFormula {
   const int32_t* cl_grp;   // m: clause group (length, bucket); -1 = empty clause
   const int64_t* cl_w;     // m weights
   const int32_t* var_off;  // n + 1 offsets into var_inc
+  int32_t n_inst;          // formulas in the batch (1 for a single formula)
+  const int2* var_inst;    // n: {instance, index within it}; NULL for one formula
   const int4* var_inc;     // incidence of a variable: {clause, gq_off + position
                            // (bit 31 set when negated), clause length K,
                            // per-temperature stride 2^L K of gq}
+};
+
+// Work list of the clause gather: blocks of consecutive clauses that never
+// straddle two formulas of a batch.
+struct GatherPlan {
+  const int4* blk;          // per block: {instance, first clause, end clause,
+                            //             the instance's first clause}
+  const int32_t* inst_blk;  // n_inst + 1: first block of each instance
+  int32_t n_blk;
 };
 
 struct DevTables {
@@ -76,6 +87,8 @@ struct DevChains {
   int32_t B_total;  // chains of the whole ensemble (temperature blocks)
   float inv_B_total;  // 1 / B_total (first guess of the temperature index)
   int32_t cost32;     // sparse gather: every clause block's weight sum < 2^31
+  int32_t n_inst;     // formulas: best / cost / fe / improved are n_inst x Bp,
+                      // tickets n_inst x (Bp / kChainTile)
   uint32_t key0, key1;
   RoundKeys keys;
   uint8_t* xt;        // sparse layout: n x Bp, 0/1
@@ -135,19 +148,20 @@ int gather_blocks_per_sm(const DevTables& T, bool wide_h);
 
 // sparse.cu launchers (all asynchronous on `st`)
 enum GatherMode { kStep = 0, kScore = 1, kEval = 2 };
-cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st);
-// kStep: cost, free energy, hidden draws, then (last block of each chain tile)
-// best-keep; kScore: the same without draws; kEval: cost only, written to
-// eval_out. xt / Bp / B / tickets / partials may differ from C's (eval).
+cudaError_t launch_init_sparse(const DevFormula& F, const DevChains& C, int n, cudaStream_t st);
+// kStep: cost, free energy, hidden draws, then (last block of each instance
+// and chain tile) best-keep; kScore: the same without draws; kEval: cost only,
+// written to eval_out (n_inst x B). xt / Bp / B / tickets / partials may
+// differ from C's (eval). Grid: chain tiles x P.n_blk.
 cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
-                          const DevChains& C, const uint8_t* xt, int B, int Bp, int cb,
-                          const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
-                          float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide_h,
-                          cudaStream_t st);
+                          const DevChains& C, const uint8_t* xt, int B, int Bp,
+                          const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
+                          int64_t* cost_part, float* fe_part, int32_t* tickets,
+                          int64_t* eval_out, bool wide_h, cudaStream_t st);
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
                            float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide_h,
                            cudaStream_t st);
-cudaError_t launch_keep_copy(const DevChains& C, int n, cudaStream_t st);
+cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st);
 cudaError_t launch_advance(uint32_t* tdev, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t st);
 cudaError_t launch_transpose_in(const uint8_t* assign, int B, int n, uint8_t* xt, int Bp,

@@ -51,18 +51,18 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {
 template <bool SAT, int I0, int NW, bool FE>
 __device__ __forceinline__ void hidden_words(const uint4* tab, const int (&row4)[8], int j, int hi,
                                              uint32_t clause, uint32_t cy, uint32_t t,
-                                             const RoundKeys& K, uint32_t (&hp)[8],
-                                             float (&fe)[8]) {
+                                             uint32_t phase, const RoundKeys& K,
+                                             uint32_t (&hp)[8], float (&fe)[8]) {
   uint4 R[NW];
   if (I0 + NW <= hi) {
 #pragma unroll
     for (int i = 0; i < NW; ++i)
-      R[i] = philox4x32_10(make_uint4(clause, cy + ((uint32_t)(I0 + i) << 24), t, kPhaseHidden), K);
+      R[i] = philox4x32_10(make_uint4(clause, cy + ((uint32_t)(I0 + i) << 24), t, phase), K);
   } else {
 #pragma unroll
     for (int i = 0; i < NW; ++i)
       R[i] = I0 + i < hi ? philox4x32_10(make_uint4(clause, cy + ((uint32_t)(I0 + i) << 24), t,
-                                                    kPhaseHidden),
+                                                    phase),
                                          K)
                          : make_uint4(0u, 0u, 0u, 0u);
   }
@@ -86,21 +86,24 @@ __device__ __forceinline__ void hidden_words(const uint4* tab, const int (&row4)
 
 // All hidden draws (and the free energy) of one clause for 8 chains. ONE:
 // every group's record is one chunk (L <= 3), so no later chunk exists.
+// clause is the clause's index within its formula and phase the hidden
+// phase with the formula's batch index in bits 8..31.
 template <bool SAT, bool ONE>
 __device__ __forceinline__ void hidden_draws(const uint4* tab, const int (&row4)[8], int chunks,
                                              int nh, uint32_t clause, uint32_t octet, uint32_t t,
-                                             const RoundKeys& K, uint32_t (&hp)[8],
-                                             float (&fe)[8]) {
+                                             uint32_t phase, const RoundKeys& K,
+                                             uint32_t (&hp)[8], float (&fe)[8]) {
   // chunk 0: free energy and units 0..2
   const uint32_t cy0 = octet | (0xFFu << 24);  // unit of word 0 is -1
-  hidden_words<SAT, 1, 3, true>(tab, row4, 0, nh + 1 < 4 ? nh + 1 : 4, clause, cy0, t, K, hp, fe);
+  hidden_words<SAT, 1, 3, true>(tab, row4, 0, nh + 1 < 4 ? nh + 1 : 4, clause, cy0, t, phase, K, hp,
+                                 fe);
   if (ONE) return;
   for (int j = 1; j < chunks; ++j) {
     const int h0 = 4 * j - 1;
     const int hi = nh - h0 < 4 ? nh - h0 : 4;
     const uint32_t cy = octet | ((uint32_t)h0 << 24);
-    hidden_words<SAT, 0, 2, false>(tab, row4, j, hi, clause, cy, t, K, hp, fe);
-    if (hi > 2) hidden_words<SAT, 2, 2, false>(tab, row4, j, hi, clause, cy, t, K, hp, fe);
+    hidden_words<SAT, 0, 2, false>(tab, row4, j, hi, clause, cy, t, phase, K, hp, fe);
+    if (hi > 2) hidden_words<SAT, 2, 2, false>(tab, row4, j, hi, clause, cy, t, phase, K, hp, fe);
   }
 }
 

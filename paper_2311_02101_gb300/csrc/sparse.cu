@@ -21,6 +21,12 @@
 // State layout: x and nu are variable-major (n x Bp) so 8 consecutive chains of
 // one variable are one 8-byte (x) or 32-byte (nu) access. The small
 // probability tables are staged in shared memory when they fit.
+// A batch of formulas is their disjoint union: every instance has its own B
+// chains in the same chain columns, clause blocks never straddle two
+// instances (GatherPlan), per-instance costs and best-so-far live in
+// n_inst x Bp arrays, and draws use the instance's own clause and variable
+// indices with the instance index in bits 8..31 of the phase word, so each
+// instance follows the trajectory it would follow alone under that index.
 #include <algorithm>
 #include <cstdint>
 #include <type_traits>
@@ -45,12 +51,22 @@ __device__ __forceinline__ void stage(void* dst, const void* src, int bytes) {
 
 __host__ __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
-__global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
+// (instance, index within it) of variable i
+__device__ __forceinline__ int2 var_instance(const DevFormula& F, int i) {
+  return F.var_inst ? __ldg(F.var_inst + i) : make_int2(0, i);
+}
+
+// Kernels over variables take vg0, the first group of 8 variables of this
+// launch (grids have at most 65535 groups; larger n takes several launches).
+__global__ void __launch_bounds__(256) k_init(DevFormula F, DevChains C, int n, int vg0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
-  const int i = blockIdx.y * 8 + warp;
+  const int i = (vg0 + blockIdx.y) * 8 + warp;
   if (i < n) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), 0u, kPhaseInit), C.keys);
+    const int2 vi = var_instance(F, i);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), 0u,
+                                             kPhaseInit | ((uint32_t)vi.x << 8)),
+                                  C.keys);
     uint64_t x = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) x |= (uint64_t)(lane16(r, q) < 32768u) << (8 * q);
@@ -61,22 +77,26 @@ __global__ void __launch_bounds__(256) k_init(DevChains C, int n) {
     reinterpret_cast<float4*>(C.nu + o)[0] = v;
     reinterpret_cast<float4*>(C.nu + o)[1] = v;
   }
-  if (blockIdx.y == 0 && warp == 0) {
+  if (vg0 + blockIdx.y == 0) {
+    for (int in = warp; in < C.n_inst; in += 8) {
+      const size_t ib = (size_t)in * C.Bp + b0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      C.best[b0 + q] = INT64_MAX;
-      C.improved[b0 + q] = 0;
+      for (int q = 0; q < 8; ++q) {
+        C.best[ib + q] = INT64_MAX;
+        C.improved[ib + q] = 0;
+      }
+      if (lane == 0) C.tickets[in * gridDim.x + blockIdx.x] = 0;
     }
-    if (lane == 0) C.tickets[blockIdx.x] = 0;
   }
 }
 
 template <int MODE, bool SM, typename HT, bool ONE>
 __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, DevChains C,
                                                 const uint8_t* __restrict__ xt, int B, int Bp,
-                                                int cblock, const uint32_t* tdev, uint32_t t_rel,
-                                                int64_t* cost_part, float* fe_part,
-                                                int32_t* tickets, int64_t* eval_out) {
+                                                GatherPlan P, const uint32_t* tdev,
+                                                uint32_t t_rel, int64_t* cost_part,
+                                                float* fe_part, int32_t* tickets,
+                                                int64_t* eval_out) {
   constexpr bool FE = MODE != kEval;
   constexpr bool SAMPLE = MODE == kStep;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -85,8 +105,10 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
-  const int c_begin = blockIdx.y * cblock;
-  const int c_end = min(c_begin + cblock, F.m);
+  // this block's clauses: one instance, clauses c_begin .. c_end - 1
+  const int4 bd = __ldg(P.blk + blockIdx.y);
+  const int inst = bd.x, c_begin = bd.y, c_end = bd.z, cl_base = bd.w;
+  const uint32_t phase_h = kPhaseHidden | ((uint32_t)inst << 8);
   const int E = T.n_temps;
 
   const GroupMeta* meta = T.meta;
@@ -217,10 +239,11 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
       for (int q = 0; q < 8; ++q) hp[q] = 0;
       const uint32_t octet = (uint32_t)(g8 + C.g8_off);
       const int chunks = gm.stride >> 2;
+      const uint32_t lc = (uint32_t)(c - cl_base);  // clause index within its instance
       if (!gm.sat)
-        hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, t, C.keys, hp, fe);
+        hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
       else
-        hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, (uint32_t)c, octet, t, C.keys, hp, fe);
+        hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
       HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
       if (sizeof(HT) == 1) {
         uint64_t v = 0;
@@ -238,8 +261,9 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
     }
   }
 
-  // per-block partial sums, then the block that arrives last for this tile of
-  // 256 chains reduces all partials in block order and keeps improvements
+  // per-block partial sums, then the block that arrives last among its
+  // instance's blocks for this tile of 256 chains reduces their partials in
+  // block order and keeps improvements
   if (FE) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) s_fe[warp][lane * 8 + q] = fe[q];
@@ -260,32 +284,36 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   if (FE) fe_part[out] = tf;
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = atomicAdd(tickets + blockIdx.x, 1) == (int)gridDim.y - 1;
+  const int k0 = __ldg(P.inst_blk + inst), k1 = __ldg(P.inst_blk + inst + 1);
+  int32_t* ticket = tickets + inst * gridDim.x + blockIdx.x;
+  if (tid == 0) s_last = atomicAdd(ticket, 1) == k1 - k0 - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   const int b = blockIdx.x * 256 + tid;
   int64_t csum = 0;
   float fsum = 0.f;
-  for (int k = 0; k < (int)gridDim.y; ++k) {
+  for (int k = k0; k < k1; ++k) {
     csum += __ldcg(cost_part + (size_t)k * Bp + b);
     if (FE) fsum += __ldcg(fe_part + (size_t)k * Bp + b);
   }
   if (MODE == kEval) {
-    if (b < B) eval_out[b] = csum;
+    if (b < B) eval_out[(size_t)inst * B + b] = csum;
   } else {
-    C.cost[b] = csum;
-    C.fe[b] = fsum;
-    const bool imp = csum < C.best[b];
-    if (imp) C.best[b] = csum;
-    C.improved[b] = imp ? 1 : 0;
+    const size_t ib = (size_t)inst * Bp + b;
+    C.cost[ib] = csum;
+    C.fe[ib] = fsum;
+    const bool imp = csum < C.best[ib];
+    if (imp) C.best[ib] = csum;
+    C.improved[ib] = imp ? 1 : 0;
   }
-  if (tid == 0) tickets[blockIdx.x] = 0;
+  if (tid == 0) *ticket = 0;
 }
 
-__device__ __forceinline__ void keep_improved(const DevChains& C, size_t o, int b0,
+__device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size_t o, int b0,
                                               uint64_t xold) {
-  const uint64_t imp = *reinterpret_cast<const uint64_t*>(C.improved + b0);
+  const uint64_t imp =
+      *reinterpret_cast<const uint64_t*>(C.improved + (size_t)inst * C.Bp + b0);
   if (imp) {
     const uint64_t mask = imp * 0xFFull;  // 0x01 flags -> 0xFF byte masks
     uint64_t* bx = reinterpret_cast<uint64_t*>(C.best_xt + o);
@@ -298,7 +326,7 @@ constexpr int kVisBatch = 4;
 template <bool SM, typename HT>
 __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
-                                                 uint32_t t_rel) {
+                                                 uint32_t t_rel, int vg0) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
@@ -312,8 +340,9 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
     gq = reinterpret_cast<const int16_t*>(smem);
     pv = reinterpret_cast<const uint32_t*>(smem + gb);
   }
-  const int i = blockIdx.y * 8 + warp;
+  const int i = (vg0 + blockIdx.y) * 8 + warp;
   if (i >= F.n) return;
+  const int2 vi = var_instance(F, i);
   const uint32_t t = step_index(tdev, t_rel);
   const int gb0 = C.g8_off * 8 + b0;  // global chain index
   const int e0 = temp_of(gb0, T.n_temps, C.B_total, C.inv_B_total);
@@ -379,10 +408,12 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
   };
   if (e_uni) sums(std::true_type{});
   else sums(std::false_type{});
-  keep_improved(C, o, b0, xold);
+  keep_improved(C, vi.x, o, b0, xold);
 
   const uint4 r =
-      philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(g8 + C.g8_off), t, kPhaseVisible), C.keys);
+      philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), t,
+                               kPhaseVisible | ((uint32_t)vi.x << 8)),
+                    C.keys);
   float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
   const float keep = 1.0f - alpha;
   uint64_t xnew = 0;
@@ -400,13 +431,13 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
   *reinterpret_cast<uint64_t*>(C.xt + o) = xnew;
 }
 
-__global__ void __launch_bounds__(256) k_keep_copy(DevChains C, int n) {
+__global__ void __launch_bounds__(256) k_keep_copy(DevFormula F, DevChains C, int n, int vg0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int b0 = (blockIdx.x * 32 + lane) * 8;
-  const int i = blockIdx.y * 8 + warp;
+  const int i = (vg0 + blockIdx.y) * 8 + warp;
   if (i >= n) return;
   const size_t o = (size_t)i * C.Bp + b0;
-  keep_improved(C, o, b0, *reinterpret_cast<const uint64_t*>(C.xt + o));
+  keep_improved(C, var_instance(F, i).x, o, b0, *reinterpret_cast<const uint64_t*>(C.xt + o));
 }
 
 __global__ void k_advance(uint32_t* tdev, uint32_t by) { *tdev += by; }
@@ -438,11 +469,12 @@ int visible_smem_bytes(const DevTables& T) {
 }
 
 constexpr int kSmemLimit = 160 * 1024;
+constexpr int kMaxGridY = 65535;
 
 template <int MODE, bool SM, typename HT>
 cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
                            const DevTables& T, const DevChains& C, const uint8_t* xt, int B,
-                           int Bp, int cb, const uint32_t* tdev, uint32_t t_rel,
+                           int Bp, const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
                            int64_t* cost_part, float* fe_part, int32_t* tickets,
                            int64_t* eval_out) {
   // one-chunk records (L <= 3 everywhere): the sampling has no chunk loop
@@ -453,7 +485,7 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 256, smem, st>>>(F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part, fe_part, tickets,
+  kern<<<grid, 256, smem, st>>>(F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part, fe_part, tickets,
                                 eval_out);
   return cudaGetLastError();
 }
@@ -472,20 +504,20 @@ int gather_occupancy(int smem) {
 template <int MODE>
 cudaError_t gather_mode(dim3 grid, cudaStream_t st, bool wide, const DevFormula& F,
                         const DevTables& T, const DevChains& C, const uint8_t* xt, int B, int Bp,
-                        int cb, const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
-                        float* fe_part, int32_t* tickets, int64_t* eval_out) {
+                        const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
+                        int64_t* cost_part, float* fe_part, int32_t* tickets, int64_t* eval_out) {
   const int sm = gather_smem_bytes(T);
   const bool use_sm = MODE != kEval && sm <= kSmemLimit;
   if (use_sm && !wide)
-    return gather_variant<MODE, true, uint8_t>(grid, sm, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+    return gather_variant<MODE, true, uint8_t>(grid, sm, st, F, T, C, xt, B, Bp, P, tdev, t_rel,
                                                cost_part, fe_part, tickets, eval_out);
   if (use_sm)
-    return gather_variant<MODE, true, uint16_t>(grid, sm, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+    return gather_variant<MODE, true, uint16_t>(grid, sm, st, F, T, C, xt, B, Bp, P, tdev, t_rel,
                                                 cost_part, fe_part, tickets, eval_out);
   if (!wide)
-    return gather_variant<MODE, false, uint8_t>(grid, 0, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+    return gather_variant<MODE, false, uint8_t>(grid, 0, st, F, T, C, xt, B, Bp, P, tdev, t_rel,
                                                 cost_part, fe_part, tickets, eval_out);
-  return gather_variant<MODE, false, uint16_t>(grid, 0, st, F, T, C, xt, B, Bp, cb, tdev, t_rel,
+  return gather_variant<MODE, false, uint16_t>(grid, 0, st, F, T, C, xt, B, Bp, P, tdev, t_rel,
                                                cost_part, fe_part, tickets, eval_out);
 }
 
@@ -498,7 +530,11 @@ cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormu
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, 256, smem, st>>>(F, T, C, alpha, tdev, t_rel);
+  const int groups = (F.n + 7) / 8;
+  for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
+    grid.y = std::min(kMaxGridY, groups - vg0);
+    kern<<<grid, 256, smem, st>>>(F, T, C, alpha, tdev, t_rel, vg0);
+  }
   return cudaGetLastError();
 }
 
@@ -551,28 +587,31 @@ int gather_blocks_per_sm(const DevTables& T, bool wide) {
   return gather_occupancy<false, uint16_t>(0);
 }
 
-cudaError_t launch_init_sparse(const DevChains& C, int n, cudaStream_t st) {
-  dim3 grid(C.Bp / kChainTile, (n + 7) / 8);
-  k_init<<<grid, 256, 0, st>>>(C, n);
+cudaError_t launch_init_sparse(const DevFormula& F, const DevChains& C, int n, cudaStream_t st) {
+  const int groups = std::max((n + 7) / 8, 1);
+  for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
+    dim3 grid(C.Bp / kChainTile, std::min(kMaxGridY, groups - vg0));
+    k_init<<<grid, 256, 0, st>>>(F, C, n, vg0);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables& T,
-                          const DevChains& C, const uint8_t* xt, int B, int Bp, int cb,
-                          const uint32_t* tdev, uint32_t t_rel, int64_t* cost_part,
-                          float* fe_part, int32_t* tickets, int64_t* eval_out, bool wide,
-                          cudaStream_t st) {
-  if (cb < 1) return cudaErrorInvalidValue;
-  dim3 grid(Bp / kChainTile, F.m > 0 ? (F.m + cb - 1) / cb : 1);
+                          const DevChains& C, const uint8_t* xt, int B, int Bp,
+                          const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
+                          int64_t* cost_part, float* fe_part, int32_t* tickets,
+                          int64_t* eval_out, bool wide, cudaStream_t st) {
+  if (P.n_blk < 1 || P.n_blk > kMaxGridY) return cudaErrorInvalidValue;
+  dim3 grid(Bp / kChainTile, P.n_blk);
   switch (mode) {
     case kStep:
-      return gather_mode<kStep>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+      return gather_mode<kStep>(grid, st, wide, F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part,
                                 fe_part, tickets, eval_out);
     case kScore:
-      return gather_mode<kScore>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+      return gather_mode<kScore>(grid, st, wide, F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part,
                                  fe_part, tickets, eval_out);
     default:
-      return gather_mode<kEval>(grid, st, wide, F, T, C, xt, B, Bp, cb, tdev, t_rel, cost_part,
+      return gather_mode<kEval>(grid, st, wide, F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part,
                                 fe_part, tickets, eval_out);
   }
 }
@@ -589,9 +628,12 @@ cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevCha
   return visible_variant<false, uint16_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel);
 }
 
-cudaError_t launch_keep_copy(const DevChains& C, int n, cudaStream_t st) {
-  dim3 grid(C.Bp / kChainTile, (n + 7) / 8);
-  k_keep_copy<<<grid, 256, 0, st>>>(C, n);
+cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st) {
+  const int groups = (n + 7) / 8;
+  for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
+    dim3 grid(C.Bp / kChainTile, std::min(kMaxGridY, groups - vg0));
+    k_keep_copy<<<grid, 256, 0, st>>>(F, C, n, vg0);
+  }
   return cudaGetLastError();
 }
 

@@ -85,12 +85,36 @@ def test_create_validates_before_device(n, off, lits, w, msg):
     assert msg in str(e.value)
 
 
+@pytest.mark.parametrize("insts,msg", [
+    ([(0, [0, 1], [1], None)], "n_vars >= 1"),
+    ([(3, [0, 2], [1, 2], None), (2, [0, 1], [3], None)], "instance 1: literal"),
+    ([(3, [0, 2], [1, -4], None)], "instance 0: literal"),
+    ([(3, [0, 2], [1, 2], [0])], "weights"),
+    ([(13, [0, 13], list(range(1, 14)), None)], "MAXSAT_MAX_LEN"),
+])
+def test_create_batch_validates_before_device(insts, msg):
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_create_batch(insts)
+    assert e.value.code == ms.MAXSAT_EINVAL
+    assert msg in str(e.value)
+
+
+def test_create_batch_dense_path_is_rejected():
+    p = ms.maxsat_default_params(path=ms.MAXSAT_PATH_DENSE)
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_create_batch([(3, [0, 2], [1, 2], None), (2, [0, 1], [-2], None)], p)
+    assert e.value.code == ms.MAXSAT_EINVAL and "sparse path" in str(e.value)
+
+
 def test_create_without_device_fails_loudly():
     import torch
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     with pytest.raises(ms.MaxsatError) as e:
         ms.maxsat_create(3, [0, 2], [1, -2])
+    assert e.value.code == ms.MAXSAT_ENODEV
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_create_batch([(3, [0, 2], [1, -2], None), (2, [0, 1], [2], None)])
     assert e.value.code == ms.MAXSAT_ENODEV
 
 

@@ -407,3 +407,102 @@ def test_chain_shards_reproduce_one_run(ms, stream, small_table, path):
         sl = slice(256 * r, 256 * r + 256)
         for k in ["x", "best_cost", "best_x", "cost", "nu", "free_energy"]:
             assert np.array_equal(part[k], whole[k][sl]), (k, r)
+
+
+# --------------------------------------------------------------------------
+# Batches of formulas (maxsat_create_batch): every formula against the oracle
+# run alone with its batch index
+# --------------------------------------------------------------------------
+def small_batch(seed=3):
+    rng = np.random.default_rng(seed)
+    insts = workloads.ragged_batch(count=9, n_lo=12, n_hi=160, seed=seed)
+    # a formula without clauses and one with an empty clause and a tautology
+    insts.insert(4, (7, np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64)))
+    cl = [[1, -2, 3], [], [4, -4], [2, 5, -6]] + [list(rng.choice([-1, 1], 3) * (rng.permutation(6)[:3] + 1))
+                                                 for _ in range(30)]
+    e = oracle.Instance.from_clauses(6, cl, list(rng.integers(1, 50, size=len(cl))))
+    insts.insert(7, (e.n, e.off, e.lits, e.w))
+    return insts
+
+
+def batch_ctx(ms, stream, insts, table, n_buckets=4, alpha=0.01):
+    params = ms.maxsat_default_params(sets=table.sets, n_temps=2, n_buckets=n_buckets,
+                                      alpha=alpha)
+    params.fstar = None
+    return ms.maxsat_create_batch(insts, params, stream)
+
+
+@pytest.mark.parametrize("B", [256, 300])
+def test_batch_trajectories_match_oracle(ms, stream, golden_table, B):
+    insts = small_batch()
+    T, seed = 9, 17
+    ctx = batch_ctx(ms, stream, insts, golden_table)
+    assert ms.maxsat_get_n_instances(ctx) == len(insts)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, T)
+    g = ms.maxsat_get_state(ctx)
+    vb = ctx.var_base
+    for k, (n, off, lits, w) in enumerate(insts):
+        inst = oracle.Instance(n, off, lits, w)
+        st = oracle.init_chains(n, B, seed, instance=k)
+        oracle.gibbs(inst, golden_table, st, T, seed, n_temps=2, n_buckets=4,
+                     threads=os.cpu_count() or 4)
+        sl = slice(int(vb[k]), int(vb[k + 1]))
+        assert np.array_equal(g["x"][:, sl], st.x), k
+        assert np.array_equal(g["best_x"][:, sl], st.best_x), k
+        assert np.array_equal(g["best_cost"][k], st.best_cost), k
+        assert np.array_equal(g["cost"][k], st.cost), k
+        np.testing.assert_allclose(g["free_energy"][k], st.free_energy, rtol=1e-3, atol=1e-6)
+        assert np.max(np.abs(g["nu"][:, sl] - st.nu)) <= nu_tol(T, 0.01)
+    ms.maxsat_destroy(ctx)
+
+
+def test_batch_eval_and_solve_match_oracle(ms, stream, golden_table):
+    import torch
+    insts = small_batch(5)
+    ctx = batch_ctx(ms, stream, insts, golden_table)
+    rng = np.random.default_rng(2)
+    B = 37
+    a = rng.integers(0, 2, size=(B, ctx.n)).astype(np.uint8)
+    cost = torch.zeros(len(insts) * B, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        ms.maxsat_eval(ctx, torch.tensor(a, device="cuda"), cost)
+    stream.synchronize()
+    cost = cost.cpu().numpy().reshape(len(insts), B)
+    vb = ctx.var_base
+    for k, (n, off, lits, w) in enumerate(insts):
+        ref = oracle.evaluate(oracle.Instance(n, off, lits, w), a[:, vb[k]:vb[k + 1]])
+        assert np.array_equal(cost[k], ref), k
+    T, seed, Bs = 12, 8, 64
+    best, assign = ms.maxsat_solve(ctx, Bs, T, seed)
+    for k, (n, off, lits, w) in enumerate(insts):
+        inst = oracle.Instance(n, off, lits, w)
+        c, x, _ = oracle.solve(inst, golden_table, Bs, T, seed, n_temps=2, n_buckets=4,
+                               threads=os.cpu_count() or 4, instance=k)
+        assert best[k] == c, k
+        assert np.array_equal(assign[vb[k]:vb[k + 1]], x), k
+        assert oracle.evaluate(inst, assign[None, vb[k]:vb[k + 1]])[0] == c
+    ms.maxsat_destroy(ctx)
+
+
+def test_batch_full_size_sampled(ms, stream, golden_table):
+    """512 formulas, n log-uniform in [100, 5000], m / n in [4, 8], B = 256:
+    three formulas (first, middle, last) recomputed by the oracle."""
+    insts = workloads.ragged_batch(seed=0)
+    B, T, seed = 256, 4, 23
+    ctx = batch_ctx(ms, stream, insts, golden_table)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, T)
+    g = ms.maxsat_get_state(ctx)
+    vb = ctx.var_base
+    for k in (0, 255, 511):
+        n, off, lits, w = insts[k]
+        inst = oracle.Instance(n, off, lits, w)
+        st = oracle.init_chains(n, B, seed, instance=k)
+        oracle.gibbs(inst, golden_table, st, T, seed, n_temps=2, n_buckets=4,
+                     threads=os.cpu_count() or 4)
+        sl = slice(int(vb[k]), int(vb[k + 1]))
+        assert np.array_equal(g["x"][:, sl], st.x), k
+        assert np.array_equal(g["best_cost"][k], st.best_cost), k
+        assert np.array_equal(g["cost"][k], st.cost), k
+    ms.maxsat_destroy(ctx)

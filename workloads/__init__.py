@@ -102,6 +102,9 @@ WORKLOADS = {
     "w3sat-n1000-m6000": dict(gen=lambda seed=0: weighted_3sat(1000, 6000, 1000, seed), B=4096),
     # mixed clause lengths 2 + Geom(0.4) capped at 12, 10 % hard, 1024 restarts
     "mixed-n20000-m100000": dict(gen=lambda seed=0: mixed_length(seed=seed), B=1024),
+    # batch of 512 weighted 3-SAT instances, n log-uniform in [100, 5000], m / n uniform in
+    # [4, 8], 256 restarts each (gen returns a list of instances)
+    "ragged-512": dict(gen=lambda seed=0: ragged_batch(seed=seed), B=256, batch=True),
 }
 
 
