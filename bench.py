@@ -261,7 +261,7 @@ def run_mine(args):
     stream = torch.cuda.Stream()
     path_code = {"auto": ms.MAXSAT_PATH_AUTO, "sparse": ms.MAXSAT_PATH_SPARSE,
                  "dense": ms.MAXSAT_PATH_DENSE}[args.path]
-    params = ms.maxsat_default_params(path=path_code)
+    params = ms.maxsat_default_params(path=path_code, tune_blocks=1)
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
     # every rank runs its own shard of one ensemble of ws * B chains (weak
     # scaling): global chains rank * B .. rank * B + B - 1
@@ -371,7 +371,8 @@ def run_mine(args):
                 scaling="weak", vs_baseline=None, dtype="fp8" if path == "dense" else "int32",
                 data="synthetic",
                 config=dict(workload=args.workload, n=n, m=m, B=B, path=path, path_requested=args.path,
-                            steps_per_graph=S, parallelism=f"chain-shards{ws}",
+                            steps_per_graph=S, clause_block=ms.maxsat_get_clause_block(ctx),
+                            parallelism=f"chain-shards{ws}",
                             l2="working set above L2 (no flush): G/hidden state, nu and "
                                "x of 4096 chains; state carried step to step"),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck,
@@ -526,13 +527,14 @@ def ragged_probe(ms, torch, stream, sets, args):
     insts = spec["gen"](args.seed)
     B = spec["B"]
     m_tot = sum(len(i[1]) - 1 for i in insts)
-    p = ms.maxsat_default_params(sets=sets)
+    p = ms.maxsat_default_params(sets=sets, tune_blocks=1)
     try:
         ctx = ms.maxsat_create_batch(insts, p, stream)
     except ms.MaxsatError as e:
         return dict(unavailable=str(e))
     K = max(20, min(200, args.steps))
     ms.maxsat_reset(ctx, B, 7)
+    cb = ms.maxsat_get_clause_block(ctx)
     ms.maxsat_step(ctx, max(3, min(args.warmup, 20)))
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -547,7 +549,7 @@ def ragged_probe(ms, torch, stream, sets, args):
     ms.maxsat_set_profiling(ctx, False)
     best, _ = ms.maxsat_solve(ctx, B, 50, 7)
     ms.maxsat_destroy(ctx)
-    return dict(workload="ragged-512", instances=len(insts), clauses=m_tot,
+    return dict(workload="ragged-512", instances=len(insts), clauses=m_tot, clause_block=cb,
                 variables=int(sum(i[0] for i in insts)), B=B, rounds=K, ms_per_round=ms_round,
                 evals_per_s=m_tot * B / (ms_round / 1e3), unit="evals/s",
                 kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()},

@@ -94,6 +94,12 @@ typedef struct {
   int32_t steps_per_graph; /* Gibbs rounds per CUDA-graph launch (the paper runs
                               500 rounds per device dispatch); default 500;
                               0 = plain launches */
+  int32_t tune_blocks;   /* 1: at the first maxsat_reset for each B, time a few
+                            clause-block sizes of the sparse gather (3 rounds
+                            each, CUDA events) and keep the fastest. Costs,
+                            states and draws do not depend on the blocking;
+                            the free energy's float summation order does.
+                            Default 0 (the wave-fitted size) */
 } maxsat_params;
 
 typedef struct maxsat_ctx maxsat_ctx;
@@ -158,6 +164,11 @@ int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
 /* Number of formulas of the context (1 unless made by maxsat_create_batch),
  * or a negative code. */
 int maxsat_get_n_instances(const maxsat_ctx* ctx);
+
+/* Clauses per block of the sparse gather for the current chains (wave-fitted
+ * to the SM count, or measured with params.tune_blocks); 0 before the first
+ * maxsat_reset; a negative code for a NULL context. */
+int maxsat_get_clause_block(const maxsat_ctx* ctx);
 
 /* Starts B fresh chains (Fig. code initialisation): every variable drawn
  * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */

@@ -45,7 +45,7 @@ class maxsat_params(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("quant_bits", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("fit_iters", ctypes.c_int32),
                 ("n_sets", ctypes.c_int32), ("sets", ctypes.POINTER(maxsat_rbm_set)),
-                ("steps_per_graph", ctypes.c_int32)]
+                ("steps_per_graph", ctypes.c_int32), ("tune_blocks", ctypes.c_int32)]
 
 
 _lib = None
@@ -68,6 +68,7 @@ def lib():
         L.maxsat_create_batch.argtypes = [ctypes.POINTER(P), i32, P, P, P, P, P,
                                           ctypes.POINTER(maxsat_params), P]
         L.maxsat_get_n_instances.argtypes = [P]
+        L.maxsat_get_clause_block.argtypes = [P]
         L.maxsat_reset.argtypes = [P, i32, u64]
         L.maxsat_reset_shard.argtypes = [P, i32, u64, i32, i32]
         L.maxsat_step.argtypes = [P, i64]
@@ -86,6 +87,7 @@ def lib():
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
         for name in ["maxsat_create", "maxsat_create_batch", "maxsat_get_n_instances",
+                     "maxsat_get_clause_block",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
@@ -204,6 +206,10 @@ def maxsat_create_batch(instances, params=None, stream=None) -> Context:
 
 def maxsat_get_n_instances(ctx: Context) -> int:
     return int(lib().maxsat_get_n_instances(ctx.handle))
+
+
+def maxsat_get_clause_block(ctx: Context) -> int:
+    return int(lib().maxsat_get_clause_block(ctx.handle))
 
 
 def maxsat_reset(ctx: Context, restarts: int, seed: int):

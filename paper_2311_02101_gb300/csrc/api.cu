@@ -86,6 +86,9 @@ struct maxsat_ctx {
   GatherPlan ev_plan{};                // clause blocks of the sparse eval
   int gather_slots = 0;  // SMs x resident gather blocks per SM
   int gather_cb = 0;     // clauses per gather block for the chains' Bp
+  int cb_force = 0;      // clause block used instead of the wave-fitted one (0 = none)
+  int tuned_B = 0;       // B of the last measured clause-block choice
+  std::vector<std::pair<int, float>> tune_ms;  // measured (clause block, ms per round)
   bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
 
   cudaGraphExec_t graph = nullptr;
@@ -320,7 +323,8 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
     CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     ctx->gather_slots = std::max(sms, 1) * gather_blocks_per_sm(ctx->T, ctx->wide_h);
   }
-  ctx->gather_cb = gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
+  ctx->gather_cb = ctx->cb_force > 0 ? ctx->cb_force
+                                     : gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
   DevAllocs& A = ctx->chain_mem;
   int64_t wmax_block = 0;
   int rcp = upload_plan(ctx, A, ctx->gather_cb, &ctx->plan, &wmax_block);
@@ -440,6 +444,73 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   if (rc != MAXSAT_OK) return rc;
   ctx->dense = ctx->auto_ms[1] < ctx->auto_ms[0];
   ctx->auto_B = B;
+  ctx->have_chains = false;  // the timing runs left no valid chains
+  return MAXSAT_OK;
+}
+
+// Measured clause-block size of the sparse gather (params.tune_blocks): times
+// 3 Gibbs rounds for each candidate (the wave-fitted size, half and twice it,
+// and the plain m / 256 rule) with CUDA events and keeps the fastest.
+int tune_blocks(maxsat_ctx* ctx, int32_t B) {
+  const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
+  ctx->cb_force = 0;
+  if (ctx->gather_slots == 0) {
+    int rc0 = alloc_chains(ctx, B);  // sets gather_slots
+    if (rc0 != MAXSAT_OK) return rc0;
+  }
+  const int fit = gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
+  std::vector<int> cand = {fit, std::max(16, fit / 2), fit * 2, clause_block_for(ctx->m)};
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  cudaEvent_t e0, e1;
+  CK(ctx, cudaEventCreate(&e0));
+  CK(ctx, cudaEventCreate(&e1));
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  ctx->tune_ms.clear();
+  int rc = MAXSAT_OK, best = fit;
+  float best_ms = 0.f;
+  for (int cb : cand) {
+    ctx->cb_force = cb;
+    ctx->have_chains = false;
+    rc = alloc_chains(ctx, B);
+    if (rc != MAXSAT_OK) break;
+    ctx->C.keys = philox_keys(0x5EEDu, 0u);
+    ctx->C.g8_off = 0;
+    ctx->C.B_total = B;
+    ctx->C.inv_B_total = 1.0f / (float)B;
+    cudaError_t e = launch_init_sparse(ctx->F, ctx->C, ctx->n, ctx->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "init");
+      break;
+    }
+    constexpr int kRounds = 3;
+    for (int r = 0; r <= kRounds && rc == MAXSAT_OK; ++r) {
+      if (r == 1) cudaEventRecord(e0, ctx->stream);
+      rc = launch_round(ctx, ctx->stream, nullptr, (uint32_t)r);
+    }
+    if (rc != MAXSAT_OK) break;
+    cudaEventRecord(e1, ctx->stream);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "cudaEventSynchronize");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= kRounds;
+    ctx->tune_ms.emplace_back(ctx->gather_cb, ms);
+    if (ctx->tune_ms.size() == 1 || ms < best_ms) {
+      best_ms = ms;
+      best = ctx->gather_cb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->profiling = prof;
+  if (rc != MAXSAT_OK) return rc;
+  ctx->cb_force = best;
+  ctx->tuned_B = B;
   ctx->have_chains = false;  // the timing runs left no valid chains
   return MAXSAT_OK;
 }
@@ -585,6 +656,7 @@ void maxsat_default_params(maxsat_params* p) {
   p->n_sets = 0;
   p->sets = nullptr;
   p->steps_per_graph = 500;
+  p->tune_blocks = 0;
 }
 
 const char* maxsat_last_error(const maxsat_ctx* ctx) {
@@ -925,6 +997,11 @@ int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
                      cl_base);
 }
 
+int maxsat_get_clause_block(const maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  return ctx->gather_cb;
+}
+
 int maxsat_get_n_instances(const maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   return ctx->n_inst;
@@ -945,6 +1022,10 @@ int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_
                 "<= total_chains < 2^26 - 256");
   if (ctx->prm.path == MAXSAT_PATH_AUTO && ctx->dense_built && ctx->auto_B != B) {
     int rc0 = choose_path(ctx, B);
+    if (rc0 != MAXSAT_OK) return rc0;
+  }
+  if (ctx->prm.tune_blocks && !ctx->dense && ctx->tuned_B != B) {
+    int rc0 = tune_blocks(ctx, B);
     if (rc0 != MAXSAT_OK) return rc0;
   }
   int rc = alloc_chains(ctx, B);

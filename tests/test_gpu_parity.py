@@ -64,9 +64,11 @@ def inst_of(gen):
     return oracle.Instance(*gen)
 
 
-def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0):
+def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0,
+             tune=0):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=n_temps, n_buckets=n_buckets,
-                                      alpha=alpha, steps_per_graph=spg, path=path)
+                                      alpha=alpha, steps_per_graph=spg, path=path,
+                                      tune_blocks=tune)
     params.fstar = None
     return ms.maxsat_create(inst.n, inst.off, inst.lits, inst.w, params, stream)
 
@@ -506,3 +508,19 @@ def test_batch_full_size_sampled(ms, stream, golden_table):
         assert np.array_equal(g["best_cost"][k], st.best_cost), k
         assert np.array_equal(g["cost"][k], st.cost), k
     ms.maxsat_destroy(ctx)
+
+
+def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
+    """With tune_blocks the gather's clause-block size is measured at the first
+    reset; the trajectory is the oracle's whatever size wins."""
+    inst = inst_of(workloads.mixed_length(n=400, m=2000, seed=9))
+    T, seed, B = 10, 5, 512
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=ms.MAXSAT_PATH_SPARSE,
+                   tune=1, spg=4)
+    ms.maxsat_reset(ctx, B, seed)
+    cb = ms.maxsat_get_clause_block(ctx)
+    assert cb >= 16
+    ms.maxsat_step(ctx, T)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    assert_same(gpu, run_oracle(inst, golden_table, B, T, seed, n_buckets=4), T, 0.01)
