@@ -48,7 +48,8 @@ def build(force: bool = False) -> str:
     ):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-o",
+             tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -68,10 +69,11 @@ def lib():
         _lib.oracle_draw16.argtypes = [u64, u32, u32, u32, u32, u32]
         _lib.oracle_draw16.restype = u32
         _lib.oracle_eval.argtypes = [i32, i64, P, P, P, P, i32, P]
-        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P, P, u32]
+        _lib.oracle_init.argtypes = [i32, i32, u64, P, P, P, P, P, u32]
         _lib.oracle_gibbs.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32, i32,
-                                      f64, u64, i32, P, i32, u32, i32, P, P, P, P, P, P, i32,
-                                      u32]
+                                      f64, u64, i32, P, i32, u32, i32, P, P, P, P, P, P, P,
+                                      i32, u32]
+        _lib.oracle_unit_prop.argtypes = [i32, i64, P, P, P, P, P]
         _lib.oracle_free_energy.argtypes = [i32, i64, P, P, P, i32, P, P, P, P, P, P, i32,
                                             i32, P, i32, P]
     return _lib
@@ -330,12 +332,13 @@ class ChainState:
     chain_ids: np.ndarray | None = None  # global chain index of each row
     B_total: int = 0  # ensemble size the temperatures are spread over
     instance: int = 0  # index of the formula in a batch (draws carry it)
+    nu32: np.ndarray | None = None  # B x n float32: nu in the solver's FP32 sequence
 
     def copy(self):
         return ChainState(self.x.copy(), self.nu.copy(), self.best_cost.copy(),
                           self.best_x.copy(), self.cost.copy(), self.free_energy.copy(), self.t,
                           None if self.chain_ids is None else self.chain_ids.copy(), self.B_total,
-                          self.instance)
+                          self.instance, None if self.nu32 is None else self.nu32.copy())
 
 
 def init_chains(n: int, B: int, seed: int, chain_ids=None, B_total=None,
@@ -349,10 +352,12 @@ def init_chains(n: int, B: int, seed: int, chain_ids=None, B_total=None,
         B = len(chain_ids)
     x = np.zeros((B, n), np.uint8)
     nu = np.zeros((B, n), np.float64)
+    nu32 = np.zeros((B, n), np.float32)
     best = np.zeros(B, np.int64)
-    lib().oracle_init(n, B, seed, _ptr(chain_ids), _ptr(x), _ptr(nu), _ptr(best), instance)
+    lib().oracle_init(n, B, seed, _ptr(chain_ids), _ptr(x), _ptr(nu), _ptr(nu32), _ptr(best),
+                      instance)
     return ChainState(x, nu, best, x.copy(), np.zeros(B, np.int64), np.zeros(B), 0,
-                      chain_ids, int(B_total if B_total is not None else B), int(instance))
+                      chain_ids, int(B_total if B_total is not None else B), int(instance), nu32)
 
 
 def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int,
@@ -365,7 +370,8 @@ def gibbs(inst: Instance, table: RbmTable, st: ChainState, steps: int, seed: int
                             len(ln), _ptr(ln), _ptr(bk), _ptr(tp), _ptr(nh), _ptr(W), _ptr(b),
                             n_temps, n_buckets, alpha, seed, B, _ptr(st.chain_ids),
                             st.B_total or B, st.t, steps,
-                            _ptr(st.x), _ptr(st.nu), _ptr(st.best_cost), _ptr(st.best_x),
+                            _ptr(st.x), _ptr(st.nu), _ptr(st.nu32), _ptr(st.best_cost),
+                            _ptr(st.best_x),
                             _ptr(st.cost), _ptr(st.free_energy), threads, st.instance)
     if rc != 0:
         raise ValueError("a clause has no RBM parameter set")
@@ -393,6 +399,36 @@ def solve(inst, table, B, steps, seed, n_temps, n_buckets=1, alpha=0.01, threads
     score_and_keep(inst, st)
     b = int(np.argmin(st.best_cost))
     return int(st.best_cost[b]), st.best_x[b].copy(), st
+
+
+def unit_prop(inst: Instance, x, nu32):
+    """Prioritized unit propagation (Sec. 4.4) of each row of x (B x n, or
+    one assignment) ranked by the FP32 nu of the same shape; see
+    oracle_unit_prop for the steps."""
+    x = np.ascontiguousarray(np.atleast_2d(x), np.uint8)
+    nu32 = np.ascontiguousarray(np.atleast_2d(nu32), np.float32)
+    out = np.zeros_like(x)
+    for b in range(x.shape[0]):
+        lib().oracle_unit_prop(inst.n, inst.m, _ptr(inst.off), _ptr(inst.lits), _ptr(x[b]),
+                               _ptr(nu32[b]), _ptr(out[b]))
+    return out
+
+
+def up_merge(inst: Instance, st: ChainState, up_x) -> ChainState:
+    """The B-of-2B merge of the appendix code: the B current states and the B
+    unit-propagation results are stacked (current first), scored, sorted by
+    satisfied weight ascending with a stable sort, and the last B rows become
+    the new chains in that order; nu rows follow their states (the results
+    inherit the nu of the chain they came from). In place on st."""
+    B = st.x.shape[0]
+    cand = np.vstack([st.x, np.asarray(up_x, np.uint8)])
+    cost = evaluate(inst, cand)
+    ranks = np.argsort(-cost, kind="stable")  # satisfied weight ascending
+    sel = ranks[-B:]
+    st.x = np.ascontiguousarray(cand[sel])
+    st.nu = np.ascontiguousarray(np.vstack([st.nu, st.nu])[sel])
+    st.nu32 = np.ascontiguousarray(np.vstack([st.nu32, st.nu32])[sel])
+    return st
 
 
 def free_energy(inst, table, x, temp, n_buckets=1):

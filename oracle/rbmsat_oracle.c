@@ -185,13 +185,14 @@ static void negation_transform(const rbm_table* t, int s, const int32_t* lits,
 /* best-so-far empty).                                                      */
 /* ---------------------------------------------------------------------- */
 int oracle_init(int32_t n, int32_t B, uint64_t seed, const int32_t* chain_ids,
-                uint8_t* x, double* nu, int64_t* best_cost, uint32_t inst) {
+                uint8_t* x, double* nu, float* nu32, int64_t* best_cost, uint32_t inst) {
   for (int32_t b = 0; b < B; ++b) {
     uint32_t gb = (uint32_t)(chain_ids ? chain_ids[b] : b);
     for (int32_t i = 0; i < n; ++i) {
       uint32_t u = oracle_draw16(seed, PH_INIT | (inst << 8), 0u, (uint32_t)i, 0u, gb);
       x[(int64_t)b * n + i] = u < 32768u;
       nu[(int64_t)b * n + i] = 0.25;
+      if (nu32) nu32[(int64_t)b * n + i] = 0.25f;
     }
     best_cost[b] = INT64_MAX;
   }
@@ -216,8 +217,9 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
                  const int32_t* set_nh, const double* W, const double* bias,
                  int32_t n_temps, int32_t n_buckets, double alpha, uint64_t seed,
                  int32_t B, const int32_t* chain_ids, int32_t B_total, uint32_t t0,
-                 int32_t T, uint8_t* x, double* nu, int64_t* best_cost, uint8_t* best_x,
-                 int64_t* cost, double* free_energy, int32_t n_threads, uint32_t inst) {
+                 int32_t T, uint8_t* x, double* nu, float* nu32, int64_t* best_cost,
+                 uint8_t* best_x, int64_t* cost, double* free_energy, int32_t n_threads,
+                 uint32_t inst) {
   rbm_table tab = {n_sets, set_len, set_bucket, set_temp, set_nh, W, bias};
   int64_t wmin = INT64_MAX;
   for (int64_t c = 0; c < m; ++c) {
@@ -235,6 +237,7 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
     int32_t e = (int32_t)(((int64_t)gb * n_temps) / B_total);
     uint8_t* xb = x + (int64_t)b * n;
     double* nub = nu + (int64_t)b * n;
+    float* nu32b = nu32 ? nu32 + (int64_t)b * n : NULL;
     double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     uint8_t* hid = (uint8_t*)malloc((size_t)(m > 0 ? m : 1) * OR_MAX_H);
     for (int32_t step = 0; step < T && !bad; ++step) {
@@ -294,6 +297,16 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
         uint32_t P = prob16(z[i]);
         double rho = (double)P / 65536.0;
         nub[i] = (1.0 - alpha) * nub[i] + alpha * rho * (1.0 - rho);
+        if (nu32b) {
+          /* the same update in FP32 with a fixed operation order (the
+           * precision the solver ranks variables in): var = fl(P (65536 - P))
+           * 2^-32, nu = fma(1 - alpha, nu, fl(alpha var)) */
+          const float a32 = (float)alpha;
+          const float keep = 1.0f - a32;
+          const float var = (float)(P * (65536u - P)) * 0x1p-32f;
+          const float av = a32 * var;
+          nu32b[i] = fmaf(keep, nu32b[i], av);
+        }
         uint32_t u = oracle_draw16(seed, PH_VIS | (inst << 8), t, (uint32_t)i, 0u, gb);
         xb[i] = u < P;
       }
@@ -339,6 +352,133 @@ int oracle_free_energy(int32_t n, int64_t m, const int64_t* off, const int32_t* 
     }
     F_out[b] = F;
   }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Prioritized unit propagation (Sec. 4.4, after Si et al. 2019) on one     */
+/* assignment x, ranking variables by nu (the solver's FP32 nu):            */
+/*   1. order the variables by nu, highest first (ties: lower index);       */
+/*   2. the first floor(n/2) keep their values from x (no propagation yet); */
+/*   3. every clause that is not satisfied and has exactly one unassigned   */
+/*      literal occurrence puts that literal on a queue (clauses in index   */
+/*      order); the queue is emptied first-in first-out: a literal whose    */
+/*      variable is unassigned is made true, and each clause of that        */
+/*      variable (in index order) that becomes unit queues its literal;     */
+/*   4. the remaining variables, in order, each take its value from x if   */
+/*      still unassigned, and the queue is emptied again.                   */
+/* Falsified clauses are left as they are (MaxSAT). out gets the result.    */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t n;
+  int64_t m;
+  const int64_t* off;
+  const int32_t* lits;
+  const int64_t* voff;   /* n + 1 offsets into vocc */
+  const int64_t* vocc;   /* literal positions j of each variable, clause order */
+  int8_t* val;           /* -1 unassigned, else 0 / 1 */
+  int32_t* nfalse;       /* false literal occurrences per clause */
+  uint8_t* sat;          /* clause has a true literal */
+  int32_t* queue;        /* literals (DIMACS) */
+  int64_t qhead, qtail;
+} up_state;
+
+static void up_push_if_unit(up_state* S, int64_t c) {
+  const int64_t len = S->off[c + 1] - S->off[c];
+  if (S->sat[c] || len - S->nfalse[c] != 1) return;
+  for (int64_t j = S->off[c]; j < S->off[c + 1]; ++j) {
+    const int32_t l = S->lits[j];
+    const int32_t v = (l > 0 ? l : -l) - 1;
+    if (S->val[v] < 0) {
+      S->queue[S->qtail++] = l;
+      return;
+    }
+  }
+}
+
+/* assigns variable v := b and updates its clauses; with `check`, clauses
+ * that become unit queue their open literal */
+static void up_assign(up_state* S, int32_t v, int8_t b, int check) {
+  S->val[v] = b;
+  for (int64_t k = S->voff[v]; k < S->voff[v + 1]; ++k) {
+    const int64_t j = S->vocc[k];
+    int64_t c = 0;
+    /* clause of literal position j (binary search over off) */
+    int64_t lo = 0, hi = S->m;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (S->off[mid] <= j) lo = mid; else hi = mid;
+    }
+    c = lo;
+    const int32_t l = S->lits[j];
+    if ((l > 0) == (b == 1)) S->sat[c] = 1;
+    else S->nfalse[c]++;
+  }
+  if (!check) return;
+  for (int64_t k = S->voff[v]; k < S->voff[v + 1]; ++k) {
+    const int64_t j = S->vocc[k];
+    int64_t lo = 0, hi = S->m;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (S->off[mid] <= j) lo = mid; else hi = mid;
+    }
+    up_push_if_unit(S, lo);
+  }
+}
+
+static void up_drain(up_state* S) {
+  while (S->qhead < S->qtail) {
+    const int32_t l = S->queue[S->qhead++];
+    const int32_t v = (l > 0 ? l : -l) - 1;
+    if (S->val[v] < 0) up_assign(S, v, (int8_t)(l > 0), 1);
+  }
+}
+
+typedef struct { float key; int32_t idx; } up_rank;
+
+static int up_rank_cmp(const void* a, const void* b) {
+  const up_rank* x = (const up_rank*)a;
+  const up_rank* y = (const up_rank*)b;
+  if (x->key > y->key) return -1;
+  if (x->key < y->key) return 1;
+  return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+int oracle_unit_prop(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
+                     const uint8_t* x, const float* nu, uint8_t* out) {
+  const int64_t nnz = off[m];
+  int64_t* voff = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t* vocc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t j = 0; j < nnz; ++j) voff[(lits[j] > 0 ? lits[j] : -lits[j])]++;
+  for (int32_t i = 0; i < n; ++i) voff[i + 1] += voff[i];
+  for (int32_t i = 0; i < n; ++i) fill[i] = voff[i];
+  for (int64_t j = 0; j < nnz; ++j) {  /* positions in increasing order: clause order */
+    const int32_t v = (lits[j] > 0 ? lits[j] : -lits[j]) - 1;
+    vocc[fill[v]++] = j;
+  }
+  up_state S = {n, m, off, lits, voff, vocc, (int8_t*)malloc((size_t)n),
+                (int32_t*)calloc((size_t)(m > 0 ? m : 1), sizeof(int32_t)),
+                (uint8_t*)calloc((size_t)(m > 0 ? m : 1), 1),
+                (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz + m + 1)), 0, 0};
+  memset(S.val, -1, (size_t)n);
+  up_rank* order = (up_rank*)malloc(sizeof(up_rank) * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) { order[i].key = nu[i]; order[i].idx = i; }
+  qsort(order, (size_t)n, sizeof(up_rank), up_rank_cmp);
+  const int32_t half = n / 2;
+  for (int32_t r = 0; r < half; ++r) up_assign(&S, order[r].idx, (int8_t)(x[order[r].idx] != 0), 0);
+  for (int64_t c = 0; c < m; ++c) up_push_if_unit(&S, c);
+  up_drain(&S);
+  for (int32_t r = half; r < n; ++r) {
+    const int32_t v = order[r].idx;
+    if (S.val[v] < 0) {
+      up_assign(&S, v, (int8_t)(x[v] != 0), 1);
+      up_drain(&S);
+    }
+  }
+  for (int32_t i = 0; i < n; ++i) out[i] = (uint8_t)S.val[i];
+  free(voff); free(vocc); free(fill); free(S.val); free(S.nfalse); free(S.sat); free(S.queue);
+  free(order);
   return 0;
 }
 

@@ -51,7 +51,7 @@ def _paper_examples():
     with open(os.path.join(GOLDEN, "paper_examples.txt")) as f:
         for line in f:
             line = line.strip()
-            if not line or line.startswith("#"):
+            if not line or line.startswith("#") or line.startswith("up "):
                 continue
             if line.startswith("formula"):
                 head, body = line.split("|")
@@ -299,6 +299,100 @@ def test_instance_index_enters_only_the_phase_word(cfg1_table):
     oracle.gibbs(inst, cfg1_table, b, 1, seed=9, n_temps=2)
     assert np.array_equal(a.cost, b.cost) and np.array_equal(a.best_cost, b.best_cost)
     assert not np.array_equal(a.x, b.x)
+
+
+def test_fp32_nu_sequence_tracks_fp64_nu(cfg1_table):
+    """The oracle's FP32 nu (the solver's operation sequence, used where nu
+    decides a ranking) stays within the FP32 rounding bound of the FP64 EMA
+    of Sec. 4.4: each round adds at most ~4 roundings of a value <= 0.25 and
+    shrinks older errors by (1 - alpha)."""
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    T, alpha = 60, 0.05
+    st = oracle.init_chains(50, 64, seed=3)
+    oracle.gibbs(inst, cfg1_table, st, T, seed=3, n_temps=2, alpha=alpha)
+    bound = 4 * 2.0 ** -24 * 0.25 * min(T, 1 / alpha) + 0.25 * abs(np.float32(alpha) - alpha) * T
+    assert np.max(np.abs(st.nu32.astype(np.float64) - st.nu)) <= bound
+    assert st.nu32.dtype == np.float32 and np.all(st.nu32 <= 0.25) and np.all(st.nu32 >= 0)
+
+
+def _paper_up_cases():
+    out = []
+    with open(os.path.join(GOLDEN, "paper_examples.txt")) as f:
+        for line in f:
+            if line.startswith("up "):
+                left, right = line[3:].split("->")
+                xs, nus = left.split(" nu ")
+                out.append((np.array([int(c) for c in xs.strip()], np.uint8),
+                            np.array([float(v) for v in nus.split()], np.float32),
+                            np.array([int(c) for c in right.strip()], np.uint8)))
+    return out
+
+
+def test_unit_prop_paper_example():
+    """Sec. 4.4: with a = b = False held fixed, (a OR b OR c) AND (NOT c OR
+    NOT d) implies c = True, then d = False."""
+    inst = oracle.Instance.from_clauses(4, [[1, 2, 3], [-3, -4]])
+    cases = _paper_up_cases()
+    assert len(cases) == 3
+    for x, nu, want in cases:
+        assert np.array_equal(oracle.unit_prop(inst, x, nu)[0], want)
+
+
+def test_unit_prop_keeps_a_satisfying_assignment():
+    """If x satisfies every clause, every clause that becomes unit is satisfied
+    by x's value of its open literal, so propagation reproduces x."""
+    rng = np.random.default_rng(8)
+    n, m = 60, 240
+    sol = rng.integers(0, 2, n).astype(np.uint8)
+    cl = []
+    while len(cl) < m:
+        v = rng.choice(n, 3, replace=False)
+        s = rng.choice([-1, 1], 3)
+        lits = [int(s[k] * (v[k] + 1)) for k in range(3)]
+        if any((l > 0) == bool(sol[abs(l) - 1]) for l in lits):
+            cl.append(lits)
+    inst = oracle.Instance.from_clauses(n, cl)
+    assert oracle.evaluate(inst, sol[None])[0] == 0
+    nu = rng.random((16, n)).astype(np.float32)
+    out = oracle.unit_prop(inst, np.repeat(sol[None], 16, 0), nu)
+    assert np.all(out == sol[None])
+
+
+def test_unit_prop_follows_an_implication_chain():
+    """(v1) AND (NOT v1 OR v2) AND ... AND (NOT v9 OR v10), with v1..v10
+    ranked below the fixed half: the unit clause forces v1 and the chain
+    forces every later variable True, whatever x says."""
+    n = 20
+    cl = [[1]] + [[-k, k + 1] for k in range(1, 10)]
+    inst = oracle.Instance.from_clauses(n, cl)
+    nu = np.concatenate([np.zeros(10), np.ones(10)]).astype(np.float32)
+    x = np.zeros(n, np.uint8)
+    x[10:] = 1
+    out = oracle.unit_prop(inst, x, nu)[0]
+    assert np.all(out[:10] == 1) and np.all(out[10:] == 1)
+    # a conflicting fixed value stays fixed: v2 fixed False breaks the chain there
+    nu2 = nu.copy()
+    nu2[1] = 2.0
+    x2 = x.copy()
+    x2[1] = 0
+    out2 = oracle.unit_prop(inst, x2, nu2)[0]
+    assert out2[0] == 1 and out2[1] == 0
+
+
+def test_up_merge_keeps_the_lowest_costs():
+    """The B-of-2B merge keeps the B lowest-cost candidates, ordered as a
+    stable ascending sort of satisfied weight (ties: later candidates later)."""
+    inst = oracle.Instance.from_clauses(3, [[1], [2], [3]])
+    st = oracle.init_chains(3, 3, seed=1)
+    st.x = np.array([[1, 1, 0], [0, 0, 0], [1, 1, 1]], np.uint8)  # costs 1, 3, 0
+    up = np.array([[1, 0, 0], [0, 1, 1], [1, 1, 1]], np.uint8)     # costs 2, 1, 0
+    st.nu32 = np.arange(9, dtype=np.float32).reshape(3, 3)
+    st.nu = st.nu32.astype(np.float64)
+    oracle.up_merge(inst, st, up)
+    # stacked costs [1, 3, 0, 2, 1, 0]; ascending satisfied weight, stable:
+    # 3(1) 2(3) 1(0) 1(4) 0(2) 0(5) -> last three: candidates 4, 2, 5
+    assert np.array_equal(st.x, np.array([[0, 1, 1], [1, 1, 1], [1, 1, 1]], np.uint8))
+    assert np.array_equal(st.nu32, np.array([[3, 4, 5], [6, 7, 8], [6, 7, 8]], np.float32))
 
 
 def test_determinism_and_resume(cfg1_table):
