@@ -224,6 +224,27 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t restarts, uint64_t seed,
                      const uint8_t* x, const float* nu, const int64_t* best_cost,
                      const uint8_t* best_x, uint32_t t);
 
+/* Prioritized unit propagation with the B-of-2B merge (Sec. 4.4; the
+ * appendix code's send / fetch / merge). maxsat_up_begin copies the chains'
+ * states x and their nu to the host and starts unit propagation on host
+ * threads (it returns at once; maxsat_step may run meanwhile, as the paper
+ * keeps sampling while the host works). For each chain: variables ranked by
+ * nu, highest first (ties to the lower index); the top floor(n/2) keep their
+ * values; unit clauses are propagated first in, first out; the remaining
+ * variables, in rank order, take their values from x when still unassigned,
+ * each followed by propagation. maxsat_up_end waits for the results, scores
+ * the B current states and the B propagated ones (exact costs), and keeps
+ * the B with the lowest costs: sorted by satisfied weight ascending with a
+ * stable sort over [current states, propagated states], the last B become
+ * chains 0..B-1 in that order, each propagated state with the nu of the
+ * chain it came from. The best-so-far of each chain is kept. maxsat_up is
+ * begin + end. Single-formula contexts only (MAXSAT_EINVAL for a batch);
+ * MAXSAT_ESTATE without chains, for a second begin, for end without begin,
+ * or when the chains were reset in between. Synchronises. */
+int maxsat_up_begin(maxsat_ctx* ctx);
+int maxsat_up_end(maxsat_ctx* ctx);
+int maxsat_up(maxsat_ctx* ctx);
+
 /* Per-kernel timing. While profiling is on, maxsat_step and maxsat_score use
  * plain launches (no CUDA graph) and bracket every kernel launch with CUDA
  * events on the context's stream; maxsat_kernel_times then synchronises and

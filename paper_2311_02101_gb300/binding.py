@@ -69,6 +69,9 @@ def lib():
                                           ctypes.POINTER(maxsat_params), P]
         L.maxsat_get_n_instances.argtypes = [P]
         L.maxsat_get_clause_block.argtypes = [P]
+        L.maxsat_up_begin.argtypes = [P]
+        L.maxsat_up_end.argtypes = [P]
+        L.maxsat_up.argtypes = [P]
         L.maxsat_reset.argtypes = [P, i32, u64]
         L.maxsat_reset_shard.argtypes = [P, i32, u64, i32, i32]
         L.maxsat_step.argtypes = [P, i64]
@@ -87,7 +90,7 @@ def lib():
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
         for name in ["maxsat_create", "maxsat_create_batch", "maxsat_get_n_instances",
-                     "maxsat_get_clause_block",
+                     "maxsat_get_clause_block", "maxsat_up_begin", "maxsat_up_end", "maxsat_up",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
@@ -311,6 +314,18 @@ def maxsat_kernel_times(ctx: Context, max_kernels: int = 32):
     raw = names.raw
     return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (int(cnt[i]), float(ms[i]))
             for i in range(k)}
+
+
+def maxsat_up_begin(ctx: Context):
+    _check(lib().maxsat_up_begin(ctx.handle), ctx)
+
+
+def maxsat_up_end(ctx: Context):
+    _check(lib().maxsat_up_end(ctx.handle), ctx)
+
+
+def maxsat_up(ctx: Context):
+    _check(lib().maxsat_up(ctx.handle), ctx)
 
 
 def maxsat_get_path(ctx: Context) -> int:

@@ -17,6 +17,7 @@
 #include <string>
 #include <thread>
 #include <vector>
+#include <numeric>
 
 #include "internal.h"
 #include "philox.cuh"
@@ -79,6 +80,17 @@ struct maxsat_ctx {
   int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
   std::vector<int64_t> h_w;  // clause weights (host copy)
+  // unit-propagation heuristic (Sec. 4.4): host formula, worker, results
+  UpFormula upf;
+  std::thread up_worker;
+  bool up_pending = false;
+  int up_B = 0;
+  std::vector<uint8_t> up_x0, up_out;  // snapshot of the states, propagated states
+  std::vector<float> up_nu0;           // snapshot of nu (the ranking keys)
+  DevAllocs up_mem;                    // device candidates and their costs
+  uint8_t* d_up_cand = nullptr;
+  int64_t* d_up_cost = nullptr;
+  size_t up_cap = 0;
   int n_inst = 1;                      // formulas in the batch
   std::vector<int32_t> inst_var_base;  // n_inst + 1 first variable of each formula
   std::vector<int32_t> inst_cl_base;   // n_inst + 1 first clause of each formula
@@ -829,6 +841,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   for (int64_t c = 0; c <= m; ++c) cl_off[c] = (int32_t)off[c];
   for (int64_t c = 0; c < m; ++c) cl_w[c] = weights ? weights[c] : 1;
   ctx->h_w = cl_w;
+  up_prepare(n, m, off, lits, &ctx->upf);
   for (int64_t j = 0; j < nnz; ++j) {
     const int32_t l = lits[j];
     const int32_t v = (l > 0 ? l : -l) - 1;
@@ -1351,8 +1364,121 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t B, uint64_t seed, const uint8_t* x
   return MAXSAT_OK;
 }
 
+// Writes chain-major states x (B x n bytes) and nu (B x n floats) of chains
+// 0..B-1 into the device layout of the current path; the padding chains and
+// the best-so-far are untouched.
+static int put_states(maxsat_ctx* ctx, const uint8_t* x, const float* nu) {
+  const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->dense) {
+    const int np = ctx->n_pad;
+    uint8_t one, minus_one;
+    fp8_encode_int(1, ctx->e5m2, &one);
+    fp8_encode_int(-1, ctx->e5m2, &minus_one);
+    std::vector<uint8_t> hx((size_t)np * Bp);
+    std::vector<float> hn((size_t)np * Bp);
+    CK(ctx, cudaMemcpy(hx.data(), ctx->dX, hx.size(), cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(hn.data(), ctx->dnu, 4 * hn.size(), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < B; ++b)
+      for (int i = 0; i < n; ++i) {
+        hx[(size_t)b * np + i] = x[(size_t)b * n + i] ? one : minus_one;
+        hn[(size_t)b * np + i] = nu[(size_t)b * n + i];
+      }
+    CK(ctx, cudaMemcpy(ctx->dX, hx.data(), hx.size(), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->dnu, hn.data(), 4 * hn.size(), cudaMemcpyHostToDevice));
+    return MAXSAT_OK;
+  }
+  const size_t nB = (size_t)n * Bp;
+  std::vector<uint8_t> hx(nB);
+  std::vector<float> hn(nB);
+  CK(ctx, cudaMemcpy(hx.data(), ctx->C.xt, nB, cudaMemcpyDeviceToHost));
+  CK(ctx, cudaMemcpy(hn.data(), ctx->C.nu, 4 * nB, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < B; ++b)
+    for (int i = 0; i < n; ++i) {
+      hx[(size_t)i * Bp + b] = x[(size_t)b * n + i] ? 1 : 0;
+      hn[(size_t)i * Bp + b] = nu[(size_t)b * n + i];
+    }
+  CK(ctx, cudaMemcpy(ctx->C.xt, hx.data(), nB, cudaMemcpyHostToDevice));
+  CK(ctx, cudaMemcpy(ctx->C.nu, hn.data(), 4 * nB, cudaMemcpyHostToDevice));
+  return MAXSAT_OK;
+}
+
+int maxsat_up_begin(maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_begin before maxsat_reset");
+  if (ctx->n_inst != 1) return fail(ctx, MAXSAT_EINVAL, "unit propagation runs on single-formula contexts");
+  if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is already pending");
+  const int B = ctx->C.B, n = ctx->n;
+  ctx->up_x0.resize((size_t)B * n);
+  ctx->up_nu0.resize((size_t)B * n);
+  ctx->up_out.resize((size_t)B * n);
+  int rc = maxsat_get_state(ctx, ctx->up_x0.data(), ctx->up_nu0.data(), nullptr, nullptr, nullptr,
+                            nullptr, nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  ctx->up_B = B;
+  ctx->up_pending = true;
+  const int threads = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  ctx->up_worker = std::thread([ctx, B, threads]() {
+    up_chains(ctx->upf, B, ctx->up_x0.data(), ctx->up_nu0.data(), ctx->up_out.data(), threads);
+  });
+  return MAXSAT_OK;
+}
+
+int maxsat_up_end(maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_end without maxsat_up_begin");
+  if (ctx->up_worker.joinable()) ctx->up_worker.join();
+  ctx->up_pending = false;
+  const int B = ctx->up_B, n = ctx->n;
+  if (!ctx->have_chains || ctx->C.B != B)
+    return fail(ctx, MAXSAT_ESTATE, "the chains were reset during unit propagation");
+  // candidates: the B current states, then the B propagated ones
+  std::vector<uint8_t> cand((size_t)2 * B * n);
+  std::vector<float> nu((size_t)B * n);
+  int rc = maxsat_get_state(ctx, cand.data(), nu.data(), nullptr, nullptr, nullptr, nullptr,
+                            nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  std::memcpy(cand.data() + (size_t)B * n, ctx->up_out.data(), (size_t)B * n);
+  if (cand.size() > ctx->up_cap) {
+    ctx->up_mem.release();
+    ctx->up_cap = 0;
+    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cand, cand.size()));
+    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cost, (size_t)2 * B));
+    ctx->up_cap = cand.size();
+  }
+  CK(ctx, cudaMemcpyAsync(ctx->d_up_cand, cand.data(), cand.size(), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  rc = maxsat_eval(ctx, ctx->d_up_cand, 2 * B, ctx->d_up_cost);
+  if (rc != MAXSAT_OK) return rc;
+  std::vector<int64_t> cost((size_t)2 * B);
+  CK(ctx, cudaMemcpyAsync(cost.data(), ctx->d_up_cost, 8 * cost.size(), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  // the appendix code's merge: satisfied weight ascending (stable), keep the
+  // last B in that order; a propagated state keeps its chain's nu
+  std::vector<int32_t> rank((size_t)2 * B);
+  std::iota(rank.begin(), rank.end(), 0);
+  std::stable_sort(rank.begin(), rank.end(),
+                   [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<uint8_t> nx((size_t)B * n);
+  std::vector<float> nnu((size_t)B * n);
+  for (int j = 0; j < B; ++j) {
+    const int32_t r = rank[(size_t)B + j];
+    std::memcpy(nx.data() + (size_t)j * n, cand.data() + (size_t)r * n, (size_t)n);
+    std::memcpy(nnu.data() + (size_t)j * n, nu.data() + (size_t)(r % B) * n, 4 * (size_t)n);
+  }
+  return put_states(ctx, nx.data(), nnu.data());
+}
+
+int maxsat_up(maxsat_ctx* ctx) {
+  const int rc = maxsat_up_begin(ctx);
+  if (rc != MAXSAT_OK) return rc;
+  return maxsat_up_end(ctx);
+}
+
 void maxsat_destroy(maxsat_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->up_worker.joinable()) ctx->up_worker.join();
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   drain_marks(ctx);

@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
     const int ew = warp - 2 - kBld;  // 0 .. kEpi2 - 1
     const int cgrp = ew / 4;
     const uint32_t tround = step_index(a.tdev, a.t_rel);
-    const float keep = 1.0f - a.alpha;
+    // nu update with the sparse path's exact FP32 operation sequence
+    const float keep = __fsub_rn(1.0f, a.alpha);
     int li = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
       const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
@@ -638,11 +639,11 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
             const int z = __float2int_rn(__uint_as_float(r[sub * 8 + q]));
             const int qq = max(-T.qmax, min(T.qmax, z));
             const uint32_t P = pv[qq + T.qmax];
-            const float var = (float)(P * (65536u - P)) * 2.3283064365386963e-10f;
+            const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
             const size_t o = (size_t)b * a.n_pad + i;
             const uint8_t xold = a.X[o];
             if (C.improved[b]) a.best_x[o] = xold == a.one ? 1 : 0;
-            a.nu[o] = keep * a.nu[o] + a.alpha * var;
+            a.nu[o] = __fmaf_rn(keep, a.nu[o], __fmul_rn(a.alpha, var));
             a.X[o] = lane16(R, q) < P ? a.one : a.minus_one;
           }
         }

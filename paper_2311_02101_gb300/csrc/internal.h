@@ -123,6 +123,19 @@ struct HostTables {
   int32_t gq_absmax = 0;  // largest |2^Q G|
 };
 
+// up.cpp: prioritized unit propagation on the host (Sec. 4.4)
+struct UpFormula {
+  int32_t n = 0, m = 0;
+  std::vector<int64_t> cl_off;   // m + 1
+  std::vector<int32_t> lit;      // DIMACS literals
+  std::vector<int64_t> occ_off;  // n + 1
+  std::vector<int32_t> occ;      // per variable, clause order: clause | sign bit 31
+};
+void up_prepare(int32_t n, int64_t m, const int64_t* off, const int32_t* lits, UpFormula* F);
+// out (B x n) = unit propagation of every row of x (B x n) ranked by nu (B x n)
+void up_chains(const UpFormula& F, int32_t B, const uint8_t* x, const float* nu, uint8_t* out,
+               int threads);
+
 // fit.cpp
 int fit_or_rbm(int len, int nh, double fstar, int quant_bits, int iters, double* W,
                double* b);

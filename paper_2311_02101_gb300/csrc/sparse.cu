@@ -415,15 +415,17 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
                                kPhaseVisible | ((uint32_t)vi.x << 8)),
                     C.keys);
   float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-  const float keep = 1.0f - alpha;
+  // nu in FP32 with a fixed operation sequence (one rounding per step):
+  // var = fl(P (65536 - P)) 2^-32, nu = fma(1 - alpha, nu, fl(alpha var))
+  const float keep = __fsub_rn(1.0f, alpha);
   uint64_t xnew = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int qq = max(-T.qmax, min(T.qmax, z[q]));
     const uint32_t P = pv[qq + T.qmax];
     // rho (1 - rho) with rho = P / 65536: P (65536 - P) <= 2^30, scaled by 2^-32
-    const float var = (float)(P * (65536u - P)) * 2.3283064365386963e-10f;
-    nu[q] = keep * nu[q] + alpha * var;
+    const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
+    nu[q] = __fmaf_rn(keep, nu[q], __fmul_rn(alpha, var));
     xnew |= (uint64_t)(lane16(r, q) < P) << (8 * q);
   }
   nu4[0] = make_float4(nu[0], nu[1], nu[2], nu[3]);

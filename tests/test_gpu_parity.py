@@ -98,6 +98,8 @@ def assert_same(gpu, ora, T, alpha, rows=None):
     assert np.array_equal(g["cost"], ora.cost), "costs"
     np.testing.assert_allclose(g["free_energy"], ora.free_energy, rtol=1e-3, atol=1e-6)
     assert np.max(np.abs(g["nu"] - ora.nu)) <= nu_tol(T, alpha)
+    # the FP32 operation sequence of nu is reproduced exactly
+    assert np.array_equal(g["nu"], ora.nu32), "nu (FP32 sequence)"
 
 
 def edge_instance(seed=0):
@@ -456,6 +458,7 @@ def test_batch_trajectories_match_oracle(ms, stream, golden_table, B):
         assert np.array_equal(g["cost"][k], st.cost), k
         np.testing.assert_allclose(g["free_energy"][k], st.free_energy, rtol=1e-3, atol=1e-6)
         assert np.max(np.abs(g["nu"][:, sl] - st.nu)) <= nu_tol(T, 0.01)
+        assert np.array_equal(g["nu"][:, sl], st.nu32), k
     ms.maxsat_destroy(ctx)
 
 
@@ -524,3 +527,52 @@ def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
     gpu = ms.maxsat_get_state(ctx)
     ms.maxsat_destroy(ctx)
     assert_same(gpu, run_oracle(inst, golden_table, B, T, seed, n_buckets=4), T, 0.01)
+
+
+# --------------------------------------------------------------------------
+# Unit-propagation heuristic (maxsat_up_begin / maxsat_up_end, Sec. 4.4)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("path", [2, 1])
+def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path):
+    """reset, T1 rounds, send for propagation, upw rounds while the host
+    works, fetch + B-of-2B merge, T2 rounds: the oracle's same sequence
+    (its FP32 nu ranks the variables) gives the same chains bit for bit."""
+    inst = inst_of(workloads.weighted_3sat(300, 1500, 1000, seed=4))
+    B, T1, upw, T2, seed = 256, 6, 3, 5, 13
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=path, spg=2)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, T1)
+    ms.maxsat_up_begin(ctx)
+    ms.maxsat_step(ctx, upw)
+    ms.maxsat_up_end(ctx)
+    ms.maxsat_step(ctx, T2)
+    gpu = ms.maxsat_get_state(ctx)
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_up_end(ctx)
+    assert e.value.code == ms.MAXSAT_ESTATE
+    ms.maxsat_destroy(ctx)
+
+    st = oracle.init_chains(inst.n, B, seed)
+    kw = dict(n_temps=2, n_buckets=4, threads=os.cpu_count() or 4)
+    oracle.gibbs(inst, golden_table, st, T1, seed, **kw)
+    up_x = oracle.unit_prop(inst, st.x, st.nu32)
+    oracle.gibbs(inst, golden_table, st, upw, seed, **kw)
+    before = evaluate_min(inst, st.x)
+    oracle.up_merge(inst, st, up_x)
+    assert evaluate_min(inst, st.x) <= before
+    oracle.gibbs(inst, golden_table, st, T2, seed, **kw)
+    assert_same(gpu, st, T1 + upw + T2, 0.01)
+
+
+def evaluate_min(inst, x):
+    return int(oracle.evaluate(inst, x).min())
+
+
+def test_unit_propagation_rejects_batches_and_misuse(ms, stream, golden_table):
+    insts = small_batch()
+    ctx = batch_ctx(ms, stream, insts, golden_table)
+    ms.maxsat_reset(ctx, 64, 1)
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_up(ctx)
+    assert e.value.code == ms.MAXSAT_EINVAL
+    ms.maxsat_destroy(ctx)
