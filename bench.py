@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--path", default="auto", choices=["auto", "sparse", "dense"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--no-up", action="store_true",
+                    help="skip the unit-propagation ablation probe")
     ap.add_argument("--no-ragged", action="store_true",
                     help="skip the batched ragged-instance probe (512 formulas)")
     ap.add_argument("--fixed-seconds", type=float, default=3.0,
@@ -361,6 +363,7 @@ def run_mine(args):
     fp32 = fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args,
                            ms_total / args.steps) if not args.no_fp32 else None
     ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
+    up = up_probe(ms, torch, n, off, lits, w, B, stream, sets, args) if not args.no_up else None
 
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
@@ -379,7 +382,7 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32, ragged=ragged)
+                fp32_form=fp32, ragged=ragged, unit_prop=up)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -515,6 +518,42 @@ def fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args, our
                 fixed_time_s=budget, rounds_fp32=rounds_fp32, rounds_ours=rounds_ours,
                 best_cost_fp32=best_fp32, best_cost_ours=best_ours,
                 note="FP32 torch matmuls (TF32 off) + lookups, torch generator draws")
+
+
+def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20):
+    """The paper's unit-propagation ablation at equal wall time (Sec. 4.4,
+    Table "RbmSAT - UP"): Gibbs alone vs Gibbs with a unit-propagation round
+    sent every `upp` rounds and merged `upw` rounds later (the host works
+    while the GPU samples). Same seed, same seconds; lowest best cost over
+    all chains. Also the host time of one propagation round."""
+    secs = args.fixed_seconds
+    p = ms.maxsat_default_params(sets=sets)
+    out = dict(upp=upp, upw=upw, seconds=secs, chains=B)
+    for mode in ("gibbs", "gibbs+up"):
+        ctx = ms.maxsat_create(n, off, lits, w, p, stream)
+        ms.maxsat_reset(ctx, B, 99)
+        rounds, ups, t_up = 0, 0, 0.0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < secs:
+            if mode == "gibbs+up":
+                ms.maxsat_step(ctx, upp - upw)
+                ta = time.perf_counter()
+                ms.maxsat_up_begin(ctx)
+                ms.maxsat_step(ctx, upw)
+                ms.maxsat_up_end(ctx)
+                t_up += time.perf_counter() - ta
+                ups += 1
+            else:
+                ms.maxsat_step(ctx, upp)
+            rounds += upp
+        ms.maxsat_score(ctx)
+        st = ms.maxsat_get_state(ctx)
+        ms.maxsat_destroy(ctx)
+        out[mode] = dict(rounds=rounds, best_cost=int(st["best_cost"].min()))
+        if ups:
+            out[mode]["up_rounds"] = ups
+            out[mode]["ms_per_up_round"] = 1e3 * t_up / ups
+    return out
 
 
 def ragged_probe(ms, torch, stream, sets, args):
