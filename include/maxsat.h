@@ -245,6 +245,59 @@ int maxsat_up_begin(maxsat_ctx* ctx);
 int maxsat_up_end(maxsat_ctx* ctx);
 int maxsat_up(maxsat_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Learned proposal: a message-passing network over the variable-clause
+ * incidence that predicts p(x_v = 1) from the formula alone, trained on the
+ * solver's own best assignments, and used as the distribution of the chains'
+ * initial states (the paper names learned initial assignments as
+ * complementary to RbmSAT, Sec. 2). With hidden size 64 and L layers:
+ *   f_v = [pos_v / deg_v - 1/2, log(1 + deg_v) / 4, 1]
+ *   g_c = [log(w_c) / 8, len_c / 4, 1]
+ *   h_v^0 = relu(Wf f_v), h_c^0 = relu(Wg g_c)
+ *   layer l: m_c = mean over c's literals of s h_v^{l-1};
+ *            h_c^l = relu(Wc_l [m_c ; h_c^{l-1}] + bc_l);
+ *            a_v = mean over v's occurrences of s h_c^l;
+ *            h_v^l = relu(Wv_l [a_v ; h_v^{l-1}] + bv_l)
+ *   z_v = wo . h_v^L + bo, p_v = sigmoid(z_v); loss = mean BCE(z_v, y_v)
+ * (s = +1 / -1 for a plain / negated literal). The flat FP32 parameter
+ * vector holds, in order: Wf (64 x 3), Wg (64 x 3), then per layer Wc (64 x
+ * 128), bc (64), Wv (64 x 128), bv (64), then wo (64), bo (1), matrices
+ * row-major. Weight matrices are used in BF16 (round to nearest even of the
+ * FP32 master); activations and sums are FP32. Work runs on the stream of
+ * the formula context passed in. */
+typedef struct maxsat_mp maxsat_mp;
+
+/* New network with L layers (1..8), He-normal weights from `seed`, zero
+ * biases, Adam moments zero. MAXSAT_ENODEV without a device. */
+int maxsat_mp_create(maxsat_mp** out, int32_t n_layers, uint64_t seed);
+/* Number of parameters (the flat vector's length). */
+int maxsat_mp_n_params(const maxsat_mp* mp);
+/* Replaces the parameters (host FP32 vector) and clears the Adam state. */
+int maxsat_mp_set_params(maxsat_mp* mp, const float* theta);
+/* Copies the parameters and / or the last gradient to host buffers (NULL to
+ * skip). Synchronises. */
+int maxsat_mp_get_params(maxsat_mp* mp, float* theta, float* grad);
+/* p_v for every variable of ctx's formula (a batch: every formula at once)
+ * into prob_dev (n device floats). Asynchronous on ctx's stream. */
+int maxsat_mp_forward(maxsat_mp* mp, maxsat_ctx* ctx, float* prob_dev);
+/* Forward and backward against labels (n device bytes, 0 / 1): the
+ * gradient of the mean binary cross entropy is kept for maxsat_mp_adam;
+ * *loss (may be NULL) receives the loss (synchronises when given). */
+int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev,
+                       double* loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with the last
+ * gradient, then the BF16 weights are refreshed. */
+int maxsat_mp_adam(maxsat_mp* mp, maxsat_ctx* ctx, float lr);
+const char* maxsat_mp_last_error(const maxsat_mp* mp);
+void maxsat_mp_destroy(maxsat_mp* mp);
+
+/* maxsat_reset, except that variable v of every chain starts True with
+ * probability prob[v] (n host floats in [0, 1]): x = [u < P_v], P_v =
+ * rint(65536 prob[v]) in FP64, u the same 16-bit initial draw as
+ * maxsat_reset (prob = 1/2 everywhere gives exactly maxsat_reset's states).
+ * Synchronises. */
+int maxsat_reset_probs(maxsat_ctx* ctx, int32_t restarts, uint64_t seed, const float* prob);
+
 /* Per-kernel timing. While profiling is on, maxsat_step and maxsat_score use
  * plain launches (no CUDA graph) and bracket every kernel launch with CUDA
  * events on the context's stream; maxsat_kernel_times then synchronises and

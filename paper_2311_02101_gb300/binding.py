@@ -69,6 +69,18 @@ def lib():
                                           ctypes.POINTER(maxsat_params), P]
         L.maxsat_get_n_instances.argtypes = [P]
         L.maxsat_get_clause_block.argtypes = [P]
+        L.maxsat_mp_create.argtypes = [ctypes.POINTER(P), i32, u64]
+        L.maxsat_mp_n_params.argtypes = [P]
+        L.maxsat_mp_set_params.argtypes = [P, P]
+        L.maxsat_mp_get_params.argtypes = [P, P, P]
+        L.maxsat_mp_forward.argtypes = [P, P, P]
+        L.maxsat_mp_gradient.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double)]
+        L.maxsat_mp_adam.argtypes = [P, P, ctypes.c_float]
+        L.maxsat_mp_last_error.argtypes = [P]
+        L.maxsat_mp_last_error.restype = ctypes.c_char_p
+        L.maxsat_mp_destroy.argtypes = [P]
+        L.maxsat_mp_destroy.restype = None
+        L.maxsat_reset_probs.argtypes = [P, i32, u64, P]
         L.maxsat_up_begin.argtypes = [P]
         L.maxsat_up_end.argtypes = [P]
         L.maxsat_up.argtypes = [P]
@@ -91,6 +103,9 @@ def lib():
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
         for name in ["maxsat_create", "maxsat_create_batch", "maxsat_get_n_instances",
                      "maxsat_get_clause_block", "maxsat_up_begin", "maxsat_up_end", "maxsat_up",
+                     "maxsat_mp_create", "maxsat_mp_n_params", "maxsat_mp_set_params",
+                     "maxsat_mp_get_params", "maxsat_mp_forward", "maxsat_mp_gradient",
+                     "maxsat_mp_adam", "maxsat_reset_probs",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
@@ -326,6 +341,83 @@ def maxsat_up_end(ctx: Context):
 
 def maxsat_up(ctx: Context):
     _check(lib().maxsat_up(ctx.handle), ctx)
+
+
+class Model:
+    """Handle of a learned-proposal network (the C maxsat_mp*)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            maxsat_mp_destroy(self)
+        except Exception:
+            pass
+
+
+def _check_mp(rc, mp=None):
+    if rc != MAXSAT_OK:
+        h = None if mp is None else mp.handle
+        raise MaxsatError(rc, lib().maxsat_mp_last_error(h).decode())
+    return rc
+
+
+def maxsat_mp_create(n_layers: int = 3, seed: int = 0) -> Model:
+    h = ctypes.c_void_p()
+    _check_mp(lib().maxsat_mp_create(ctypes.byref(h), int(n_layers), int(seed) & (2 ** 64 - 1)))
+    return Model(h.value)
+
+
+def maxsat_mp_n_params(mp: Model) -> int:
+    return int(lib().maxsat_mp_n_params(mp.handle))
+
+
+def maxsat_mp_set_params(mp: Model, theta):
+    theta = np.ascontiguousarray(theta, np.float32)
+    assert theta.size == maxsat_mp_n_params(mp)
+    _check_mp(lib().maxsat_mp_set_params(mp.handle, _np_ptr(theta)), mp)
+
+
+def maxsat_mp_get_params(mp: Model):
+    """(parameters, last gradient) as FP32 host vectors."""
+    k = maxsat_mp_n_params(mp)
+    theta, grad = np.zeros(k, np.float32), np.zeros(k, np.float32)
+    _check_mp(lib().maxsat_mp_get_params(mp.handle, _np_ptr(theta), _np_ptr(grad)), mp)
+    return theta, grad
+
+
+def maxsat_mp_forward(mp: Model, ctx: Context, prob_dev):
+    """prob_dev: torch float32 CUDA tensor of ctx.n elements."""
+    assert prob_dev.is_cuda and prob_dev.numel() >= ctx.n
+    _check_mp(lib().maxsat_mp_forward(mp.handle, ctx.handle, prob_dev.data_ptr()), mp)
+
+
+def maxsat_mp_gradient(mp: Model, ctx: Context, labels_dev) -> float:
+    """labels_dev: torch uint8 CUDA tensor (0 / 1) of ctx.n elements."""
+    assert labels_dev.is_cuda and labels_dev.numel() >= ctx.n
+    loss = ctypes.c_double()
+    _check_mp(lib().maxsat_mp_gradient(mp.handle, ctx.handle, labels_dev.data_ptr(),
+                                       ctypes.byref(loss)), mp)
+    return float(loss.value)
+
+
+def maxsat_mp_adam(mp: Model, ctx: Context, lr: float):
+    _check_mp(lib().maxsat_mp_adam(mp.handle, ctx.handle, float(lr)), mp)
+
+
+def maxsat_mp_destroy(mp: Model):
+    if mp is not None and mp.handle:
+        lib().maxsat_mp_destroy(mp.handle)
+        mp.handle = None
+
+
+def maxsat_reset_probs(ctx: Context, restarts: int, seed: int, prob):
+    prob = np.ascontiguousarray(prob, np.float32)
+    assert prob.size == ctx.n
+    _check(lib().maxsat_reset_probs(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1),
+                                    _np_ptr(prob)), ctx)
+    ctx.B = int(restarts)
 
 
 def maxsat_get_path(ctx: Context) -> int:

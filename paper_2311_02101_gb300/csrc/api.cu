@@ -8,6 +8,8 @@
 // launched on the caller's stream, optionally replayed from a CUDA graph of
 // `steps_per_graph` rounds (the paper dispatches 500 rounds at a time,
 // appendix "Batching operations").
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -1481,6 +1483,279 @@ int maxsat_up(maxsat_ctx* ctx) {
   const int rc = maxsat_up_begin(ctx);
   if (rc != MAXSAT_OK) return rc;
   return maxsat_up_end(ctx);
+}
+
+// ------------------------------------------------------ learned proposal
+struct maxsat_mp {
+  MpLayout lay;
+  DevAllocs mem;  // parameters, gradients, Adam moments
+  float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+  __nv_bfloat16* Pb = nullptr;
+  int step = 0;
+  // activations and backward buffers for graphs up to (cap_n, cap_m)
+  DevAllocs act;
+  int cap_n = 0, cap_m = 0;
+  float *f = nullptr, *g = nullptr, *inv_len = nullptr, *inv_deg = nullptr;
+  float* hv[kMpMaxLayers + 1] = {};
+  float* hc[kMpMaxLayers + 1] = {};
+  float* mc[kMpMaxLayers] = {};
+  float* av[kMpMaxLayers] = {};
+  float *dz = nullptr, *dhv = nullptr, *dhv2 = nullptr, *dav = nullptr, *dhc = nullptr,
+        *dhc2 = nullptr, *dmc = nullptr, *part = nullptr;
+  double* loss_part = nullptr;
+  std::string err;
+};
+
+namespace {
+int mp_fail(maxsat_mp* mp, int code, const std::string& msg) {
+  if (mp) mp->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+#define MPCK(mp, expr)                                                         \
+  do {                                                                          \
+    cudaError_t e_ = (expr);                                                    \
+    if (e_ != cudaSuccess) return mp_fail(mp, MAXSAT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// splitmix64 + Box-Muller: a deterministic normal stream for the initial weights
+struct NormalStream {
+  uint64_t s;
+  double spare = 0.0;
+  bool have = false;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double normal() {
+    if (have) {
+      have = false;
+      return spare;
+    }
+    const double u1 = uniform(), u2 = uniform();
+    const double r = std::sqrt(-2.0 * std::log(u1));
+    spare = r * std::sin(6.283185307179586 * u2);
+    have = true;
+    return r * std::cos(6.283185307179586 * u2);
+  }
+};
+
+int mp_reserve(maxsat_mp* mp, int n, int m) {
+  if (n <= mp->cap_n && m <= mp->cap_m) return MAXSAT_OK;
+  mp->act.release();
+  mp->cap_n = mp->cap_m = 0;
+  const int L = mp->lay.L;
+  const size_t nH = (size_t)std::max(n, 1) * kMpHidden, mH = (size_t)std::max(m, 1) * kMpHidden;
+  DevAllocs& A = mp->act;
+  MPCK(mp, A.alloc(&mp->f, 3 * (size_t)std::max(n, 1)));
+  MPCK(mp, A.alloc(&mp->g, 3 * (size_t)std::max(m, 1)));
+  MPCK(mp, A.alloc(&mp->inv_len, (size_t)std::max(m, 1)));
+  MPCK(mp, A.alloc(&mp->inv_deg, (size_t)std::max(n, 1)));
+  for (int l = 0; l <= L; ++l) {
+    MPCK(mp, A.alloc(&mp->hv[l], nH));
+    MPCK(mp, A.alloc(&mp->hc[l], mH));
+  }
+  for (int l = 0; l < L; ++l) {
+    MPCK(mp, A.alloc(&mp->mc[l], mH));
+    MPCK(mp, A.alloc(&mp->av[l], nH));
+  }
+  MPCK(mp, A.alloc(&mp->dz, (size_t)std::max(n, 1)));
+  MPCK(mp, A.alloc(&mp->dhv, nH));
+  MPCK(mp, A.alloc(&mp->dhv2, nH));
+  MPCK(mp, A.alloc(&mp->dav, nH));
+  MPCK(mp, A.alloc(&mp->dhc, mH));
+  MPCK(mp, A.alloc(&mp->dhc2, mH));
+  MPCK(mp, A.alloc(&mp->dmc, mH));
+  const size_t rows = (size_t)std::max(n, m);
+  MPCK(mp, A.alloc(&mp->part, ((rows + 255) / 256) * (kMpHidden * 2 * kMpHidden + kMpHidden)));
+  MPCK(mp, A.alloc(&mp->loss_part, (size_t)std::max(n, 1) / 8 + 1));
+  mp->cap_n = n;
+  mp->cap_m = m;
+  return MAXSAT_OK;
+}
+
+// forward pass over the formula of ctx; with labels, dz and the loss partials
+int mp_forward(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* y, float* prob) {
+  const DevFormula& F = ctx->F;
+  const int n = F.n, m = F.m, L = mp->lay.L;
+  cudaStream_t st = ctx->stream;
+  int rc = mp_reserve(mp, n, m);
+  if (rc != MAXSAT_OK) return rc;
+  const MpLayout& Y = mp->lay;
+  MPCK(mp, mp_launch_features(F, mp->f, mp->g, mp->inv_len, mp->inv_deg, st));
+  MPCK(mp, mp_launch_proj(mp->f, n, mp->Pb + Y.Wf, mp->hv[0], st));
+  MPCK(mp, mp_launch_proj(mp->g, m, mp->Pb + Y.Wg, mp->hc[0], st));
+  for (int l = 0; l < L; ++l) {
+    MPCK(mp, mp_launch_clause_agg(F, mp->hv[l], mp->inv_len, nullptr, mp->mc[l], false, st));
+    MPCK(mp, mp_launch_dense_fwd(mp->mc[l], mp->hc[l], m, mp->Pb + Y.Wc[l], mp->P + Y.bc[l],
+                                 mp->hc[l + 1], st));
+    MPCK(mp, mp_launch_var_agg(F, mp->hc[l + 1], nullptr, mp->inv_deg, mp->av[l], false, st));
+    MPCK(mp, mp_launch_dense_fwd(mp->av[l], mp->hv[l], n, mp->Pb + Y.Wv[l], mp->P + Y.bv[l],
+                                 mp->hv[l + 1], st));
+  }
+  MPCK(mp, mp_launch_out(mp->hv[L], n, mp->P + Y.wo, mp->P + Y.bo, y, prob, y ? mp->dz : nullptr,
+                         y ? mp->loss_part : nullptr, st));
+  return MAXSAT_OK;
+}
+}  // namespace
+
+int maxsat_mp_create(maxsat_mp** out, int32_t n_layers, uint64_t seed) {
+  g_create_error.clear();
+  if (!out) return mp_fail(nullptr, MAXSAT_EINVAL, "out is NULL");
+  *out = nullptr;
+  MpLayout lay;
+  if (mp_layout(n_layers, &lay) != 0) return mp_fail(nullptr, MAXSAT_EINVAL, "n_layers must be in 1..8");
+  int rc = check_device(nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  maxsat_mp* mp = new maxsat_mp();
+  mp->lay = lay;
+  const int T = lay.total;
+  // He-normal weight matrices (std sqrt(2 / fan_in)), read-out sqrt(1 / 64), zero biases
+  std::vector<float> h((size_t)T, 0.f);
+  NormalStream R{seed};
+  auto fill = [&](int off, int rows, int cols, double sd) {
+    for (int e = 0; e < rows * cols; ++e) h[(size_t)off + e] = (float)(sd * R.normal());
+  };
+  fill(lay.Wf, kMpHidden, 3, std::sqrt(2.0 / 3));
+  fill(lay.Wg, kMpHidden, 3, std::sqrt(2.0 / 3));
+  for (int l = 0; l < n_layers; ++l) {
+    fill(lay.Wc[l], kMpHidden, 2 * kMpHidden, std::sqrt(2.0 / (2 * kMpHidden)));
+    fill(lay.Wv[l], kMpHidden, 2 * kMpHidden, std::sqrt(2.0 / (2 * kMpHidden)));
+  }
+  fill(lay.wo, 1, kMpHidden, std::sqrt(1.0 / kMpHidden));
+  DevAllocs& A = mp->mem;
+  cudaError_t e = A.alloc(&mp->P, T);
+  if (e == cudaSuccess) e = A.alloc(&mp->G, T);
+  if (e == cudaSuccess) e = A.alloc(&mp->M, T);
+  if (e == cudaSuccess) e = A.alloc(&mp->V, T);
+  if (e == cudaSuccess) e = A.alloc(&mp->Pb, T);
+  if (e == cudaSuccess) e = cudaMemcpy(mp->P, h.data(), 4 * (size_t)T, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(mp->G, 0, 4 * (size_t)T);
+  if (e == cudaSuccess) e = cudaMemset(mp->M, 0, 4 * (size_t)T);
+  if (e == cudaSuccess) e = cudaMemset(mp->V, 0, 4 * (size_t)T);
+  if (e == cudaSuccess) e = mp_launch_to_bf16(mp->P, mp->Pb, T, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete mp;
+    return mp_fail(nullptr, MAXSAT_ECUDA, std::string("mp create: ") + cudaGetErrorString(e));
+  }
+  *out = mp;
+  return MAXSAT_OK;
+}
+
+int maxsat_mp_n_params(const maxsat_mp* mp) { return mp ? mp->lay.total : MAXSAT_EINVAL; }
+
+int maxsat_mp_set_params(maxsat_mp* mp, const float* theta) {
+  if (!mp || !theta) return MAXSAT_EINVAL;
+  MPCK(mp, cudaMemcpy(mp->P, theta, 4 * (size_t)mp->lay.total, cudaMemcpyHostToDevice));
+  MPCK(mp, mp_launch_to_bf16(mp->P, mp->Pb, mp->lay.total, nullptr));
+  MPCK(mp, cudaMemset(mp->M, 0, 4 * (size_t)mp->lay.total));
+  MPCK(mp, cudaMemset(mp->V, 0, 4 * (size_t)mp->lay.total));
+  mp->step = 0;
+  MPCK(mp, cudaDeviceSynchronize());
+  return MAXSAT_OK;
+}
+
+int maxsat_mp_get_params(maxsat_mp* mp, float* theta, float* grad) {
+  if (!mp) return MAXSAT_EINVAL;
+  MPCK(mp, cudaDeviceSynchronize());
+  if (theta) MPCK(mp, cudaMemcpy(theta, mp->P, 4 * (size_t)mp->lay.total, cudaMemcpyDeviceToHost));
+  if (grad) MPCK(mp, cudaMemcpy(grad, mp->G, 4 * (size_t)mp->lay.total, cudaMemcpyDeviceToHost));
+  return MAXSAT_OK;
+}
+
+int maxsat_mp_forward(maxsat_mp* mp, maxsat_ctx* ctx, float* prob_dev) {
+  if (!mp || !ctx || !prob_dev) return MAXSAT_EINVAL;
+  return mp_forward(mp, ctx, nullptr, prob_dev);
+}
+
+int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev, double* loss) {
+  if (!mp || !ctx || !labels_dev) return MAXSAT_EINVAL;
+  int rc = mp_forward(mp, ctx, labels_dev, nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  const DevFormula& F = ctx->F;
+  const int n = F.n, m = F.m, L = mp->lay.L;
+  const MpLayout& Y = mp->lay;
+  cudaStream_t st = ctx->stream;
+  float* G = mp->G;
+  MPCK(mp, mp_launch_out_bwd(mp->hv[L], mp->dz, n, mp->P + Y.wo, mp->dhv, mp->part, G + Y.wo, st));
+  bool carry = false;  // dhc holds the gradient of h_c^l from clause layer l + 1
+  for (int l = L - 1; l >= 0; --l) {
+    // variable layer l: h_v^{l+1} = relu(Wv_l [a_v ; h_v^l] + bv_l)
+    MPCK(mp, mp_launch_dense_bwd(mp->dhv, mp->hv[l + 1], mp->av[l], mp->hv[l], n,
+                                 mp->Pb + Y.Wv[l], mp->dav, mp->dhv2, mp->part, G + Y.Wv[l], st));
+    // a_v = (1 / deg_v) sum s h_c^{l+1}: gradient of h_c^{l+1}
+    MPCK(mp, mp_launch_clause_agg(F, mp->dav, nullptr, mp->inv_deg, mp->dhc, carry, st));
+    // clause layer l: h_c^{l+1} = relu(Wc_l [m_c ; h_c^l] + bc_l)
+    MPCK(mp, mp_launch_dense_bwd(mp->dhc, mp->hc[l + 1], mp->mc[l], mp->hc[l], m,
+                                 mp->Pb + Y.Wc[l], mp->dmc, mp->dhc2, mp->part, G + Y.Wc[l], st));
+    // m_c = (1 / len_c) sum s h_v^l: gradient of h_v^l
+    MPCK(mp, mp_launch_var_agg(F, mp->dmc, mp->inv_len, nullptr, mp->dhv2, true, st));
+    std::swap(mp->dhv, mp->dhv2);
+    std::swap(mp->dhc, mp->dhc2);
+    carry = true;
+  }
+  MPCK(mp, mp_launch_proj_bwd(mp->dhv, mp->hv[0], mp->f, n, mp->part, G + Y.Wf, st));
+  MPCK(mp, mp_launch_proj_bwd(mp->dhc, mp->hc[0], mp->g, m, mp->part, G + Y.Wg, st));
+  if (loss) {
+    const int nb = (n + 7) / 8;
+    std::vector<double> lp((size_t)nb);
+    MPCK(mp, cudaMemcpyAsync(lp.data(), mp->loss_part, 8 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+    MPCK(mp, cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double v : lp) s += v;
+    *loss = s / std::max(n, 1);
+  }
+  return MAXSAT_OK;
+}
+
+int maxsat_mp_adam(maxsat_mp* mp, maxsat_ctx* ctx, float lr) {
+  if (!mp || !ctx || !(lr > 0.f)) return MAXSAT_EINVAL;
+  mp->step += 1;
+  MPCK(mp, mp_launch_adam(mp->P, mp->G, mp->M, mp->V, mp->lay.total, lr, 0.9f, 0.999f, 1e-8f,
+                          mp->step, mp->Pb, ctx->stream));
+  return MAXSAT_OK;
+}
+
+const char* maxsat_mp_last_error(const maxsat_mp* mp) {
+  return mp ? mp->err.c_str() : g_create_error.c_str();
+}
+
+void maxsat_mp_destroy(maxsat_mp* mp) {
+  if (!mp) return;
+  cudaDeviceSynchronize();
+  delete mp;
+}
+
+int maxsat_reset_probs(maxsat_ctx* ctx, int32_t B, uint64_t seed, const float* prob) {
+  if (!ctx || !prob) return MAXSAT_EINVAL;
+  const int n = ctx->n;
+  std::vector<uint32_t> P((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const double p = prob[i];
+    if (!(p >= 0.0 && p <= 1.0)) return fail(ctx, MAXSAT_EINVAL, "probabilities must be in [0, 1]");
+    P[i] = (uint32_t)std::nearbyint(p * 65536.0);
+  }
+  int rc = maxsat_reset(ctx, B, seed);
+  if (rc != MAXSAT_OK) return rc;
+  DevAllocs tmp;  // freed on return, after the synchronisation below
+  uint32_t* dP = nullptr;
+  CK(ctx, tmp.alloc(&dP, (size_t)n));
+  CK(ctx, cudaMemcpyAsync(dP, P.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->dense) {
+    uint8_t one, minus_one;
+    fp8_encode_int(1, ctx->e5m2, &one);
+    fp8_encode_int(-1, ctx->e5m2, &minus_one);
+    CK(ctx, launch_init_probs_dense(n, ctx->n_pad, ctx->C, dP, ctx->dX, ctx->dbest_x, one,
+                                    minus_one, ctx->stream));
+  } else {
+    CK(ctx, launch_init_probs_sparse(ctx->F, ctx->C, dP, ctx->stream));
+  }
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MAXSAT_OK;
 }
 
 void maxsat_destroy(maxsat_ctx* ctx) {

@@ -136,6 +136,48 @@ void up_prepare(int32_t n, int64_t m, const int64_t* off, const int32_t* lits, U
 void up_chains(const UpFormula& F, int32_t B, const uint8_t* x, const float* nu, uint8_t* out,
                int threads);
 
+// mp.cu: the learned proposal's kernels (message passing, hidden size 64)
+constexpr int kMpHidden = 64;
+constexpr int kMpMaxLayers = 8;
+struct MpLayout {  // offsets into the flat FP32 parameter vector
+  int L = 0, Wf = 0, Wg = 0, Wc[kMpMaxLayers] = {}, bc[kMpMaxLayers] = {},
+      Wv[kMpMaxLayers] = {}, bv[kMpMaxLayers] = {}, wo = 0, bo = 0, total = 0;
+};
+int mp_layout(int L, MpLayout* out);
+}  // namespace rbmsat
+#include <cuda_bf16.h>
+namespace rbmsat {
+cudaError_t mp_launch_features(const DevFormula& F, float* f, float* g, float* inv_len,
+                               float* inv_deg, cudaStream_t st);
+cudaError_t mp_launch_proj(const float* in, int rows, const __nv_bfloat16* W, float* out,
+                           cudaStream_t st);
+cudaError_t mp_launch_clause_agg(const DevFormula& F, const float* h, const float* cscale,
+                                 const float* vscale, float* out, bool acc, cudaStream_t st);
+cudaError_t mp_launch_var_agg(const DevFormula& F, const float* h, const float* cscale,
+                              const float* vscale, float* out, bool acc, cudaStream_t st);
+cudaError_t mp_launch_dense_fwd(const float* A, const float* Bm, int rows, const __nv_bfloat16* W,
+                                const float* b, float* out, cudaStream_t st);
+// gW receives 64 x 128 weight gradients followed by the 64 bias gradients
+cudaError_t mp_launch_dense_bwd(const float* dout, const float* out, const float* A,
+                                const float* Bm, int rows, const __nv_bfloat16* W, float* dA,
+                                float* dB, float* part, float* gW, cudaStream_t st);
+cudaError_t mp_launch_proj_bwd(const float* dout, const float* out, const float* in, int rows,
+                               float* part, float* gW, cudaStream_t st);
+cudaError_t mp_launch_out(const float* h, int n, const float* wo, const float* bo,
+                          const uint8_t* y, float* prob, float* dz, double* loss_part,
+                          cudaStream_t st);
+cudaError_t mp_launch_out_bwd(const float* h, const float* dz, int n, const float* wo, float* dh,
+                              float* part, float* g_wo, cudaStream_t st);
+cudaError_t mp_launch_adam(float* P, const float* G, float* M, float* V, int count, float lr,
+                           float b1, float b2, float eps, int step, __nv_bfloat16* Pb,
+                           cudaStream_t st);
+cudaError_t mp_launch_to_bf16(const float* P, __nv_bfloat16* Pb, int count, cudaStream_t st);
+cudaError_t launch_init_probs_sparse(const DevFormula& F, const DevChains& C, const uint32_t* P,
+                                     cudaStream_t st);
+cudaError_t launch_init_probs_dense(int n, int n_pad, const DevChains& C, const uint32_t* P,
+                                    uint8_t* X, uint8_t* best_x, uint8_t one, uint8_t minus_one,
+                                    cudaStream_t st);
+
 // fit.cpp
 int fit_or_rbm(int len, int nh, double fstar, int quant_bits, int iters, double* W,
                double* b);
