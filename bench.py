@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--path", default="auto", choices=["auto", "sparse", "dense"])
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--no-proposal", action="store_true",
+                    help="skip the learned-proposal probe (training + held-out comparison)")
+    ap.add_argument("--proposal-train", type=int, default=1024,
+                    help="solver-labelled training formulas for the proposal probe")
     ap.add_argument("--no-up", action="store_true",
                     help="skip the unit-propagation ablation probe")
     ap.add_argument("--no-ragged", action="store_true",
@@ -364,6 +368,7 @@ def run_mine(args):
                            ms_total / args.steps) if not args.no_fp32 else None
     ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
     up = up_probe(ms, torch, n, off, lits, w, B, stream, sets, args) if not args.no_up else None
+    prop = proposal_probe(ms, torch, stream, sets, args) if not args.no_proposal else None
 
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
@@ -382,7 +387,7 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32, ragged=ragged, unit_prop=up)
+                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -518,6 +523,77 @@ def fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args, our
                 fixed_time_s=budget, rounds_fp32=rounds_fp32, rounds_ours=rounds_ours,
                 best_cost_fp32=best_fp32, best_cost_ours=best_ours,
                 note="FP32 torch matmuls (TF32 off) + lookups, torch generator draws")
+
+
+def proposal_probe(ms, torch, stream, sets, args):
+    """Learned proposal (config 5): a 3-layer, 64-wide message-passing network
+    trained by the library's kernels on solver-labelled random weighted
+    3-SAT formulas (n uniform in [500, 2000], m = 6 n, weights uniform in
+    [1, 1000]; labels = best assignment of 256 chains after 1000 rounds), then
+    held-out formulas (n = 2000, m = 12000) solved from uniform starts and
+    from the network's starts with the same seed and chains. Reports the mean
+    best cost at round checkpoints and, per formula, the fraction of plain's
+    rounds (and wall time) the learned start needs to reach plain's final
+    best cost."""
+    from paper_2311_02101_gb300 import proposal as P
+    rng = np.random.default_rng(args.seed + 17)
+
+    def gen(k, n_lo, n_hi):
+        out = []
+        for _ in range(k):
+            nv = int(rng.integers(n_lo, n_hi + 1))
+            out.append(workloads.random_ksat(nv, 6 * nv, 3, int(rng.integers(1 << 30)), 1000))
+        return out
+
+    p = ms.maxsat_default_params(sets=sets)
+    t0 = time.perf_counter()
+    train = gen(args.proposal_train, 500, 2000)
+    labels = P.label_with_solver(train, p, restarts=256, steps=1000, seed=3, stream=stream)
+    t1 = time.perf_counter()
+    model = ms.maxsat_mp_create(3, seed=0)
+    epochs = 20
+    losses = P.train(model, train, labels, p, epochs=epochs, batch=32, lr=2e-3, stream=stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    cps = [0, 50, 100, 200, 400, 600, 800, 1000, 1500, 2000]
+    mean = {"plain": np.zeros(len(cps)), "learned": np.zeros(len(cps))}
+    frac, frac_t = [], []
+    test = gen(8, 2000, 2000)
+    for f in test:
+        ctx = ms.maxsat_create(*f, p, stream)
+        curves, times = {}, {}
+        for mode in ("plain", "learned"):
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            if mode == "plain":
+                ms.maxsat_reset(ctx, 256, 11)
+            else:
+                ms.maxsat_reset_probs(ctx, 256, 11, P.propose(model, ctx))
+            cur, tt, done = [], [], 0
+            for T in cps:
+                ms.maxsat_step(ctx, T - done)
+                done = T
+                ms.maxsat_score(ctx)  # scores the current state too (keeps the best)
+                st = ms.maxsat_get_state(ctx)
+                tt.append(time.perf_counter() - ts)
+                cur.append(int(st["best_cost"].min()))
+            curves[mode], times[mode] = cur, tt
+            mean[mode] += np.array(cur, float) / len(test)
+        target = curves["plain"][-1]
+        k = next((i for i, c in enumerate(curves["learned"]) if c <= target), None)
+        frac.append(cps[k] / cps[-1] if k is not None else None)
+        frac_t.append(times["learned"][k] / times["plain"][-1] if k is not None else None)
+        ms.maxsat_destroy(ctx)
+    ms.maxsat_mp_destroy(model)
+    ok = [x for x in frac if x is not None]
+    return dict(train_formulas=len(train), label_s=t1 - t0, train_s=t2 - t1,
+                train_steps=len(losses), loss_first=losses[0],
+                loss_last=float(np.mean(losses[-32:])), held_out=len(test), checkpoints=cps,
+                mean_best_plain=[int(x) for x in mean["plain"]],
+                mean_best_learned=[int(x) for x in mean["learned"]],
+                rounds_fraction_to_plain_final=frac, wall_fraction_to_plain_final=frac_t,
+                median_rounds_fraction=float(np.median(ok)) if ok else None,
+                note="checkpoint scoring (maxsat_score + state copy) is inside both wall times")
 
 
 def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20):

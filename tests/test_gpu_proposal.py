@@ -109,3 +109,43 @@ def test_reset_from_probabilities(ms, stream):
         for i in (0, 5, n - 1):
             assert x[b, i] == (oracle.draw16(seed, 1, 0, i, 0, b) < P[i])
     ms.maxsat_destroy(ctx)
+
+
+def test_learned_start_reaches_lower_costs(ms, stream):
+    """Trained on solver-labelled formulas, the network's start distribution
+    gives lower best costs than uniform starts on held-out formulas after the
+    same number of rounds (same seed, same chains, deterministic training)."""
+    from paper_2311_02101_gb300 import proposal as P
+    import os
+    table = oracle.RbmTable.load(os.path.join(os.path.dirname(__file__), "golden",
+                                              "or_rbm_params.txt"))
+    params = ms.maxsat_default_params(sets=[s for s in table.sets if s["len"] == 3],
+                                      n_temps=2, n_buckets=4)
+    params.fstar = None
+    rng = np.random.default_rng(5)
+
+    def gen(k, n_lo, n_hi):
+        out = []
+        for _ in range(k):
+            n = int(rng.integers(n_lo, n_hi + 1))
+            out.append(workloads.random_ksat(n, 6 * n, 3, int(rng.integers(1 << 30)), 1000))
+        return out
+
+    train = gen(512, 300, 800)
+    labels = P.label_with_solver(train, params, restarts=256, steps=500, seed=3, stream=stream)
+    model = ms.maxsat_mp_create(3, seed=0)
+    losses = P.train(model, train, labels, params, epochs=12, batch=32, lr=2e-3, stream=stream)
+    assert np.mean(losses[-16:]) < losses[0]
+    plain, learned = [], []
+    for f in gen(8, 800, 800):
+        ctx = ms.maxsat_create(*f, params, stream)
+        p = P.propose(model, ctx)
+        for out, reset in ((plain, lambda: ms.maxsat_reset(ctx, 256, 11)),
+                           (learned, lambda: ms.maxsat_reset_probs(ctx, 256, 11, p))):
+            reset()
+            ms.maxsat_step(ctx, 400)
+            ms.maxsat_score(ctx)
+            out.append(int(ms.maxsat_get_state(ctx)["best_cost"].min()))
+        ms.maxsat_destroy(ctx)
+    assert np.mean(learned) < np.mean(plain)
+    ms.maxsat_mp_destroy(model)
