@@ -431,18 +431,71 @@ def up_merge(inst: Instance, st: ChainState, up_x) -> ChainState:
     return st
 
 
-def free_energy(inst, table, x, temp, n_buckets=1):
+def free_energy(inst, table, x, temp, n_buckets=1, fixed=False):
+    """Formula free energy (Eq. 1) of each row of x at temperature `temp`;
+    with fixed=True also its fixed-point form sum_c rint(2^20 F_c) (int64)."""
     ln, bk, tp, nh, W, b = table.arrays()
     x = np.ascontiguousarray(x, np.uint8)
     B = x.shape[0]
     F = np.zeros(B, np.float64)
+    Fq = np.zeros(B, np.int64)
     rc = lib().oracle_free_energy(inst.n, inst.m, _ptr(inst.off), _ptr(inst.lits),
                                   _ptr(inst.w), len(ln), _ptr(ln), _ptr(bk), _ptr(tp),
                                   _ptr(nh), _ptr(W), _ptr(b), n_buckets, temp, _ptr(x), B,
-                                  _ptr(F))
+                                  _ptr(F), _ptr(Fq))
     if rc != 0:
         raise ValueError("a clause has no RBM parameter set")
-    return F
+    return (F, Fq) if fixed else F
+
+
+PH_SWAP = 4  # draw phase of parallel-tempering swaps
+
+
+def swap_thresholds():
+    """T[u] = ceil(2^20 ln(u / 65536)) for the 16-bit draw u (T[0] = -inf):
+    a swap with fixed-point log-ratio D (units 2^-20) is accepted iff D >= T[u],
+    i.e. iff u < 65536 exp(D 2^-20)."""
+    u = np.arange(65536, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        T = np.ceil(np.ldexp(np.log(u / 65536.0), 20))
+    T[0] = -np.inf
+    return T
+
+
+def pt_swap(inst, table, st, seed, parity, n_temps, n_buckets=1):
+    """One parallel-tempering swap round on the ensemble st (B chains in E
+    contiguous temperature blocks of S = B / E; S a multiple of 8). For every
+    block e = parity, parity + 2, ... with e + 1 < E, chain a = e S + k and
+    chain b = a + S exchange their states (x, nu) iff
+        D = F_e(x_a) + F_{e+1}(x_b) - F_e(x_b) - F_{e+1}(x_a) >= T[u],
+    F in the fixed-point form, u the 16-bit draw of chain a in phase 4 at the
+    current round (Metropolis acceptance min(1, exp(D)) of exchanging two
+    states between the targets exp(-F_e) and exp(-F_{e+1})). The best-so-far
+    stays with the chain index. In place; returns the number of swaps."""
+    B = st.x.shape[0]
+    E = n_temps
+    S = B // E
+    assert B % E == 0 and S % 8 == 0 and st.chain_ids is None
+    T = swap_thresholds()
+    done = 0
+    for e in range(parity, E - 1, 2):
+        a = np.arange(e * S, (e + 1) * S)
+        b = a + S
+        _, Fa0 = free_energy(inst, table, st.x[a], e, n_buckets, fixed=True)
+        _, Fa1 = free_energy(inst, table, st.x[a], e + 1, n_buckets, fixed=True)
+        _, Fb0 = free_energy(inst, table, st.x[b], e, n_buckets, fixed=True)
+        _, Fb1 = free_energy(inst, table, st.x[b], e + 1, n_buckets, fixed=True)
+        D = Fa0 + Fb1 - Fb0 - Fa1
+        u = np.array([draw16(seed, PH_SWAP, st.t, 0, 0, int(k)) for k in a])
+        ok = D >= T[u]
+        for arr in (st.x, st.nu, st.nu32):
+            if arr is None:
+                continue
+            tmp = arr[a[ok]].copy()
+            arr[a[ok]] = arr[b[ok]]
+            arr[b[ok]] = tmp
+        done += int(ok.sum())
+    return done
 
 
 # --------------------------------------------------------------------------

@@ -319,12 +319,16 @@ int oracle_gibbs(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
 
 /* Free energy of arbitrary assignments under the temperature-e parameters
  * (Eq. 1 summed over clauses as in Sec. 4.1). */
+/* The formula free energy (Eq. 1) of B assignments at temperature `temp`
+ * (F_out, FP64) and, when Fq_out is given, its fixed-point form: the sum over
+ * clauses of rint(2^20 F_c) (int64), the exact quantity parallel-tempering
+ * swaps compare. */
 int oracle_free_energy(int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
                        const int64_t* w, int32_t n_sets, const int32_t* set_len,
                        const int32_t* set_bucket, const int32_t* set_temp,
                        const int32_t* set_nh, const double* W, const double* bias,
                        int32_t n_buckets, int32_t temp, const uint8_t* x, int32_t B,
-                       double* F_out) {
+                       double* F_out, int64_t* Fq_out) {
   rbm_table tab = {n_sets, set_len, set_bucket, set_temp, set_nh, W, bias};
   int64_t wmin = INT64_MAX;
   for (int64_t c = 0; c < m; ++c) {
@@ -334,6 +338,7 @@ int oracle_free_energy(int32_t n, int64_t m, const int64_t* off, const int32_t* 
   for (int32_t b = 0; b < B; ++b) {
     const uint8_t* xb = x + (int64_t)b * n;
     double F = 0.0;
+    int64_t Fq = 0;
     for (int64_t c = 0; c < m; ++c) {
       int32_t len = (int32_t)(off[c + 1] - off[c]);
       if (len == 0) continue;
@@ -341,16 +346,20 @@ int oracle_free_energy(int32_t n, int64_t m, const int64_t* off, const int32_t* 
       if (s < 0) return -1;
       double Wp[OR_MAX_LEN][OR_MAX_H], bp[OR_MAX_H];
       negation_transform(&tab, s, lits + off[c], len, Wp, bp);
+      double Fc = 0.0;
       for (int32_t h = 0; h < tab.set_nh[s]; ++h) {
         double a = bp[h];
         for (int32_t k = 0; k < len; ++k) {
           int32_t l = lits[off[c] + k];
           a += Wp[k][h] * (double)xb[(l > 0 ? l : -l) - 1];
         }
-        F -= softplus(a);
+        Fc -= softplus(a);
       }
+      F += Fc;
+      Fq += (int64_t)nearbyint(ldexp(Fc, 20));
     }
     F_out[b] = F;
+    if (Fq_out) Fq_out[b] = Fq;
   }
   return 0;
 }

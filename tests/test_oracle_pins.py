@@ -267,6 +267,49 @@ def test_stationary_distribution():
     assert 0.5 * np.abs(emp - p).sum() < 0.01
 
 
+def test_swap_threshold_is_the_metropolis_rule():
+    """A swap with log-ratio D (units 2^-20) is accepted for exactly the
+    16-bit draws u < 65536 exp(D 2^-20): ceil(65536 exp(D 2^-20)) of the
+    65536 values when exp(D 2^-20) < 1, all of them when D >= 0."""
+    T = oracle.swap_thresholds()
+    for ratio in (0.3, 0.01, 0.5, 0.9999):
+        D = int(np.floor(np.ldexp(np.log(ratio), 20)))
+        want = int(np.ceil(65536 * np.exp(np.ldexp(D, -20))))
+        assert int(np.sum(D >= T)) == want
+    assert np.all(0 >= T) and np.all(5 >= T)
+    assert int(np.sum(-(40 << 20) >= T)) == 1  # only u = 0
+
+
+def test_parallel_tempering_keeps_each_temperature_stationary():
+    """Block Gibbs interleaved with swap rounds leaves every temperature's
+    target exp(-F_e) invariant (swaps are Metropolis moves on the product of
+    the targets): the empirical state frequencies of each temperature block
+    match it, and swaps do happen."""
+    table = _tiny_table([2, 3], [0.2, 1.0])
+    inst = oracle.Instance.from_clauses(4, [[1, -2, 3], [-1, 4], [-3, -4, 2], [2, 4]])
+    X = oracle.all_assignments(4)
+    targets = []
+    for e in range(2):
+        F = oracle.free_energy(inst, table, X, temp=e)
+        p = np.exp(-(F - F.min()))
+        targets.append(p / p.sum())
+    B, S = 8192, 4096
+    st = oracle.init_chains(4, B, seed=5)
+    oracle.gibbs(inst, table, st, 10, seed=5, n_temps=2)
+    counts = np.zeros((2, 16))
+    swaps = 0
+    for r in range(40):
+        swaps += oracle.pt_swap(inst, table, st, seed=5, parity=0, n_temps=2)
+        oracle.gibbs(inst, table, st, 1, seed=5, n_temps=2)
+        code = (st.x.astype(np.int64) << np.arange(4)).sum(axis=1)
+        for e in range(2):
+            counts[e] += np.bincount(code[e * S:(e + 1) * S], minlength=16)
+    assert swaps > 1000
+    for e in range(2):
+        emp = counts[e] / counts[e].sum()
+        assert 0.5 * np.abs(emp - targets[e]).sum() < 0.01, e
+
+
 # --------------------------------------------------------------------------
 # Search: determinism, resume, best-keep, quality
 # --------------------------------------------------------------------------
