@@ -224,6 +224,22 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t restarts, uint64_t seed,
                      const uint8_t* x, const float* nu, const int64_t* best_cost,
                      const uint8_t* best_x, uint32_t t);
 
+/* One parallel-tempering swap round between adjacent temperatures (the
+ * ensemble of Sec. 4.2 with replica exchange; the paper lists tempering as
+ * future work, Sec. 7). With E temperatures and restarts = E x S (S a
+ * multiple of 8; whole ensemble on this context; sparse path), chain a =
+ * e S + k of every block e = parity, parity + 2, ... (e + 1 < E) and chain
+ * b = a + S exchange states x and nu iff
+ *   D = F_e(x_a) + F_{e+1}(x_b) - F_e(x_b) - F_{e+1}(x_a) >= ceil(2^20 ln(u / 65536)),
+ * the Metropolis rule min(1, exp(D)) for the targets exp(-F_e): F is the
+ * exact fixed-point free energy sum_c rint(2^20 F_c) (Eq. 1 per clause) and
+ * u the 16-bit draw of chain a at counter (0, a >> 3, current round, phase
+ * 4), lane a & 7 (u = 0 always accepts). The best-so-far stays with the
+ * chain index; the round index does not advance. *accepted (may be NULL)
+ * receives the number of swaps (synchronises). MAXSAT_EINVAL when the
+ * conditions above fail, MAXSAT_ESTATE without chains. */
+int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted);
+
 /* Prioritized unit propagation with the B-of-2B merge (Sec. 4.4; the
  * appendix code's send / fetch / merge). maxsat_up_begin copies the chains'
  * states x and their nu to the host and starts unit propagation on host

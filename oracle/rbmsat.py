@@ -455,10 +455,10 @@ def swap_thresholds():
     """T[u] = ceil(2^20 ln(u / 65536)) for the 16-bit draw u (T[0] = -inf):
     a swap with fixed-point log-ratio D (units 2^-20) is accepted iff D >= T[u],
     i.e. iff u < 65536 exp(D 2^-20)."""
-    u = np.arange(65536, dtype=np.float64)
-    with np.errstate(divide="ignore"):
-        T = np.ceil(np.ldexp(np.log(u / 65536.0), 20))
+    import math
+    T = np.empty(65536, np.float64)
     T[0] = -np.inf
+    T[1:] = [math.ceil(math.ldexp(math.log(u / 65536.0), 20)) for u in range(1, 65536)]
     return T
 
 

@@ -81,6 +81,7 @@ def lib():
         L.maxsat_mp_destroy.argtypes = [P]
         L.maxsat_mp_destroy.restype = None
         L.maxsat_reset_probs.argtypes = [P, i32, u64, P]
+        L.maxsat_pt_swap.argtypes = [P, i32, ctypes.POINTER(i32)]
         L.maxsat_up_begin.argtypes = [P]
         L.maxsat_up_end.argtypes = [P]
         L.maxsat_up.argtypes = [P]
@@ -105,7 +106,7 @@ def lib():
                      "maxsat_get_clause_block", "maxsat_up_begin", "maxsat_up_end", "maxsat_up",
                      "maxsat_mp_create", "maxsat_mp_n_params", "maxsat_mp_set_params",
                      "maxsat_mp_get_params", "maxsat_mp_forward", "maxsat_mp_gradient",
-                     "maxsat_mp_adam", "maxsat_reset_probs",
+                     "maxsat_mp_adam", "maxsat_reset_probs", "maxsat_pt_swap",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
@@ -329,6 +330,13 @@ def maxsat_kernel_times(ctx: Context, max_kernels: int = 32):
     raw = names.raw
     return {raw[32 * i:32 * i + 32].split(b"\0")[0].decode(): (int(cnt[i]), float(ms[i]))
             for i in range(k)}
+
+
+def maxsat_pt_swap(ctx: Context, parity: int) -> int:
+    """One parallel-tempering swap round; returns the number of swaps."""
+    acc = ctypes.c_int32()
+    _check(lib().maxsat_pt_swap(ctx.handle, int(parity), ctypes.byref(acc)), ctx)
+    return int(acc.value)
 
 
 def maxsat_up_begin(ctx: Context):

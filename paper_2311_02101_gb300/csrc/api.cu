@@ -82,6 +82,12 @@ struct maxsat_ctx {
   int32_t* ev_tickets = nullptr;
   int ev_Bp = 0;
   std::vector<int64_t> h_w;  // clause weights (host copy)
+  // parallel tempering: Metropolis thresholds and per-round scratch
+  DevAllocs pt_mem;
+  long long *d_Tc = nullptr, *d_Fown = nullptr, *d_Foth = nullptr;
+  uint8_t* d_swap = nullptr;
+  int* d_nacc = nullptr;
+  int pt_Bp = 0;
   // unit-propagation heuristic (Sec. 4.4): host formula, worker, results
   UpFormula upf;
   std::thread up_worker;
@@ -918,6 +924,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   }
   UP(ctx->tabs.meta, T.meta);
   UP(ctx->tabs.rec, T.rec);
+  UP(ctx->tabs.feq, T.feq);
   UP(ctx->tabs.gq, T.gq);
   UP(ctx->tabs.pv, T.pv);
 #define UP2(vec, dst)                                         \
@@ -1409,6 +1416,44 @@ static int put_states(maxsat_ctx* ctx, const uint8_t* x, const float* nu) {
     }
   CK(ctx, cudaMemcpy(ctx->C.xt, hx.data(), nB, cudaMemcpyHostToDevice));
   CK(ctx, cudaMemcpy(ctx->C.nu, hn.data(), 4 * nB, cudaMemcpyHostToDevice));
+  return MAXSAT_OK;
+}
+
+int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_pt_swap before maxsat_reset");
+  if (parity != 0 && parity != 1) return fail(ctx, MAXSAT_EINVAL, "parity must be 0 or 1");
+  const int E = ctx->T.n_temps, B = ctx->C.B;
+  if (ctx->dense || ctx->n_inst != 1)
+    return fail(ctx, MAXSAT_EINVAL, "parallel tempering runs on the sparse path of a single formula");
+  if (ctx->C.g8_off != 0 || ctx->C.B_total != B)
+    return fail(ctx, MAXSAT_EINVAL, "parallel tempering needs the whole ensemble on one context");
+  if (E < 2 || B % E != 0 || (B / E) % 8 != 0)
+    return fail(ctx, MAXSAT_EINVAL, "parallel tempering needs restarts = E x S with S a multiple of 8");
+  if (!ctx->tabs.feq_ok) return fail(ctx, MAXSAT_EINVAL, "free energies exceed the fixed-point range");
+  if (!ctx->d_Tc) {
+    std::vector<long long> Tc(65536);
+    Tc[0] = INT64_MIN;
+    for (int u = 1; u < 65536; ++u)
+      Tc[u] = (long long)std::ceil(std::ldexp(std::log(u / 65536.0), 20));
+    CK(ctx, ctx->pt_mem.alloc(&ctx->d_Tc, Tc.size()));
+    CK(ctx, cudaMemcpy(ctx->d_Tc, Tc.data(), 8 * Tc.size(), cudaMemcpyHostToDevice));
+    CK(ctx, ctx->pt_mem.alloc(&ctx->d_nacc, 1));
+  }
+  if (ctx->pt_Bp < ctx->C.Bp) {
+    CK(ctx, ctx->pt_mem.alloc(&ctx->d_Fown, (size_t)ctx->C.Bp));
+    CK(ctx, ctx->pt_mem.alloc(&ctx->d_Foth, (size_t)ctx->C.Bp));
+    CK(ctx, ctx->pt_mem.alloc(&ctx->d_swap, (size_t)ctx->C.Bp + 8));
+    ctx->pt_Bp = ctx->C.Bp;
+  }
+  CK(ctx, launch_pt_round(ctx->F, ctx->T, ctx->C, B / E, E, parity, ctx->t, ctx->d_Tc,
+                          ctx->d_Fown, ctx->d_Foth, ctx->d_swap, ctx->d_nacc, ctx->stream));
+  if (accepted) {
+    int h = 0;
+    CK(ctx, cudaMemcpyAsync(&h, ctx->d_nacc, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *accepted = h;
+  }
   return MAXSAT_OK;
 }
 

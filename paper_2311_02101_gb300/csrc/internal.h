@@ -17,7 +17,7 @@ namespace rbmsat {
 // 16-bit lane (b & 7) of Philox4x32-10 at counter (a, (b >> 3) | (h << 24), t,
 // phase) under key = seed. a is the variable (initial / visible draws) or the
 // clause (hidden draws); h the hidden unit.
-enum : uint32_t { kPhaseInit = 1, kPhaseHidden = 2, kPhaseVisible = 3 };
+enum : uint32_t { kPhaseInit = 1, kPhaseHidden = 2, kPhaseVisible = 3, kPhaseSwap = 4 };
 
 constexpr int kChainTile = 256;   // chains per block of the sparse kernels
 constexpr int kClauseBlock = 64;  // clauses per block of the sparse gather
@@ -32,7 +32,8 @@ struct GroupMeta {
   int32_t stride = 0;   // u32 words per pattern record: 4 ceil((L + 1) / 4)
   int32_t gq_off = 0;   // into gq (int16): + (e 2^L + hp) K + k
   int32_t sat = 0;      // 1 when some hidden probability of the group is 65536 / 65536
-  int32_t pad0 = 0, pad1 = 0;
+  int32_t feq_off = 0;  // into feq (int32): + e 2^K + p
+  int32_t pad1 = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -67,6 +68,7 @@ struct DevTables {
   int32_t n_groups;
   int32_t rec_len, gq_len, pv_len;  // element counts
   int32_t one_chunk;   // every group's pattern record is 16 bytes (L <= 3)
+  const int32_t* feq;  // fixed-point clause free energies (parallel tempering)
   int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
   const GroupMeta* meta;
   const uint32_t* rec;
@@ -118,6 +120,8 @@ struct HostTables {
   std::vector<int32_t> grp_len, grp_bucket, grp_nh;
   std::vector<GroupMeta> meta;
   std::vector<uint32_t> rec;
+  std::vector<int32_t> feq;  // rint(2^20 F) per (group, temperature, pattern)
+  bool feq_ok = true;        // every entry fits int32
   std::vector<int16_t> gq;
   std::vector<uint32_t> pv;
   int32_t gq_absmax = 0;  // largest |2^Q G|
@@ -177,6 +181,11 @@ cudaError_t launch_init_probs_sparse(const DevFormula& F, const DevChains& C, co
 cudaError_t launch_init_probs_dense(int n, int n_pad, const DevChains& C, const uint32_t* P,
                                     uint8_t* X, uint8_t* best_x, uint8_t one, uint8_t minus_one,
                                     cudaStream_t st);
+
+// pt.cu: parallel-tempering swap rounds (sparse layout)
+cudaError_t launch_pt_round(const DevFormula& F, const DevTables& T, const DevChains& C, int S,
+                            int E, int parity, uint32_t t, const long long* Tc, long long* Fown,
+                            long long* Foth, uint8_t* flag, int* n_acc, cudaStream_t st);
 
 // fit.cpp
 int fit_or_rbm(int len, int nh, double fstar, int quant_bits, int iters, double* W,

@@ -14,6 +14,7 @@
 //                     word 1 + h hidden unit h's threshold
 //                     P = rint(65536 sigma(b_h + sum_k W_kh tau_k(p))) as
 //                     (min(P, 65535) << 16) | [P == 65536], then zeros
+//   feq[g][e][p]      rint(2^20 F) of that free energy (int32; parallel tempering)
 //   gq[g][e][hp][k]   2^Q sum_h W_kh [bit h of hp]                     (int16)
 // A 16-bit draw u gives 1 iff u < P. With a threshold word t, u in the high
 // half of a 32-bit word x (any low half) gives x < t iff u < min(P, 65535),
@@ -51,6 +52,8 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
   T->grp_nh.assign(G, 0);
   T->meta.assign(G, GroupMeta{});
   T->rec.clear();
+  T->feq.clear();
+  T->feq_ok = true;
   T->gq.clear();
   T->gq_absmax = 0;
   T->max_nh = 0;
@@ -60,6 +63,7 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
     GroupMeta& gm = T->meta[g];
     gm.len = K;
     gm.rec_off = (int32_t)T->rec.size();
+    gm.feq_off = (int32_t)T->feq.size();
     gm.gq_off = (int32_t)T->gq.size();
     for (int e = 0; e < E; ++e) {
       const RbmSet* s = nullptr;
@@ -102,6 +106,9 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
           if (P == 65536u) gm.sat = 1;
           F -= softplus(a);
         }
+        const double Fq = std::nearbyint(std::ldexp(F, 20));
+        if (!(std::fabs(Fq) < 2147483647.0)) T->feq_ok = false;
+        T->feq.push_back(T->feq_ok ? (int32_t)Fq : 0);
         const float Ff = (float)F;
         std::memcpy(&words[0], &Ff, 4);
         for (uint32_t w : words) T->rec.push_back(w);

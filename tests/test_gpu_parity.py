@@ -576,3 +576,46 @@ def test_unit_propagation_rejects_batches_and_misuse(ms, stream, golden_table):
         ms.maxsat_up(ctx)
     assert e.value.code == ms.MAXSAT_EINVAL
     ms.maxsat_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Parallel tempering (maxsat_pt_swap) with a 4-temperature ensemble
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def table4():
+    """Length 3, two weight buckets, four temperatures."""
+    return oracle.make_table([3], [0.05, 0.15, 0.4, 0.9], n_buckets=2, iters=3000)
+
+
+def test_parallel_tempering_matches_oracle(ms, stream, table4):
+    inst = inst_of(workloads.weighted_3sat(200, 900, 8, seed=6))
+    B, seed = 256, 21
+    ctx = make_ctx(ms, stream, inst, table4, n_temps=4, n_buckets=2,
+                   path=ms.MAXSAT_PATH_SPARSE, spg=3)
+    ms.maxsat_reset(ctx, B, seed)
+    st = oracle.init_chains(inst.n, B, seed)
+    kw = dict(n_temps=4, n_buckets=2, threads=os.cpu_count() or 4)
+    swaps = []
+    for steps, parity in ((4, 0), (3, 1), (5, 0), (2, 1)):
+        ms.maxsat_step(ctx, steps)
+        oracle.gibbs(inst, table4, st, steps, seed, **kw)
+        got = ms.maxsat_pt_swap(ctx, parity)
+        want = oracle.pt_swap(inst, table4, st, seed, parity, n_temps=4, n_buckets=2)
+        assert got == want
+        swaps.append(got)
+    ms.maxsat_step(ctx, 3)
+    oracle.gibbs(inst, table4, st, 3, seed, **kw)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    assert sum(swaps) > 0
+    assert_same(gpu, st, 17, 0.01)
+
+
+def test_parallel_tempering_rejects_bad_ensembles(ms, stream, table4):
+    inst = inst_of(workloads.weighted_3sat(100, 400, 8, seed=6))
+    ctx = make_ctx(ms, stream, inst, table4, n_temps=4, n_buckets=2, path=ms.MAXSAT_PATH_SPARSE)
+    ms.maxsat_reset(ctx, 100, 1)  # 100 = 4 x 25, 25 not a multiple of 8
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_pt_swap(ctx, 0)
+    assert e.value.code == ms.MAXSAT_EINVAL
+    ms.maxsat_destroy(ctx)
