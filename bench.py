@@ -54,6 +54,7 @@ def parse():
                     help="skip the learned-proposal probe (training + held-out comparison)")
     ap.add_argument("--proposal-train", type=int, default=1024,
                     help="solver-labelled training formulas for the proposal probe")
+    ap.add_argument("--no-pt", action="store_true", help="skip the parallel-tempering probe")
     ap.add_argument("--no-up", action="store_true",
                     help="skip the unit-propagation ablation probe")
     ap.add_argument("--no-ragged", action="store_true",
@@ -369,6 +370,7 @@ def run_mine(args):
     ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
     up = up_probe(ms, torch, n, off, lits, w, B, stream, sets, args) if not args.no_up else None
     prop = proposal_probe(ms, torch, stream, sets, args) if not args.no_proposal else None
+    pt = pt_probe(ms, torch, n, off, lits, w, B, stream, args) if not args.no_pt else None
 
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
@@ -387,7 +389,7 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 2 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop)
+                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop, tempering=pt)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -594,6 +596,37 @@ def proposal_probe(ms, torch, stream, sets, args):
                 rounds_fraction_to_plain_final=frac, wall_fraction_to_plain_final=frac_t,
                 median_rounds_fraction=float(np.median(ok)) if ok else None,
                 note="checkpoint scoring (maxsat_score + state copy) is inside both wall times")
+
+
+def pt_probe(ms, torch, n, off, lits, w, B, stream, args, E=8, period=10):
+    """Parallel tempering on an ensemble of E = 8 temperatures (F* from 0.35 to
+    0.528, geometric: neighbours close enough for the free energies of m =
+    6000 clauses to overlap; sets fitted by the library): Gibbs alone vs Gibbs
+    with a swap round every `period` rounds (alternating parity), same
+    seconds, same seed; lowest best cost over all chains, swap acceptance."""
+    secs = args.fixed_seconds
+    fstar = list(np.geomspace(0.35, 0.528, E))
+    p = ms.maxsat_default_params(fstar=fstar, fit_iters=5000, path=ms.MAXSAT_PATH_SPARSE)
+    out = dict(temperatures=E, period=period, seconds=secs, chains=B)
+    for mode in ("gibbs", "gibbs+swaps"):
+        ctx = ms.maxsat_create(n, off, lits, w, p, stream)
+        ms.maxsat_reset(ctx, B, 99)
+        rounds, acc, tried = 0, 0, 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < secs:
+            ms.maxsat_step(ctx, period)
+            rounds += period
+            if mode == "gibbs+swaps":
+                par = (rounds // period) & 1
+                acc += ms.maxsat_pt_swap(ctx, par)
+                tried += (E - par) // 2 * (B // E)
+        ms.maxsat_score(ctx)
+        st = ms.maxsat_get_state(ctx)
+        ms.maxsat_destroy(ctx)
+        out[mode] = dict(rounds=rounds, best_cost=int(st["best_cost"].min()))
+        if tried:
+            out[mode]["swap_acceptance"] = acc / tried
+    return out
 
 
 def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20):
