@@ -1195,11 +1195,14 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
       ctx->dev_Bp = Bp;
     }
     const int Bt = ctx->dev_Bp;
-    CK(ctx, launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, ctx->stream));
+    TIMED(ctx, ctx->stream, "assign_fp8",
+          launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, ctx->stream));
     TIMED(ctx, ctx->stream, "gemm1_eval",
           launch_gemm1_eval(ctx->tmA, ctx->tmXe, ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
                             ctx->d_row_len, ctx->d_row_w, ctx->d_grp_small, ctx->d_epart,
                             ctx->d_etick, cost_dev, ctx->d_err, ctx->stream));
+    TIMED(ctx, ctx->stream, "sum_tiles",
+          launch_sum_tiles(ctx->d_epart, ctx->m_pad, B, Bt, cost_dev, ctx->stream));
     return MAXSAT_OK;
   }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;

@@ -15,16 +15,22 @@
 // exact in FP8 (E4M3 up to length 9, E5M2 beyond); the FP32 accumulator is
 // exact for |D| < 2^24.
 //
-// Kernel structure (one 128-clause x 128-chain tile per CTA, 6 warps):
+// Kernel structure (persistent: one CTA per SM walks 128-clause x 256-chain
+// tiles, chain tile fastest; 18 warps):
 //   warp 0     TMA producer: 128-byte-swizzled K-blocks of A and B into a
 //              4-stage shared-memory ring (mbarrier complete_tx);
-//   warp 1     allocates 128 TMEM columns and issues tcgen05.mma
-//              (kind::f8f6f4, M = 128, N = 128, K = 32) from one thread;
-//              tcgen05.commit frees ring slots and signals the accumulator;
-//   warps 2-5  epilogue: tcgen05.ld 32 columns at a time (one row = one
-//              clause per thread), decode patterns, reduce weighted costs per
-//              chain across the 128 rows, and (last tile of a chain column to
-//              arrive) sum the per-tile partials in tile order.
+//   warp 1     allocates 2 x 256 TMEM columns (two accumulators, so the
+//              epilogue of one tile overlaps the MMAs of the next) and issues
+//              tcgen05.mma (kind::f8f6f4, M = 128, N = 256, K = 32) from one
+//              thread; tcgen05.commit frees ring slots and signals the
+//              accumulator;
+//   warps 2-17 epilogue, four warps per TMEM lane quarter (one row = one
+//              clause per thread, 64 columns per warp): tcgen05.ld 32 columns
+//              at a time, test each entry against the all-false value, a
+//              32 x 32 bit transpose turns rows into columns, the weighted
+//              unsatisfied cost of every chain is summed over the tile's 128
+//              rows; k_sum_tiles then sums the per-tile partials (16 lanes
+//              per chain, int64: exact in any order).
 // Every mbarrier wait is bounded; a timeout records an error code that the
 // host reads after the launch, and the kernel still releases its TMEM.
 #include <cuda.h>
@@ -49,7 +55,7 @@ constexpr int kBK = 128;          // FP8 elements (bytes) per K-block: one 128-b
 constexpr int kStages = 4;
 constexpr int kStageA = kBM * kBK;  // 16 KB
 constexpr int kStageB = kBN * kBK;  // 32 KB
-constexpr int kEpiWarps = 8;  // epilogue warps (two per TMEM lane quarter)
+constexpr int kEpiWarps = 16;  // epilogue warps (four per TMEM lane quarter)
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct Gemm1Smem {
@@ -59,7 +65,7 @@ struct Gemm1Smem {
   uint64_t tempty[2];       // epilogue -> MMA: accumulator buffer drained
   uint32_t tmem_slot;
   int64_t cost[2][4 * kBN];  // per tile parity and epilogue warp: its rows' column sums
-  int64_t w[8][32];       // per epilogue warp: the weights of its 32 rows
+  int64_t w[kEpiWarps][32];  // per epilogue warp: the weights of its 32 rows
 };
 
 constexpr int kGemm1Smem = 1024 + kStages * (kStageA + kStageB) + (int)sizeof(Gemm1Smem);
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   uint8_t* sB = tiles + kStages * kStageA;
   Gemm1Smem& S = *reinterpret_cast<Gemm1Smem*>(tiles + kStages * (kStageA + kStageB));
 
-  static_assert(EPI == 4 || EPI == 8, "4 or 8 epilogue warps");
+  static_assert(EPI == 4 || EPI == 8 || EPI == 16, "4, 8 or 16 epilogue warps");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_tiles = tiles_m * tiles_n;
 
@@ -156,12 +162,12 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     }
     __syncwarp();
   } else {
-    // epilogue warps: TMEM lane quarter = warp % 4; with 8 warps the two
-    // warps of a quarter split the columns
+    // epilogue warps: TMEM lane quarter = warp % 4; the EPI / 4 warps of a
+    // quarter split the columns
     constexpr int kCols = kBN * 4 / EPI;  // columns per epilogue warp
     const int quarter = warp & 3;
     const int ew = warp - 2;
-    const int half = ew / 4;              // 0, or 1 for the second warp of a quarter
+    const int half = ew / 4;              // which column slice of its quarter
     const int t = threadIdx.x - 64;       // 0 .. 32 EPI - 1
     int li = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
@@ -228,26 +234,40 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   }
 }
 
-// assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
-// variables, 0 for padding variables and padding chains.
-// Sum of the per-tile partial costs, in tile order (deterministic).
+// Sum of the per-tile partial costs: 16 lanes per chain split the tiles and
+// combine with shuffles (int64: exact in any order).
 __global__ void k_sum_tiles(const int64_t* __restrict__ part, int tiles_m, int Bp, int B,
                             int64_t* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = gid >> 4, sub = gid & 15;
   int64_t tot = 0;
-  for (int k = 0; k < tiles_m; ++k) tot += part[(size_t)k * Bp + b];
-  out[b] = tot;
+  if (b < B)
+    for (int k = sub; k < tiles_m; k += 16) tot += __ldg(part + (size_t)k * Bp + b);
+#pragma unroll
+  for (int s = 1; s < 16; s <<= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, s);
+  if (b < B && sub == 0) out[b] = tot;
 }
 
+// assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
+// variables, 0 for padding variables and padding chains; 16 output bytes
+// (one 16-byte store) per thread.
 __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, int Bp, int n_pad,
                              uint8_t one, uint8_t minus_one, uint8_t* __restrict__ X) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)Bp * n_pad) return;
-  const int b = (int)(idx / n_pad), i = (int)(idx % n_pad);
-  uint8_t v = 0;
-  if (b < B && i < n) v = assign[(size_t)b * n + i] ? one : minus_one;
-  X[idx] = v;
+  const int chunks = n_pad / 16;
+  if (idx >= (size_t)Bp * chunks) return;
+  const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
+  uint32_t wv[4] = {0u, 0u, 0u, 0u};
+  if (b < B) {
+    const uint8_t* row = assign + (size_t)b * n;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int i = i0 + k;
+      const uint32_t v = i < n ? (__ldg(row + i) ? one : minus_one) : 0u;
+      wv[k >> 2] |= v << (8 * (k & 3));
+    }
+  }
+  reinterpret_cast<uint4*>(X)[idx] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -369,9 +389,14 @@ cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, in
   k_gemm1_eval<kEpiWarps><<<grid, 64 + 32 * kEpiWarps, kGemm1Smem, st>>>(tmA, tmB, m, n_pad / kBK, tiles_m, tiles_n, B,
                                                    Bp, idesc, row_len, row_w, grp_small, part,
                                                    tickets, out, err);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_sum_tiles<<<(B + 255) / 256, 256, 0, st>>>(part, tiles_m, Bp, B, out);
+  return cudaGetLastError();
+}
+
+
+
+cudaError_t launch_sum_tiles(const int64_t* part, int m_pad, int B, int Bp, int64_t* out,
+                             cudaStream_t st) {
+  k_sum_tiles<<<(16 * B + 255) / 256, 256, 0, st>>>(part, m_pad / kBM, Bp, B, out);
   return cudaGetLastError();
 }
 
@@ -380,7 +405,7 @@ cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n
   uint8_t one, minus_one;
   fp8_encode_int(1, e5m2, &one);
   fp8_encode_int(-1, e5m2, &minus_one);
-  const size_t total = (size_t)Bp * n_pad;
+  const size_t total = (size_t)Bp * (n_pad / 16);
   k_assign_fp8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(assign, B, n, Bp, n_pad, one,
                                                                  minus_one, X);
   return cudaGetLastError();

@@ -241,6 +241,9 @@ cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, in
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
                               const int64_t* row_w, const uint8_t* grp_small, int64_t* part,
                               int32_t* tickets, int64_t* out, int* err, cudaStream_t st);
+// per-tile partial costs of launch_gemm1_eval -> out (B)
+cudaError_t launch_sum_tiles(const int64_t* part, int m_pad, int B, int Bp, int64_t* out,
+                             cudaStream_t st);
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
                               uint8_t* X, cudaStream_t st);
 
