@@ -304,7 +304,9 @@ def run_mine(args):
     stream = torch.cuda.Stream()
     path_code = {"auto": ms.MAXSAT_PATH_AUTO, "sparse": ms.MAXSAT_PATH_SPARSE,
                  "dense": ms.MAXSAT_PATH_DENSE}[args.path]
-    params = ms.maxsat_default_params(path=path_code, tune_blocks=1)
+    # wave-fitted clause blocks (the measured choice, tune_blocks, is used for
+    # the 512-formula batch below, where it pays)
+    params = ms.maxsat_default_params(path=path_code)
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
     # every rank runs its own shard of one ensemble of ws * B chains (weak
     # scaling): global chains rank * B .. rank * B + B - 1
