@@ -596,23 +596,29 @@ def proposal_probe(ms, torch, stream, sets, args):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     cps = [0, 50, 100, 200, 400, 600, 800, 1000, 1500, 2000]
-    mean = {"plain": np.zeros(len(cps)), "learned": np.zeros(len(cps))}
-    frac, frac_t = [], []
+    modes = ("plain", "learned", "learned+flips")
+    mean = {k: np.zeros(len(cps)) for k in modes}
+    frac, frac_t, frac_f, frac_ft = [], [], [], []
     test = gen(8, 2000, 2000)
     for f in test:
         ctx = ms.maxsat_create(*f, p, stream)
         curves, times = {}, {}
-        for mode in ("plain", "learned"):
+        for mode in modes:
             torch.cuda.synchronize()
             ts = time.perf_counter()
             if mode == "plain":
                 ms.maxsat_reset(ctx, 256, 11)
             else:
-                ms.maxsat_reset_probs(ctx, 256, 11, P.propose(model, ctx))
+                prob = P.propose(model, ctx)
+                ms.maxsat_reset_probs(ctx, 256, 11, prob)
             cur, tt, done = [], [], 0
             for T in cps:
-                ms.maxsat_step(ctx, T - done)
-                done = T
+                while done < T:  # flip proposals every 200 rounds in the third mode
+                    k = min(T, (done // 200 + 1) * 200) - done
+                    ms.maxsat_step(ctx, k)
+                    done += k
+                    if mode == "learned+flips" and done % 200 == 0:
+                        ms.maxsat_propose_flips(ctx, prob, 0.2)
                 ms.maxsat_score(ctx)  # scores the current state too (keeps the best)
                 st = ms.maxsat_get_state(ctx)
                 tt.append(time.perf_counter() - ts)
@@ -623,6 +629,9 @@ def proposal_probe(ms, torch, stream, sets, args):
         k = next((i for i, c in enumerate(curves["learned"]) if c <= target), None)
         frac.append(cps[k] / cps[-1] if k is not None else None)
         frac_t.append(times["learned"][k] / times["plain"][-1] if k is not None else None)
+        k = next((i for i, c in enumerate(curves["learned+flips"]) if c <= target), None)
+        frac_f.append(cps[k] / cps[-1] if k is not None else None)
+        frac_ft.append(times["learned+flips"][k] / times["plain"][-1] if k is not None else None)
         ms.maxsat_destroy(ctx)
     ms.maxsat_mp_destroy(model)
     ok = [x for x in frac if x is not None]
@@ -631,8 +640,13 @@ def proposal_probe(ms, torch, stream, sets, args):
                 loss_last=float(np.mean(losses[-32:])), held_out=len(test), checkpoints=cps,
                 mean_best_plain=[int(x) for x in mean["plain"]],
                 mean_best_learned=[int(x) for x in mean["learned"]],
+                mean_best_learned_flips=[int(x) for x in mean["learned+flips"]],
                 rounds_fraction_to_plain_final=frac, wall_fraction_to_plain_final=frac_t,
                 median_rounds_fraction=float(np.median(ok)) if ok else None,
+                flips_rounds_fraction_to_plain_final=frac_f,
+                flips_wall_fraction_to_plain_final=frac_ft,
+                flips_median_wall_fraction=(float(np.median([x for x in frac_ft if x is not None]))
+                                            if any(x is not None for x in frac_ft) else None),
                 note="checkpoint scoring (maxsat_score + state copy) is inside both wall times")
 
 

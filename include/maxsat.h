@@ -307,6 +307,15 @@ int maxsat_mp_adam(maxsat_mp* mp, maxsat_ctx* ctx, float lr);
 const char* maxsat_mp_last_error(const maxsat_mp* mp);
 void maxsat_mp_destroy(maxsat_mp* mp);
 
+/* Flip proposals from the learned network: every chain proposes its state
+ * with each confident variable set to the network's value (1 where prob[v]
+ * >= 1 - tau, 0 where prob[v] <= tau; prob: n host floats, tau in [0,
+ * 0.5)); the B current states and the B proposals are scored exactly and
+ * merged as in maxsat_up_end (stable sort by satisfied weight over [current,
+ * proposals], the last B become chains 0..B-1, a proposal keeps its chain's
+ * nu; the best-so-far is kept). Single-formula contexts; synchronises. */
+int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau);
+
 /* maxsat_reset, except that variable v of every chain starts True with
  * probability prob[v] (n host floats in [0, 1]): x = [u < P_v], P_v =
  * rint(65536 prob[v]) in FP64, u the same 16-bit initial draw as

@@ -431,6 +431,17 @@ def up_merge(inst: Instance, st: ChainState, up_x) -> ChainState:
     return st
 
 
+def flip_proposals(x, prob, tau):
+    """Each row of x with every confident variable set to the network's
+    value: 1 where prob >= 1 - tau, 0 where prob <= tau (prob compared in
+    FP32, as given)."""
+    prob = np.asarray(prob, np.float32)
+    out = np.array(x, np.uint8, copy=True)
+    out[:, prob >= np.float32(1.0) - np.float32(tau)] = 1
+    out[:, prob <= np.float32(tau)] = 0
+    return out
+
+
 def free_energy(inst, table, x, temp, n_buckets=1, fixed=False):
     """Formula free energy (Eq. 1) of each row of x at temperature `temp`;
     with fixed=True also its fixed-point form sum_c rint(2^20 F_c) (int64)."""

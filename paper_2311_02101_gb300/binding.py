@@ -81,6 +81,7 @@ def lib():
         L.maxsat_mp_destroy.argtypes = [P]
         L.maxsat_mp_destroy.restype = None
         L.maxsat_reset_probs.argtypes = [P, i32, u64, P]
+        L.maxsat_propose_flips.argtypes = [P, P, ctypes.c_float]
         L.maxsat_pt_swap.argtypes = [P, i32, ctypes.POINTER(i32)]
         L.maxsat_up_begin.argtypes = [P]
         L.maxsat_up_end.argtypes = [P]
@@ -107,6 +108,7 @@ def lib():
                      "maxsat_mp_create", "maxsat_mp_n_params", "maxsat_mp_set_params",
                      "maxsat_mp_get_params", "maxsat_mp_forward", "maxsat_mp_gradient",
                      "maxsat_mp_adam", "maxsat_reset_probs", "maxsat_pt_swap",
+                     "maxsat_propose_flips",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
                      "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
@@ -426,6 +428,12 @@ def maxsat_reset_probs(ctx: Context, restarts: int, seed: int, prob):
     _check(lib().maxsat_reset_probs(ctx.handle, int(restarts), int(seed) & (2 ** 64 - 1),
                                     _np_ptr(prob)), ctx)
     ctx.B = int(restarts)
+
+
+def maxsat_propose_flips(ctx: Context, prob, tau: float = 0.1):
+    prob = np.ascontiguousarray(prob, np.float32)
+    assert prob.size == ctx.n
+    _check(lib().maxsat_propose_flips(ctx.handle, _np_ptr(prob), float(tau)), ctx)
 
 
 def maxsat_get_path(ctx: Context) -> int:

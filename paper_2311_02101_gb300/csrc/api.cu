@@ -1422,6 +1422,70 @@ static int put_states(maxsat_ctx* ctx, const uint8_t* x, const float* nu) {
   return MAXSAT_OK;
 }
 
+// The appendix code's B-of-2B merge: cand holds 2B x n states whose second
+// half is filled by the caller; the first half receives the B current
+// states. All 2B are scored exactly; sorted by satisfied weight ascending
+// with a stable sort, the last B become chains 0..B-1 in that order, each
+// proposed state with the nu of the chain it came from.
+static int merge_candidates(maxsat_ctx* ctx, std::vector<uint8_t>& cand) {
+  const int B = ctx->C.B, n = ctx->n;
+  std::vector<float> nu((size_t)B * n);
+  std::vector<uint8_t> cur((size_t)B * n);
+  int rc = maxsat_get_state(ctx, cur.data(), nu.data(), nullptr, nullptr, nullptr, nullptr,
+                            nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  std::memcpy(cand.data(), cur.data(), cur.size());
+  if (cand.size() > ctx->up_cap) {
+    ctx->up_mem.release();
+    ctx->up_cap = 0;
+    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cand, cand.size()));
+    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cost, (size_t)2 * B));
+    ctx->up_cap = cand.size();
+  }
+  CK(ctx, cudaMemcpyAsync(ctx->d_up_cand, cand.data(), cand.size(), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  rc = maxsat_eval(ctx, ctx->d_up_cand, 2 * B, ctx->d_up_cost);
+  if (rc != MAXSAT_OK) return rc;
+  std::vector<int64_t> cost((size_t)2 * B);
+  CK(ctx, cudaMemcpyAsync(cost.data(), ctx->d_up_cost, 8 * cost.size(), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int32_t> rank((size_t)2 * B);
+  std::iota(rank.begin(), rank.end(), 0);
+  std::stable_sort(rank.begin(), rank.end(),
+                   [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  std::vector<uint8_t> nx((size_t)B * n);
+  std::vector<float> nnu((size_t)B * n);
+  for (int j = 0; j < B; ++j) {
+    const int32_t r = rank[(size_t)B + j];
+    std::memcpy(nx.data() + (size_t)j * n, cand.data() + (size_t)r * n, (size_t)n);
+    std::memcpy(nnu.data() + (size_t)j * n, nu.data() + (size_t)(r % B) * n, 4 * (size_t)n);
+  }
+  return put_states(ctx, nx.data(), nnu.data());
+}
+
+int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau) {
+  if (!ctx || !prob) return MAXSAT_EINVAL;
+  if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_propose_flips before maxsat_reset");
+  if (ctx->n_inst != 1) return fail(ctx, MAXSAT_EINVAL, "flip proposals run on single-formula contexts");
+  if (!(tau >= 0.f && tau < 0.5f)) return fail(ctx, MAXSAT_EINVAL, "tau must be in [0, 0.5)");
+  if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is pending");
+  const int B = ctx->C.B, n = ctx->n;
+  std::vector<uint8_t> cand((size_t)2 * B * n);
+  int rc = maxsat_get_state(ctx, cand.data() + (size_t)B * n, nullptr, nullptr, nullptr, nullptr,
+                            nullptr, nullptr);
+  if (rc != MAXSAT_OK) return rc;
+  // the proposal: every confident variable takes the network's value
+  for (int i = 0; i < n; ++i) {
+    const float p = prob[i];
+    if (p >= 1.f - tau)
+      for (int b = 0; b < B; ++b) cand[(size_t)(B + b) * n + i] = 1;
+    else if (p <= tau)
+      for (int b = 0; b < B; ++b) cand[(size_t)(B + b) * n + i] = 0;
+  }
+  return merge_candidates(ctx, cand);
+}
+
 int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_pt_swap before maxsat_reset");
@@ -1489,42 +1553,9 @@ int maxsat_up_end(maxsat_ctx* ctx) {
   const int B = ctx->up_B, n = ctx->n;
   if (!ctx->have_chains || ctx->C.B != B)
     return fail(ctx, MAXSAT_ESTATE, "the chains were reset during unit propagation");
-  // candidates: the B current states, then the B propagated ones
   std::vector<uint8_t> cand((size_t)2 * B * n);
-  std::vector<float> nu((size_t)B * n);
-  int rc = maxsat_get_state(ctx, cand.data(), nu.data(), nullptr, nullptr, nullptr, nullptr,
-                            nullptr);
-  if (rc != MAXSAT_OK) return rc;
   std::memcpy(cand.data() + (size_t)B * n, ctx->up_out.data(), (size_t)B * n);
-  if (cand.size() > ctx->up_cap) {
-    ctx->up_mem.release();
-    ctx->up_cap = 0;
-    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cand, cand.size()));
-    CK(ctx, ctx->up_mem.alloc(&ctx->d_up_cost, (size_t)2 * B));
-    ctx->up_cap = cand.size();
-  }
-  CK(ctx, cudaMemcpyAsync(ctx->d_up_cand, cand.data(), cand.size(), cudaMemcpyHostToDevice,
-                          ctx->stream));
-  rc = maxsat_eval(ctx, ctx->d_up_cand, 2 * B, ctx->d_up_cost);
-  if (rc != MAXSAT_OK) return rc;
-  std::vector<int64_t> cost((size_t)2 * B);
-  CK(ctx, cudaMemcpyAsync(cost.data(), ctx->d_up_cost, 8 * cost.size(), cudaMemcpyDeviceToHost,
-                          ctx->stream));
-  CK(ctx, cudaStreamSynchronize(ctx->stream));
-  // the appendix code's merge: satisfied weight ascending (stable), keep the
-  // last B in that order; a propagated state keeps its chain's nu
-  std::vector<int32_t> rank((size_t)2 * B);
-  std::iota(rank.begin(), rank.end(), 0);
-  std::stable_sort(rank.begin(), rank.end(),
-                   [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-  std::vector<uint8_t> nx((size_t)B * n);
-  std::vector<float> nnu((size_t)B * n);
-  for (int j = 0; j < B; ++j) {
-    const int32_t r = rank[(size_t)B + j];
-    std::memcpy(nx.data() + (size_t)j * n, cand.data() + (size_t)r * n, (size_t)n);
-    std::memcpy(nnu.data() + (size_t)j * n, nu.data() + (size_t)(r % B) * n, 4 * (size_t)n);
-  }
-  return put_states(ctx, nx.data(), nnu.data());
+  return merge_candidates(ctx, cand);
 }
 
 int maxsat_up(maxsat_ctx* ctx) {

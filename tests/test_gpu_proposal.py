@@ -149,3 +149,37 @@ def test_learned_start_reaches_lower_costs(ms, stream):
         ms.maxsat_destroy(ctx)
     assert np.mean(learned) < np.mean(plain)
     ms.maxsat_mp_destroy(model)
+
+
+def test_flip_proposals_match_oracle(ms, stream):
+    """Gibbs rounds, a flip-proposal merge with given probabilities, more
+    rounds: the oracle's same sequence gives the same chains."""
+    import os
+    n, off, lits, w = formula(seed=7, n=200, m=900)
+    table = oracle.RbmTable.load(os.path.join(os.path.dirname(__file__), "golden",
+                                              "or_rbm_params.txt"))
+    sets = [s for s in table.sets if s["len"] == 3]
+    params = ms.maxsat_default_params(sets=sets, n_temps=2, n_buckets=4)
+    params.fstar = None
+    ctx = ms.maxsat_create(n, off, lits, w, params, stream)
+    rng = np.random.default_rng(3)
+    prob = rng.random(n).astype(np.float32)
+    B, seed = 128, 4
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, 6)
+    ms.maxsat_propose_flips(ctx, prob, 0.15)
+    ms.maxsat_step(ctx, 4)
+    g = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    inst = oracle.Instance(n, off, lits, w)
+    t = oracle.RbmTable()
+    for s_ in sets:
+        t.add(s_["len"], s_["bucket"], s_["temp"], s_["W"], s_["b"])
+    st = oracle.init_chains(n, B, seed)
+    kw = dict(n_temps=2, n_buckets=4, threads=os.cpu_count() or 4)
+    oracle.gibbs(inst, t, st, 6, seed, **kw)
+    oracle.up_merge(inst, st, oracle.flip_proposals(st.x, prob, 0.15))
+    oracle.gibbs(inst, t, st, 4, seed, **kw)
+    assert np.array_equal(g["x"], st.x)
+    assert np.array_equal(g["best_cost"], st.best_cost)
+    assert np.array_equal(g["nu"], st.nu32)
