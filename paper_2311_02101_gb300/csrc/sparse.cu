@@ -128,12 +128,18 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   const int gb0 = C.g8_off * 8 + b0;
   const int e0 = FE ? temp_of(gb0, E, C.B_total, C.inv_B_total) : 0;
   const bool e_uniform = !FE || e0 == temp_of(gb0 + 7, E, C.B_total, C.inv_B_total);
-  // the 8 chains' temperatures, 6 bits each (E <= 64)
+  // UNI form of the clause loop (below) when every lane of the warp has one
+  // temperature; only the one-chunk kernel carries both forms (the longer
+  // records' kernel is at its register limit)
+  const bool warp_uni = !ONE || __all_sync(0xFFFFFFFFu, e_uniform);
+  // the 8 chains' temperatures, 6 bits each (E <= 64); filled for every lane
+  // of a warp that takes the per-chain form
   uint64_t epack = 0;
-  if (FE && !e_uniform) {
+  if (FE && (!ONE || !warp_uni)) {
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      epack |= (uint64_t)temp_of(gb0 + q, E, C.B_total, C.inv_B_total) << (6 * q);
+      epack |= (uint64_t)(e_uniform ? e0 : temp_of(gb0 + q, E, C.B_total, C.inv_B_total))
+               << (6 * q);
   }
   // the weighted unsat cost accumulates in this warp's shared-memory row
   // (each entry is owned by one thread), the free energy in registers
@@ -154,111 +160,125 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   uint32_t t = 0;
   if (SAMPLE) t = step_index(tdev, t_rel);
 
-  for (int c = c_begin + warp; c < c_end; c += 8) {
-    const int o = __ldg(F.cl_off + c);
-    const int len = __ldg(F.cl_off + c + 1) - o;
-    // byte q of lo0|lo1 (chains 0..3 | 4..7): bits 0..7 of chain q's truth
-    // pattern; of hi0|hi1: bits 8..15
-    uint32_t lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
-    if (len <= 4) {
-      // short clause: all literal and state loads in flight together
-      int32_t lv[4];
+  // the clause loop; UNI (all 8 chains of every lane of the warp share one
+  // temperature, the common case) drops the per-chain temperature unpacking
+  // from every clause. One-chunk records (ONE) are 4 words long.
+  auto clause_loop = [&](auto uni_tag) {
+    constexpr bool UNI = decltype(uni_tag)::value;
+    for (int c = c_begin + warp; c < c_end; c += 8) {
+      const int o = __ldg(F.cl_off + c);
+      const int len = __ldg(F.cl_off + c + 1) - o;
+      // byte q of lo0|lo1 (chains 0..3 | 4..7): bits 0..7 of chain q's truth
+      // pattern; of hi0|hi1: bits 8..15
+      uint32_t lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
+      if (len <= 4) {
+        // short clause: all literal and state loads in flight together
+        int32_t lv[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) lv[k] = k < len ? __ldg(F.lit_var + o + k) : 0;
-      uint2 x8[4];
+        for (int k = 0; k < 4; ++k) lv[k] = k < len ? __ldg(F.lit_var + o + k) : 0;
+        uint2 x8[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
-                              xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
-                        : make_uint2(0u, 0u);
+        for (int k = 0; k < 4; ++k)
+          x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
+                                xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
+                          : make_uint2(0u, 0u);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
-        lo0 |= (x8[k].x ^ flip) << k;
-        lo1 |= (x8[k].y ^ flip) << k;
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
+          lo0 |= (x8[k].x ^ flip) << k;
+          lo1 |= (x8[k].y ^ flip) << k;
+        }
+      } else {
+        for (int k = 0; k < len; ++k) {
+          const int32_t lv = __ldg(F.lit_var + o + k);
+          const uint2 x8 =
+              __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
+          const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
+          if (k < 8) {
+            lo0 |= (x8.x ^ flip) << k;
+            lo1 |= (x8.y ^ flip) << k;
+          } else {
+            hi0 |= (x8.x ^ flip) << (k - 8);
+            hi1 |= (x8.y ^ flip) << (k - 8);
+          }
+        }
       }
-    } else {
-      for (int k = 0; k < len; ++k) {
-        const int32_t lv = __ldg(F.lit_var + o + k);
-        const uint2 x8 =
-            __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
-        const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
-        if (k < 8) {
-          lo0 |= (x8.x ^ flip) << k;
-          lo1 |= (x8.y ^ flip) << k;
+      int p[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // result byte 0 = byte q of the low word, byte 1 = byte q of the high word
+        p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
+        p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
+      }
+      // unsatisfied clauses are rare once chains settle: touch the cost rows
+      // only when one of the 8 chains has p == 0
+      uint32_t unsat = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) unsat |= (uint32_t)(p[q] == 0) << q;
+      if (unsat) {
+        const int64_t wc = __ldg(F.cl_w + c);
+        if (MODE != kEval && C.cost32) {
+          // each entry has one owner: the atomic is a one-instruction add
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if ((unsat >> q) & 1u) atomicAdd(my_cost32 + q, (int)wc);
         } else {
-          hi0 |= (x8.x ^ flip) << (k - 8);
-          hi1 |= (x8.y ^ flip) << (k - 8);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if ((unsat >> q) & 1u) my_cost[q] += wc;
+        }
+      }
+      if (!FE || len == 0) continue;
+
+      const int grp = __ldg(F.cl_grp + c);
+      const GroupMeta gm = meta[grp];
+      int row[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        row[q] = ((UNI ? e0 : (int)((epack >> (6 * q)) & 63u)) << len) + p[q];
+      if constexpr (!SAMPLE) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) fe[q] += __uint_as_float(rec[gm.rec_off + row[q] * (ONE ? 4 : gm.stride)]);
+      } else {
+        // free energy (record word 0) and hidden draws from the records
+        const uint4* tab = reinterpret_cast<const uint4*>(rec + gm.rec_off);
+        int row4[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) row4[q] = ONE ? row[q] : row[q] * (gm.stride >> 2);
+        uint32_t hp[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) hp[q] = 0;
+        const uint32_t octet = (uint32_t)(g8 + C.g8_off);
+        const int chunks = ONE ? 1 : gm.stride >> 2;
+        const uint32_t lc = (uint32_t)(c - cl_base);  // clause index within its instance
+        if (!gm.sat)
+          hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
+        else
+          hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
+        HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
+        if (sizeof(HT) == 1) {
+          uint64_t v = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v |= (uint64_t)hp[q] << (8 * q);
+          *reinterpret_cast<uint64_t*>(H) = v;
+        } else {
+          uint4 v;
+          v.x = hp[0] | (hp[1] << 16);
+          v.y = hp[2] | (hp[3] << 16);
+          v.z = hp[4] | (hp[5] << 16);
+          v.w = hp[6] | (hp[7] << 16);
+          *reinterpret_cast<uint4*>(H) = v;
         }
       }
     }
-    int p[8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      // result byte 0 = byte q of the low word, byte 1 = byte q of the high word
-      p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
-      p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
-    }
-    // unsatisfied clauses are rare once chains settle: touch the cost rows
-    // only when one of the 8 chains has p == 0
-    uint32_t unsat = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) unsat |= (uint32_t)(p[q] == 0) << q;
-    if (unsat) {
-      const int64_t wc = __ldg(F.cl_w + c);
-      if (MODE != kEval && C.cost32) {
-        // each entry has one owner: the atomic is a one-instruction add
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((unsat >> q) & 1u) atomicAdd(my_cost32 + q, (int)wc);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if ((unsat >> q) & 1u) my_cost[q] += wc;
-      }
-    }
-    if (!FE || len == 0) continue;
-
-    const int grp = __ldg(F.cl_grp + c);
-    const GroupMeta gm = meta[grp];
-    int row[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      row[q] = ((e_uniform ? e0 : (int)((epack >> (6 * q)) & 63u)) << len) + p[q];
-    if constexpr (!SAMPLE) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) fe[q] += __uint_as_float(rec[gm.rec_off + row[q] * gm.stride]);
-    } else {
-      // free energy (record word 0) and hidden draws from the records
-      const uint4* tab = reinterpret_cast<const uint4*>(rec + gm.rec_off);
-      int row4[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) row4[q] = row[q] * (gm.stride >> 2);
-      uint32_t hp[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) hp[q] = 0;
-      const uint32_t octet = (uint32_t)(g8 + C.g8_off);
-      const int chunks = gm.stride >> 2;
-      const uint32_t lc = (uint32_t)(c - cl_base);  // clause index within its instance
-      if (!gm.sat)
-        hidden_draws<false, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
-      else
-        hidden_draws<true, ONE>(tab, row4, chunks, gm.nh, lc, octet, t, phase_h, C.keys, hp, fe);
-      HT* H = static_cast<HT*>(C.H) + (size_t)c * Bp + b0;
-      if (sizeof(HT) == 1) {
-        uint64_t v = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v |= (uint64_t)hp[q] << (8 * q);
-        *reinterpret_cast<uint64_t*>(H) = v;
-      } else {
-        uint4 v;
-        v.x = hp[0] | (hp[1] << 16);
-        v.y = hp[2] | (hp[3] << 16);
-        v.z = hp[4] | (hp[5] << 16);
-        v.w = hp[6] | (hp[7] << 16);
-        *reinterpret_cast<uint4*>(H) = v;
-      }
-    }
+  };
+  if constexpr (ONE) {
+    if (warp_uni)
+      clause_loop(std::true_type{});
+    else
+      clause_loop(std::false_type{});
+  } else {
+    clause_loop(std::false_type{});
   }
 
   // per-block partial sums, then the block that arrives last among its
