@@ -914,6 +914,22 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   UP(cl_w, F.cl_w);
   UP(var_off, F.var_off);
   UP(var_inc, F.var_inc);
+  F.cl4 = nullptr;
+  if (T.one_chunk) {
+    // one 16-byte record per clause for the one-chunk gather
+    std::vector<int4> cl4(m);
+    for (int64_t c = 0; c < m; ++c) {
+      const int32_t len = cl_off[c + 1] - cl_off[c];
+      if (len > 3 || (len > 0 && cl_grp[c] < 0)) {
+        delete ctx;
+        return fail(nullptr, MAXSAT_EINVAL, "internal: clause record of a long clause");
+      }
+      int32_t lv[3] = {0, 0, 0};
+      for (int32_t k = 0; k < len; ++k) lv[k] = lit_var[cl_off[c] + k];
+      cl4[c] = make_int4(lv[0], lv[1], lv[2], len > 0 ? (cl_grp[c] << 2) | len : 0);
+    }
+    UP(cl4, F.cl4);
+  }
   F.n_inst = n_inst;
   F.var_inst = nullptr;
   if (n_inst > 1) {

@@ -51,6 +51,9 @@ struct DevFormula {
   const int4* var_inc;     // incidence of a variable: {clause, gq_off + position
                            // (bit 31 set when negated), clause length K,
                            // per-temperature stride 2^L K of gq}
+  const int4* cl4;         // m clause records {lit_var of literals 0..2 (0 when
+                           // absent), group << 2 | length} when every clause has
+                           // at most 3 literals (one-chunk tables); else NULL
 };
 
 // Work list of the clause gather: blocks of consecutive clauses that never

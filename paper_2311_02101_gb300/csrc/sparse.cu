@@ -165,50 +165,82 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   // from every clause. One-chunk records (ONE) are 4 words long.
   auto clause_loop = [&](auto uni_tag) {
     constexpr bool UNI = decltype(uni_tag)::value;
+    // ONE: a clause's literals, length and group come from its 16-byte clause
+    // record, loaded one iteration ahead (the state loads then wait on nothing)
+    int4 nxt = make_int4(0, 0, 0, 0);
+    if constexpr (ONE)
+      if (c_begin + warp < c_end) nxt = __ldg(F.cl4 + c_begin + warp);
     for (int c = c_begin + warp; c < c_end; c += 8) {
-      const int o = __ldg(F.cl_off + c);
-      const int len = __ldg(F.cl_off + c + 1) - o;
+      int len, grp_one = 0;
       // byte q of lo0|lo1 (chains 0..3 | 4..7): bits 0..7 of chain q's truth
       // pattern; of hi0|hi1: bits 8..15
       uint32_t lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
-      if (len <= 4) {
-        // short clause: all literal and state loads in flight together
-        int32_t lv[4];
+      if constexpr (ONE) {
+        const int4 cur = nxt;
+        if (c + 8 < c_end) nxt = __ldg(F.cl4 + c + 8);
+        len = cur.w & 3;
+        grp_one = cur.w >> 2;
+        const int32_t lv[3] = {cur.x, cur.y, cur.z};
+        uint2 x8[3];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) lv[k] = k < len ? __ldg(F.lit_var + o + k) : 0;
-        uint2 x8[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 3; ++k)
           x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
                                 xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
                           : make_uint2(0u, 0u);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 3; ++k) {
           const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
           lo0 |= (x8[k].x ^ flip) << k;
           lo1 |= (x8[k].y ^ flip) << k;
         }
       } else {
-        for (int k = 0; k < len; ++k) {
-          const int32_t lv = __ldg(F.lit_var + o + k);
-          const uint2 x8 =
-              __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
-          const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
-          if (k < 8) {
-            lo0 |= (x8.x ^ flip) << k;
-            lo1 |= (x8.y ^ flip) << k;
-          } else {
-            hi0 |= (x8.x ^ flip) << (k - 8);
-            hi1 |= (x8.y ^ flip) << (k - 8);
+        const int o = __ldg(F.cl_off + c);
+        len = __ldg(F.cl_off + c + 1) - o;
+        if (len <= 4) {
+          // short clause: all literal and state loads in flight together
+          int32_t lv[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) lv[k] = k < len ? __ldg(F.lit_var + o + k) : 0;
+          uint2 x8[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
+                                  xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
+                            : make_uint2(0u, 0u);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
+            lo0 |= (x8[k].x ^ flip) << k;
+            lo1 |= (x8[k].y ^ flip) << k;
+          }
+        } else {
+          for (int k = 0; k < len; ++k) {
+            const int32_t lv = __ldg(F.lit_var + o + k);
+            const uint2 x8 =
+                __ldg(reinterpret_cast<const uint2*>(xt + (size_t)(lv & 0x7FFFFFFF) * Bp + b0));
+            const uint32_t flip = lv < 0 ? 0x01010101u : 0u;
+            if (k < 8) {
+              lo0 |= (x8.x ^ flip) << k;
+              lo1 |= (x8.y ^ flip) << k;
+            } else {
+              hi0 |= (x8.x ^ flip) << (k - 8);
+              hi1 |= (x8.y ^ flip) << (k - 8);
+            }
           }
         }
       }
       int p[8];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        // result byte 0 = byte q of the low word, byte 1 = byte q of the high word
-        p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
-        p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
+        if constexpr (ONE) {
+          // byte q of the low word, zero-extended (selector 4: byte 0 of 0)
+          p[q] = (int)__byte_perm(lo0, 0u, 0x4440u | q);
+          p[q + 4] = (int)__byte_perm(lo1, 0u, 0x4440u | q);
+        } else {
+          // result byte 0 = byte q of the low word, byte 1 = byte q of the high word
+          p[q] = (int)(__byte_perm(lo0, hi0, ((4u + q) << 4) | q) & 0xFFFFu);
+          p[q + 4] = (int)(__byte_perm(lo1, hi1, ((4u + q) << 4) | q) & 0xFFFFu);
+        }
       }
       // unsatisfied clauses are rare once chains settle: touch the cost rows
       // only when one of the 8 chains has p == 0
@@ -230,7 +262,7 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
       }
       if (!FE || len == 0) continue;
 
-      const int grp = __ldg(F.cl_grp + c);
+      const int grp = ONE ? grp_one : __ldg(F.cl_grp + c);
       const GroupMeta gm = meta[grp];
       int row[8];
 #pragma unroll

@@ -102,15 +102,16 @@ def assert_same(gpu, ora, T, alpha, rows=None):
     assert np.array_equal(g["nu"], ora.nu32), "nu (FP32 sequence)"
 
 
-def edge_instance(seed=0):
-    """Random clauses of lengths 1..4 plus duplicates, a tautology, an empty
-    clause, a variable in no clause, and weights spanning several buckets."""
+def edge_instance(seed=0, kmax=4):
+    """Random clauses of lengths 1..kmax plus duplicates, a tautology, an empty
+    clause, a variable in no clause, and weights spanning several buckets
+    (kmax = 3: every clause has one-chunk tables and a 16-byte clause record)."""
     rng = np.random.default_rng(seed)
     n = 37
-    lengths = rng.integers(1, 5, size=150)
+    lengths = rng.integers(1, kmax + 1, size=150)
     _, off, lits, _ = workloads.from_lengths(n - 1, lengths, rng)
     cl = [list(lits[off[c]:off[c + 1]]) for c in range(len(lengths))]
-    cl += [[3, 3, -5], [7, -7], [], [-2, -2, -2, 9], [12]]
+    cl += [[3, 3, -5], [7, -7], [], [12]] + ([[-2, -2, -2, 9]] if kmax >= 4 else [])
     w = list(rng.integers(1, 40, size=len(cl)))
     return oracle.Instance.from_clauses(n, cl, w)
 
@@ -190,8 +191,9 @@ def test_trajectory_3sat(ms, stream, small_table, B):
     assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
 
 
-def test_trajectory_edge_cases(ms, stream, small_table):
-    inst = edge_instance(1)
+@pytest.mark.parametrize("kmax", [3, 4])
+def test_trajectory_edge_cases(ms, stream, small_table, kmax):
+    inst = edge_instance(1, kmax)
     T, seed, B = 25, 3, 40
     gpu = run_gpu(ms, stream, inst, small_table, B, T, seed, alpha=0.05)
     assert_same(gpu, run_oracle(inst, small_table, B, T, seed, alpha=0.05), T, 0.05)
