@@ -632,9 +632,11 @@ int build_dense(maxsat_ctx* ctx, int32_t n, int64_t m, const int64_t* off, const
   }
   // contributions as 16-bit floating-point bit patterns (exact: integers
   // below 2^8 in BF16, below 2^11 in FP16)
-  std::vector<uint16_t> gq16(ctx->tabs.gq.size());
+  // (both halves hold the positive values: the sign is in A2)
+  const size_t gq_len = ctx->tabs.gq.size();
+  std::vector<uint16_t> gq16(2 * gq_len);
   for (size_t k = 0; k < gq16.size(); ++k) {
-    const int v = ctx->tabs.gq[k];
+    const int v = ctx->tabs.gq[k % gq_len];
     uint16_t bits = 0;
     if (v != 0) {
       const unsigned av = (unsigned)(v < 0 ? -v : v);
@@ -873,8 +875,12 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
         const int32_t l = lits[j];
         const int32_t v = (l > 0 ? l : -l) - 1;
         const int32_t k = (int32_t)(j - off[c]);
-        var_inc[fill[v]++] = make_int4((int32_t)c, (gm.gq_off + k) | (l < 0 ? (int32_t)0x80000000 : 0),
-                                       gm.len, (1 << gm.nh) * gm.len);
+        // a negated literal points into the table's negated half
+        const int32_t gq_len = (int32_t)ctx->tabs.gq.size();
+        var_inc[fill[v]++] =
+            make_int4((int32_t)c,
+                      l < 0 ? (gm.gq_off + gq_len + k) | (int32_t)0x80000000 : gm.gq_off + k,
+                      gm.len, (1 << gm.nh) * gm.len);
       }
     }
   }
@@ -941,7 +947,13 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   UP(ctx->tabs.meta, T.meta);
   UP(ctx->tabs.rec, T.rec);
   UP(ctx->tabs.feq, T.feq);
-  UP(ctx->tabs.gq, T.gq);
+  {
+    // two-sided contribution table of the sparse visible update: a negated
+    // literal adds the second, negated half, so its sum needs no sign
+    std::vector<int16_t> gq2(ctx->tabs.gq);
+    for (int16_t v : ctx->tabs.gq) gq2.push_back((int16_t)-v);
+    UP(gq2, T.gq);
+  }
   UP(ctx->tabs.pv, T.pv);
 #define UP2(vec, dst)                                         \
   do {                                                        \

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
   const uint16_t* gq = a.gq16;
   const uint32_t* pv = T.pv;
   if (SM) {
-    const int gb = align16(T.gq_len * 2);
+    const int gb = align16(T.gq_len * 4);  // both halves
     stage16(tabs, a.gq16, gb, threadIdx.x, blockDim.x);
     stage16(tabs + gb, T.pv, align16(T.pv_len * 4), threadIdx.x, blockDim.x);
     gq = reinterpret_cast<const uint16_t*>(tabs);
@@ -814,7 +814,7 @@ cudaError_t launch_gemm2(const CUtensorMap& tmA2, int n, int n_pad, int B, int B
   a.tdev = tdev;
   a.t_rel = t_rel;
   a.err = err;
-  const int tb = align16(T.gq_len * 2) + align16(T.pv_len * 4);
+  const int tb = align16(T.gq_len * 4) + align16(T.pv_len * 4);
   const int grid = std::min(sm_count(), a.tiles_v * a.tiles_n);
   if (wide) {
     const int base_smem = 1024 + G2Stage<uint16_t>::kTabOff;

@@ -49,7 +49,8 @@ struct DevFormula {
   int32_t n_inst;          // formulas in the batch (1 for a single formula)
   const int2* var_inst;    // n: {instance, index within it}; NULL for one formula
   const int4* var_inc;     // incidence of a variable: {clause, gq_off + position
-                           // (bit 31 set when negated), clause length K,
+                           // (+ gq_len and bit 31 set when negated: the
+                           // table's negated half), clause length K,
                            // per-temperature stride 2^L K of gq}
   const int4* cl4;         // m clause records {lit_var of literals 0..2 (0 when
                            // absent), group << 2 | length} when every clause has
@@ -75,7 +76,8 @@ struct DevTables {
   int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
   const GroupMeta* meta;
   const uint32_t* rec;
-  const int16_t* gq;
+  const int16_t* gq;   // 2 gq_len entries: 2^Q G, then -2^Q G (a negated
+                       // literal's incidence reads the second half)
   const uint32_t* pv;
 };
 

@@ -374,18 +374,20 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size
 }
 
 constexpr int kVisBatch = 4;
+static_assert(32 % kVisBatch == 0, "incidence windows hold whole batches");
 
 template <bool SM, typename HT>
 __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
                                                  uint32_t t_rel, int vg0) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int4 s_inc[8][32];  // per warp: a window of its variable's incidences
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
   const int16_t* gq = T.gq;
   const uint32_t* pv = T.pv;
   if (SM) {
-    const int gb = align16(T.gq_len * 2);
+    const int gb = align16(T.gq_len * 4);  // both halves
     stage(smem, T.gq, gb);
     stage(smem + gb, T.pv, align16(T.pv_len * 4));
     __syncthreads();
@@ -412,7 +414,8 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
   const int j_begin = __ldg(F.var_off + i), j_end = __ldg(F.var_off + i + 1);
   // z += sgn * 2^Q G[e][pattern][slot] over the variable's incidences
   // (clause inc.x, table base | sign inc.y, stride K inc.z, per-temperature
-  // stride 2^L K inc.w). UNI: the 8 chains share temperature e0.
+  // stride 2^L K inc.w); a negated literal's base lies in the table's negated
+  // half, so the sum is plain adds. UNI: the 8 chains share temperature e0.
   auto sums = [&](auto uni) {
     constexpr bool UNI = decltype(uni)::value;
     int e[8];
@@ -420,23 +423,27 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
 #pragma unroll
       for (int q = 0; q < 8; ++q) e[q] = temp_of(gb0 + q, T.n_temps, C.B_total, C.inv_B_total);
     }
-    // kVisBatch incidences per pass, their record and pattern loads in
-    // flight together; the last pass is predicated (warp-uniform)
+    // the variable's incidences pass through this warp's shared-memory slot
+    // 32 at a time (one coalesced load); kVisBatch (a divisor of 32) per
+    // pass, their pattern loads in flight together, the last pass predicated
+    // (warp-uniform)
     for (int jj = j_begin; jj < j_end; jj += kVisBatch) {
-      int4 inc[kVisBatch];
-#pragma unroll
-      for (int u = 0; u < kVisBatch; ++u)
-        inc[u] = jj + u < j_end ? __ldg(F.var_inc + jj + u) : make_int4(0, 0, 0, 0);
+      const int w = (jj - j_begin) & 31;
+      if (w == 0) {
+        __syncwarp();
+        if (jj + lane < j_end) s_inc[warp][lane] = __ldg(F.var_inc + jj + lane);
+        __syncwarp();
+      }
       HV v[kVisBatch];
 #pragma unroll
       for (int u = 0; u < kVisBatch; ++u)
         if (jj + u < j_end)
-          v[u] = __ldg(reinterpret_cast<const HV*>(H + (size_t)inc[u].x * C.Bp + b0));
+          v[u] = __ldg(reinterpret_cast<const HV*>(H + (size_t)s_inc[warp][w + u].x * C.Bp + b0));
 #pragma unroll
       for (int u = 0; u < kVisBatch; ++u) {
         if (jj + u >= j_end) break;
-        const int base = inc[u].y & 0x7FFFFFFF;
-        const int sgn = inc[u].y < 0 ? -1 : 1;
+        const int4 inc = s_inc[warp][w + u];
+        const int base = inc.y & 0x7FFFFFFF;
         uint32_t hp[8];
         if constexpr (sizeof(HT) == 1) {
 #pragma unroll
@@ -447,19 +454,32 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
           for (int q = 0; q < 8; ++q) hp[q] = (wv[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
         }
         if constexpr (UNI) {
-          const int bo = base + e0 * inc[u].w;
+          if constexpr (SM) {
+            // byte offsets into the staged table: one multiply-add per address
+            const unsigned char* tb =
+                reinterpret_cast<const unsigned char*>(gq + base + e0 * inc.w);
+            const int k2 = 2 * inc.z;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) z[q] += sgn * (int)gq[bo + (int)hp[q] * inc[u].z];
+            for (int q = 0; q < 8; ++q)
+              z[q] += (int)*reinterpret_cast<const int16_t*>(tb + (int)hp[q] * k2);
+          } else {
+            const int bo = base + e0 * inc.w;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) z[q] += (int)gq[bo + (int)hp[q] * inc.z];
+          }
         } else {
 #pragma unroll
           for (int q = 0; q < 8; ++q)
-            z[q] += sgn * (int)gq[base + e[q] * inc[u].w + (int)hp[q] * inc[u].z];
+            z[q] += (int)gq[base + e[q] * inc.w + (int)hp[q] * inc.z];
         }
       }
     }
   };
-  if (e_uni) sums(std::true_type{});
-  else sums(std::false_type{});
+  // one form per warp: its lanes share the incidence window
+  if (__all_sync(0xFFFFFFFFu, e_uni))
+    sums(std::true_type{});
+  else
+    sums(std::false_type{});
   keep_improved(C, vi.x, o, b0, xold);
 
   const uint4 r =
@@ -519,7 +539,7 @@ int gather_smem_bytes(const DevTables& T) {
 }
 
 int visible_smem_bytes(const DevTables& T) {
-  return align16(T.gq_len * 2) + align16(T.pv_len * 4);
+  return align16(T.gq_len * 4) + align16(T.pv_len * 4);
 }
 
 constexpr int kSmemLimit = 160 * 1024;

@@ -123,7 +123,8 @@ std::string build_tables(const std::vector<RbmSet>& sets, int E, int Q,
           if (std::abs(acc) > T->gq_absmax) T->gq_absmax = std::abs(acc);
         }
       }
-      if (T->rec.size() > (size_t)INT32_MAX / 4 || T->gq.size() > (size_t)INT32_MAX / 2)
+      // byte counts of the tables (gq: two-sided on the device) fit an int
+      if (T->rec.size() > (size_t)INT32_MAX / 4 || T->gq.size() > (size_t)INT32_MAX / 4)
         return "tables too large";
     }
   }
