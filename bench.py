@@ -686,22 +686,25 @@ def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20)
     Table "RbmSAT - UP"): Gibbs alone vs Gibbs with a unit-propagation round
     sent every `upp` rounds and merged `upw` rounds later (the host works
     while the GPU samples). Same seed, same seconds; lowest best cost over
-    all chains. Also the host time of one propagation round."""
+    all chains. Propagation and merge on the GPU ("gibbs+up") and on host
+    threads as in the paper ("gibbs+up_host"); the wall time of one
+    propagation round (begin to end, including the upw rounds between)."""
     secs = args.fixed_seconds
-    p = ms.maxsat_default_params(sets=sets)
     out = dict(upp=upp, upw=upw, seconds=secs, chains=B)
-    for mode in ("gibbs", "gibbs+up"):
+    for mode in ("gibbs", "gibbs+up", "gibbs+up_host"):
+        p = ms.maxsat_default_params(sets=sets, up_device=0 if mode == "gibbs+up_host" else 1)
         ctx = ms.maxsat_create(n, off, lits, w, p, stream)
         ms.maxsat_reset(ctx, B, 99)
         rounds, ups, t_up = 0, 0, 0.0
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < secs:
-            if mode == "gibbs+up":
+            if mode != "gibbs":
                 ms.maxsat_step(ctx, upp - upw)
                 ta = time.perf_counter()
                 ms.maxsat_up_begin(ctx)
                 ms.maxsat_step(ctx, upw)
                 ms.maxsat_up_end(ctx)
+                stream.synchronize()
                 t_up += time.perf_counter() - ta
                 ups += 1
             else:

@@ -100,6 +100,14 @@ typedef struct {
                             states and draws do not depend on the blocking;
                             the free energy's float summation order does.
                             Default 0 (the wave-fitted size) */
+  int32_t up_device;     /* 1: maxsat_up_begin / maxsat_up_end run unit
+                            propagation and the merge on the GPU when the
+                            chains are on the sparse path and one chain's
+                            ranking state (8 n_pad + 5 n bytes, n_pad = n
+                            rounded up to a power of two) fits in 200 KB of
+                            shared memory; otherwise, and with 0, on host
+                            threads as the paper does. Same results either
+                            way. Default 1 */
 } maxsat_params;
 
 typedef struct maxsat_ctx maxsat_ctx;
@@ -241,10 +249,12 @@ int maxsat_set_state(maxsat_ctx* ctx, int32_t restarts, uint64_t seed,
 int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted);
 
 /* Prioritized unit propagation with the B-of-2B merge (Sec. 4.4; the
- * appendix code's send / fetch / merge). maxsat_up_begin copies the chains'
- * states x and their nu to the host and starts unit propagation on host
- * threads (it returns at once; maxsat_step may run meanwhile, as the paper
- * keeps sampling while the host works). For each chain: variables ranked by
+ * appendix code's send / fetch / merge). maxsat_up_begin takes a snapshot of
+ * the chains' states x and their nu and starts unit propagation: on the GPU
+ * (params.up_device, one warp per chain on a side stream; the snapshot is a
+ * device copy ordered on the context's stream), else on host threads after
+ * copying the snapshot to the host. It returns at once; maxsat_step may run
+ * meanwhile, as the paper keeps sampling while the host works. For each chain: variables ranked by
  * nu, highest first (ties to the lower index); the top floor(n/2) keep their
  * values; unit clauses are propagated first in, first out; the remaining
  * variables, in rank order, take their values from x when still unassigned,
@@ -256,7 +266,9 @@ int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted);
  * chain it came from. The best-so-far of each chain is kept. maxsat_up is
  * begin + end. Single-formula contexts only (MAXSAT_EINVAL for a batch);
  * MAXSAT_ESTATE without chains, for a second begin, for end without begin,
- * or when the chains were reset in between. Synchronises. */
+ * or when the chains were reset in between. The host form synchronises; the
+ * GPU form's merge is ordered on the context's stream (scoring with the
+ * sparse eval gather, a stable rank by counting, a column permutation). */
 int maxsat_up_begin(maxsat_ctx* ctx);
 int maxsat_up_end(maxsat_ctx* ctx);
 int maxsat_up(maxsat_ctx* ctx);

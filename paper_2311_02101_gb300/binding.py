@@ -45,7 +45,8 @@ class maxsat_params(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("quant_bits", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("fit_iters", ctypes.c_int32),
                 ("n_sets", ctypes.c_int32), ("sets", ctypes.POINTER(maxsat_rbm_set)),
-                ("steps_per_graph", ctypes.c_int32), ("tune_blocks", ctypes.c_int32)]
+                ("steps_per_graph", ctypes.c_int32), ("tune_blocks", ctypes.c_int32),
+                ("up_device", ctypes.c_int32)]
 
 
 _lib = None

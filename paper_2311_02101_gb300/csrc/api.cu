@@ -99,6 +99,22 @@ struct maxsat_ctx {
   uint8_t* d_up_cand = nullptr;
   int64_t* d_up_cost = nullptr;
   size_t up_cap = 0;
+  // unit propagation on the GPU (sparse path): occurrence lists, snapshot,
+  // candidates (n x Bp2: current states, then propagated ones), their costs
+  // and the merge permutation; a side stream with its events
+  bool up_on_gpu = false;  // the pending round runs on the GPU
+  DevAllocs upg_formula;
+  int32_t* d_occ_off = nullptr;
+  int32_t* d_occ = nullptr;
+  DevAllocs upg_mem;
+  int upg_Bp = 0;
+  uint8_t* d_upg_xs = nullptr;
+  float* d_upg_nus = nullptr;
+  uint8_t* d_upg_cand = nullptr;
+  int64_t* d_upg_cost = nullptr;
+  int32_t* d_upg_perm = nullptr;
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_ev_snap = nullptr, up_ev_done = nullptr;
   int n_inst = 1;                      // formulas in the batch
   std::vector<int32_t> inst_var_base;  // n_inst + 1 first variable of each formula
   std::vector<int32_t> inst_cl_base;   // n_inst + 1 first clause of each formula
@@ -686,6 +702,7 @@ void maxsat_default_params(maxsat_params* p) {
   p->sets = nullptr;
   p->steps_per_graph = 500;
   p->tune_blocks = 0;
+  p->up_device = 1;
 }
 
 const char* maxsat_last_error(const maxsat_ctx* ctx) {
@@ -1204,6 +1221,20 @@ int maxsat_kernel_times(maxsat_ctx* ctx, int32_t max_kernels, char* names, int64
   return k;
 }
 
+// sparse eval scratch for Bp chains (grown on demand)
+static int ensure_eval_scratch(maxsat_ctx* ctx, int Bp) {
+  if (Bp <= ctx->ev_Bp) return MAXSAT_OK;
+  ctx->eval_mem.release();
+  ctx->ev_Bp = 0;
+  const size_t ntk = (size_t)ctx->n_inst * (Bp / kChainTile);
+  CK(ctx, ctx->eval_mem.alloc(&ctx->ev_xt, (size_t)ctx->n * Bp));
+  CK(ctx, ctx->eval_mem.alloc(&ctx->ev_part, (size_t)ctx->ev_plan.n_blk * Bp));
+  CK(ctx, ctx->eval_mem.alloc(&ctx->ev_tickets, ntk));
+  CK(ctx, cudaMemsetAsync(ctx->ev_tickets, 0, sizeof(int32_t) * ntk, ctx->stream));
+  ctx->ev_Bp = Bp;
+  return MAXSAT_OK;
+}
+
 int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* cost_dev) {
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
@@ -1234,17 +1265,8 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
     return MAXSAT_OK;
   }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
-  const int nblk = ctx->ev_plan.n_blk;
-  if (Bp > ctx->ev_Bp) {
-    ctx->eval_mem.release();
-    ctx->ev_Bp = 0;
-    const size_t ntk = (size_t)ctx->n_inst * (Bp / kChainTile);
-    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_xt, (size_t)ctx->n * Bp));
-    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_part, (size_t)nblk * Bp));
-    CK(ctx, ctx->eval_mem.alloc(&ctx->ev_tickets, ntk));
-    CK(ctx, cudaMemsetAsync(ctx->ev_tickets, 0, sizeof(int32_t) * ntk, ctx->stream));
-    ctx->ev_Bp = Bp;
-  }
+  const int rc = ensure_eval_scratch(ctx, Bp);
+  if (rc != MAXSAT_OK) return rc;
   CK(ctx, launch_transpose_in(assign_dev, B, ctx->n, ctx->ev_xt, Bp, ctx->stream));
   CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->ev_xt, B, Bp, ctx->ev_plan, nullptr, 0,
                         ctx->ev_part, nullptr, ctx->ev_tickets, cost_dev, ctx->wide_h,
@@ -1552,12 +1574,94 @@ int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
   return MAXSAT_OK;
 }
 
+// GPU round: snapshot of x and nu on the context's stream, propagation on
+// the side stream (the Gibbs rounds may run meanwhile), merge on the
+// context's stream after it.
+static int up_begin_gpu(maxsat_ctx* ctx) {
+  const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
+  const int Bp2 = (2 * B + kChainTile - 1) / kChainTile * kChainTile;
+  if (!ctx->d_occ_off) {
+    std::vector<int32_t> oo(ctx->upf.occ_off.size()), oc(ctx->upf.occ.size());
+    for (size_t i = 0; i < oo.size(); ++i) oo[i] = (int32_t)ctx->upf.occ_off[i];
+    for (size_t k = 0; k < oc.size(); ++k) oc[k] = ctx->upf.occ[k] & 0x7FFFFFFF;
+    CK(ctx, ctx->upg_formula.alloc(&ctx->d_occ_off, oo.size()));
+    CK(ctx, ctx->upg_formula.alloc(&ctx->d_occ, oc.size()));
+    CK(ctx, cudaMemcpy(ctx->d_occ_off, oo.data(), 4 * oo.size(), cudaMemcpyHostToDevice));
+    if (!oc.empty())
+      CK(ctx, cudaMemcpy(ctx->d_occ, oc.data(), 4 * oc.size(), cudaMemcpyHostToDevice));
+  }
+  if (!ctx->up_stream) {
+    CK(ctx, cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->up_ev_snap, cudaEventDisableTiming));
+    CK(ctx, cudaEventCreateWithFlags(&ctx->up_ev_done, cudaEventDisableTiming));
+  }
+  if (ctx->upg_Bp != Bp2) {
+    // the previous round's kernels are done (merge waited on them)
+    CK(ctx, cudaStreamSynchronize(ctx->up_stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->upg_mem.release();
+    ctx->upg_Bp = 0;
+    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_xs, (size_t)n * Bp));
+    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_nus, (size_t)n * Bp));
+    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cand, (size_t)n * Bp2));
+    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, (size_t)Bp2));
+    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, (size_t)Bp2));  // B <= Bp2 / 2 for this Bp2
+    ctx->upg_Bp = Bp2;
+  }
+  CK(ctx, cudaMemcpyAsync(ctx->d_upg_xs, ctx->C.xt, (size_t)n * Bp, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  CK(ctx, cudaMemcpyAsync(ctx->d_upg_nus, ctx->C.nu, sizeof(float) * n * Bp,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(ctx, cudaEventRecord(ctx->up_ev_snap, ctx->stream));
+  CK(ctx, cudaStreamWaitEvent(ctx->up_stream, ctx->up_ev_snap, 0));
+  UpDev U;
+  U.n = n;
+  U.m = ctx->m;
+  U.cl_off = ctx->F.cl_off;
+  U.lit_var = ctx->F.lit_var;
+  U.occ_off = ctx->d_occ_off;
+  U.occ = ctx->d_occ;
+  CK(ctx, launch_up_chains(U, ctx->d_upg_xs, ctx->d_upg_nus, Bp, B, ctx->d_upg_cand, Bp2, B,
+                           ctx->up_stream));
+  CK(ctx, cudaEventRecord(ctx->up_ev_done, ctx->up_stream));
+  ctx->up_B = B;
+  ctx->up_pending = true;
+  ctx->up_on_gpu = true;
+  return MAXSAT_OK;
+}
+
+static int up_end_gpu(maxsat_ctx* ctx) {
+  ctx->up_pending = false;
+  ctx->up_on_gpu = false;
+  CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->up_ev_done, 0));
+  const int B = ctx->up_B, n = ctx->n;
+  if (!ctx->have_chains || ctx->C.B != B || ctx->dense)
+    return fail(ctx, MAXSAT_ESTATE, "the chains were reset during unit propagation");
+  const int Bp = ctx->C.Bp, Bp2 = ctx->upg_Bp;
+  // candidates 0..B-1: the current states
+  CK(ctx, cudaMemcpy2DAsync(ctx->d_upg_cand, Bp2, ctx->C.xt, Bp, B, n, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  const int rc = ensure_eval_scratch(ctx, Bp2);
+  if (rc != MAXSAT_OK) return rc;
+  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->d_upg_cand, 2 * B, Bp2, ctx->ev_plan,
+                        nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, ctx->d_upg_cost,
+                        ctx->wide_h, ctx->stream));
+  // the snapshot's nu buffer receives the permuted nu, then the chains' nu
+  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_perm, ctx->d_upg_cand, Bp2, ctx->C.xt,
+                          ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
+  CK(ctx, cudaMemcpy2DAsync(ctx->C.nu, sizeof(float) * Bp, ctx->d_upg_nus, sizeof(float) * Bp,
+                            sizeof(float) * B, n, cudaMemcpyDeviceToDevice, ctx->stream));
+  return MAXSAT_OK;
+}
+
 int maxsat_up_begin(maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_begin before maxsat_reset");
   if (ctx->n_inst != 1) return fail(ctx, MAXSAT_EINVAL, "unit propagation runs on single-formula contexts");
   if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is already pending");
   const int B = ctx->C.B, n = ctx->n;
+  if (ctx->prm.up_device && !ctx->dense && up_gpu_chains_per_block(n) > 0)
+    return up_begin_gpu(ctx);
   ctx->up_x0.resize((size_t)B * n);
   ctx->up_nu0.resize((size_t)B * n);
   ctx->up_out.resize((size_t)B * n);
@@ -1566,6 +1670,7 @@ int maxsat_up_begin(maxsat_ctx* ctx) {
   if (rc != MAXSAT_OK) return rc;
   ctx->up_B = B;
   ctx->up_pending = true;
+  ctx->up_on_gpu = false;
   const int threads = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   ctx->up_worker = std::thread([ctx, B, threads]() {
     up_chains(ctx->upf, B, ctx->up_x0.data(), ctx->up_nu0.data(), ctx->up_out.data(), threads);
@@ -1576,6 +1681,7 @@ int maxsat_up_begin(maxsat_ctx* ctx) {
 int maxsat_up_end(maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_end without maxsat_up_begin");
+  if (ctx->up_on_gpu) return up_end_gpu(ctx);
   if (ctx->up_worker.joinable()) ctx->up_worker.join();
   ctx->up_pending = false;
   const int B = ctx->up_B, n = ctx->n;
@@ -1868,6 +1974,12 @@ int maxsat_reset_probs(maxsat_ctx* ctx, int32_t B, uint64_t seed, const float* p
 void maxsat_destroy(maxsat_ctx* ctx) {
   if (!ctx) return;
   if (ctx->up_worker.joinable()) ctx->up_worker.join();
+  if (ctx->up_stream) {
+    cudaStreamSynchronize(ctx->up_stream);
+    cudaStreamDestroy(ctx->up_stream);
+  }
+  if (ctx->up_ev_snap) cudaEventDestroy(ctx->up_ev_snap);
+  if (ctx->up_ev_done) cudaEventDestroy(ctx->up_ev_done);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   drain_marks(ctx);

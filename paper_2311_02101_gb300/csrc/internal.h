@@ -145,6 +145,28 @@ void up_prepare(int32_t n, int64_t m, const int64_t* off, const int32_t* lits, U
 void up_chains(const UpFormula& F, int32_t B, const uint8_t* x, const float* nu, uint8_t* out,
                int threads);
 
+// up_gpu.cu: unit propagation and the B-of-2B merge on the GPU (sparse path)
+struct UpDev {
+  int32_t n, m;
+  const int32_t* cl_off;   // m + 1 (the formula's)
+  const int32_t* lit_var;  // nnz (the formula's)
+  const int32_t* occ_off;  // n + 1
+  const int32_t* occ;      // per variable, its clauses in clause order
+};
+// chains per block of the propagation kernel (0: a chain's state does not
+// fit in shared memory)
+int up_gpu_chains_per_block(int n);
+// out[v * Bp2 + col0 + b] = unit propagation of chain b of the snapshot
+// (xs: n x Bp states, nus: n x Bp nu)
+cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus, int Bp, int B,
+                             uint8_t* out, int Bp2, int col0, cudaStream_t st);
+// cost: 2B candidate costs (cand columns 0..2B-1, n x Bp2); chain j of xt
+// takes the candidate at position B + j of the stable sort by cost
+// descending, nu_out gets nu of the chain it came from
+cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* perm, const uint8_t* cand,
+                            int Bp2, uint8_t* xt, const float* nu, float* nu_out, int Bp, int n,
+                            cudaStream_t st);
+
 // mp.cu: the learned proposal's kernels (message passing, hidden size 64)
 constexpr int kMpHidden = 64;
 constexpr int kMpMaxLayers = 8;

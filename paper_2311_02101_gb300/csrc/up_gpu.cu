@@ -1,0 +1,252 @@
+// Prioritized unit propagation (Sec. 4.4) and the B-of-2B merge on the GPU.
+//
+// The paper runs the heuristic on host cores while the accelerator keeps
+// sampling. Here the same procedure runs as one warp per chain on a side
+// stream (the Gibbs rounds keep running on the context's stream meanwhile),
+// and the merge scores, ranks and permutes the candidates on the device.
+//
+// k_up_chains  one warp = one chain, its state in shared memory:
+//   keys   n_pad u64: nu ranking keys, sorted by a warp bitonic sort
+//          (nu descending, ties to the lower index; -0 == +0);
+//   val    n bytes: 0 / 1 assigned, 2 unassigned, 3 unassigned and queued;
+//   queue  n int32 literals (bit 31 = negated), first in, first out.
+// A clause's state is read from val directly (satisfied: a true literal;
+// unit: no true literal and exactly one unassigned literal occurrence),
+// which is what the host's incremental counters hold. Queue entries are
+// appended in the host's order, but a variable is queued at most once: only
+// the first entry of a variable can assign it (a later entry finds it
+// assigned), so the dropped entries change nothing, and the queue holds at
+// most n entries.
+// k_up_rank    position of each of the 2B candidates in the stable sort by
+//              cost descending (= satisfied weight ascending), by counting.
+// k_up_permute chain j takes the candidate at position B + j; nu of the
+//              chain it came from.
+#include <cstdint>
+
+#include "internal.h"
+
+namespace rbmsat {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kUpMaxWarps = 4;             // chains per block
+constexpr int kUpSmemBudget = 200 * 1024;  // shared memory of one block
+
+int up_npad(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+int up_warp_bytes(int n) { return (8 * up_npad(n) + 4 * n + n + 15) & ~15; }
+
+// descending order of nu as an ascending u32 (-0 and +0 equal)
+__device__ __forceinline__ uint32_t desc_key(float f) {
+  uint32_t u = __float_as_uint(f);
+  if ((u << 1) == 0u) u = 0u;
+  const uint32_t asc = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ~asc;
+}
+
+// lit_var of clause c's only unassigned literal occurrence when the clause is
+// not satisfied and exactly one occurrence is unassigned
+__device__ __forceinline__ bool unit_literal(const UpDev& U, const int8_t* val, int c,
+                                             int32_t* lv_out) {
+  const int o = __ldg(U.cl_off + c), e = __ldg(U.cl_off + c + 1);
+  int nun = 0;
+  int32_t first = 0;
+  for (int j = o; j < e; ++j) {
+    const int32_t lv = __ldg(U.lit_var + j);
+    const int s = val[lv & 0x7FFFFFFF];
+    if (s >= 2) {
+      if (nun == 0) first = lv;
+      ++nun;
+    } else if ((s == 1) != (lv < 0)) {
+      return false;  // satisfied
+    }
+  }
+  *lv_out = first;
+  return nun == 1;
+}
+
+struct ChainState {
+  int8_t* val;
+  int32_t* queue;
+  int head, tail;
+};
+
+// appends the literals of the lanes in `ballot`, in lane order, each
+// variable at most once
+__device__ __forceinline__ void append(uint32_t ballot, int32_t lv, ChainState& S, int lane) {
+  while (ballot) {
+    const int src = __ffs(ballot) - 1;
+    ballot &= ballot - 1;
+    const int32_t l = __shfl_sync(kFull, lv, src);
+    const int v = l & 0x7FFFFFFF;
+    const bool fresh = S.val[v] == 2;
+    __syncwarp();
+    if (fresh && lane == 0) {
+      S.val[v] = 3;
+      S.queue[S.tail] = l;
+    }
+    __syncwarp();
+    S.tail += fresh ? 1 : 0;
+  }
+}
+
+// assigns v and queues the open literal of every clause of v that became
+// unit (v's occurrences in clause order)
+__device__ __forceinline__ void set_check(const UpDev& U, ChainState& S, int v, int value,
+                                          int lane) {
+  if (lane == 0) S.val[v] = (int8_t)value;
+  __syncwarp();
+  const int k0 = __ldg(U.occ_off + v), k1 = __ldg(U.occ_off + v + 1);
+  for (int k = k0; k < k1; k += 32) {
+    int32_t lv = 0;
+    bool unit = false;
+    if (k + lane < k1) unit = unit_literal(U, S.val, __ldg(U.occ + k + lane), &lv);
+    append(__ballot_sync(kFull, unit), lv, S, lane);
+  }
+}
+
+__device__ __forceinline__ void drain(const UpDev& U, ChainState& S, int lane) {
+  while (S.head < S.tail) {
+    const int32_t l = S.queue[S.head++];
+    const int v = l & 0x7FFFFFFF;
+    if (S.val[v] >= 2) set_check(U, S, v, l >= 0 ? 1 : 0, lane);
+  }
+}
+
+__global__ void __launch_bounds__(32 * kUpMaxWarps)
+    k_up_chains(UpDev U, const uint8_t* __restrict__ xs, const float* __restrict__ nus, int Bp,
+                int B, uint8_t* __restrict__ out, int Bp2, int col0, int n_pad, int wbytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (b >= B) return;  // whole warps
+  const int n = U.n;
+  unsigned char* base = smem + (size_t)warp * wbytes;
+  uint64_t* keys = reinterpret_cast<uint64_t*>(base);
+  ChainState S;
+  S.queue = reinterpret_cast<int32_t*>(base + 8 * (size_t)n_pad);
+  S.val = reinterpret_cast<int8_t*>(base + 8 * (size_t)n_pad + 4 * (size_t)n);
+  S.head = S.tail = 0;
+
+  // 1. rank the variables by nu (bitonic sort of unique keys, ascending)
+  for (int v = lane; v < n_pad; v += 32)
+    keys[v] = v < n ? ((uint64_t)desc_key(nus[(size_t)v * Bp + b]) << 32) | (uint32_t)v
+                    : ~0ull;
+  for (int v = lane; v < n; v += 32) S.val[v] = 2;
+  __syncwarp();
+  for (int k = 2; k <= n_pad; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n_pad / 2; t += 32) {
+        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const uint64_t a = keys[i], c = keys[i + j];
+        if ((a > c) == ((i & k) == 0)) {
+          keys[i] = c;
+          keys[i + j] = a;
+        }
+      }
+      __syncwarp();
+    }
+
+  // 2. the floor(n / 2) highest-ranked variables keep their values
+  const int half = n / 2;
+  for (int r = lane; r < half; r += 32) {
+    const int v = (int)(uint32_t)keys[r];
+    S.val[v] = xs[(size_t)v * Bp + b] ? 1 : 0;
+  }
+  __syncwarp();
+
+  // 3. unit clauses in clause order, then propagation
+  for (int c0 = 0; c0 < U.m; c0 += 32) {
+    int32_t lv = 0;
+    bool unit = false;
+    if (c0 + lane < U.m) unit = unit_literal(U, S.val, c0 + lane, &lv);
+    append(__ballot_sync(kFull, unit), lv, S, lane);
+  }
+  drain(U, S, lane);
+
+  // 4. the rest in rank order, each still unassigned one from x, propagated
+  for (int r = half; r < n; ++r) {
+    const int v = (int)(uint32_t)keys[r];
+    if (S.val[v] >= 2) {
+      set_check(U, S, v, xs[(size_t)v * Bp + b] ? 1 : 0, lane);
+      drain(U, S, lane);
+    }
+  }
+  for (int v = lane; v < n; v += 32) out[(size_t)v * Bp2 + col0 + b] = (uint8_t)S.val[v];
+}
+
+__global__ void __launch_bounds__(256) k_up_rank(const int64_t* __restrict__ cost, int N, int B,
+                                                 int32_t* __restrict__ perm) {
+  __shared__ int64_t s[1024];
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ca = a < N ? cost[a] : 0;
+  int r = 0;
+  for (int t0 = 0; t0 < N; t0 += 1024) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < 1024; k += blockDim.x) s[k] = t0 + k < N ? cost[t0 + k] : 0;
+    __syncthreads();
+    const int lim = min(1024, N - t0);
+    for (int k = 0; k < lim; ++k) {
+      const int64_t cb = s[k];
+      r += (cb > ca || (cb == ca && t0 + k < a)) ? 1 : 0;
+    }
+  }
+  if (a < N && r >= B) perm[r - B] = a;
+}
+
+__global__ void __launch_bounds__(256) k_up_permute(const uint8_t* __restrict__ cand, int Bp2,
+                                                    const int32_t* __restrict__ perm, int B,
+                                                    uint8_t* __restrict__ xt,
+                                                    const float* __restrict__ nu,
+                                                    float* __restrict__ nu_out, int Bp, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  const int a = perm[j];
+  const int src = a % B;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    xt[(size_t)i * Bp + j] = cand[(size_t)i * Bp2 + a];
+    nu_out[(size_t)i * Bp + j] = nu[(size_t)i * Bp + src];
+  }
+}
+
+}  // namespace
+
+int up_gpu_chains_per_block(int n) {
+  if (n < 1) return 0;
+  const int w = up_warp_bytes(n);
+  const int k = kUpSmemBudget / w;
+  return k < 1 ? 0 : (k < kUpMaxWarps ? k : kUpMaxWarps);
+}
+
+cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus, int Bp, int B,
+                             uint8_t* out, int Bp2, int col0, cudaStream_t st) {
+  const int W = up_gpu_chains_per_block(U.n);
+  if (W < 1 || B < 1) return cudaErrorInvalidValue;
+  const int wbytes = up_warp_bytes(U.n);
+  const int smem = W * wbytes;
+  if (smem > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_up_chains, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_up_chains<<<(B + W - 1) / W, 32 * W, smem, st>>>(U, xs, nus, Bp, B, out, Bp2, col0,
+                                                      up_npad(U.n), wbytes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* perm, const uint8_t* cand,
+                            int Bp2, uint8_t* xt, const float* nu, float* nu_out, int Bp, int n,
+                            cudaStream_t st) {
+  const int N = 2 * B;
+  k_up_rank<<<(N + 255) / 256, 256, 0, st>>>(cost, N, B, perm);
+  const dim3 grid((B + 255) / 256, n < 4096 ? n : 4096);
+  k_up_permute<<<grid, 256, 0, st>>>(cand, Bp2, perm, B, xt, nu, nu_out, Bp, n);
+  return cudaGetLastError();
+}
+
+}  // namespace rbmsat

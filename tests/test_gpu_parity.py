@@ -65,10 +65,10 @@ def inst_of(gen):
 
 
 def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0,
-             tune=0):
+             tune=0, up_device=1):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=n_temps, n_buckets=n_buckets,
                                       alpha=alpha, steps_per_graph=spg, path=path,
-                                      tune_blocks=tune)
+                                      tune_blocks=tune, up_device=up_device)
     params.fstar = None
     return ms.maxsat_create(inst.n, inst.off, inst.lits, inst.w, params, stream)
 
@@ -534,14 +534,17 @@ def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
 # --------------------------------------------------------------------------
 # Unit-propagation heuristic (maxsat_up_begin / maxsat_up_end, Sec. 4.4)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("path", [2, 1])
-def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path):
-    """reset, T1 rounds, send for propagation, upw rounds while the host
-    works, fetch + B-of-2B merge, T2 rounds: the oracle's same sequence
-    (its FP32 nu ranks the variables) gives the same chains bit for bit."""
+@pytest.mark.parametrize("path,up_device", [(2, 1), (1, 1), (1, 0)])
+def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path, up_device):
+    """reset, T1 rounds, send for propagation, upw rounds while it works,
+    fetch + B-of-2B merge, T2 rounds: the oracle's same sequence (its FP32
+    nu ranks the variables) gives the same chains bit for bit. Propagation
+    and merge on the GPU (sparse path, up_device 1) or on host threads
+    (up_device 0, and the dense path)."""
     inst = inst_of(workloads.weighted_3sat(300, 1500, 1000, seed=4))
     B, T1, upw, T2, seed = 256, 6, 3, 5, 13
-    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=path, spg=2)
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=path, spg=2,
+                   up_device=up_device)
     ms.maxsat_reset(ctx, B, seed)
     ms.maxsat_step(ctx, T1)
     ms.maxsat_up_begin(ctx)
@@ -568,6 +571,38 @@ def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path):
 
 def evaluate_min(inst, x):
     return int(oracle.evaluate(inst, x).min())
+
+
+@pytest.mark.parametrize("up_device", [1, 0])
+def test_unit_propagation_edge_cases_two_rounds(ms, stream, small_table, up_device):
+    """Duplicate literals, a tautology, an empty clause, a variable in no
+    clause, B not a multiple of 256, and two propagation rounds in a row
+    (the second as maxsat_up): the same chains as the oracle."""
+    inst = edge_instance(1, 4)
+    B, seed, alpha = 300, 5, 0.05
+    ctx = make_ctx(ms, stream, inst, small_table, alpha=alpha, path=1, spg=2,
+                   up_device=up_device)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, 4)
+    ms.maxsat_up_begin(ctx)
+    ms.maxsat_step(ctx, 2)
+    ms.maxsat_up_end(ctx)
+    ms.maxsat_step(ctx, 3)
+    ms.maxsat_up(ctx)
+    ms.maxsat_step(ctx, 2)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+
+    st = oracle.init_chains(inst.n, B, seed)
+    kw = dict(n_temps=2, n_buckets=1, alpha=alpha, threads=os.cpu_count() or 4)
+    oracle.gibbs(inst, small_table, st, 4, seed, **kw)
+    up_x = oracle.unit_prop(inst, st.x, st.nu32)
+    oracle.gibbs(inst, small_table, st, 2, seed, **kw)
+    oracle.up_merge(inst, st, up_x)
+    oracle.gibbs(inst, small_table, st, 3, seed, **kw)
+    oracle.up_merge(inst, st, oracle.unit_prop(inst, st.x, st.nu32))
+    oracle.gibbs(inst, small_table, st, 2, seed, **kw)
+    assert_same(gpu, st, 11, alpha)
 
 
 def test_unit_propagation_rejects_batches_and_misuse(ms, stream, golden_table):
