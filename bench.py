@@ -700,6 +700,7 @@ def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20)
         while time.perf_counter() - t0 < secs:
             if mode != "gibbs":
                 ms.maxsat_step(ctx, upp - upw)
+                stream.synchronize()  # the propagation round alone is timed
                 ta = time.perf_counter()
                 ms.maxsat_up_begin(ctx)
                 ms.maxsat_step(ctx, upw)
