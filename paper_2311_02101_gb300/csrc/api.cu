@@ -113,6 +113,7 @@ struct maxsat_ctx {
   uint8_t* d_upg_cand = nullptr;
   int64_t* d_upg_cost = nullptr;
   int32_t* d_upg_perm = nullptr;
+  uint8_t* d_flip_code = nullptr;  // flip proposals: per variable 0 / 1 / 2 = keep
   cudaStream_t up_stream = nullptr;
   cudaEvent_t up_ev_snap = nullptr, up_ev_done = nullptr;
   int n_inst = 1;                      // formulas in the batch
@@ -1472,6 +1473,9 @@ static int put_states(maxsat_ctx* ctx, const uint8_t* x, const float* nu) {
   return MAXSAT_OK;
 }
 
+static int ensure_merge_buffers(maxsat_ctx* ctx);
+static int merge_on_device(maxsat_ctx* ctx, int B);
+
 // The appendix code's B-of-2B merge: cand holds 2B x n states whose second
 // half is filled by the caller; the first half receives the B current
 // states. All 2B are scored exactly; sorted by satisfied weight ascending
@@ -1521,6 +1525,21 @@ int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau) {
   if (!(tau >= 0.f && tau < 0.5f)) return fail(ctx, MAXSAT_EINVAL, "tau must be in [0, 0.5)");
   if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is pending");
   const int B = ctx->C.B, n = ctx->n;
+  if (!ctx->dense) {
+    // on the device: proposals from the current states, then the merge
+    std::vector<uint8_t> code(n);
+    for (int i = 0; i < n; ++i) code[i] = prob[i] >= 1.f - tau ? 1 : (prob[i] <= tau ? 0 : 2);
+    int rc = ensure_merge_buffers(ctx);
+    if (rc != MAXSAT_OK) return rc;
+    CK(ctx, cudaMemcpyAsync(ctx->d_flip_code, code.data(), n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_flip_candidates(ctx->C.xt, ctx->C.Bp, ctx->d_flip_code, n, B, ctx->d_upg_cand,
+                                   ctx->upg_Bp, ctx->stream));
+    rc = merge_on_device(ctx, B);
+    if (rc != MAXSAT_OK) return rc;
+    // code is a host buffer read by the copy above
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MAXSAT_OK;
+  }
   std::vector<uint8_t> cand((size_t)2 * B * n);
   int rc = maxsat_get_state(ctx, cand.data() + (size_t)B * n, nullptr, nullptr, nullptr, nullptr,
                             nullptr, nullptr);
@@ -1574,6 +1593,47 @@ int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
   return MAXSAT_OK;
 }
 
+// Device buffers of the GPU merge for the chains' B: snapshot of x and nu,
+// the 2B candidates (n x Bp2), their costs and the permutation.
+static int ensure_merge_buffers(maxsat_ctx* ctx) {
+  const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
+  const int Bp2 = (2 * B + kChainTile - 1) / kChainTile * kChainTile;
+  if (ctx->upg_Bp == Bp2) return MAXSAT_OK;  // Bp2 determines Bp
+  // earlier kernels that use the buffers are done before they are freed
+  if (ctx->up_stream) CK(ctx, cudaStreamSynchronize(ctx->up_stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->upg_mem.release();
+  ctx->upg_Bp = 0;
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_xs, (size_t)n * Bp));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_nus, (size_t)n * Bp));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cand, (size_t)n * Bp2));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, (size_t)Bp2));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, (size_t)Bp2));  // B <= Bp2 / 2 for this Bp2
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_flip_code, (size_t)n));
+  ctx->upg_Bp = Bp2;
+  return MAXSAT_OK;
+}
+
+// The B-of-2B merge on the device, candidates B..2B-1 already in place:
+// candidates 0..B-1 become the current states, all 2B are scored with the
+// sparse eval gather, ranked, and chain j takes position B + j (nu of the
+// chain it came from; the snapshot's nu buffer is the staging area).
+static int merge_on_device(maxsat_ctx* ctx, int B) {
+  const int n = ctx->n, Bp = ctx->C.Bp, Bp2 = ctx->upg_Bp;
+  CK(ctx, cudaMemcpy2DAsync(ctx->d_upg_cand, Bp2, ctx->C.xt, Bp, B, n, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+  const int rc = ensure_eval_scratch(ctx, Bp2);
+  if (rc != MAXSAT_OK) return rc;
+  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->d_upg_cand, 2 * B, Bp2, ctx->ev_plan,
+                        nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, ctx->d_upg_cost,
+                        ctx->wide_h, ctx->stream));
+  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_perm, ctx->d_upg_cand, Bp2, ctx->C.xt,
+                          ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
+  CK(ctx, cudaMemcpy2DAsync(ctx->C.nu, sizeof(float) * Bp, ctx->d_upg_nus, sizeof(float) * Bp,
+                            sizeof(float) * B, n, cudaMemcpyDeviceToDevice, ctx->stream));
+  return MAXSAT_OK;
+}
+
 // GPU round: snapshot of x and nu on the context's stream, propagation on
 // the side stream (the Gibbs rounds may run meanwhile), merge on the
 // context's stream after it.
@@ -1595,19 +1655,8 @@ static int up_begin_gpu(maxsat_ctx* ctx) {
     CK(ctx, cudaEventCreateWithFlags(&ctx->up_ev_snap, cudaEventDisableTiming));
     CK(ctx, cudaEventCreateWithFlags(&ctx->up_ev_done, cudaEventDisableTiming));
   }
-  if (ctx->upg_Bp != Bp2) {
-    // the previous round's kernels are done (merge waited on them)
-    CK(ctx, cudaStreamSynchronize(ctx->up_stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->upg_mem.release();
-    ctx->upg_Bp = 0;
-    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_xs, (size_t)n * Bp));
-    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_nus, (size_t)n * Bp));
-    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cand, (size_t)n * Bp2));
-    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, (size_t)Bp2));
-    CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, (size_t)Bp2));  // B <= Bp2 / 2 for this Bp2
-    ctx->upg_Bp = Bp2;
-  }
+  int rc = ensure_merge_buffers(ctx);
+  if (rc != MAXSAT_OK) return rc;
   CK(ctx, cudaMemcpyAsync(ctx->d_upg_xs, ctx->C.xt, (size_t)n * Bp, cudaMemcpyDeviceToDevice,
                           ctx->stream));
   CK(ctx, cudaMemcpyAsync(ctx->d_upg_nus, ctx->C.nu, sizeof(float) * n * Bp,
@@ -1634,24 +1683,10 @@ static int up_end_gpu(maxsat_ctx* ctx) {
   ctx->up_pending = false;
   ctx->up_on_gpu = false;
   CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->up_ev_done, 0));
-  const int B = ctx->up_B, n = ctx->n;
-  if (!ctx->have_chains || ctx->C.B != B || ctx->dense)
+  const int B = ctx->up_B;
+  if (!ctx->have_chains || ctx->C.B != B || ctx->dense || ctx->upg_Bp == 0)
     return fail(ctx, MAXSAT_ESTATE, "the chains were reset during unit propagation");
-  const int Bp = ctx->C.Bp, Bp2 = ctx->upg_Bp;
-  // candidates 0..B-1: the current states
-  CK(ctx, cudaMemcpy2DAsync(ctx->d_upg_cand, Bp2, ctx->C.xt, Bp, B, n, cudaMemcpyDeviceToDevice,
-                            ctx->stream));
-  const int rc = ensure_eval_scratch(ctx, Bp2);
-  if (rc != MAXSAT_OK) return rc;
-  CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->d_upg_cand, 2 * B, Bp2, ctx->ev_plan,
-                        nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, ctx->d_upg_cost,
-                        ctx->wide_h, ctx->stream));
-  // the snapshot's nu buffer receives the permuted nu, then the chains' nu
-  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_perm, ctx->d_upg_cand, Bp2, ctx->C.xt,
-                          ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
-  CK(ctx, cudaMemcpy2DAsync(ctx->C.nu, sizeof(float) * Bp, ctx->d_upg_nus, sizeof(float) * Bp,
-                            sizeof(float) * B, n, cudaMemcpyDeviceToDevice, ctx->stream));
-  return MAXSAT_OK;
+  return merge_on_device(ctx, B);
 }
 
 int maxsat_up_begin(maxsat_ctx* ctx) {

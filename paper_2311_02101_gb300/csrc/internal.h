@@ -160,6 +160,10 @@ int up_gpu_chains_per_block(int n);
 // (xs: n x Bp states, nus: n x Bp nu)
 cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus, int Bp, int B,
                              uint8_t* out, int Bp2, int col0, cudaStream_t st);
+// cand columns B..2B-1 = xt columns 0..B-1 with variable i set to code[i]
+// where code[i] < 2
+cudaError_t launch_flip_candidates(const uint8_t* xt, int Bp, const uint8_t* code, int n, int B,
+                                   uint8_t* cand, int Bp2, cudaStream_t st);
 // cost: 2B candidate costs (cand columns 0..2B-1, n x Bp2); chain j of xt
 // takes the candidate at position B + j of the stable sort by cost
 // descending, nu_out gets nu of the chain it came from

@@ -214,7 +214,28 @@ __global__ void __launch_bounds__(256) k_up_permute(const uint8_t* __restrict__ 
   }
 }
 
+// proposal columns B..2B-1 of cand: chain b's state with every variable of
+// code 0 / 1 set to it (code 2: kept)
+__global__ void __launch_bounds__(256) k_flip_candidates(const uint8_t* __restrict__ xt, int Bp,
+                                                         const uint8_t* __restrict__ code, int n,
+                                                         int B, uint8_t* __restrict__ cand,
+                                                         int Bp2) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const uint8_t k = code[i];
+    cand[(size_t)i * Bp2 + B + b] = k < 2 ? k : xt[(size_t)i * Bp + b];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_flip_candidates(const uint8_t* xt, int Bp, const uint8_t* code, int n, int B,
+                                   uint8_t* cand, int Bp2, cudaStream_t st) {
+  const dim3 grid((B + 255) / 256, n < 4096 ? n : 4096);
+  k_flip_candidates<<<grid, 256, 0, st>>>(xt, Bp, code, n, B, cand, Bp2);
+  return cudaGetLastError();
+}
 
 int up_gpu_chains_per_block(int n) {
   if (n < 1) return 0;

@@ -151,15 +151,17 @@ def test_learned_start_reaches_lower_costs(ms, stream):
     ms.maxsat_mp_destroy(model)
 
 
-def test_flip_proposals_match_oracle(ms, stream):
+@pytest.mark.parametrize("path", [1, 2])
+def test_flip_proposals_match_oracle(ms, stream, path):
     """Gibbs rounds, a flip-proposal merge with given probabilities, more
-    rounds: the oracle's same sequence gives the same chains."""
+    rounds: the oracle's same sequence gives the same chains (merge on the
+    device on the sparse path, on the host on the dense path)."""
     import os
     n, off, lits, w = formula(seed=7, n=200, m=900)
     table = oracle.RbmTable.load(os.path.join(os.path.dirname(__file__), "golden",
                                               "or_rbm_params.txt"))
     sets = [s for s in table.sets if s["len"] == 3]
-    params = ms.maxsat_default_params(sets=sets, n_temps=2, n_buckets=4)
+    params = ms.maxsat_default_params(sets=sets, n_temps=2, n_buckets=4, path=path)
     params.fstar = None
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
     rng = np.random.default_rng(3)
