@@ -534,7 +534,7 @@ def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
 # --------------------------------------------------------------------------
 # Unit-propagation heuristic (maxsat_up_begin / maxsat_up_end, Sec. 4.4)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("path,up_device", [(2, 1), (1, 1), (1, 0)])
+@pytest.mark.parametrize("path,up_device", [("sparse", 1), ("sparse", 0), ("dense", 1)])
 def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path, up_device):
     """reset, T1 rounds, send for propagation, upw rounds while it works,
     fetch + B-of-2B merge, T2 rounds: the oracle's same sequence (its FP32
@@ -543,6 +543,7 @@ def test_unit_propagation_round_matches_oracle(ms, stream, golden_table, path, u
     (up_device 0, and the dense path)."""
     inst = inst_of(workloads.weighted_3sat(300, 1500, 1000, seed=4))
     B, T1, upw, T2, seed = 256, 6, 3, 5, 13
+    path = {"sparse": ms.MAXSAT_PATH_SPARSE, "dense": ms.MAXSAT_PATH_DENSE}[path]
     ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=path, spg=2,
                    up_device=up_device)
     ms.maxsat_reset(ctx, B, seed)
@@ -580,7 +581,7 @@ def test_unit_propagation_edge_cases_two_rounds(ms, stream, small_table, up_devi
     (the second as maxsat_up): the same chains as the oracle."""
     inst = edge_instance(1, 4)
     B, seed, alpha = 300, 5, 0.05
-    ctx = make_ctx(ms, stream, inst, small_table, alpha=alpha, path=1, spg=2,
+    ctx = make_ctx(ms, stream, inst, small_table, alpha=alpha, path=ms.MAXSAT_PATH_SPARSE, spg=2,
                    up_device=up_device)
     ms.maxsat_reset(ctx, B, seed)
     ms.maxsat_step(ctx, 4)

@@ -151,7 +151,7 @@ def test_learned_start_reaches_lower_costs(ms, stream):
     ms.maxsat_mp_destroy(model)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", ["sparse", "dense"])
 def test_flip_proposals_match_oracle(ms, stream, path):
     """Gibbs rounds, a flip-proposal merge with given probabilities, more
     rounds: the oracle's same sequence gives the same chains (merge on the
@@ -161,6 +161,7 @@ def test_flip_proposals_match_oracle(ms, stream, path):
     table = oracle.RbmTable.load(os.path.join(os.path.dirname(__file__), "golden",
                                               "or_rbm_params.txt"))
     sets = [s for s in table.sets if s["len"] == 3]
+    path = {"sparse": ms.MAXSAT_PATH_SPARSE, "dense": ms.MAXSAT_PATH_DENSE}[path]
     params = ms.maxsat_default_params(sets=sets, n_temps=2, n_buckets=4, path=path)
     params.fstar = None
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
