@@ -51,6 +51,17 @@ __device__ __forceinline__ void stage(void* dst, const void* src, int bytes) {
 
 __host__ __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
+// Programmatic dependent launch between the rounds' kernels: a gather or
+// visible launch may start while its predecessor in the stream finishes. It
+// lets its own dependent start early (release), stages its constant tables,
+// and waits for the predecessor's completion and memory (griddepcontrol.wait)
+// before it reads or writes any chain state. Without a programmatic
+// predecessor both are no-ops.
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // (instance, index within it) of variable i
 __device__ __forceinline__ int2 var_instance(const DevFormula& F, int i) {
   return F.var_inst ? __ldg(F.var_inst + i) : make_int2(0, i);
@@ -99,6 +110,7 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
                                                 int64_t* eval_out) {
   constexpr bool FE = MODE != kEval;
   constexpr bool SAMPLE = MODE == kStep;
+  pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_cost[8][256];
   __shared__ float s_fe[8][256];
@@ -157,6 +169,7 @@ __global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, De
   float fe[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) fe[q] = 0.f;
+  pdl_wait();  // chain state from here on
   uint32_t t = 0;
   if (SAMPLE) t = step_index(tdev, t_rel);
 
@@ -380,6 +393,7 @@ template <bool SM, typename HT>
 __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
                                                  uint32_t t_rel, int vg0) {
+  pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_inc[8][32];  // per warp: a window of its variable's incidences
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -397,6 +411,7 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
   const int i = (vg0 + blockIdx.y) * 8 + warp;
   if (i >= F.n) return;
   const int2 vi = var_instance(F, i);
+  pdl_wait();  // chain state from here on
   const uint32_t t = step_index(tdev, t_rel);
   const int gb0 = C.g8_off * 8 + b0;  // global chain index
   const int e0 = temp_of(gb0, T.n_temps, C.B_total, C.inv_B_total);
@@ -545,6 +560,23 @@ int visible_smem_bytes(const DevTables& T) {
 constexpr int kSmemLimit = 160 * 1024;
 constexpr int kMaxGridY = 65535;
 
+// a launch that may overlap its predecessor's tail (see pdl_wait)
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, int smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int MODE, bool SM, typename HT>
 cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
                            const DevTables& T, const DevChains& C, const uint8_t* xt, int B,
@@ -559,6 +591,9 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
+  if constexpr (MODE == kStep)
+    return launch_pdl(kern, grid, smem, st, F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part,
+                      fe_part, tickets, eval_out);
   kern<<<grid, 256, smem, st>>>(F, T, C, xt, B, Bp, P, tdev, t_rel, cost_part, fe_part, tickets,
                                 eval_out);
   return cudaGetLastError();
@@ -607,7 +642,8 @@ cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormu
   const int groups = (F.n + 7) / 8;
   for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
     grid.y = std::min(kMaxGridY, groups - vg0);
-    kern<<<grid, 256, smem, st>>>(F, T, C, alpha, tdev, t_rel, vg0);
+    const cudaError_t e = launch_pdl(kern, grid, smem, st, F, T, C, alpha, tdev, t_rel, vg0);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
