@@ -92,7 +92,10 @@ typedef struct {
   int32_t n_sets;        /* 0 with sets == NULL: fit every needed set at create */
   const maxsat_rbm_set* sets;
   int32_t steps_per_graph; /* Gibbs rounds per CUDA-graph launch (the paper runs
-                              500 rounds per device dispatch); default 500;
+                              500 rounds per device dispatch); default 100:
+                              the rounds' kernels overlap at their boundaries
+                              (programmatic dependent launch), so longer
+                              graphs run no faster and take longer to build;
                               0 = plain launches */
   int32_t tune_blocks;   /* 1: at the first maxsat_reset for each B, time a few
                             clause-block sizes of the sparse gather (3 rounds

@@ -701,7 +701,7 @@ void maxsat_default_params(maxsat_params* p) {
   p->fit_iters = 50000;
   p->n_sets = 0;
   p->sets = nullptr;
-  p->steps_per_graph = 500;
+  p->steps_per_graph = 100;
   p->tune_blocks = 0;
   p->up_device = 1;
 }

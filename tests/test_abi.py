@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported():
 def test_default_params():
     p = ms.maxsat_default_params()
     assert (p.n_temps, p.n_buckets, p.quant_bits, p.path, p.fit_iters, p.steps_per_graph) == \
-        (2, 4, 4, ms.MAXSAT_PATH_AUTO, 50000, 500)
+        (2, 4, 4, ms.MAXSAT_PATH_AUTO, 50000, 100)
     assert p.alpha == 0.01 and p.bucket_gamma == 0.5 and not p.fstar and p.n_sets == 0
 
 
