@@ -667,6 +667,7 @@ def pt_probe(ms, torch, n, off, lits, w, B, stream, args, E=8, period=10):
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < secs:
             ms.maxsat_step(ctx, period)
+            stream.synchronize()  # the host clock bounds the GPU's work
             rounds += period
             if mode == "gibbs+swaps":
                 par = (rounds // period) & 1
@@ -710,6 +711,7 @@ def up_probe(ms, torch, n, off, lits, w, B, stream, sets, args, upp=200, upw=20)
                 ups += 1
             else:
                 ms.maxsat_step(ctx, upp)
+                stream.synchronize()  # the host clock bounds the GPU's work
             rounds += upp
         ms.maxsat_score(ctx)
         st = ms.maxsat_get_state(ctx)
