@@ -113,6 +113,7 @@ struct maxsat_ctx {
   uint8_t* d_upg_cand = nullptr;
   int64_t* d_upg_cost = nullptr;
   int32_t* d_upg_perm = nullptr;
+  int32_t* d_upg_rank = nullptr;
   uint8_t* d_flip_code = nullptr;  // flip proposals: per variable 0 / 1 / 2 = keep
   cudaStream_t up_stream = nullptr;
   cudaEvent_t up_ev_snap = nullptr, up_ev_done = nullptr;
@@ -1609,6 +1610,7 @@ static int ensure_merge_buffers(maxsat_ctx* ctx) {
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cand, (size_t)n * Bp2));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, (size_t)Bp2));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, (size_t)Bp2));  // B <= Bp2 / 2 for this Bp2
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_rank, (size_t)Bp2));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_flip_code, (size_t)n));
   ctx->upg_Bp = Bp2;
   return MAXSAT_OK;
@@ -1627,8 +1629,8 @@ static int merge_on_device(maxsat_ctx* ctx, int B) {
   CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->d_upg_cand, 2 * B, Bp2, ctx->ev_plan,
                         nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, ctx->d_upg_cost,
                         ctx->wide_h, ctx->stream));
-  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_perm, ctx->d_upg_cand, Bp2, ctx->C.xt,
-                          ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
+  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_rank, ctx->d_upg_perm, ctx->d_upg_cand,
+                          Bp2, ctx->C.xt, ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
   CK(ctx, cudaMemcpy2DAsync(ctx->C.nu, sizeof(float) * Bp, ctx->d_upg_nus, sizeof(float) * Bp,
                             sizeof(float) * B, n, cudaMemcpyDeviceToDevice, ctx->stream));
   return MAXSAT_OK;

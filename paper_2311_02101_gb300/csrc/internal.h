@@ -167,9 +167,9 @@ cudaError_t launch_flip_candidates(const uint8_t* xt, int Bp, const uint8_t* cod
 // cost: 2B candidate costs (cand columns 0..2B-1, n x Bp2); chain j of xt
 // takes the candidate at position B + j of the stable sort by cost
 // descending, nu_out gets nu of the chain it came from
-cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* perm, const uint8_t* cand,
-                            int Bp2, uint8_t* xt, const float* nu, float* nu_out, int Bp, int n,
-                            cudaStream_t st);
+cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* rank, int32_t* perm,
+                            const uint8_t* cand, int Bp2, uint8_t* xt, const float* nu,
+                            float* nu_out, int Bp, int n, cudaStream_t st);
 
 // mp.cu: the learned proposal's kernels (message passing, hidden size 64)
 constexpr int kMpHidden = 64;

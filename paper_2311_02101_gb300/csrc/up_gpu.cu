@@ -7,9 +7,11 @@
 //
 // k_up_chains  one warp = one chain, its state in shared memory:
 //   keys   n_pad u64: nu ranking keys, sorted by a warp bitonic sort
-//          (nu descending, ties to the lower index; -0 == +0);
-//   val    n bytes: 0 / 1 assigned, 2 unassigned, 3 unassigned and queued;
-//   queue  n int32 literals (bit 31 = negated), first in, first out.
+//          (nu descending, ties to the lower index; -0 == +0); once sorted,
+//          compacted in place to n int32 variable indices (the ranking), and
+//          the bytes after them hold the queue: n int32 literals (bit 31 =
+//          negated), first in, first out;
+//   val    n bytes: 0 / 1 assigned, 2 unassigned, 3 unassigned and queued.
 // A clause's state is read from val directly (satisfied: a true literal;
 // unit: no true literal and exactly one unassigned literal occurrence),
 // which is what the host's incremental counters hold. Queue entries are
@@ -18,7 +20,10 @@
 // assigned), so the dropped entries change nothing, and the queue holds at
 // most n entries.
 // k_up_rank    position of each of the 2B candidates in the stable sort by
-//              cost descending (= satisfied weight ascending), by counting.
+//              cost descending (= satisfied weight ascending), by counting:
+//              each block counts one slice of the compared candidates and
+//              adds its counts to a zeroed rank array (integer atomics);
+// k_up_place   candidates at positions B .. 2B - 1 become chains 0 .. B - 1.
 // k_up_permute chain j takes the candidate at position B + j; nu of the
 //              chain it came from.
 #include <cstdint>
@@ -31,7 +36,7 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kUpMaxWarps = 4;             // chains per block
-constexpr int kUpSmemBudget = 200 * 1024;  // shared memory of one block
+constexpr int kUpSmemBudget = 200 * 1024;  // shared memory of one block (cap)
 
 int up_npad(int n) {
   int p = 1;
@@ -39,7 +44,7 @@ int up_npad(int n) {
   return p;
 }
 
-int up_warp_bytes(int n) { return (8 * up_npad(n) + 4 * n + n + 15) & ~15; }
+int up_warp_bytes(int n) { return (8 * up_npad(n) + n + 15) & ~15; }
 
 // descending order of nu as an ascending u32 (-0 and +0 equal)
 __device__ __forceinline__ uint32_t desc_key(float f) {
@@ -128,9 +133,10 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
   const int n = U.n;
   unsigned char* base = smem + (size_t)warp * wbytes;
   uint64_t* keys = reinterpret_cast<uint64_t*>(base);
+  int32_t* order = reinterpret_cast<int32_t*>(base);  // after the sort
   ChainState S;
-  S.queue = reinterpret_cast<int32_t*>(base + 8 * (size_t)n_pad);
-  S.val = reinterpret_cast<int8_t*>(base + 8 * (size_t)n_pad + 4 * (size_t)n);
+  S.queue = reinterpret_cast<int32_t*>(base + 4 * (size_t)n);  // after the sort
+  S.val = reinterpret_cast<int8_t*>(base + 8 * (size_t)n_pad);
   S.head = S.tail = 0;
 
   // 1. rank the variables by nu (bitonic sort of unique keys, ascending)
@@ -151,11 +157,20 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
       }
       __syncwarp();
     }
+  // the ranking as int32 over the keys' first 4 n bytes: chunks in increasing
+  // order, each chunk's reads before its writes; later chunks read past them
+  for (int r0 = 0; r0 < n; r0 += 32) {
+    const int r = r0 + lane;
+    const int v = r < n ? (int)(uint32_t)keys[r] : 0;
+    __syncwarp();
+    if (r < n) order[r] = v;
+    __syncwarp();
+  }
 
   // 2. the floor(n / 2) highest-ranked variables keep their values
   const int half = n / 2;
   for (int r = lane; r < half; r += 32) {
-    const int v = (int)(uint32_t)keys[r];
+    const int v = order[r];
     S.val[v] = xs[(size_t)v * Bp + b] ? 1 : 0;
   }
   __syncwarp();
@@ -171,7 +186,7 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
 
   // 4. the rest in rank order, each still unassigned one from x, propagated
   for (int r = half; r < n; ++r) {
-    const int v = (int)(uint32_t)keys[r];
+    const int v = order[r];
     if (S.val[v] >= 2) {
       set_check(U, S, v, xs[(size_t)v * Bp + b] ? 1 : 0, lane);
       drain(U, S, lane);
@@ -180,23 +195,31 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
   for (int v = lane; v < n; v += 32) out[(size_t)v * Bp2 + col0 + b] = (uint8_t)S.val[v];
 }
 
-__global__ void __launch_bounds__(256) k_up_rank(const int64_t* __restrict__ cost, int N, int B,
-                                                 int32_t* __restrict__ perm) {
-  __shared__ int64_t s[1024];
+constexpr int kRankSlice = 1024;  // compared candidates per block
+
+__global__ void __launch_bounds__(256) k_up_rank(const int64_t* __restrict__ cost, int N,
+                                                 int32_t* __restrict__ rank) {
+  __shared__ int64_t s[kRankSlice];
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ca = a < N ? cost[a] : 0;
+  const int lo = blockIdx.y * kRankSlice, hi = min(N, lo + kRankSlice);
+  for (int k = threadIdx.x; k < hi - lo; k += blockDim.x) s[k] = cost[lo + k];
+  __syncthreads();
+  if (a >= N) return;
+  const int64_t ca = cost[a];
   int r = 0;
-  for (int t0 = 0; t0 < N; t0 += 1024) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < 1024; k += blockDim.x) s[k] = t0 + k < N ? cost[t0 + k] : 0;
-    __syncthreads();
-    const int lim = min(1024, N - t0);
-    for (int k = 0; k < lim; ++k) {
-      const int64_t cb = s[k];
-      r += (cb > ca || (cb == ca && t0 + k < a)) ? 1 : 0;
-    }
+  for (int k = 0; k < hi - lo; ++k) {
+    const int64_t cb = s[k];
+    r += (cb > ca || (cb == ca && lo + k < a)) ? 1 : 0;
   }
-  if (a < N && r >= B) perm[r - B] = a;
+  if (r) atomicAdd(rank + a, r);
+}
+
+__global__ void __launch_bounds__(256) k_up_place(const int32_t* __restrict__ rank, int N, int B,
+                                                  int32_t* __restrict__ perm) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= N) return;
+  const int r = rank[a];
+  if (r >= B) perm[r - B] = a;
 }
 
 __global__ void __launch_bounds__(256) k_up_permute(const uint8_t* __restrict__ cand, int Bp2,
@@ -255,16 +278,28 @@ cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus
         cudaFuncSetAttribute(k_up_chains, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
+  // three quarters of the unified memory as shared memory: as many chains per
+  // SM as fit, with some L1 left for the formula's clause and occurrence lists
+  // (measured: 6 % faster than the whole as shared memory; a larger L1 with
+  // fewer chains is slower)
+  const cudaError_t ce =
+      cudaFuncSetAttribute(k_up_chains, cudaFuncAttributePreferredSharedMemoryCarveout, 75);
+  if (ce != cudaSuccess) return ce;
   k_up_chains<<<(B + W - 1) / W, 32 * W, smem, st>>>(U, xs, nus, Bp, B, out, Bp2, col0,
                                                       up_npad(U.n), wbytes);
   return cudaGetLastError();
 }
 
-cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* perm, const uint8_t* cand,
-                            int Bp2, uint8_t* xt, const float* nu, float* nu_out, int Bp, int n,
-                            cudaStream_t st) {
+cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* rank, int32_t* perm,
+                            const uint8_t* cand, int Bp2, uint8_t* xt, const float* nu,
+                            float* nu_out, int Bp, int n, cudaStream_t st) {
   const int N = 2 * B;
-  k_up_rank<<<(N + 255) / 256, 256, 0, st>>>(cost, N, B, perm);
+  cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int32_t) * N, st);
+  if (e != cudaSuccess) return e;
+  const dim3 rgrid((N + 255) / 256, (N + kRankSlice - 1) / kRankSlice);
+  if (rgrid.y > 65535) return cudaErrorInvalidValue;
+  k_up_rank<<<rgrid, 256, 0, st>>>(cost, N, rank);
+  k_up_place<<<(N + 255) / 256, 256, 0, st>>>(rank, N, B, perm);
   const dim3 grid((B + 255) / 256, n < 4096 ? n : 4096);
   k_up_permute<<<grid, 256, 0, st>>>(cand, Bp2, perm, B, xt, nu, nu_out, Bp, n);
   return cudaGetLastError();
