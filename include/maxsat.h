@@ -106,7 +106,7 @@ typedef struct {
   int32_t up_device;     /* 1: maxsat_up_begin / maxsat_up_end run unit
                             propagation and the merge on the GPU when the
                             chains are on the sparse path and one chain's
-                            ranking state (8 n_pad + 5 n bytes, n_pad = n
+                            ranking state (8 n_pad + n bytes, n_pad = n
                             rounded up to a power of two) fits in 200 KB of
                             shared memory; otherwise, and with 0, on host
                             threads as the paper does. Same results either
