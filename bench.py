@@ -80,15 +80,18 @@ def workload(name, seed):
 # --------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
-def oracle_rate(n, off, lits, w, B, seconds, seed, table=None, n_buckets=4):
+def oracle_rate(n, off, lits, w, B, seconds, seed, table=None, n_buckets=4, threads=None):
     """Times the oracle's Gibbs rounds on a sample of chains with every host
-    core; returns (evals/s, threads, sample description)."""
+    core (or `threads` of them); returns (evals/s, threads, sample
+    description, seconds)."""
     import oracle
     inst = oracle.Instance(n, off, lits, w)
     if table is None:
         table = oracle.make_table(sorted(set(np.diff(off)) - {0}), [0.068, 0.528],
                                   n_buckets=n_buckets, iters=2000)
-    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if threads is None:
+        threads = (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                   else os.cpu_count())
     m = len(off) - 1
     # calibrate on one round of `threads` chains, then size the sample
     ids = np.linspace(0, B - 1, threads).astype(np.int32)
@@ -390,6 +393,10 @@ def run_mine(args):
     if rank == 0 and not args.no_cpu_baseline:
         v, threads, sample, _ = oracle_rate(n, off, lits, w, B, args.cpu_seconds, seed)
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
+        # the same oracle on one host core (a shorter sample)
+        v1, _, sample1, _ = oracle_rate(n, off, lits, w, B, max(1.0, args.cpu_seconds / 4), seed,
+                                        threads=1)
+        cpu["single_thread"] = dict(value=v1, unit=UNIT, cores=1, sample=sample1)
 
     # the one exchange of the multi-rank path: best cost and assignment
     ms.maxsat_score(ctx)
