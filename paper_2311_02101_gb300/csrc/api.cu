@@ -939,6 +939,23 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   UP(cl_w, F.cl_w);
   UP(var_off, F.var_off);
   UP(var_inc, F.var_inc);
+  {
+    // by degree within windows of 512 variables of one formula: a block's 8
+    // variables carry similar work, and neighbouring blocks stay in one
+    // region of the hidden patterns (a global sort scatters a batch's
+    // accesses over every formula)
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    constexpr int kOrderWindow = 512;
+    for (int k = 0; k < n_inst; ++k)
+      for (int w0 = var_base[k]; w0 < var_base[k + 1]; w0 += kOrderWindow) {
+        const int w1 = std::min(w0 + kOrderWindow, (int)var_base[k + 1]);
+        std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int32_t a, int32_t b) {
+          return var_off[a + 1] - var_off[a] > var_off[b + 1] - var_off[b];
+        });
+      }
+    UP(order, F.var_order);
+  }
   F.cl4 = nullptr;
   if (T.one_chunk) {
     // one 16-byte record per clause for the one-chunk gather

@@ -55,6 +55,9 @@ struct DevFormula {
   const int4* cl4;         // m clause records {lit_var of literals 0..2 (0 when
                            // absent), group << 2 | length} when every clause has
                            // at most 3 literals (one-chunk tables); else NULL
+  const int32_t* var_order;  // n: the visible update's order: variables by
+                             // degree, highest first (ties to the lower index),
+                             // within windows of 512 variables of one formula
 };
 
 // Work list of the clause gather: blocks of consecutive clauses that never

@@ -408,8 +408,10 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
     gq = reinterpret_cast<const int16_t*>(smem);
     pv = reinterpret_cast<const uint32_t*>(smem + gb);
   }
-  const int i = (vg0 + blockIdx.y) * 8 + warp;
-  if (i >= F.n) return;
+  // variables in descending degree: a block's 8 warps carry similar work
+  const int slot = (vg0 + blockIdx.y) * 8 + warp;
+  if (slot >= F.n) return;
+  const int i = F.var_order ? __ldg(F.var_order + slot) : slot;
   const int2 vi = var_instance(F, i);
   pdl_wait();  // chain state from here on
   const uint32_t t = step_index(tdev, t_rel);
