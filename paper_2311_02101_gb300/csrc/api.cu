@@ -309,10 +309,16 @@ int capture_graph(maxsat_ctx* ctx, int S) {
 // the batch (a formula without clauses still gets one empty block, so its
 // costs are written); uploaded into A. *wmax receives the largest weight sum
 // of a block.
+// Clause blocks of one formula of mk clauses for the nominal size cb: as many
+// as cb gives, but no more than its groups of 8 clauses.
+static int64_t blocks_of(int64_t mk, int cb) {
+  return std::max<int64_t>(1, std::min<int64_t>((mk + cb - 1) / cb, (mk + 7) / 8));
+}
+
 int plan_blocks(const maxsat_ctx* ctx, int cb) {
   int64_t nb = 0;
   for (int in = 0; in < ctx->n_inst; ++in)
-    nb += std::max<int64_t>(1, (ctx->inst_cl_base[in + 1] - ctx->inst_cl_base[in] + cb - 1) / cb);
+    nb += blocks_of(ctx->inst_cl_base[in + 1] - ctx->inst_cl_base[in], cb);
   return (int)std::min<int64_t>(nb, INT32_MAX);
 }
 
@@ -325,15 +331,20 @@ int upload_plan(maxsat_ctx* ctx, DevAllocs& A, int cb, GatherPlan* P, int64_t* w
   *wmax = 0;
   for (int in = 0; in < ctx->n_inst; ++in) {
     const int c0 = ctx->inst_cl_base[in], c1 = ctx->inst_cl_base[in + 1];
+    // block sizes in whole groups of 8 clauses (a block's 8 warps then take
+    // equal counts), as even as possible, the larger ones first
+    const int64_t nb = blocks_of(c1 - c0, cb);
+    const int64_t groups = (c1 - c0 + 7) / 8;
     int c = c0;
-    do {
-      const int e = std::min(c1, c + cb);
+    for (int64_t k = 0; k < nb; ++k) {
+      const int64_t g = groups / nb + (k < groups % nb ? 1 : 0);
+      const int e = (int)std::min<int64_t>(c1, c + 8 * g);
       blk.push_back(make_int4(in, c, e, c0));
       int64_t sum = 0;
-      for (int k = c; k < e; ++k) sum += ctx->h_w[k];
+      for (int q = c; q < e; ++q) sum += ctx->h_w[q];
       *wmax = std::max(*wmax, sum);
       c = e;
-    } while (c < c1);
+    }
     ib.push_back((int32_t)blk.size());
   }
   int4* dblk = nullptr;
