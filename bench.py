@@ -863,18 +863,28 @@ def kernel_source_hash(kernel):
 
 def ms_fitted_sets(ms, off, params):
     """The library's own fitted sets for this formula's clause lengths and
-    weight buckets (host fitting, outside the timed region)."""
+    weight buckets (host fitting, outside the timed region), with the
+    iteration count the library uses at create (beyond 7 literals the fit
+    enumerates 2^K inputs per step, so the count is divided by 2^(K - 7), at
+    least 2000), fitted on every host core."""
+    from concurrent.futures import ThreadPoolExecutor
     lengths = sorted(set(np.diff(off).tolist()) - {0})
     fstar = [0.068, 0.528]
-    out = []
-    for e, fs in enumerate(fstar):
-        for j in range(params.n_buckets):
-            for K in lengths:
-                L = 3 if K <= 3 else K + 1
-                W, b = ms.maxsat_fit_or_rbm(K, L, fs * (1 + j * params.bucket_gamma),
-                                            params.quant_bits, params.fit_iters)
-                out.append(dict(len=K, bucket=j, temp=e, W=W, b=b))
-    return out
+    jobs = [(e, fs, j, K) for e, fs in enumerate(fstar) for j in range(params.n_buckets)
+            for K in lengths]
+
+    def fit(job):
+        e, fs, j, K = job
+        L = 3 if K <= 3 else K + 1
+        iters = params.fit_iters
+        if K > 7:
+            iters = max(min(2000, iters), iters >> (K - 7))
+        W, b = ms.maxsat_fit_or_rbm(K, L, fs * (1 + j * params.bucket_gamma),
+                                    params.quant_bits, iters)
+        return dict(len=K, bucket=j, temp=e, W=W, b=b)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(fit, jobs))
 
 
 def main():
