@@ -456,7 +456,9 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   const bool prof = ctx->profiling;
   ctx->profiling = false;
   int rc = MAXSAT_OK;
-  for (int d = 0; d < 2 && rc == MAXSAT_OK; ++d) {
+  // dense first: when the sparse path wins, its chain memory is the one left
+  // allocated and the reset that follows keeps it
+  for (int d = 1; d >= 0 && rc == MAXSAT_OK; --d) {
     ctx->dense = d == 1;
     rc = alloc_chains(ctx, B);
     if (rc != MAXSAT_OK) break;
@@ -493,7 +495,9 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   if (rc != MAXSAT_OK) return rc;
   ctx->dense = ctx->auto_ms[1] < ctx->auto_ms[0];
   ctx->auto_B = B;
-  ctx->have_chains = false;  // the timing runs left no valid chains
+  // the timing runs left no valid states (the caller, maxsat_reset, initialises
+  // them next); the sparse layout's memory stays allocated when it won
+  ctx->have_chains = !ctx->dense && !ctx->chains_dense && ctx->C.B == B;
   return MAXSAT_OK;
 }
 
