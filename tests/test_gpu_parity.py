@@ -606,6 +606,27 @@ def test_unit_propagation_edge_cases_two_rounds(ms, stream, small_table, up_devi
     assert_same(gpu, st, 11, alpha)
 
 
+def test_unit_propagation_large_formula_takes_the_host_form(ms, stream, golden_table):
+    """n = 17000 (a chain's ranking state would need 279 KB of shared
+    memory): the round runs on host threads and still equals the oracle."""
+    inst = inst_of(workloads.weighted_3sat(17000, 68000, 1000, seed=8))
+    B, seed = 64, 17
+    ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=ms.MAXSAT_PATH_SPARSE, spg=2,
+                   up_device=1)
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, 3)
+    ms.maxsat_up(ctx)
+    ms.maxsat_step(ctx, 2)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    st = oracle.init_chains(inst.n, B, seed)
+    kw = dict(n_temps=2, n_buckets=4, threads=os.cpu_count() or 4)
+    oracle.gibbs(inst, golden_table, st, 3, seed, **kw)
+    oracle.up_merge(inst, st, oracle.unit_prop(inst, st.x, st.nu32))
+    oracle.gibbs(inst, golden_table, st, 2, seed, **kw)
+    assert_same(gpu, st, 5, 0.01)
+
+
 def test_unit_propagation_rejects_batches_and_misuse(ms, stream, golden_table):
     insts = small_batch()
     ctx = batch_ctx(ms, stream, insts, golden_table)
