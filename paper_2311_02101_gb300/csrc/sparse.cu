@@ -102,7 +102,11 @@ __global__ void __launch_bounds__(256) k_init(DevFormula F, DevChains C, int n, 
 }
 
 template <int MODE, bool SM, typename HT, bool ONE>
-__global__ void __launch_bounds__(256, 3) k_gather(DevFormula F, DevTables T, DevChains C,
+// 4 blocks per SM for one-chunk records (64 registers: a few loop-invariant
+// values spill, and the fuller SM is 0.7 % faster per round at weighted
+// 3-SAT n = 1000, m = 6000, 4096 chains); 3 for longer records, which spill
+// far more at 64 registers
+__global__ void __launch_bounds__(256, ONE ? 4 : 3) k_gather(DevFormula F, DevTables T, DevChains C,
                                                 const uint8_t* __restrict__ xt, int B, int Bp,
                                                 GatherPlan P, const uint32_t* tdev,
                                                 uint32_t t_rel, int64_t* cost_part,
@@ -601,9 +605,9 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
   return cudaGetLastError();
 }
 
-template <bool SM, typename HT>
+template <bool SM, typename HT, bool ONE>
 int gather_occupancy(int smem) {
-  auto kern = k_gather<kStep, SM, HT, false>;
+  auto kern = k_gather<kStep, SM, HT, ONE>;
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 1;
@@ -690,13 +694,18 @@ int gather_clause_block(int m, int tiles, int slots) {
   return best;
 }
 
+// resident blocks per SM of the step gather that will run (the one-chunk
+// variant when every record is one chunk)
 int gather_blocks_per_sm(const DevTables& T, bool wide) {
   const int sm = gather_smem_bytes(T);
   const bool use_sm = sm <= kSmemLimit;
-  if (use_sm && !wide) return gather_occupancy<true, uint8_t>(sm);
-  if (use_sm) return gather_occupancy<true, uint16_t>(sm);
-  if (!wide) return gather_occupancy<false, uint8_t>(0);
-  return gather_occupancy<false, uint16_t>(0);
+  const bool one = T.one_chunk && !wide;
+  if (use_sm && one) return gather_occupancy<true, uint8_t, true>(sm);
+  if (!use_sm && one) return gather_occupancy<false, uint8_t, true>(0);
+  if (use_sm && !wide) return gather_occupancy<true, uint8_t, false>(sm);
+  if (use_sm) return gather_occupancy<true, uint16_t, false>(sm);
+  if (!wide) return gather_occupancy<false, uint8_t, false>(0);
+  return gather_occupancy<false, uint16_t, false>(0);
 }
 
 cudaError_t launch_init_sparse(const DevFormula& F, const DevChains& C, int n, cudaStream_t st) {
