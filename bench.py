@@ -390,7 +390,7 @@ def run_mine(args):
                d2h_bytes_per_step=(n + 8 * B) / e2e_steps, best_cost=int(cost))
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:  # one GPU only: the host is shared
         v, threads, sample, _ = oracle_rate(n, off, lits, w, B, args.cpu_seconds, seed)
         cpu = dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample)
         # the same oracle on one host core (a shorter sample)
