@@ -267,8 +267,10 @@ int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted);
  * stable sort over [current states, propagated states], the last B become
  * chains 0..B-1 in that order, each propagated state with the nu of the
  * chain it came from. The best-so-far of each chain is kept. maxsat_up is
- * begin + end. Single-formula contexts only (MAXSAT_EINVAL for a batch);
- * MAXSAT_ESTATE without chains, for a second begin, for end without begin,
+ * begin + end. A batch of formulas (maxsat_create_batch) runs in the GPU form
+ * only, every formula with its own B chains, ranking and merge
+ * (MAXSAT_EINVAL otherwise); MAXSAT_ESTATE without chains, for a second
+ * begin, for end without begin,
  * or when the chains were reset in between. The host form synchronises; the
  * GPU form's merge is ordered on the context's stream (scoring with the
  * sparse eval gather, a stable rank by counting, a column permutation). */
@@ -328,7 +330,10 @@ void maxsat_mp_destroy(maxsat_mp* mp);
  * 0.5)); the B current states and the B proposals are scored exactly and
  * merged as in maxsat_up_end (stable sort by satisfied weight over [current,
  * proposals], the last B become chains 0..B-1, a proposal keeps its chain's
- * nu; the best-so-far is kept). Single-formula contexts; synchronises. */
+ * nu; the best-so-far is kept). On the sparse path the proposals and the
+ * merge run on the device, and a batch of formulas merges every formula
+ * separately (prob: the batch's n variables); the dense path merges on the
+ * host, single formulas only. Synchronises. */
 int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau);
 
 /* maxsat_reset, except that variable v of every chain starts True with

@@ -106,6 +106,8 @@ struct maxsat_ctx {
   DevAllocs upg_formula;
   int32_t* d_occ_off = nullptr;
   int32_t* d_occ = nullptr;
+  int32_t* d_inst_var_base = nullptr;  // n_inst + 1 (device copies of the batch layout)
+  int32_t* d_inst_cl_base = nullptr;
   DevAllocs upg_mem;
   int upg_Bp = 0;
   uint8_t* d_upg_xs = nullptr;
@@ -1554,7 +1556,8 @@ static int merge_candidates(maxsat_ctx* ctx, std::vector<uint8_t>& cand) {
 int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau) {
   if (!ctx || !prob) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_propose_flips before maxsat_reset");
-  if (ctx->n_inst != 1) return fail(ctx, MAXSAT_EINVAL, "flip proposals run on single-formula contexts");
+  if (ctx->n_inst != 1 && ctx->dense)
+    return fail(ctx, MAXSAT_EINVAL, "flip proposals of a batch run on the sparse path");
   if (!(tau >= 0.f && tau < 0.5f)) return fail(ctx, MAXSAT_EINVAL, "tau must be in [0, 0.5)");
   if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is pending");
   const int B = ctx->C.B, n = ctx->n;
@@ -1626,6 +1629,20 @@ int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
   return MAXSAT_OK;
 }
 
+// variables of the context's largest formula
+static int max_formula_vars(const maxsat_ctx* ctx) {
+  int mx = 0;
+  for (int k = 0; k < ctx->n_inst; ++k)
+    mx = std::max(mx, ctx->inst_var_base[k + 1] - ctx->inst_var_base[k]);
+  return mx;
+}
+
+// the GPU form of unit propagation and of the merges applies: sparse path
+// and every formula's chain state fits in shared memory
+static bool gpu_merge_form(const maxsat_ctx* ctx) {
+  return !ctx->dense && up_gpu_chains_per_block(max_formula_vars(ctx)) > 0;
+}
+
 // Device buffers of the GPU merge for the chains' B: snapshot of x and nu,
 // the 2B candidates (n x Bp2), their costs and the permutation.
 static int ensure_merge_buffers(maxsat_ctx* ctx) {
@@ -1640,9 +1657,11 @@ static int ensure_merge_buffers(maxsat_ctx* ctx) {
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_xs, (size_t)n * Bp));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_nus, (size_t)n * Bp));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cand, (size_t)n * Bp2));
-  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, (size_t)Bp2));
-  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, (size_t)Bp2));  // B <= Bp2 / 2 for this Bp2
-  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_rank, (size_t)Bp2));
+  // per formula: 2B costs and ranks, B permutation entries (B <= Bp2 / 2)
+  const size_t per = (size_t)ctx->n_inst * Bp2;
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_cost, per));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_perm, per));
+  CK(ctx, ctx->upg_mem.alloc(&ctx->d_upg_rank, per));
   CK(ctx, ctx->upg_mem.alloc(&ctx->d_flip_code, (size_t)n));
   ctx->upg_Bp = Bp2;
   return MAXSAT_OK;
@@ -1661,8 +1680,9 @@ static int merge_on_device(maxsat_ctx* ctx, int B) {
   CK(ctx, launch_gather(kEval, ctx->F, ctx->T, ctx->C, ctx->d_upg_cand, 2 * B, Bp2, ctx->ev_plan,
                         nullptr, 0, ctx->ev_part, nullptr, ctx->ev_tickets, ctx->d_upg_cost,
                         ctx->wide_h, ctx->stream));
-  CK(ctx, launch_up_merge(ctx->d_upg_cost, B, ctx->d_upg_rank, ctx->d_upg_perm, ctx->d_upg_cand,
-                          Bp2, ctx->C.xt, ctx->C.nu, ctx->d_upg_nus, Bp, n, ctx->stream));
+  CK(ctx, launch_up_merge(ctx->d_upg_cost, ctx->n_inst, B, ctx->d_upg_rank, ctx->d_upg_perm,
+                          ctx->d_upg_cand, Bp2, ctx->C.xt, ctx->C.nu, ctx->d_upg_nus, Bp, n,
+                          ctx->F.var_inst, ctx->stream));
   CK(ctx, cudaMemcpy2DAsync(ctx->C.nu, sizeof(float) * Bp, ctx->d_upg_nus, sizeof(float) * Bp,
                             sizeof(float) * B, n, cudaMemcpyDeviceToDevice, ctx->stream));
   return MAXSAT_OK;
@@ -1680,6 +1700,12 @@ static int up_begin_gpu(maxsat_ctx* ctx) {
     for (size_t k = 0; k < oc.size(); ++k) oc[k] = ctx->upf.occ[k] & 0x7FFFFFFF;
     CK(ctx, ctx->upg_formula.alloc(&ctx->d_occ_off, oo.size()));
     CK(ctx, ctx->upg_formula.alloc(&ctx->d_occ, oc.size()));
+    CK(ctx, ctx->upg_formula.alloc(&ctx->d_inst_var_base, ctx->inst_var_base.size()));
+    CK(ctx, ctx->upg_formula.alloc(&ctx->d_inst_cl_base, ctx->inst_cl_base.size()));
+    CK(ctx, cudaMemcpy(ctx->d_inst_var_base, ctx->inst_var_base.data(),
+                       4 * ctx->inst_var_base.size(), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMemcpy(ctx->d_inst_cl_base, ctx->inst_cl_base.data(),
+                       4 * ctx->inst_cl_base.size(), cudaMemcpyHostToDevice));
     CK(ctx, cudaMemcpy(ctx->d_occ_off, oo.data(), 4 * oo.size(), cudaMemcpyHostToDevice));
     if (!oc.empty())
       CK(ctx, cudaMemcpy(ctx->d_occ, oc.data(), 4 * oc.size(), cudaMemcpyHostToDevice));
@@ -1704,6 +1730,10 @@ static int up_begin_gpu(maxsat_ctx* ctx) {
   U.lit_var = ctx->F.lit_var;
   U.occ_off = ctx->d_occ_off;
   U.occ = ctx->d_occ;
+  U.n_inst = ctx->n_inst;
+  U.var_base = ctx->d_inst_var_base;
+  U.cl_base = ctx->d_inst_cl_base;
+  U.n_max = max_formula_vars(ctx);
   CK(ctx, launch_up_chains(U, ctx->d_upg_xs, ctx->d_upg_nus, Bp, B, ctx->d_upg_cand, Bp2, B,
                            ctx->up_stream));
   CK(ctx, cudaEventRecord(ctx->up_ev_done, ctx->up_stream));
@@ -1726,11 +1756,14 @@ static int up_end_gpu(maxsat_ctx* ctx) {
 int maxsat_up_begin(maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_begin before maxsat_reset");
-  if (ctx->n_inst != 1) return fail(ctx, MAXSAT_EINVAL, "unit propagation runs on single-formula contexts");
+  const bool gpu = ctx->prm.up_device && gpu_merge_form(ctx);
+  if (ctx->n_inst != 1 && !gpu)
+    return fail(ctx, MAXSAT_EINVAL,
+                "unit propagation of a batch of formulas runs in its GPU form only (sparse path, "
+                "params.up_device)");
   if (ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "a unit-propagation round is already pending");
   const int B = ctx->C.B, n = ctx->n;
-  if (ctx->prm.up_device && !ctx->dense && up_gpu_chains_per_block(n) > 0)
-    return up_begin_gpu(ctx);
+  if (gpu) return up_begin_gpu(ctx);
   ctx->up_x0.resize((size_t)B * n);
   ctx->up_nu0.resize((size_t)B * n);
   ctx->up_out.resize((size_t)B * n);

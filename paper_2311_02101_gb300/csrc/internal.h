@@ -150,29 +150,36 @@ void up_chains(const UpFormula& F, int32_t B, const uint8_t* x, const float* nu,
 
 // up_gpu.cu: unit propagation and the B-of-2B merge on the GPU (sparse path)
 struct UpDev {
-  int32_t n, m;
-  const int32_t* cl_off;   // m + 1 (the formula's)
-  const int32_t* lit_var;  // nnz (the formula's)
+  int32_t n, m;            // all formulas of the context
+  const int32_t* cl_off;   // m + 1
+  const int32_t* lit_var;  // nnz (global variable indices)
   const int32_t* occ_off;  // n + 1
   const int32_t* occ;      // per variable, its clauses in clause order
+  int32_t n_inst;          // formulas; each has its own B chains
+  const int32_t* var_base; // n_inst + 1: first variable of each formula
+  const int32_t* cl_base;  // n_inst + 1: first clause of each formula
+  int32_t n_max;           // variables of the largest formula
 };
-// chains per block of the propagation kernel (0: a chain's state does not
-// fit in shared memory)
-int up_gpu_chains_per_block(int n);
-// out[v * Bp2 + col0 + b] = unit propagation of chain b of the snapshot
-// (xs: n x Bp states, nus: n x Bp nu)
+// chains per block of the propagation kernel for formulas of at most n_max
+// variables (0: a chain's state does not fit in shared memory)
+int up_gpu_chains_per_block(int n_max);
+// out[v * Bp2 + col0 + b] = unit propagation of chain b of the snapshot, for
+// every formula (xs: n x Bp states, nus: n x Bp nu; one warp per formula and
+// chain)
 cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus, int Bp, int B,
                              uint8_t* out, int Bp2, int col0, cudaStream_t st);
 // cand columns B..2B-1 = xt columns 0..B-1 with variable i set to code[i]
 // where code[i] < 2
 cudaError_t launch_flip_candidates(const uint8_t* xt, int Bp, const uint8_t* code, int n, int B,
                                    uint8_t* cand, int Bp2, cudaStream_t st);
-// cost: 2B candidate costs (cand columns 0..2B-1, n x Bp2); chain j of xt
-// takes the candidate at position B + j of the stable sort by cost
-// descending, nu_out gets nu of the chain it came from
-cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* rank, int32_t* perm,
+// cost: per formula k its 2B candidate costs at cost + 2B k (cand columns
+// 0..2B-1, n x Bp2); in every formula chain j of xt takes the candidate at
+// position B + j of the formula's stable sort by cost descending, and
+// nu_out gets nu of the chain it came from. var_inst: NULL for one formula.
+cudaError_t launch_up_merge(const int64_t* cost, int n_inst, int B, int32_t* rank, int32_t* perm,
                             const uint8_t* cand, int Bp2, uint8_t* xt, const float* nu,
-                            float* nu_out, int Bp, int n, cudaStream_t st);
+                            float* nu_out, int Bp, int n, const int2* var_inst,
+                            cudaStream_t st);
 
 // mp.cu: the learned proposal's kernels (message passing, hidden size 64)
 constexpr int kMpHidden = 64;

@@ -55,15 +55,16 @@ __device__ __forceinline__ uint32_t desc_key(float f) {
 }
 
 // lit_var of clause c's only unassigned literal occurrence when the clause is
-// not satisfied and exactly one occurrence is unassigned
-__device__ __forceinline__ bool unit_literal(const UpDev& U, const int8_t* val, int c,
+// not satisfied and exactly one occurrence is unassigned; val is indexed by a
+// variable's index within its formula (global index - vb)
+__device__ __forceinline__ bool unit_literal(const UpDev& U, const int8_t* val, int vb, int c,
                                              int32_t* lv_out) {
   const int o = __ldg(U.cl_off + c), e = __ldg(U.cl_off + c + 1);
   int nun = 0;
   int32_t first = 0;
   for (int j = o; j < e; ++j) {
     const int32_t lv = __ldg(U.lit_var + j);
-    const int s = val[lv & 0x7FFFFFFF];
+    const int s = val[(lv & 0x7FFFFFFF) - vb];
     if (s >= 2) {
       if (nun == 0) first = lv;
       ++nun;
@@ -76,9 +77,10 @@ __device__ __forceinline__ bool unit_literal(const UpDev& U, const int8_t* val, 
 }
 
 struct ChainState {
-  int8_t* val;
-  int32_t* queue;
+  int8_t* val;     // by index within the formula
+  int32_t* queue;  // lit_var entries (global variable indices)
   int head, tail;
+  int vb;          // the formula's first variable
 };
 
 // appends the literals of the lanes in `ballot`, in lane order, each
@@ -88,7 +90,7 @@ __device__ __forceinline__ void append(uint32_t ballot, int32_t lv, ChainState& 
     const int src = __ffs(ballot) - 1;
     ballot &= ballot - 1;
     const int32_t l = __shfl_sync(kFull, lv, src);
-    const int v = l & 0x7FFFFFFF;
+    const int v = (l & 0x7FFFFFFF) - S.vb;
     const bool fresh = S.val[v] == 2;
     __syncwarp();
     if (fresh && lane == 0) {
@@ -100,17 +102,17 @@ __device__ __forceinline__ void append(uint32_t ballot, int32_t lv, ChainState& 
   }
 }
 
-// assigns v and queues the open literal of every clause of v that became
-// unit (v's occurrences in clause order)
+// assigns v (index within the formula) and queues the open literal of every
+// clause of v that became unit (v's occurrences in clause order)
 __device__ __forceinline__ void set_check(const UpDev& U, ChainState& S, int v, int value,
                                           int lane) {
   if (lane == 0) S.val[v] = (int8_t)value;
   __syncwarp();
-  const int k0 = __ldg(U.occ_off + v), k1 = __ldg(U.occ_off + v + 1);
+  const int k0 = __ldg(U.occ_off + S.vb + v), k1 = __ldg(U.occ_off + S.vb + v + 1);
   for (int k = k0; k < k1; k += 32) {
     int32_t lv = 0;
     bool unit = false;
-    if (k + lane < k1) unit = unit_literal(U, S.val, __ldg(U.occ + k + lane), &lv);
+    if (k + lane < k1) unit = unit_literal(U, S.val, S.vb, __ldg(U.occ + k + lane), &lv);
     append(__ballot_sync(kFull, unit), lv, S, lane);
   }
 }
@@ -118,7 +120,7 @@ __device__ __forceinline__ void set_check(const UpDev& U, ChainState& S, int v, 
 __device__ __forceinline__ void drain(const UpDev& U, ChainState& S, int lane) {
   while (S.head < S.tail) {
     const int32_t l = S.queue[S.head++];
-    const int v = l & 0x7FFFFFFF;
+    const int v = (l & 0x7FFFFFFF) - S.vb;
     if (S.val[v] >= 2) set_check(U, S, v, l >= 0 ? 1 : 0, lane);
   }
 }
@@ -128,9 +130,14 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
                 int B, uint8_t* __restrict__ out, int Bp2, int col0, int n_pad, int wbytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int b = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (b >= B) return;  // whole warps
-  const int n = U.n;
+  // warp g: formula g / B, chain g % B (whole warps leave together)
+  const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (g >= U.n_inst * B) return;
+  const int fk = g / B, b = g - fk * B;
+  const int vb = __ldg(U.var_base + fk), n = __ldg(U.var_base + fk + 1) - vb;
+  const int cb0 = __ldg(U.cl_base + fk), cb1 = __ldg(U.cl_base + fk + 1);
+  int np = 1;  // this formula's sort size (n_pad: the largest formula's)
+  while (np < n) np <<= 1;
   unsigned char* base = smem + (size_t)warp * wbytes;
   uint64_t* keys = reinterpret_cast<uint64_t*>(base);
   int32_t* order = reinterpret_cast<int32_t*>(base);  // after the sort
@@ -138,16 +145,17 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
   S.queue = reinterpret_cast<int32_t*>(base + 4 * (size_t)n);  // after the sort
   S.val = reinterpret_cast<int8_t*>(base + 8 * (size_t)n_pad);
   S.head = S.tail = 0;
+  S.vb = vb;
 
   // 1. rank the variables by nu (bitonic sort of unique keys, ascending)
-  for (int v = lane; v < n_pad; v += 32)
-    keys[v] = v < n ? ((uint64_t)desc_key(nus[(size_t)v * Bp + b]) << 32) | (uint32_t)v
+  for (int v = lane; v < np; v += 32)
+    keys[v] = v < n ? ((uint64_t)desc_key(nus[(size_t)(vb + v) * Bp + b]) << 32) | (uint32_t)v
                     : ~0ull;
   for (int v = lane; v < n; v += 32) S.val[v] = 2;
   __syncwarp();
-  for (int k = 2; k <= n_pad; k <<= 1)
+  for (int k = 2; k <= np; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < n_pad / 2; t += 32) {
+      for (int t = lane; t < np / 2; t += 32) {
         const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
         const uint64_t a = keys[i], c = keys[i + j];
         if ((a > c) == ((i & k) == 0)) {
@@ -171,15 +179,15 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
   const int half = n / 2;
   for (int r = lane; r < half; r += 32) {
     const int v = order[r];
-    S.val[v] = xs[(size_t)v * Bp + b] ? 1 : 0;
+    S.val[v] = xs[(size_t)(vb + v) * Bp + b] ? 1 : 0;
   }
   __syncwarp();
 
-  // 3. unit clauses in clause order, then propagation
-  for (int c0 = 0; c0 < U.m; c0 += 32) {
+  // 3. the formula's unit clauses in clause order, then propagation
+  for (int c0 = cb0; c0 < cb1; c0 += 32) {
     int32_t lv = 0;
     bool unit = false;
-    if (c0 + lane < U.m) unit = unit_literal(U, S.val, c0 + lane, &lv);
+    if (c0 + lane < cb1) unit = unit_literal(U, S.val, vb, c0 + lane, &lv);
     append(__ballot_sync(kFull, unit), lv, S, lane);
   }
   drain(U, S, lane);
@@ -188,18 +196,22 @@ __global__ void __launch_bounds__(32 * kUpMaxWarps)
   for (int r = half; r < n; ++r) {
     const int v = order[r];
     if (S.val[v] >= 2) {
-      set_check(U, S, v, xs[(size_t)v * Bp + b] ? 1 : 0, lane);
+      set_check(U, S, v, xs[(size_t)(vb + v) * Bp + b] ? 1 : 0, lane);
       drain(U, S, lane);
     }
   }
-  for (int v = lane; v < n; v += 32) out[(size_t)v * Bp2 + col0 + b] = (uint8_t)S.val[v];
+  for (int v = lane; v < n; v += 32)
+    out[(size_t)(vb + v) * Bp2 + col0 + b] = (uint8_t)S.val[v];
 }
 
 constexpr int kRankSlice = 1024;  // compared candidates per block
 
+// blockIdx.z: the formula (its 2B costs and ranks at offset 2B z)
 __global__ void __launch_bounds__(256) k_up_rank(const int64_t* __restrict__ cost, int N,
                                                  int32_t* __restrict__ rank) {
   __shared__ int64_t s[kRankSlice];
+  cost += (size_t)blockIdx.z * N;
+  rank += (size_t)blockIdx.z * N;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int lo = blockIdx.y * kRankSlice, hi = min(N, lo + kRankSlice);
   for (int k = threadIdx.x; k < hi - lo; k += blockDim.x) s[k] = cost[lo + k];
@@ -218,22 +230,25 @@ __global__ void __launch_bounds__(256) k_up_place(const int32_t* __restrict__ ra
                                                   int32_t* __restrict__ perm) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= N) return;
-  const int r = rank[a];
-  if (r >= B) perm[r - B] = a;
+  const int r = rank[(size_t)blockIdx.y * N + a];
+  if (r >= B) perm[(size_t)blockIdx.y * B + r - B] = a;
 }
 
+// variable i of formula k (var_inst[i].x; 0 without var_inst) takes the
+// candidate perm[k B + j] in chain j
 __global__ void __launch_bounds__(256) k_up_permute(const uint8_t* __restrict__ cand, int Bp2,
                                                     const int32_t* __restrict__ perm, int B,
                                                     uint8_t* __restrict__ xt,
                                                     const float* __restrict__ nu,
-                                                    float* __restrict__ nu_out, int Bp, int n) {
+                                                    float* __restrict__ nu_out, int Bp, int n,
+                                                    const int2* __restrict__ var_inst) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= B) return;
-  const int a = perm[j];
-  const int src = a % B;
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const int k = var_inst ? __ldg(var_inst + i).x : 0;
+    const int a = perm[(size_t)k * B + j];
     xt[(size_t)i * Bp + j] = cand[(size_t)i * Bp2 + a];
-    nu_out[(size_t)i * Bp + j] = nu[(size_t)i * Bp + src];
+    nu_out[(size_t)i * Bp + j] = nu[(size_t)i * Bp + a % B];
   }
 }
 
@@ -260,18 +275,18 @@ cudaError_t launch_flip_candidates(const uint8_t* xt, int Bp, const uint8_t* cod
   return cudaGetLastError();
 }
 
-int up_gpu_chains_per_block(int n) {
-  if (n < 1) return 0;
-  const int w = up_warp_bytes(n);
+int up_gpu_chains_per_block(int n_max) {
+  if (n_max < 1) return 0;
+  const int w = up_warp_bytes(n_max);
   const int k = kUpSmemBudget / w;
   return k < 1 ? 0 : (k < kUpMaxWarps ? k : kUpMaxWarps);
 }
 
 cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus, int Bp, int B,
                              uint8_t* out, int Bp2, int col0, cudaStream_t st) {
-  const int W = up_gpu_chains_per_block(U.n);
-  if (W < 1 || B < 1) return cudaErrorInvalidValue;
-  const int wbytes = up_warp_bytes(U.n);
+  const int W = up_gpu_chains_per_block(U.n_max);
+  if (W < 1 || B < 1 || U.n_inst < 1) return cudaErrorInvalidValue;
+  const int wbytes = up_warp_bytes(U.n_max);
   const int smem = W * wbytes;
   if (smem > 48 * 1024) {
     const cudaError_t e =
@@ -285,23 +300,27 @@ cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus
   const cudaError_t ce =
       cudaFuncSetAttribute(k_up_chains, cudaFuncAttributePreferredSharedMemoryCarveout, 75);
   if (ce != cudaSuccess) return ce;
-  k_up_chains<<<(B + W - 1) / W, 32 * W, smem, st>>>(U, xs, nus, Bp, B, out, Bp2, col0,
-                                                      up_npad(U.n), wbytes);
+  const int64_t warps = (int64_t)U.n_inst * B;
+  if (warps > INT32_MAX - W) return cudaErrorInvalidValue;
+  k_up_chains<<<(unsigned)((warps + W - 1) / W), 32 * W, smem, st>>>(
+      U, xs, nus, Bp, B, out, Bp2, col0, up_npad(U.n_max), wbytes);
   return cudaGetLastError();
 }
 
-cudaError_t launch_up_merge(const int64_t* cost, int B, int32_t* rank, int32_t* perm,
+cudaError_t launch_up_merge(const int64_t* cost, int n_inst, int B, int32_t* rank, int32_t* perm,
                             const uint8_t* cand, int Bp2, uint8_t* xt, const float* nu,
-                            float* nu_out, int Bp, int n, cudaStream_t st) {
+                            float* nu_out, int Bp, int n, const int2* var_inst,
+                            cudaStream_t st) {
   const int N = 2 * B;
-  cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int32_t) * N, st);
+  if (n_inst < 1 || n_inst > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int32_t) * (size_t)N * n_inst, st);
   if (e != cudaSuccess) return e;
-  const dim3 rgrid((N + 255) / 256, (N + kRankSlice - 1) / kRankSlice);
+  const dim3 rgrid((N + 255) / 256, (N + kRankSlice - 1) / kRankSlice, n_inst);
   if (rgrid.y > 65535) return cudaErrorInvalidValue;
   k_up_rank<<<rgrid, 256, 0, st>>>(cost, N, rank);
-  k_up_place<<<(N + 255) / 256, 256, 0, st>>>(rank, N, B, perm);
+  k_up_place<<<dim3((N + 255) / 256, n_inst), 256, 0, st>>>(rank, N, B, perm);
   const dim3 grid((B + 255) / 256, n < 4096 ? n : 4096);
-  k_up_permute<<<grid, 256, 0, st>>>(cand, Bp2, perm, B, xt, nu, nu_out, Bp, n);
+  k_up_permute<<<grid, 256, 0, st>>>(cand, Bp2, perm, B, xt, nu, nu_out, Bp, n, var_inst);
   return cudaGetLastError();
 }
 

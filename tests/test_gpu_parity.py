@@ -431,9 +431,9 @@ def small_batch(seed=3):
     return insts
 
 
-def batch_ctx(ms, stream, insts, table, n_buckets=4, alpha=0.01):
+def batch_ctx(ms, stream, insts, table, n_buckets=4, alpha=0.01, up_device=1):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=2, n_buckets=n_buckets,
-                                      alpha=alpha)
+                                      alpha=alpha, up_device=up_device)
     params.fstar = None
     return ms.maxsat_create_batch(insts, params, stream)
 
@@ -627,14 +627,57 @@ def test_unit_propagation_large_formula_takes_the_host_form(ms, stream, golden_t
     assert_same(gpu, st, 5, 0.01)
 
 
-def test_unit_propagation_rejects_batches_and_misuse(ms, stream, golden_table):
+def test_unit_propagation_of_a_batch_needs_the_gpu_form(ms, stream, golden_table):
     insts = small_batch()
-    ctx = batch_ctx(ms, stream, insts, golden_table)
+    ctx = batch_ctx(ms, stream, insts, golden_table, up_device=0)
     ms.maxsat_reset(ctx, 64, 1)
     with pytest.raises(ms.MaxsatError) as e:
         ms.maxsat_up(ctx)
     assert e.value.code == ms.MAXSAT_EINVAL
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_up_end(ctx)
+    assert e.value.code == ms.MAXSAT_ESTATE
     ms.maxsat_destroy(ctx)
+
+
+@pytest.mark.parametrize("B", [256, 300])
+def test_batch_unit_propagation_and_flips_match_oracle(ms, stream, golden_table, B):
+    """A batch of 11 formulas (one without clauses, one with an empty clause
+    and a tautology): rounds, a unit-propagation round sent and merged 2
+    rounds later, rounds, a flip-proposal merge, rounds; every formula equals
+    the oracle run alone with its batch index."""
+    insts = small_batch()
+    seed = 23
+    ctx = batch_ctx(ms, stream, insts, golden_table)
+    n_all = int(ctx.var_base[-1])
+    prob = np.random.default_rng(5).random(n_all).astype(np.float32)
+    tau = 0.2
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, 4)
+    ms.maxsat_up_begin(ctx)
+    ms.maxsat_step(ctx, 2)
+    ms.maxsat_up_end(ctx)
+    ms.maxsat_step(ctx, 3)
+    ms.maxsat_propose_flips(ctx, prob, tau)
+    ms.maxsat_step(ctx, 2)
+    g = ms.maxsat_get_state(ctx)
+    vb = ctx.var_base
+    ms.maxsat_destroy(ctx)
+    kw = dict(n_temps=2, n_buckets=4, threads=os.cpu_count() or 4)
+    for k, (n, off, lits, w) in enumerate(insts):
+        inst = oracle.Instance(n, off, lits, w)
+        sl = slice(int(vb[k]), int(vb[k + 1]))
+        st = oracle.init_chains(n, B, seed, instance=k)
+        oracle.gibbs(inst, golden_table, st, 4, seed, **kw)
+        up_x = oracle.unit_prop(inst, st.x, st.nu32)
+        oracle.gibbs(inst, golden_table, st, 2, seed, **kw)
+        oracle.up_merge(inst, st, up_x)
+        oracle.gibbs(inst, golden_table, st, 3, seed, **kw)
+        oracle.up_merge(inst, st, oracle.flip_proposals(st.x, prob[sl], tau))
+        oracle.gibbs(inst, golden_table, st, 2, seed, **kw)
+        assert np.array_equal(g["x"][:, sl], st.x), k
+        assert np.array_equal(g["best_cost"][k], st.best_cost), k
+        assert np.array_equal(g["nu"][:, sl], st.nu32), k
 
 
 # --------------------------------------------------------------------------
