@@ -106,11 +106,12 @@ typedef struct {
   int32_t up_device;     /* 1: maxsat_up_begin / maxsat_up_end run unit
                             propagation and the merge on the GPU when the
                             chains are on the sparse path and one chain's
-                            ranking state (8 n_pad + n bytes, n_pad = n
+                            ranking state (8 n_pad + n bytes, n the
+                            variables of the largest formula, n_pad = n
                             rounded up to a power of two) fits in 200 KB of
                             shared memory; otherwise, and with 0, on host
-                            threads as the paper does. Same results either
-                            way. Default 1 */
+                            threads as the paper does (single formulas
+                            only). Same results either way. Default 1 */
 } maxsat_params;
 
 typedef struct maxsat_ctx maxsat_ctx;
