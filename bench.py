@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--proposal-train", type=int, default=1024,
                     help="solver-labelled training formulas for the proposal probe")
     ap.add_argument("--no-pt", action="store_true", help="skip the parallel-tempering probe")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="skip the dense-path probes (path comparison, FP8 eval product)")
     ap.add_argument("--no-up", action="store_true",
                     help="skip the unit-propagation ablation probe")
     ap.add_argument("--no-ragged", action="store_true",
@@ -446,8 +448,10 @@ def run_mine(args):
         c_, ch_, _ = dd.reduce_best(gbest[0], gbest[1], stt["best_x"][lb])
         gbest = (c_, ch_)
 
-    dense_eval = dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
-    paths = compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
+    dense_eval = (dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args)
+                  if not args.no_dense else None)
+    paths = (compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args)
+             if not args.no_dense else None)
     fp32 = fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args,
                            ms_total / args.steps) if not args.no_fp32 else None
     ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
