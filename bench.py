@@ -459,6 +459,11 @@ def run_mine(args):
     prop = proposal_probe(ms, torch, stream, sets, args) if not args.no_proposal else None
     pt = pt_probe(ms, torch, n, off, lits, w, B, stream, args) if not args.no_pt else None
 
+    # the chains' state per round: hidden patterns (2 bytes when some clause
+    # has 8 literals or more), x and best x, nu, per-block partials
+    Bp = (B + 255) // 256 * 256
+    hbytes = 2 if int(np.max(np.diff(off), initial=0)) >= 8 else 1
+    state_mb = (m * Bp * hbytes + n * Bp * 6 + 12 * Bp * (m // 100 + 1)) / 2**20
     S = params.steps_per_graph
     per_round = len([k for k in kt if k not in ("gather_score", "keep_copy", "gemm1_score")])
     launches_timed = per_round * args.steps  # one plain-launch round per interval
@@ -471,8 +476,10 @@ def run_mine(args):
                             steps_per_graph=S, clause_block=ms.maxsat_get_clause_block(ctx),
                             parallelism=f"chain-shards{ws}",
                             l2=f"flushed before every timed round ({2 * l2 >> 20} MB buffer written "
-                               "outside the round's event interval; the state, about 50 MB, fits "
-                               "in L2); steady_state: the same rounds without flushes"),
+                               f"outside the round's event interval; the chains' state, about "
+                               f"{state_mb:.0f} MB, {'fits in' if state_mb * 2**20 < l2 else 'exceeds'} "
+                               f"the {l2 >> 20} MB L2); steady_state: the same rounds without "
+                               "flushes"),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=ck, steady_state=steady,
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 3 + 3 * args.steps,
