@@ -502,3 +502,101 @@ def test_draw_decision_is_strict_below_threshold():
     assert (draws == 32768).any()
     assert np.array_equal(st.x, (draws < 32768).astype(np.uint8))
     assert np.allclose(st.nu, 0.99 * 0.25 + 0.01 * 0.25)
+
+
+# --------------------------------------------------------------------------
+# Weight buckets (reading of the unweighted paper, Sec. 5 "Datasets": clause c
+# uses the set of bucket j, the largest j < J with w_min 2^j <= w_c). The
+# expected buckets below are written out by hand for weights on both sides of
+# every boundary; the oracle's choice is read through the free energy of a
+# probe formula whose bucket sets differ only in their bias.
+# --------------------------------------------------------------------------
+def _bucket_probe_table(J):
+    """Length-1 sets, one hidden unit, W = 0 and bias j + 1 for bucket j: the
+    clause free energy is -softplus(j + 1) whatever the assignment."""
+    t = oracle.RbmTable()
+    for j in range(J):
+        t.add(1, j, 0, np.zeros((1, 1)), np.array([float(j + 1)]))
+    return t
+
+
+def _bucket_chosen(w_min, w, J):
+    inst = oracle.Instance.from_clauses(2, [[1], [-2]], [w_min, w])
+    F = oracle.free_energy(inst, _bucket_probe_table(J), np.zeros((1, 2), np.uint8), temp=0,
+                           n_buckets=J)[0]
+    # clause 0 (the lightest) is in bucket 0: -softplus(1); the rest is clause 1
+    rest = F + np.log1p(np.exp(1.0))
+    cand = [-np.log1p(np.exp(float(j + 1))) for j in range(J)]
+    j = int(np.argmin([abs(rest - c) for c in cand]))
+    assert abs(rest - cand[j]) < 1e-12
+    return j
+
+
+@pytest.mark.parametrize("w_min,cases", [
+    (1, [(1, 0), (2, 1), (3, 1), (4, 2), (5, 2), (7, 2), (8, 3), (9, 3), (1000, 3)]),
+    (3, [(3, 0), (5, 0), (6, 1), (7, 1), (11, 1), (12, 2), (13, 2), (23, 2), (24, 3),
+         (25, 3), (10 ** 6, 3)]),
+    (7, [(7, 0), (8, 0), (13, 0), (14, 1), (15, 1), (27, 1), (28, 2), (29, 2), (55, 2),
+         (56, 3), (57, 3)]),
+])
+def test_weight_bucket_boundaries(w_min, cases):
+    for w, want in cases:
+        assert _bucket_chosen(w_min, w, 4) == want, (w_min, w)
+
+
+def test_weight_bucket_hard_clause_and_limits():
+    """A hard clause (weight 1 + the sum of the soft weights, as in the mixed-
+    length workload) lands in the top bucket; J = 1 puts everything in bucket
+    0; J = 2 stops at bucket 1; weights near 2^63 do not overflow the rule
+    (2^61 and 2^63 - 1: 2^62 <= w < 2^63, so bucket 1)."""
+    soft = [1, 100, 37]
+    hard = 1 + sum(soft)
+    assert _bucket_chosen(1, hard, 4) == 3
+    assert _bucket_chosen(1, hard, 1) == 0
+    assert _bucket_chosen(1, hard, 2) == 1
+    assert _bucket_chosen(2 ** 61, 2 ** 63 - 1, 4) == 1
+    assert _bucket_chosen(2 ** 61, 2 ** 62 - 1, 4) == 0
+
+
+# --------------------------------------------------------------------------
+# Sampled chains: a row of a run started with chain_ids is that chain of the
+# full ensemble (the full-size GPU parity tests compare such samples).
+# --------------------------------------------------------------------------
+def test_sampled_chains_equal_rows_of_the_full_run(cfg1_table):
+    inst = inst_of(workloads.random_ksat(20, 86, 3, seed=4))
+    ids = np.array([0, 7, 8, 300, 511], np.int32)
+    full = oracle.init_chains(20, 512, seed=11)
+    oracle.gibbs(inst, cfg1_table, full, 12, seed=11, n_temps=2, threads=4)
+    part = oracle.init_chains(20, 0, seed=11, chain_ids=ids, B_total=512)
+    oracle.gibbs(inst, cfg1_table, part, 12, seed=11, n_temps=2)
+    for f in ["x", "nu", "nu32", "best_cost", "best_x", "cost", "free_energy"]:
+        assert np.array_equal(getattr(part, f), getattr(full, f)[ids]), f
+
+
+def test_temperature_blocks_follow_the_global_chain_index(cfg1_table):
+    """With E = 2 over 512 chains, chains 0..255 run the temperature-0 sets
+    and chains 256..511 the temperature-1 sets: each block equals a run with
+    E = 1 whose only sets are that temperature's (relabelled as 0)."""
+    inst = inst_of(workloads.random_ksat(20, 86, 3, seed=4))
+    ids = np.array([0, 7, 255, 256, 300, 511], np.int32)
+    full = oracle.init_chains(20, 0, seed=11, chain_ids=ids, B_total=512)
+    oracle.gibbs(inst, cfg1_table, full, 8, seed=11, n_temps=2)
+    for e, rows in [(0, [0, 1, 2]), (1, [3, 4, 5])]:
+        single = oracle.init_chains(20, 0, seed=11, chain_ids=ids[rows], B_total=512)
+        oracle.gibbs(inst, cfg1_table.select(temps=[e]), single, 8, seed=11, n_temps=1)
+        assert np.array_equal(single.x, full.x[rows]), e
+        assert np.array_equal(single.best_cost, full.best_cost[rows]), e
+
+
+# --------------------------------------------------------------------------
+# Swap thresholds T[u] = ceil(2^20 ln(u / 65536)) against 60-digit arithmetic
+# --------------------------------------------------------------------------
+def test_swap_thresholds_match_high_precision_logs():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    T = oracle.swap_thresholds()
+    assert T[0] == -np.inf
+    scale = mpmath.mpf(2) ** 20
+    for u in range(1, 65536):
+        exact = scale * mpmath.log(mpmath.mpf(u) / 65536)
+        assert T[u] == int(mpmath.ceil(exact)), u
