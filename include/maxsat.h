@@ -361,19 +361,20 @@ int maxsat_get_path(const maxsat_ctx* ctx);
 
 /* Allocation-free cost evaluation (the paper has no counterpart: it is an
  * interface for callers that cannot allocate device memory). Some callers
- * cannot call cudaMalloc: code issuing work while a stream is being captured
- * into a CUDA graph, frameworks whose own allocator owns the device memory
- * budget, and latency-critical loops that cannot take the implicit device
- * synchronisation an allocation may cause. This call allocates nothing (no
- * cudaMalloc, no cudaFree, no allocating library routine) and needs no
- * context: it computes the same weighted unsatisfied costs as maxsat_eval
- * for a formula held in the caller's device memory.
+ * cannot call cudaMalloc: frameworks whose own caching allocator owns the
+ * device memory budget (an allocation behind its back can fail or fragment
+ * its pool), and latency-critical loops that cannot take the implicit device
+ * synchronisation that cudaMalloc or cudaFree may cause. This call allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine) and
+ * needs no context: it computes the same weighted unsatisfied costs as
+ * maxsat_eval for a formula held in the caller's device memory.
  *   n_vars, n_clauses, n_lits  sizes (n_lits = clause_off[n_clauses])
  *   clause_off_dev  n_clauses + 1 device int64 offsets (as maxsat_create)
  *   lits_dev        n_lits device int32 DIMACS literals (as maxsat_create);
  *                   offsets are clamped to [0, n_lits] and literals outside
- *                   [-n_vars, n_vars] \ {0} are skipped, so nothing is read
- *                   outside the caller's buffers
+ *                   [-n_vars, n_vars] \ {0} are skipped (a clause left with
+ *                   no literal is unsatisfied), so nothing is read outside
+ *                   the caller's buffers when the sizes given are theirs
  *   weights_dev     n_clauses device int64 weights, or NULL for all 1
  *   assign_dev      B x n_vars device bytes (nonzero = true); cost_dev: B int64
  * Its scratch memory (the assignments transposed to variable-major,
@@ -381,12 +382,13 @@ int maxsat_get_path(const maxsat_ctx* ctx);
  * ceil(n_clauses / max(64, ceil(n_clauses / 256))) x B' x 8 bytes, with B'
  * = B rounded up to 256) is one file-scope device array of
  * MAXSAT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
- * until exit; larger requests fail with MAXSAT_EINVAL. The first call on each
- * device looks the array's address up (cudaGetSymbolAddress), so make that
- * first call before any stream capture. Every call overwrites all of the
- * scratch it reads, but all calls share the one array: calls that overlap on
- * the GPU (different streams or host threads) race. Asynchronous on
- * cuda_stream; on failure maxsat_last_error(NULL) gives the message. */
+ * until exit; larger requests fail with MAXSAT_EINVAL before any launch. The
+ * first call on each device looks the array's address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call overwrites all of the scratch it reads, but all calls share the
+ * one array: calls that overlap on the GPU (different streams or host
+ * threads) race. Asynchronous on cuda_stream; every launch is checked before
+ * the next is issued; on failure maxsat_last_error(NULL) gives the message. */
 #define MAXSAT_NOALLOC_SCRATCH_BYTES (32u << 20)
 int maxsat_eval_noalloc(int32_t n_vars, int64_t n_clauses, int64_t n_lits,
                         const int64_t* clause_off_dev, const int32_t* lits_dev,

@@ -264,12 +264,38 @@ def maxsat_eval(ctx: Context, assign_dev, cost_dev):
 
 
 def maxsat_eval_noalloc(n, off_dev, lits_dev, weights_dev, assign_dev, cost_dev, stream=None):
-    """Allocation-free evaluation (no context): all arguments are torch CUDA
-    tensors (int64 offsets, int32 DIMACS literals, int64 weights or None,
-    uint8 B x n assignments, int64 B costs)."""
-    B = int(assign_dev.shape[0])
-    assert assign_dev.is_contiguous() and tuple(assign_dev.shape) == (B, n)
+    """Allocation-free evaluation (no context): all arguments are contiguous
+    torch tensors on the current CUDA device (int64 offsets, int32 DIMACS
+    literals, int64 weights or None, uint8 B x n assignments, int64 B costs).
+    stream=None runs on torch's current stream. Every tensor is checked here,
+    because the C entry point trusts the pointers and sizes it is given."""
+    import torch
+    dev = torch.cuda.current_device()
+    named = [("off_dev", off_dev, torch.int64), ("lits_dev", lits_dev, torch.int32),
+             ("assign_dev", assign_dev, torch.uint8), ("cost_dev", cost_dev, torch.int64)]
+    if weights_dev is not None:
+        named.append(("weights_dev", weights_dev, torch.int64))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{dev})")
+        if t.dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if off_dev.dim() != 1 or off_dev.numel() < 1:
+        raise ValueError("off_dev must hold n_clauses + 1 offsets")
+    if assign_dev.dim() != 2 or int(assign_dev.shape[1]) != int(n):
+        raise ValueError(f"assign_dev must be B x {int(n)}")
     m = int(off_dev.numel()) - 1
+    B = int(assign_dev.shape[0])
+    if weights_dev is not None and weights_dev.numel() < m:
+        raise ValueError(f"weights_dev holds {weights_dev.numel()} weights for {m} clauses")
+    if cost_dev.numel() < B:
+        raise ValueError(f"cost_dev holds {cost_dev.numel()} entries for {B} assignments")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     _check(lib().maxsat_eval_noalloc(int(n), m, int(lits_dev.numel()), off_dev.data_ptr(),
                                      lits_dev.data_ptr(),
                                      None if weights_dev is None else weights_dev.data_ptr(),

@@ -1,14 +1,14 @@
 // Allocation-free cost evaluation: maxsat_eval_noalloc.
 //
-// Some callers cannot call cudaMalloc: code that issues work while a stream is
-// being captured into a CUDA graph (allocation calls are not allowed during a
-// global-mode capture), frameworks whose own allocator owns the device memory
-// budget, and latency-critical loops that cannot take the implicit device
-// synchronisation an allocation may cause. This entry point scores assignments
-// of a formula that already lives in the caller's device memory and uses no
-// memory beyond the caller's inputs and outputs except one file-scope device
-// array, g_scratch, of MAXSAT_NOALLOC_SCRATCH_BYTES bytes that every GPU that
-// loads the library holds until the process exits.
+// Some callers cannot call cudaMalloc: frameworks whose own caching allocator
+// owns the device memory budget (an allocation behind its back can fail or
+// fragment its pool), and latency-critical loops that cannot take the implicit
+// device synchronisation that cudaMalloc or cudaFree may cause. This entry
+// point scores assignments of a formula that already lives in the caller's
+// device memory and uses no memory beyond the caller's inputs and outputs
+// except one file-scope device array, g_scratch, of
+// MAXSAT_NOALLOC_SCRATCH_BYTES bytes that every GPU that loads the library
+// holds until the process exits.
 //
 // It is a variant of the sparse evaluation pipeline of sparse.cu (transpose
 // the assignments to variable-major, gather the literal truths of every clause
@@ -42,10 +42,12 @@ int noalloc_fail(int code, const std::string& msg) {
 
 // assign (B x n, chain-major, nonzero = true) -> xt (n x Bp, 0/1); chains B..Bp-1
 // read as all-false.
+// by0: the first 32-chain tile of this launch (grids have at most 65535 tiles
+// in y; more chains take several launches).
 __global__ void k_na_transpose(const uint8_t* __restrict__ assign, int B, int n,
-                               uint8_t* __restrict__ xt, int Bp) {
+                               uint8_t* __restrict__ xt, int Bp, int by0) {
   __shared__ uint8_t tile[32][33];
-  const int i0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int i0 = blockIdx.x * 32, b0 = (by0 + blockIdx.y) * 32;
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int b = b0 + r, i = i0 + threadIdx.x;
     tile[r][threadIdx.x] = (b < B && i < n) ? (assign[(size_t)b * n + i] != 0) : 0;
@@ -79,8 +81,9 @@ __global__ void __launch_bounds__(256) k_na_gather(int m, int n, int64_t n_lits,
     uint64_t sat = 0;  // byte q = 1 when some literal is true for chain q
     for (int64_t j = o0; j < o1; ++j) {
       const int32_t l = __ldg(lits + j);
-      const int v = (l > 0 ? l : -l) - 1;
-      if (l == 0 || v >= n) continue;
+      // the variable index in 64-bit arithmetic: |INT32_MIN| does not fit an int
+      const int64_t v = (l > 0 ? (int64_t)l : -(int64_t)l) - 1;
+      if (l == 0 || v < 0 || v >= n) continue;
       uint64_t x8 = __ldg(reinterpret_cast<const unsigned long long*>(xt + (size_t)v * Bp + b0));
       if (l < 0) x8 ^= 0x0101010101010101ull;
       sat |= x8;
@@ -146,28 +149,42 @@ extern "C" int maxsat_eval_noalloc(int32_t n, int64_t m, int64_t n_lits,
   if (B == 0) return MAXSAT_OK;
   if (!off_dev || (n_lits > 0 && !lits_dev) || !assign_dev || !cost_dev)
     return noalloc_fail(MAXSAT_EINVAL, "NULL device pointer");
-  const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
+  const int64_t Bp64 = ((int64_t)B + kChainTile - 1) / kChainTile * kChainTile;
   const int cblock = clause_block_for((int)m);
   const int nblk = clause_blocks_for((int)m);
-  const size_t xt_bytes = ((size_t)n * Bp + 255) / 256 * 256;
-  const size_t need = xt_bytes + (size_t)nblk * Bp * sizeof(int64_t);
+  const size_t xt_bytes = ((size_t)n * (size_t)Bp64 + 255) / 256 * 256;
+  const size_t need = xt_bytes + (size_t)nblk * (size_t)Bp64 * sizeof(int64_t);
   if (need > (size_t)MAXSAT_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(MAXSAT_EINVAL,
                         "maxsat_eval_noalloc needs " + std::to_string(need) +
                             " bytes of scratch for n_vars = " + std::to_string(n) + ", B = " +
                             std::to_string(B) + "; the limit is MAXSAT_NOALLOC_SCRATCH_BYTES = " +
                             std::to_string((size_t)MAXSAT_NOALLOC_SCRATCH_BYTES));
+  // the scratch bound keeps Bp below 2^25, so it is an int from here on
+  const int Bp = (int)Bp64;
   unsigned char* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != MAXSAT_OK) return rc;
   uint8_t* xt = scratch;
   int64_t* part = reinterpret_cast<int64_t*>(scratch + xt_bytes);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  k_na_transpose<<<dim3((n + 31) / 32, Bp / 32), dim3(32, 8), 0, st>>>(assign_dev, B, n, xt, Bp);
+  // every launch is checked before the next one is issued, so a failed
+  // transpose never lets the gather and the reduce write costs from stale
+  // scratch
+  auto launched = [](const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MAXSAT_OK;
+    return noalloc_fail(MAXSAT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  const int tiles = Bp / 32;
+  for (int by0 = 0; by0 < tiles; by0 += 65535) {
+    const int ny = tiles - by0 < 65535 ? tiles - by0 : 65535;
+    k_na_transpose<<<dim3((n + 31) / 32, ny), dim3(32, 8), 0, st>>>(assign_dev, B, n, xt, Bp, by0);
+    if ((rc = launched("transpose launch")) != MAXSAT_OK) return rc;
+  }
   k_na_gather<<<dim3(Bp / kChainTile, nblk), 256, 0, st>>>((int)m, n, n_lits, off_dev, lits_dev,
                                                             w_dev, xt, Bp, cblock, part);
+  if ((rc = launched("gather launch")) != MAXSAT_OK) return rc;
   k_na_reduce<<<(B + 255) / 256, 256, 0, st>>>(part, nblk, Bp, B, cost_dev);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return noalloc_fail(MAXSAT_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
-  return MAXSAT_OK;
+  return launched("reduce launch");
 }
