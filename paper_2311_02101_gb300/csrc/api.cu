@@ -984,10 +984,38 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
         return fail(nullptr, MAXSAT_EINVAL, "internal: clause record of a long clause");
       }
       int32_t lv[3] = {0, 0, 0};
-      for (int32_t k = 0; k < len; ++k) lv[k] = lit_var[cl_off[c] + k];
-      cl4[c] = make_int4(lv[0], lv[1], lv[2], len > 0 ? (cl_grp[c] << 2) | len : 0);
+      int32_t neg = 0;
+      for (int32_t k = 0; k < len; ++k) {
+        const int32_t l = lit_var[cl_off[c] + k];
+        lv[k] = l & 0x7FFFFFFF;
+        if (l < 0) neg |= 1 << k;
+      }
+      cl4[c] = make_int4(lv[0], lv[1], lv[2], len > 0 ? (cl_grp[c] << 8) | (neg << 2) | len : 0);
     }
     UP(cl4, F.cl4);
+  }
+  T.rec3 = nullptr;
+  T.rec3_words = 0;
+  if (T.one_chunk && (int64_t)T.n_groups * T.n_temps * 256 <= 32 * 1024) {
+    // one 256-byte block per (group, temperature): the group's 2^K records,
+    // then its flags at word 32 (bit 8: a saturated hidden unit)
+    const int E = T.n_temps;
+    std::vector<uint32_t> rec3((size_t)T.n_groups * E * 64, 0u);
+    for (int g = 0; g < T.n_groups; ++g) {
+      const GroupMeta& gm = ctx->tabs.meta[g];
+      const int np = 1 << gm.len;
+      if (np > 8) {  // one-chunk formulas have clauses of at most 3 literals
+        delete ctx;
+        return fail(nullptr, MAXSAT_EINVAL, "internal: record block of a long clause group");
+      }
+      for (int e = 0; e < E; ++e) {
+        uint32_t* blk = rec3.data() + ((size_t)g * E + e) * 64;
+        for (int w = 0; w < 4 * np; ++w) blk[w] = ctx->tabs.rec[(size_t)gm.rec_off + (size_t)e * 4 * np + w];
+        blk[32] = gm.sat ? 0x100u : 0u;
+      }
+    }
+    UP(rec3, T.rec3);
+    T.rec3_words = (int32_t)rec3.size();
   }
   F.n_inst = n_inst;
   F.var_inst = nullptr;

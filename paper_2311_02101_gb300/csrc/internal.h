@@ -52,9 +52,11 @@ struct DevFormula {
                            // (+ gq_len and bit 31 set when negated: the
                            // table's negated half), clause length K,
                            // per-temperature stride 2^L K of gq}
-  const int4* cl4;         // m clause records {lit_var of literals 0..2 (0 when
-                           // absent), group << 2 | length} when every clause has
-                           // at most 3 literals (one-chunk tables); else NULL
+  const int4* cl4;         // m clause records {0-based variable of literals
+                           // 0..2 (0 when absent), group << 8 | negated << 2 |
+                           // length}, bit k of `negated` set when literal k is
+                           // negated, when every clause has at most 3
+                           // literals (one-chunk tables); else NULL
   const int32_t* var_order;  // n: the visible update's order: variables by
                              // degree, highest first (ties to the lower index),
                              // within windows of 512 variables of one formula
@@ -79,6 +81,12 @@ struct DevTables {
   int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
   const GroupMeta* meta;
   const uint32_t* rec;
+  // one-chunk tables only: the records of group g at temperature e as a
+  // 256-byte block at word (g E + e) 64: the 2^K records of 4 words, then at
+  // word 32 the group's flags (bit 8: some hidden probability is 65536); NULL
+  // when not built (too large)
+  const uint32_t* rec3;
+  int32_t rec3_words;
   const int16_t* gq;   // 2 gq_len entries: 2^Q G, then -2^Q G (a negated
                        // literal's incidence reads the second half)
   const uint32_t* pv;

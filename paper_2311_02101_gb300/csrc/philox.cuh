@@ -21,14 +21,24 @@ __host__ __device__ __forceinline__ RoundKeys philox_keys(uint32_t key0, uint32_
   return r;
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& K) {
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;  // multiplier of counter word x
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;  // multiplier of counter word z
+
+// Rounds FIRST .. 9 of Philox4x32-10 on counter state c.
+template <int FIRST>
+__device__ __forceinline__ uint4 philox_rounds(uint4 c, const RoundKeys& K) {
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ K.k0[i], lo1, hi0 ^ c.w ^ K.k1[i], lo0);
+  for (int i = FIRST; i < 10; ++i) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c.x;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k0[i], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[i], (uint32_t)p0);
   }
   return c;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& K) {
+  return philox_rounds<0>(c, K);
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {

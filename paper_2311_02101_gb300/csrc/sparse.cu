@@ -196,17 +196,16 @@ __global__ void __launch_bounds__(256, ONE ? 4 : 3) k_gather(DevFormula F, DevTa
         const int4 cur = nxt;
         if (c + 8 < c_end) nxt = __ldg(F.cl4 + c + 8);
         len = cur.w & 3;
-        grp_one = cur.w >> 2;
+        grp_one = cur.w >> 8;
         const int32_t lv[3] = {cur.x, cur.y, cur.z};
         uint2 x8[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-          x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(
-                                xt + (size_t)(lv[k] & 0x7FFFFFFF) * Bp + b0))
+          x8[k] = k < len ? __ldg(reinterpret_cast<const uint2*>(xt + (size_t)lv[k] * Bp + b0))
                           : make_uint2(0u, 0u);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const uint32_t flip = (k < len && lv[k] < 0) ? 0x01010101u : 0u;
+          const uint32_t flip = ((cur.w >> (2 + k)) & 1) ? 0x01010101u : 0u;
           lo0 |= (x8[k].x ^ flip) << k;
           lo1 |= (x8[k].y ^ flip) << k;
         }
@@ -376,6 +375,291 @@ __global__ void __launch_bounds__(256, ONE ? 4 : 3) k_gather(DevFormula F, DevTa
     if (imp) C.best[ib] = csum;
     C.improved[ib] = imp ? 1 : 0;
   }
+  if (tid == 0) *ticket = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Step gather for formulas whose clauses all have at most 3 literals (one
+// 16-byte record per truth pattern) when every octet of chains has a single
+// temperature: the same results as k_gather<kStep, true, uint8_t, true> with
+// fewer instructions per clause and 8 chains.
+//  - Philox4x32-10 rounds 0..2: unit h of chain octet o draws from counter
+//    (clause, o | h << 24, t, phase). Round 0's product of word z (= t) is
+//    the same for every unit and clause; round 1's product of word x depends
+//    only on (o, h, t), so each thread computes it once; round 0's product of
+//    word x, round 1's of word z and round 2's of word x depend only on the
+//    clause, so the 3 units share them. A unit's own work starts with round
+//    2's product of word z; the result is the Philox block, bit for bit.
+//  - The truth patterns of 8 chains are two words of 4 bytes built by adds
+//    (literal k contributes 2^k), the literal signs applied by one XOR with
+//    the clause's flip mask.
+//  - One SWAR test finds whether some chain leaves the clause unsatisfied.
+//  - The records of each (group, temperature) form a 256-byte-aligned block,
+//    so a chain's record address is one byte permute of 16 x its pattern
+//    into the block's address.
+//  - Each draw is a compare and a predicated OR into the hidden pattern word
+//    (even chains move their draw into the high half first; groups with a
+//    saturated unit, P = 65536 stored as 0xFFFF0001, also clear the low half
+//    of odd chains' words).
+//  - The weighted unsatisfied costs stay in registers: each chain adds the
+//    clause weight times its 0/1 "no true literal" byte, without branches.
+//  - Latency: the state bytes and weight of the next clause are loaded while
+//    the current one is sampled (two clauses per loop trip), and each block
+//    first asks the L2 for its slice of the chain tile's state rows and for
+//    its clause records and weights (bulk prefetches), so the loop rarely
+//    waits on DRAM after the previous round's writes. 2 blocks of 256
+//    threads per SM: the registers of two clauses in flight, no spills.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+
+// acc |= BIT when x < w (unsigned): one compare and one predicated OR
+template <uint32_t BIT>
+__device__ __forceinline__ void or_if_below(uint32_t& acc, uint32_t x, uint32_t w) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc)
+      : "r"(x), "r"(w), "n"(BIT));
+}
+
+// Asks the L2 to fetch `bytes` (a multiple of 16) from a 16-byte aligned
+// global address (a bulk prefetch: no data returns to the thread).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The 8 state bytes of the thread's chains for each literal of clause record
+// r (zero for absent literals).
+__device__ __forceinline__ void load_clause_state(const uint8_t* xtb, int Bp, const int4& r,
+                                                  uint2& xa, uint2& xb, uint2& xc) {
+  const int len = r.w & 3;
+  xa = len > 0 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.x * Bp)) : make_uint2(0u, 0u);
+  xb = len > 1 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.y * Bp)) : make_uint2(0u, 0u);
+  xc = len > 2 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.z * Bp)) : make_uint2(0u, 0u);
+}
+
+// Unit H's draw for chain Q of the octet against threshold word w: bit
+// 8 (Q & 3) + H of hw.
+template <bool SAT, int Q, int H>
+__device__ __forceinline__ void unit_draw(const uint4 (&R)[3], uint32_t w, uint32_t& hw) {
+  const uint32_t word = word_of(R[H], Q >> 1);
+  const uint32_t x = (Q & 1) ? (SAT ? (word & 0xFFFF0000u) : word) : (word << 16);
+  or_if_below<(1u << (8 * (Q & 3) + H))>(hw, x, w);
+}
+
+// Chain Q of the octet: its record (free energy, thresholds of units 0..2)
+// and its three draws.
+template <bool SAT, int Q>
+__device__ __forceinline__ void chain_draws(uint32_t addr_bytes, uint32_t rb, const uint4 (&R)[3],
+                                            float& fe, uint32_t& hw) {
+  const uint4 r = lds128(__byte_perm(addr_bytes, rb, 0x7650u | (Q & 3)));
+  fe += __uint_as_float(r.x);
+  unit_draw<SAT, Q, 0>(R, r.y, hw);
+  unit_draw<SAT, Q, 1>(R, r.z, hw);
+  unit_draw<SAT, Q, 2>(R, r.w, hw);
+}
+
+template <bool SAT>
+__device__ __forceinline__ void octet_draws(uint32_t a_lo, uint32_t a_hi, uint32_t rb,
+                                            const uint4 (&R)[3], float (&fe)[8], uint32_t& h_lo,
+                                            uint32_t& h_hi) {
+  chain_draws<SAT, 0>(a_lo, rb, R, fe[0], h_lo);
+  chain_draws<SAT, 1>(a_lo, rb, R, fe[1], h_lo);
+  chain_draws<SAT, 2>(a_lo, rb, R, fe[2], h_lo);
+  chain_draws<SAT, 3>(a_lo, rb, R, fe[3], h_lo);
+  chain_draws<SAT, 4>(a_hi, rb, R, fe[4], h_hi);
+  chain_draws<SAT, 5>(a_hi, rb, R, fe[5], h_hi);
+  chain_draws<SAT, 6>(a_hi, rb, R, fe[6], h_hi);
+  chain_draws<SAT, 7>(a_hi, rb, R, fe[7], h_hi);
+}
+
+__global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, DevChains C,
+                                                    GatherPlan P, const uint32_t* tdev,
+                                                    uint32_t t_rel, int64_t* cost_part,
+                                                    float* fe_part, int32_t* tickets) {
+  pdl_release();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int64_t s_cost[8][256];
+  __shared__ float s_fe[8][256];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
+  const int Bp = C.Bp;
+  const int4 bd = __ldg(P.blk + blockIdx.y);
+  const int inst = bd.x, c_begin = bd.y, c_end = bd.z, cl_base = bd.w;
+  // the record blocks, staged at a 256-byte boundary of the dynamic shared memory
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t tab = (s0 + 255u) & ~255u;
+  stage(smem + (tab - s0), T.rec3, T.rec3_words * 4);
+  __syncthreads();
+  const int E = T.n_temps;
+  const int e0 = temp_of(C.g8_off * 8 + b0, E, C.B_total, C.inv_B_total);
+  const uint32_t tab_e = tab + (uint32_t)e0 * 256u;  // group 0 at the thread's temperature
+  const uint32_t gstride = (uint32_t)E * 256u;       // from one group to the next
+  // the weighted unsatisfied cost of the thread's 8 chains in registers:
+  // the host runs this kernel only when every clause block's weight sum is
+  // below 2^31 (C.cost32)
+  int32_t cost[8];
+  float fe[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    cost[q] = 0;
+    fe[q] = 0.f;
+  }
+  pdl_wait();  // chain state from here on
+  // bulk L2 prefetches: the blocks of a chain tile split its n state rows
+  // (256 bytes each) among themselves; each block fetches its own clause
+  // records and weights
+  for (int r = blockIdx.y + (int)gridDim.y * threadIdx.x; r < F.n; r += (int)gridDim.y * 256)
+    l2_prefetch(C.xt + (size_t)r * Bp + blockIdx.x * 256, 256);
+  if (threadIdx.x == 0 && c_end > c_begin) {
+    l2_prefetch(F.cl4 + c_begin, (uint32_t)(c_end - c_begin) * 16u);
+    const uintptr_t w0 = reinterpret_cast<uintptr_t>(F.cl_w + c_begin) & ~(uintptr_t)15;
+    const uintptr_t w1 = reinterpret_cast<uintptr_t>(F.cl_w + c_end) & ~(uintptr_t)15;
+    if (w1 > w0) l2_prefetch(reinterpret_cast<const void*>(w0), (uint32_t)(w1 - w0));
+  }
+  const uint32_t t = step_index(tdev, t_rel);
+  const RoundKeys& K = C.keys;
+  const uint32_t octet = (uint32_t)(g8 + C.g8_off);
+  const uint32_t phase = kPhaseHidden | ((uint32_t)inst << 8);
+  // round 0, word z = t: common to every unit and clause
+  const uint64_t pt = (uint64_t)kPhiloxM1 * t;
+  const uint32_t u1 = (uint32_t)(pt >> 32) ^ K.k0[0];
+  const uint32_t u2 = (uint32_t)pt;
+  // round 1, word x = round 0's (octet | h << 24) ^ u1: per thread and unit
+  uint32_t th[3], sh[3];
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    const uint64_t p = (uint64_t)kPhiloxM0 * ((octet | ((uint32_t)h << 24)) ^ u1);
+    th[h] = (uint32_t)(p >> 32) ^ K.k1[1];
+    sh[h] = (uint32_t)p;
+  }
+  const uint8_t* xtb = C.xt + b0;
+  uint8_t* hb = static_cast<uint8_t*>(C.H) + b0;
+
+  // software pipeline: the state bytes of the next clause and the record of
+  // the one after it are loaded while the current clause is sampled
+  const int c0 = c_begin + warp;
+  int4 rec_n = make_int4(0, 0, 0, 0);
+  if (c0 < c_end) rec_n = __ldg(F.cl4 + c0);
+  uint2 xa, xb, xc;
+  uint32_t info = (uint32_t)rec_n.w;
+  int32_t wc = 0;
+  if (c0 < c_end) wc = (int32_t)__ldg(F.cl_w + c0);
+  load_clause_state(xtb, Bp, rec_n, xa, xb, xc);
+  if (c0 + 8 < c_end) rec_n = __ldg(F.cl4 + c0 + 8);
+#pragma unroll 2
+  for (int c = c0; c < c_end; c += 8) {
+    uint2 na = make_uint2(0u, 0u), nb = na, nc = na;
+    const uint32_t ninfo = (uint32_t)rec_n.w;
+    int32_t nwc = 0;
+    if (c + 8 < c_end) {
+      load_clause_state(xtb, Bp, rec_n, na, nb, nc);
+      nwc = (int32_t)__ldg(F.cl_w + c + 8);
+    }
+    if (c + 16 < c_end) rec_n = __ldg(F.cl4 + c + 16);
+    const int len = info & 3;
+    // byte q: chain q's truth pattern (chains 0..3 | 4..7)
+    const uint32_t flip = ((info >> 2) & 7u) * 0x01010101u;
+    const uint32_t lo = (xa.x + 2u * xb.x + 4u * xc.x) ^ flip;
+    const uint32_t hi = (xa.y + 2u * xb.y + 4u * xc.y) ^ flip;
+    const uint32_t grp = info >> 8;
+    const int32_t w_cur = wc;
+    xa = na;
+    xb = nb;
+    xc = nc;
+    info = ninfo;
+    wc = nwc;
+    // byte q is 1 when chain q has no true literal (pattern 0: 0x7F + p sets
+    // bit 7 for every p in 1..7 and never carries), else 0; each chain adds
+    // the clause weight times its byte, without branches
+    const uint32_t u_lo = (~(lo + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+    const uint32_t u_hi = (~(hi + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      cost[q] += (int32_t)__byte_perm(u_lo, 0u, 0x4440u | q) * w_cur;
+      cost[q + 4] += (int32_t)__byte_perm(u_hi, 0u, 0x4440u | q) * w_cur;
+    }
+    if (len == 0) continue;  // an empty clause has no clause RBM
+
+    const uint32_t rb = tab_e + grp * gstride;
+    const bool sat = (lds32(rb + 128u) & 0x100u) != 0;
+    // Philox rounds 0..2: the clause's share, then each unit's
+    const uint32_t cl = (uint32_t)(c - cl_base);
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * cl;
+    const uint32_t c1 = (uint32_t)(p0 >> 32) ^ phase ^ K.k1[0];
+    const uint32_t c2 = (uint32_t)p0;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c1;
+    const uint32_t c3 = (uint32_t)(p1 >> 32) ^ u2 ^ K.k0[1];
+    const uint32_t c4 = (uint32_t)p1;
+    const uint64_t p2 = (uint64_t)kPhiloxM0 * c3;
+    const uint32_t c5 = (uint32_t)(p2 >> 32) ^ K.k1[2];
+    const uint32_t c6 = (uint32_t)p2;
+    uint4 R[3];
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const uint64_t pz = (uint64_t)kPhiloxM1 * (th[h] ^ c2);
+      R[h] = philox_rounds<3>(
+          make_uint4((uint32_t)(pz >> 32) ^ c4 ^ K.k0[2], (uint32_t)pz, c5 ^ sh[h], c6), K);
+    }
+    uint32_t h_lo = 0, h_hi = 0;
+    if (!sat)
+      octet_draws<false>(lo << 4, hi << 4, rb, R, fe, h_lo, h_hi);
+    else
+      octet_draws<true>(lo << 4, hi << 4, rb, R, fe, h_lo, h_hi);
+    *reinterpret_cast<uint2*>(hb + (size_t)c * Bp) = make_uint2(h_lo, h_hi);
+  }
+
+  // per-block partial sums; the block that arrives last among its instance's
+  // blocks for this tile of 256 chains reduces them in block order and keeps
+  // improvements (as k_gather)
+  int32_t* my_cost32 = reinterpret_cast<int32_t*>(&s_cost[0][0]) + warp * 256 + lane * 8;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    my_cost32[q] = cost[q];
+    s_fe[warp][lane * 8 + q] = fe[q];
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  int64_t tc = 0;
+  float tf = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    tc += reinterpret_cast<const int32_t*>(&s_cost[0][0])[w * 256 + tid];
+    tf += s_fe[w][tid];
+  }
+  const size_t out = (size_t)blockIdx.y * Bp + (size_t)blockIdx.x * 256 + tid;
+  cost_part[out] = tc;
+  fe_part[out] = tf;
+  __threadfence();
+  __syncthreads();
+  const int k0 = __ldg(P.inst_blk + inst), k1 = __ldg(P.inst_blk + inst + 1);
+  int32_t* ticket = tickets + inst * gridDim.x + blockIdx.x;
+  if (tid == 0) s_last = atomicAdd(ticket, 1) == k1 - k0 - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int b = blockIdx.x * 256 + tid;
+  int64_t csum = 0;
+  float fsum = 0.f;
+  for (int k = k0; k < k1; ++k) {
+    csum += __ldcg(cost_part + (size_t)k * Bp + b);
+    fsum += __ldcg(fe_part + (size_t)k * Bp + b);
+  }
+  const size_t ib = (size_t)inst * Bp + b;
+  C.cost[ib] = csum;
+  C.fe[ib] = fsum;
+  const bool imp = csum < C.best[ib];
+  if (imp) C.best[ib] = csum;
+  C.improved[ib] = imp ? 1 : 0;
   if (tid == 0) *ticket = 0;
 }
 
@@ -583,12 +867,38 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, int smem, cudaStream_
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// dynamic shared memory of k_gather3: the record blocks plus the slack that
+// moves them to a 256-byte boundary
+int gather3_smem_bytes(const DevTables& T) { return T.rec3_words * 4 + 256; }
+
+// every octet of chains has one temperature: each temperature block starts
+// at a multiple of 8 (block e starts at ceil(e B_total / E); local chain 0 is
+// a multiple of 8 of the ensemble)
+bool octets_single_temperature(const DevTables& T, const DevChains& C) {
+  const long long Bt = C.B_total, E = T.n_temps;
+  for (long long e = 1; e < E; ++e)
+    if (((e * Bt + E - 1) / E) % 8 != 0) return false;
+  return true;
+}
+
 template <int MODE, bool SM, typename HT>
 cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
                            const DevTables& T, const DevChains& C, const uint8_t* xt, int B,
                            int Bp, const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
                            int64_t* cost_part, float* fe_part, int32_t* tickets,
                            int64_t* eval_out) {
+  if constexpr (MODE == kStep && SM && sizeof(HT) == 1) {
+    if (T.one_chunk && T.rec3 && F.cl4 && C.cost32 && octets_single_temperature(T, C)) {
+      const int sm3 = gather3_smem_bytes(T);
+      if (sm3 > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_gather3, cudaFuncAttributeMaxDynamicSharedMemorySize, sm3);
+        if (e != cudaSuccess) return e;
+      }
+      return launch_pdl(k_gather3, grid, sm3, st, F, T, C, P, tdev, t_rel, cost_part, fe_part,
+                        tickets);
+    }
+  }
   // one-chunk records (L <= 3 everywhere): the sampling has no chunk loop
   auto kern = k_gather<MODE, SM, HT, false>;
   if constexpr (MODE == kStep && sizeof(HT) == 1)
@@ -700,6 +1010,18 @@ int gather_blocks_per_sm(const DevTables& T, bool wide) {
   const int sm = gather_smem_bytes(T);
   const bool use_sm = sm <= kSmemLimit;
   const bool one = T.one_chunk && !wide;
+  if (use_sm && one && T.rec3) {
+    // k_gather3 runs whenever the chains' octets have single temperatures
+    const int sm3 = gather3_smem_bytes(T);
+    if (sm3 > 48 * 1024 &&
+        cudaFuncSetAttribute(k_gather3, cudaFuncAttributeMaxDynamicSharedMemorySize, sm3) !=
+            cudaSuccess)
+      return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather3, 256, sm3) != cudaSuccess)
+      return 1;
+    return nb > 0 ? nb : 1;
+  }
   if (use_sm && one) return gather_occupancy<true, uint8_t, true>(sm);
   if (!use_sm && one) return gather_occupancy<false, uint8_t, true>(0);
   if (use_sm && !wide) return gather_occupancy<true, uint8_t, false>(sm);
