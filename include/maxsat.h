@@ -50,8 +50,12 @@ extern "C" {
 #define MAXSAT_MAX_HIDDEN 16  /* most hidden units per clause RBM */
 
 #define MAXSAT_PATH_AUTO 0    /* measured choice: the first maxsat_reset for a
-                                 given B times a few rounds of each path (when
-                                 the dense operands are exact and fit) and
+                                 given B times a few rounds of the sparse path,
+                                 then of the dense path unless its two tensor-
+                                 core products alone, at the GB300's nominal
+                                 dense peaks, would take longer than the
+                                 measured sparse round (the dense operands are
+                                 built then, when exact and within 8 GB), and
                                  keeps the faster */
 #define MAXSAT_PATH_DENSE 1   /* tensor-core products over dense operands */
 #define MAXSAT_PATH_SPARSE 2  /* gather / pull-scatter over the literal lists */

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -30,19 +31,81 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// Device blocks freed by contexts, kept per device for later contexts:
+// cudaMalloc and cudaFree take tens of microseconds each (and cudaFree waits
+// for the device), which dominates short solves that create and destroy a
+// context around a few Gibbs rounds. A request takes the smallest cached
+// block of at least its size and at most twice it; blocks beyond 4 GiB of
+// cache per device go back to the driver.
+class BlockCache {
+ public:
+  static constexpr int kMaxDevices = 64;
+  static constexpr size_t kCap = size_t(4) << 30;
+  void* get(int dev, size_t bytes, size_t* got) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu_);
+    auto& f = free_[dev];
+    auto it = f.lower_bound(bytes);
+    if (it == f.end() || it->first > 2 * bytes) return nullptr;
+    void* p = it->second;
+    *got = it->first;
+    cached_[dev] -= it->first;
+    f.erase(it);
+    return p;
+  }
+  // the caller guarantees that no device work still uses p
+  void put(int dev, void* p, size_t bytes) {
+    if (dev >= 0 && dev < kMaxDevices) {
+      std::lock_guard<std::mutex> lock(mu_);
+      if (cached_[dev] + bytes <= kCap) {
+        free_[dev].emplace(bytes, p);
+        cached_[dev] += bytes;
+        return;
+      }
+    }
+    cudaFree(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, void*> free_[kMaxDevices];
+  size_t cached_[kMaxDevices] = {};
+};
+
+BlockCache& block_cache() {
+  static BlockCache* c = new BlockCache();  // kept until exit: no teardown order issues
+  return *c;
+}
+
 struct DevAllocs {
-  std::vector<void*> ptrs;
+  struct Block {
+    void* p;
+    size_t bytes;
+    int dev;
+  };
+  std::vector<Block> blocks;
   ~DevAllocs() { release(); }
+  // returns the blocks to the cache once the device is idle (as cudaFree would
+  // wait): work still queued on any stream may use them
   void release() {
-    for (void* p : ptrs) cudaFree(p);
-    ptrs.clear();
+    if (blocks.empty()) return;
+    cudaDeviceSynchronize();
+    for (const Block& b : blocks) block_cache().put(b.dev, b.p, b.bytes);
+    blocks.clear();
   }
   template <class T>
   cudaError_t alloc(T** out, size_t count) {
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    const size_t bytes = (std::max<size_t>(count, 1) * sizeof(T) + 511) / 512 * 512;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    ptrs.push_back(p);
+    size_t got = bytes;
+    void* p = block_cache().get(dev, bytes, &got);
+    if (!p) {
+      e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) return e;
+    }
+    blocks.push_back(Block{p, got, dev});
     *out = static_cast<T*>(p);
     return cudaSuccess;
   }
@@ -137,6 +200,12 @@ struct maxsat_ctx {
   // dense tensor-core path (built when requested or for the measured choice)
   DevAllocs dense_mem;
   bool dense_built = false;  // dense operands exist
+  // MAXSAT_PATH_AUTO builds the dense operands only when its measurement
+  // needs them; until then it keeps the host inputs of that build
+  bool dense_pending = false;
+  std::vector<int64_t> lazy_off;
+  std::vector<int32_t> lazy_lits, lazy_var_off;
+  std::vector<int4> lazy_var_inc;
   bool dense = false;        // Gibbs rounds run on the dense path
   bool chains_dense = false; // layout of the allocated chain state
   int auto_B = 0;            // B of the last measured choice (AUTO)
@@ -449,8 +518,38 @@ int upload(maxsat_ctx* ctx, DevAllocs& A, std::vector<T> h, const T** out) {
 
 }  // namespace
 
+int build_dense(maxsat_ctx* ctx, int32_t n, int64_t m, const int64_t* off, const int32_t* lits,
+                const int64_t* weights, const std::vector<int32_t>& var_off,
+                const std::vector<int4>& var_inc, std::string* why);
+
+// Lower bound (ms) of one dense Gibbs round of B chains: its two tensor-core
+// products alone (the FP8 gather C x states, 2 m_pad n_pad Bp FLOPs, and the
+// block-diagonal BF16 scatter-add, 2 Bp x 128 x each 128-variable tile's
+// incidence range padded to 64) at the GB300's nominal dense peaks (4.5
+// PFLOP/s FP8, 2.25 PFLOP/s BF16 on 152 SMs), scaled to this device's SMs.
+double dense_round_lower_bound_ms(const maxsat_ctx* ctx, int32_t B) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  const double Bp = (double)((B + 255) / 256 * 256);
+  const int n = ctx->n;
+  const double n_pad = (double)((n + 127) / 128 * 128), m_pad = (double)((ctx->m + 127) / 128 * 128);
+  const std::vector<int32_t>& vo = ctx->lazy_var_off;
+  double scatter = 0.0;
+  for (int v0 = 0; v0 < n; v0 += 128) {
+    const int k = vo[std::min(v0 + 128, n)] - vo[v0];
+    scatter += 128.0 * 64.0 * std::max(1, (k + 63) / 64);
+  }
+  const double scale = (double)sms / 152.0;
+  return 1e3 * (2.0 * m_pad * n_pad * Bp / (4.5e15 * scale) + 2.0 * Bp * scatter / (2.25e15 * scale));
+}
+
 // Measured path choice (MAXSAT_PATH_AUTO): times a few Gibbs rounds of B
-// chains on each path with CUDA events and keeps the faster one.
+// chains on the sparse path, then on the dense path unless its tensor-core
+// products alone (at nominal peaks) would take longer than the measured
+// sparse round, and keeps the faster. The dense operands are built here, the
+// first time the dense path is measured.
 int choose_path(maxsat_ctx* ctx, int32_t B) {
   cudaEvent_t e0, e1;
   CK(ctx, cudaEventCreate(&e0));
@@ -458,9 +557,30 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   const bool prof = ctx->profiling;
   ctx->profiling = false;
   int rc = MAXSAT_OK;
-  // dense first: when the sparse path wins, its chain memory is the one left
-  // allocated and the reset that follows keeps it
-  for (int d = 1; d >= 0 && rc == MAXSAT_OK; --d) {
+  ctx->auto_ms[1] = -1.f;  // not measured
+  for (int d = 0; d <= 1 && rc == MAXSAT_OK; ++d) {
+    if (d == 1) {
+      if (ctx->dense_pending &&
+          dense_round_lower_bound_ms(ctx, B) >= (double)ctx->auto_ms[0])
+        break;  // the dense path cannot win: neither build nor measure it
+      if (ctx->dense_pending) {
+        std::string why;
+        const int drc =
+            build_dense(ctx, ctx->n, ctx->m, ctx->lazy_off.data(), ctx->lazy_lits.data(),
+                        ctx->h_w.data(), ctx->lazy_var_off, ctx->lazy_var_inc, &why);
+        ctx->dense_pending = false;
+        std::vector<int64_t>().swap(ctx->lazy_off);
+        std::vector<int32_t>().swap(ctx->lazy_lits);
+        std::vector<int32_t>().swap(ctx->lazy_var_off);
+        std::vector<int4>().swap(ctx->lazy_var_inc);
+        if (drc != MAXSAT_OK) {
+          ctx->dense_mem.release();  // not exact or too large: sparse only
+          break;
+        }
+        ctx->dense_built = true;
+      }
+      if (!ctx->dense_built) break;
+    }
     ctx->dense = d == 1;
     rc = alloc_chains(ctx, B);
     if (rc != MAXSAT_OK) break;
@@ -495,7 +615,7 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   cudaEventDestroy(e1);
   ctx->profiling = prof;
   if (rc != MAXSAT_OK) return rc;
-  ctx->dense = ctx->auto_ms[1] < ctx->auto_ms[0];
+  ctx->dense = ctx->auto_ms[1] >= 0.f && ctx->auto_ms[1] < ctx->auto_ms[0];
   ctx->auto_B = B;
   // the timing runs left no valid states (the caller, maxsat_reset, initialises
   // them next); the sparse layout's memory stays allocated when it won
@@ -1064,19 +1184,21 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
       return fail(nullptr, rcp, e_);
     }
   }
-  if (prm.path != MAXSAT_PATH_SPARSE && n_inst == 1) {
+  if (prm.path == MAXSAT_PATH_DENSE && n_inst == 1) {
     std::string why;
     const int drc = build_dense(ctx, n, m, off, lits, weights, var_off, var_inc, &why);
-    if (drc == MAXSAT_OK) {
-      ctx->dense_built = true;
-      ctx->dense = prm.path == MAXSAT_PATH_DENSE;
-    } else {
-      ctx->dense_mem.release();
-      if (prm.path == MAXSAT_PATH_DENSE) {
-        delete ctx;
-        return fail(nullptr, drc, why);
-      }
+    if (drc != MAXSAT_OK) {
+      delete ctx;
+      return fail(nullptr, drc, why);
     }
+    ctx->dense_built = true;
+    ctx->dense = true;
+  } else if (prm.path == MAXSAT_PATH_AUTO && n_inst == 1) {
+    ctx->dense_pending = true;
+    ctx->lazy_off.assign(off, off + m + 1);
+    ctx->lazy_lits.assign(lits, lits + off[m]);
+    ctx->lazy_var_off = var_off;
+    ctx->lazy_var_inc = var_inc;
   }
   *out = ctx;
   return MAXSAT_OK;
@@ -1158,7 +1280,8 @@ int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_
     return fail(ctx, MAXSAT_EINVAL,
                 "chain_offset must be a non-negative multiple of 8 and chain_offset + restarts "
                 "<= total_chains < 2^26 - 256");
-  if (ctx->prm.path == MAXSAT_PATH_AUTO && ctx->dense_built && ctx->auto_B != B) {
+  if (ctx->prm.path == MAXSAT_PATH_AUTO && (ctx->dense_built || ctx->dense_pending) &&
+      ctx->auto_B != B) {
     int rc0 = choose_path(ctx, B);
     if (rc0 != MAXSAT_OK) return rc0;
   }
