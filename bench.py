@@ -61,6 +61,10 @@ def parse():
                     help="skip the unit-propagation ablation probe")
     ap.add_argument("--no-ragged", action="store_true",
                     help="skip the batched ragged-instance probe (512 formulas)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the config 1 and config 3 probes")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the config 3 probe (mixed lengths, n = 20000, m = 100000)")
     ap.add_argument("--fixed-seconds", type=float, default=3.0,
                     help="wall time of the equal-time best-cost comparison")
     return ap.parse_args()
@@ -243,10 +247,10 @@ def dense_block_work(n, off, lits):
     return tot
 
 
-def alu_peak(clock_mhz):
-    """Instruction-issue peak: 152 SMs x 4 sub-partitions x 32 lanes, one
+def alu_peak(clock_mhz, sms):
+    """Instruction-issue peak: SMs x 4 sub-partitions x 32 lanes, one
     instruction per sub-partition per clock, at the SM clock seen."""
-    return 152 * 4 * 32 * clock_mhz * 1e6 / 1e12
+    return sms * 4 * 32 * clock_mhz * 1e6 / 1e12
 
 
 def sampling_ops(off):
@@ -260,7 +264,7 @@ def sampling_ops(off):
     return float((6 * L + lens).sum())
 
 
-def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks, clock_mhz, fp8=None):
+def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks, clock_mhz, sms, fp8=None):
     """(bound, algorithmic amount per launch, unit, peak) of one kernel.
     Sparse gather: integer operations of the hidden sampling against the
     instruction-issue peak. Sparse visible update: compulsory bytes against
@@ -274,7 +278,7 @@ def kernel_roofline(kernel, n, m, nnz, B, off, lits, peaks, clock_mhz, fp8=None)
     if kernel == "gemm2":
         return "tensor", 2.0 * B * dense_block_work(n, off, lits), "TFLOP/s", peaks["bf16_tflops_sustained"]
     if kernel == "gather_hidden":
-        return "alu", B * sampling_ops(off), "Tops/s", alu_peak(clock_mhz)
+        return "alu", B * sampling_ops(off), "Tops/s", alu_peak(clock_mhz, sms)
     return "hbm", algorithmic_bytes(kernel, n, m, nnz, B), "GB/s", peaks["hbm_gbs"]
 
 
@@ -392,7 +396,8 @@ def run_mine(args):
     peaks, peak_src = measured_peaks()
     clock = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp8 = fp8_peak(torch, peaks) if "gemm1" in top else None
-    bound, alg, unit, peak = kernel_roofline(top, n, m, nnz, B, off, lits, peaks, clock, fp8)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    bound, alg, unit, peak = kernel_roofline(top, n, m, nnz, B, off, lits, peaks, clock, sms, fp8)
     scale = 1e9 if unit == "GB/s" else 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -405,7 +410,7 @@ def run_mine(args):
                     frac=alg / avg_s / scale / peak, traffic=traffic,
                     algorithmic=alg, avg_launch_us=avg_s * 1e6,
                     peak_source=(f"{peak_src} copy bandwidth" if unit == "GB/s" else
-                                 f"issue peak 152 SM x 4 x 32 lanes at {clock:.0f} MHz (SM clock "
+                                 f"issue peak {sms} SM x 4 x 32 lanes at {clock:.0f} MHz (SM clock "
                                  "seen in the timed region)" if unit == "Tops/s" else
                                  (fp8[2] + ", sustained") if fp8 else f"{peak_src} BF16 sustained"),
                     kernels={k: dict(launches=v[0], avg_us=1e3 * v[1] / v[0])
@@ -477,6 +482,7 @@ def run_mine(args):
     up = up_probe(ms, torch, n, off, lits, w, B, stream, sets, args) if not args.no_up else None
     prop = proposal_probe(ms, torch, stream, sets, args) if not args.no_proposal else None
     pt = pt_probe(ms, torch, n, off, lits, w, B, stream, args) if not args.no_pt else None
+    configs = config_probe(ms, torch, stream, args) if not args.no_configs else None
 
     # the chains' state per round: hidden patterns (2 bytes when some clause
     # has 8 literals or more), x and best x, nu, per-block partials
@@ -503,7 +509,9 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 3 + 3 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop, tempering=pt)
+                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop, tempering=pt,
+                configs=configs)
+    line["summary"] = summary_of(line)
     ms.maxsat_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -907,6 +915,135 @@ def compare_paths(ms, torch, n, off, lits, w, B, stream, sets, seed, args):
         ms.maxsat_destroy(ctx)
         out[name] = dict(ms_per_round=ms_round, evals_per_s=(len(off) - 1) * B / (ms_round / 1e3),
                          kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()})
+    return out
+
+
+def _rounds_ms(ms, torch, ctx, stream, K):
+    """Device ms per Gibbs round over K rounds (CUDA events on the library's
+    stream), after the chains ran K rounds once."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ms.maxsat_step(ctx, K)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / K
+
+
+def config_probe(ms, torch, stream, args):
+    """The other configurations on this GPU (they are not the headline):
+    config 1, uniform 3-SAT n = 50, m = 215, 256 chains, 200 rounds (launch
+    and latency bound): evals/s of the rounds replayed from one CUDA graph and
+    of whole create + solve + destroy calls; config 3, mixed lengths 2..12,
+    n = 20000, m = 100000, 1024 chains: both paths (device ms per round, per
+    kernel) and the path MAXSAT_PATH_AUTO picks."""
+    out = {}
+    n, off, lits, w, B = workload("3sat-n50-m215", 0)
+    m = len(off) - 1
+    T = workloads.WORKLOADS["3sat-n50-m215"]["steps"]
+    p = ms.maxsat_default_params(n_buckets=1)
+    sets = ms_fitted_sets(ms, off, p)
+    p = ms.maxsat_default_params(sets=sets, n_buckets=1, steps_per_graph=T)
+    ctx = ms.maxsat_create(n, off, lits, w, p, stream)
+    ms.maxsat_reset(ctx, B, 0)
+    ms.maxsat_step(ctx, T)
+    ms_r = _rounds_ms(ms, torch, ctx, stream, T)
+    ms.maxsat_destroy(ctx)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        c = ms.maxsat_create(n, off, lits, w, p, stream)
+        best, _ = ms.maxsat_solve(c, B, T, 0)
+        ms.maxsat_destroy(c)
+    solve_s = (time.perf_counter() - t0) / 5
+    out["config1"] = dict(workload="3sat-n50-m215", B=B, rounds=T, path="auto",
+                          us_per_round=1e3 * ms_r, evals_per_s=m * B / (ms_r / 1e3),
+                          solve_ms=1e3 * solve_s, solve_evals_per_s=m * B * T / solve_s,
+                          best_cost=int(best))
+    if args.no_config3:
+        return out
+    n, off, lits, w, B = workload("mixed-n20000-m100000", 0)
+    m = len(off) - 1
+    t0 = time.perf_counter()
+    p = ms.maxsat_default_params()
+    sets = ms_fitted_sets(ms, off, p)
+    c3 = dict(workload="mixed-n20000-m100000", B=B, fit_s=time.perf_counter() - t0)
+    for name, code in [("sparse", ms.MAXSAT_PATH_SPARSE), ("dense", ms.MAXSAT_PATH_DENSE)]:
+        try:
+            t0 = time.perf_counter()
+            ctx = ms.maxsat_create(n, off, lits, w, ms.maxsat_default_params(sets=sets, path=code,
+                                                                             steps_per_graph=5),
+                                   stream)
+            create_s = time.perf_counter() - t0
+        except ms.MaxsatError as e:
+            c3[name] = dict(unavailable=str(e))
+            continue
+        ms.maxsat_reset(ctx, B, 1)
+        ms.maxsat_step(ctx, 5)
+        ms_r = _rounds_ms(ms, torch, ctx, stream, 10)
+        ms.maxsat_set_profiling(ctx, True)
+        ms.maxsat_step(ctx, 3)
+        kt = ms.maxsat_kernel_times(ctx)
+        ms.maxsat_set_profiling(ctx, False)
+        ms.maxsat_get_state(ctx)  # surfaces a device-side wait timeout, if any
+        ms.maxsat_destroy(ctx)
+        c3[name] = dict(ms_per_round=ms_r, evals_per_s=m * B / (ms_r / 1e3), create_s=create_s,
+                        kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()})
+        if name == "dense":
+            us = c3[name]["kernels_us"].get("gemm1_step")
+            if us:
+                burst, sust, fsrc = fp8_peak(torch, measured_peaks()[0])
+                m_pad, n_pad = (m + 127) // 128 * 128, (n + 127) // 128 * 128
+                Bp = (B + 255) // 256 * 256
+                c3[name]["gemm1_tflops"] = 2.0 * m_pad * n_pad * Bp / (us / 1e6) / 1e12
+                c3[name]["gemm1_frac_fp8"] = c3[name]["gemm1_tflops"] / sust
+    t0 = time.perf_counter()
+    ctx = ms.maxsat_create(n, off, lits, w, ms.maxsat_default_params(sets=sets), stream)
+    ms.maxsat_reset(ctx, B, 1)
+    stream.synchronize()
+    c3["auto"] = dict(choice={1: "dense", 2: "sparse"}[ms.maxsat_get_path(ctx)],
+                      create_and_reset_s=time.perf_counter() - t0)
+    ms.maxsat_destroy(ctx)
+    out["config3"] = c3
+    return out
+
+
+def summary_of(line):
+    """The figures a reader needs first, kept short: the line's end survives a
+    truncated log."""
+    r, e2e = line["roofline"], line["e2e"]
+    out = dict(value=line["value"], roofline=dict(kernel=r["kernel"], frac=round(r["frac"], 3),
+                                                    us=round(r["avg_launch_us"], 1)),
+               e2e_over_value=round(line["value"] / e2e["value"], 2) if e2e else None)
+    st = line.get("steady_state")
+    if st:
+        out["steady_state"] = st["value"]
+    de = line.get("dense_eval")
+    if de and "frac" in de:
+        out["dense_eval"] = dict(frac_fp8=round(de["frac"], 3), us=round(de["avg_launch_us"], 1),
+                                 pflops=round(de["achieved_tflops"] / 1e3, 3),
+                                 fp8_peak_pflops=round(de["peak_tflops"] / 1e3, 3),
+                                 whole_eval=de.get("whole_eval_evals_per_s"))
+    pa = line.get("paths")
+    if pa:
+        out["paths_ms"] = {k: round(v["ms_per_round"], 4) for k, v in pa.items() if "ms_per_round" in v}
+    cf = line.get("configs") or {}
+    if "config1" in cf:
+        out["config1"] = dict(evals_per_s=cf["config1"]["evals_per_s"],
+                              solve_evals_per_s=cf["config1"]["solve_evals_per_s"])
+    c3 = cf.get("config3")
+    if c3:
+        out["config3"] = {k: (dict(ms=round(v["ms_per_round"], 3), evals_per_s=v["evals_per_s"],
+                                   **({"gemm1_frac_fp8": round(v["gemm1_frac_fp8"], 3)}
+                                      if "gemm1_frac_fp8" in v else {}))
+                              if isinstance(v, dict) and "ms_per_round" in v else v)
+                          for k, v in c3.items() if k in ("sparse", "dense")}
+        out["config3"]["auto"] = c3.get("auto", {}).get("choice")
+    rg = line.get("ragged")
+    if rg and "evals_per_s" in rg:
+        out["ragged"] = {k: rg[k] for k in ("evals_per_s", "per_instance_evals_per_s") if k in rg}
+    pr = line.get("proposal")
+    if pr:
+        out["proposal"] = {k: pr[k] for k in ("median_wall_fraction", "flips_median_wall_fraction",
+                                              "held_out", "formulas") if k in pr}
     return out
 
 
