@@ -218,8 +218,6 @@ struct maxsat_ctx {
   uint8_t* d_grp_small = nullptr; // per 32-row group: 1 when its rows share one weight
   CUtensorMap tmA{};
   uint8_t* dXe = nullptr;         // eval scratch: Bp x n_pad FP8 states
-  int64_t* d_epart = nullptr;     // eval scratch: (m_pad / 128) x Bp partial costs
-  int32_t* d_etick = nullptr;     // eval scratch: Bp / 128 tickets
   int dev_Bp = 0;
   CUtensorMap tmXe{};
   int* d_err = nullptr;           // device wait-timeout code (0 = none)
@@ -1429,26 +1427,22 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
   if (ctx->dense_built) {
     const int Bp = (B + 255) / 256 * 256;
     if (Bp > ctx->dev_Bp) {
-      // grow the eval scratch (cudaFree of the old one synchronises the device)
+      // grow the eval scratch (releasing the old one waits for the device)
       ctx->dense_eval_mem.release();
       ctx->dev_Bp = 0;
       CK(ctx, ctx->dense_eval_mem.alloc(&ctx->dXe, (size_t)Bp * ctx->n_pad));
-      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_epart, (size_t)(ctx->m_pad / 128) * Bp));
-      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->d_etick, Bp / 256));
-      CK(ctx, cudaMemsetAsync(ctx->d_etick, 0, sizeof(int32_t) * (Bp / 256), ctx->stream));
       std::string e = make_tmap_2d(&ctx->tmXe, ctx->dXe, ctx->n_pad, Bp, ctx->n_pad, 128, 256, false);
       if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
       ctx->dev_Bp = Bp;
     }
     const int Bt = ctx->dev_Bp;
     TIMED(ctx, ctx->stream, "assign_fp8",
-          launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, ctx->stream));
+          launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, cost_dev,
+                            ctx->stream));
     TIMED(ctx, ctx->stream, "gemm1_eval",
           launch_gemm1_eval(ctx->tmA, ctx->tmXe, ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
-                            ctx->d_row_len, ctx->d_row_w, ctx->d_grp_small, ctx->d_epart,
-                            ctx->d_etick, cost_dev, ctx->d_err, ctx->stream));
-    TIMED(ctx, ctx->stream, "sum_tiles",
-          launch_sum_tiles(ctx->d_epart, ctx->m_pad, B, Bt, cost_dev, ctx->stream));
+                            ctx->d_row_len, ctx->d_row_w, ctx->d_grp_small, cost_dev, ctx->d_err,
+                            ctx->stream));
     return MAXSAT_OK;
   }
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;

@@ -29,8 +29,12 @@
 //              at a time, test each entry against the all-false value, a
 //              32 x 32 bit transpose turns rows into columns, the weighted
 //              unsatisfied cost of every chain is summed over the tile's 128
-//              rows; k_sum_tiles then sums the per-tile partials (16 lanes
-//              per chain, int64: exact in any order).
+//              rows and added to the chain's cost with a 64-bit atomic
+//              (integers: exact in any order).
+// An evaluation is two launches: k_assign_fp8 converts the assignments to
+// the FP8 B operand and zeroes the costs; k_gemm1_eval is its programmatic
+// dependent, so its setup (barriers, TMEM, tensor-map prefetch) overlaps the
+// conversion and it waits (griddepcontrol.wait) only before touching them.
 // Every mbarrier wait is bounded; a timeout records an error code that the
 // host reads after the launch, and the kernel still releases its TMEM.
 #include <cuda.h>
@@ -79,8 +83,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     k_gemm1_eval(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  int m, int num_kb, int tiles_m, int tiles_n, int B, int Bp, uint32_t idesc,
                  const int32_t* __restrict__ row_len, const int64_t* __restrict__ row_w,
-                 const uint8_t* __restrict__ grp_small, int64_t* __restrict__ part,
-                 int32_t* __restrict__ tickets, int64_t* __restrict__ out, int* err) {
+                 const uint8_t* __restrict__ grp_small, int64_t* __restrict__ out, int* err) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* tiles = smem_raw + (base - tc::smem_u32(smem_raw));
@@ -113,6 +116,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = S.tmem_slot;
+  // the B operand and the zeroed costs come from the preceding conversion
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == 0) {
     if (lane == 0) {
@@ -222,7 +227,9 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         int64_t csum = 0;
 #pragma unroll
         for (int qd = 0; qd < 4; ++qd) csum += S.cost[buf][(h * 4 + qd) * kCols + cc];
-        part[(size_t)tm * Bp + (size_t)tn * kBN + col] = csum;
+        const int b = tn * kBN + col;
+        if (b < B && csum != 0)
+          atomicAdd(reinterpret_cast<unsigned long long*>(out + b), (unsigned long long)csum);
       }
     }
   }
@@ -234,26 +241,16 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   }
 }
 
-// Sum of the per-tile partial costs: 16 lanes per chain split the tiles and
-// combine with shuffles (int64: exact in any order).
-__global__ void k_sum_tiles(const int64_t* __restrict__ part, int tiles_m, int Bp, int B,
-                            int64_t* __restrict__ out) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int b = gid >> 4, sub = gid & 15;
-  int64_t tot = 0;
-  if (b < B)
-    for (int k = sub; k < tiles_m; k += 16) tot += __ldg(part + (size_t)k * Bp + b);
-#pragma unroll
-  for (int s = 1; s < 16; s <<= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, s);
-  if (b < B && sub == 0) out[b] = tot;
-}
-
 // assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
 // variables, 0 for padding variables and padding chains; 16 output bytes
-// (one 16-byte store) per thread.
+// (one 16-byte store) per thread. Also zeroes the B costs the product then
+// accumulates into.
 __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, int Bp, int n_pad,
-                             uint8_t one, uint8_t minus_one, uint8_t* __restrict__ X) {
+                             uint8_t one, uint8_t minus_one, uint8_t* __restrict__ X,
+                             int64_t* __restrict__ cost) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (size_t)B) cost[idx] = 0;
   const int chunks = n_pad / 16;
   if (idx >= (size_t)Bp * chunks) return;
   const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
@@ -367,8 +364,8 @@ std::string build_gather_matrix(int n, int m, const int64_t* off, const int32_t*
 
 cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
-                              const int64_t* row_w, const uint8_t* grp_small, int64_t* part,
-                              int32_t* tickets, int64_t* out, int* err, cudaStream_t st) {
+                              const int64_t* row_w, const uint8_t* grp_small, int64_t* out,
+                              int* err, cudaStream_t st) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -386,28 +383,29 @@ cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, in
   const uint32_t idesc = tc::instr_desc(kBM, kBN, fmt, fmt);
   const int tiles_m = m_pad / kBM, tiles_n = Bp / kBN;
   const int grid = std::min(sms, tiles_m * tiles_n);
-  k_gemm1_eval<kEpiWarps><<<grid, 64 + 32 * kEpiWarps, kGemm1Smem, st>>>(tmA, tmB, m, n_pad / kBK, tiles_m, tiles_n, B,
-                                                   Bp, idesc, row_len, row_w, grp_small, part,
-                                                   tickets, out, err);
-  return cudaGetLastError();
-}
-
-
-
-cudaError_t launch_sum_tiles(const int64_t* part, int m_pad, int B, int Bp, int64_t* out,
-                             cudaStream_t st) {
-  k_sum_tiles<<<(16 * B + 255) / 256, 256, 0, st>>>(part, m_pad / kBM, Bp, B, out);
-  return cudaGetLastError();
+  // programmatic dependent of the conversion launched just before it
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(64 + 32 * kEpiWarps);
+  cfg.dynamicSmemBytes = kGemm1Smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gemm1_eval<kEpiWarps>, tmA, tmB, m, n_pad / kBK, tiles_m,
+                            tiles_n, B, Bp, idesc, row_len, row_w, grp_small, out, err);
 }
 
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
-                              uint8_t* X, cudaStream_t st) {
+                              uint8_t* X, int64_t* cost, cudaStream_t st) {
   uint8_t one, minus_one;
   fp8_encode_int(1, e5m2, &one);
   fp8_encode_int(-1, e5m2, &minus_one);
-  const size_t total = (size_t)Bp * (n_pad / 16);
+  const size_t total = std::max((size_t)Bp * (n_pad / 16), (size_t)B);
   k_assign_fp8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(assign, B, n, Bp, n_pad, one,
-                                                                 minus_one, X);
+                                                                 minus_one, X, cost);
   return cudaGetLastError();
 }
 

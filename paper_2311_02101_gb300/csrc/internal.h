@@ -286,15 +286,15 @@ std::string build_gather_matrix(int n, int m, const int64_t* off, const int32_t*
                                 bool* e5m2, int* n_pad, int* m_pad, std::vector<uint8_t>* A);
 std::string make_tmap_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows,
                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows, bool bf16);
+// adds every chain's weighted unsatisfied cost into out (B, zeroed by
+// launch_assign_fp8, which must be the launch just before it on st)
 cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
-                              const int64_t* row_w, const uint8_t* grp_small, int64_t* part,
-                              int32_t* tickets, int64_t* out, int* err, cudaStream_t st);
-// per-tile partial costs of launch_gemm1_eval -> out (B)
-cudaError_t launch_sum_tiles(const int64_t* part, int m_pad, int B, int Bp, int64_t* out,
-                             cudaStream_t st);
+                              const int64_t* row_w, const uint8_t* grp_small, int64_t* out,
+                              int* err, cudaStream_t st);
+// assignments -> FP8 B operand X; zeroes cost (B)
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
-                              uint8_t* X, cudaStream_t st);
+                              uint8_t* X, int64_t* cost, cudaStream_t st);
 
 // dense_step.cu: the dense Gibbs round
 cudaError_t launch_gemm1_step(bool sample, const CUtensorMap& tmA, const CUtensorMap& tmB, int m,
