@@ -52,7 +52,11 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-proposal", action="store_true",
                     help="skip the learned-proposal probe (training + held-out comparison)")
-    ap.add_argument("--proposal-train", type=int, default=1024,
+    ap.add_argument("--proposal-epochs", type=int, default=4,
+                    help="training epochs of the learned proposal")
+    ap.add_argument("--proposal-held-out", type=int, default=32,
+                    help="held-out formulas of the learned proposal")
+    ap.add_argument("--proposal-train", type=int, default=10000,
                     help="solver-labelled training formulas for the proposal probe")
     ap.add_argument("--no-pt", action="store_true", help="skip the parallel-tempering probe")
     ap.add_argument("--no-dense", action="store_true",
@@ -167,6 +171,16 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+
+    def wait_first(self, timeout=5.0):
+        """Blocks until nvidia-smi has written its first sample (or timeout)."""
+        t0 = time.perf_counter()
+        while self.p is not None and time.perf_counter() - t0 < timeout:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                return True
+            time.sleep(0.02)
+        return False
 
     def stop(self):
         if self.p is None:
@@ -349,13 +363,31 @@ def run_mine(args):
     flushed_rounds(3)  # warm-up of this launch pattern
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    # SM clocks are sampled every 100 ms over a load window that contains the
+    # timed region (which alone is a few ms): a second context of the same
+    # formula runs Gibbs rounds for 0.5 s before and 0.3 s after it
     clocks = Clocks(local)
+    clocks.wait_first()
+    load_ctx = ms.maxsat_create(n, off, lits, w, params, stream)
+    ms.maxsat_reset_shard(load_ctx, B, seed + 1, offset, total)
+
+    def load(seconds):
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            ms.maxsat_step(load_ctx, 100)
+            stream.synchronize()
+
+    load(0.5)
     barrier()
     torch.cuda.synchronize()
     flushed_rounds(args.steps, evs)
     torch.cuda.synchronize()
     barrier()
+    load(0.3)
     ck = clocks.stop()
+    if ck is not None:
+        ck["window"] = "load window of about 0.8 s containing the timed region"
+    ms.maxsat_destroy(load_ctx)
     ms_total = sum(a.elapsed_time(b) for a, b in evs)
     if ws > 1:
         t = torch.tensor([ms_total], device="cuda")
@@ -649,16 +681,50 @@ def fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args, our
                 note="FP32 torch matmuls (TF32 off) + lookups, torch generator draws")
 
 
+def _features(n, off, lits):
+    """The network's variable input features without the constant:
+    positive-occurrence share minus 1/2 and log(1 + degree) / 4 (0 share for
+    a variable without occurrences)."""
+    var = np.abs(lits.astype(np.int64)) - 1
+    deg = np.bincount(var, minlength=n).astype(np.float64)
+    pos = np.bincount(var[lits > 0], minlength=n).astype(np.float64)
+    share = np.where(deg > 0, pos / np.maximum(deg, 1.0), 0.5) - 0.5
+    return np.stack([share, np.log1p(deg) / 4.0, np.ones(n)], axis=1)
+
+
+def _logistic_fit(X, y, iters=12):
+    """Logistic regression by Newton's method (a features-only baseline)."""
+    w = np.zeros(X.shape[1])
+    for _ in range(iters):
+        p = 1.0 / (1.0 + np.exp(-X @ w))
+        g = X.T @ (p - y)
+        H = (X * (p * (1 - p))[:, None]).T @ X + 1e-9 * np.eye(X.shape[1])
+        w -= np.linalg.solve(H, g)
+    return w
+
+
+def _bce_acc(p, y):
+    p = np.clip(p.astype(np.float64), 1e-7, 1 - 1e-7)
+    return (float(-np.mean(y * np.log(p) + (1 - y) * np.log(1 - p))),
+            float(np.mean((p >= 0.5) == (y == 1))))
+
+
 def proposal_probe(ms, torch, stream, sets, args):
     """Learned proposal (config 5): a 3-layer, 64-wide message-passing network
     trained by the library's kernels on solver-labelled random weighted
     3-SAT formulas (n uniform in [500, 2000], m = 6 n, weights uniform in
-    [1, 1000]; labels = best assignment of 256 chains after 1000 rounds), then
-    held-out formulas (n = 2000, m = 12000) solved from uniform starts and
-    from the network's starts with the same seed and chains. Reports the mean
-    best cost at round checkpoints and, per formula, the fraction of plain's
-    rounds (and wall time) the learned start needs to reach plain's final
-    best cost."""
+    [1, 1000]; label = best assignment of 256 chains after 500 rounds).
+    On held-out formulas (n = 2000, m = 12000, labelled the same way):
+    binary cross entropy and per-variable accuracy of the network and of a
+    features-only logistic regression on the network's own input features;
+    then each held-out formula is solved from uniform starts (plain), from
+    the network's starts, from the network's starts with flip proposals
+    every 200 rounds, and from the features-only model's starts, the same
+    seed and chains, best cost read every 50
+    rounds; per formula the fraction of plain's rounds and wall time the
+    learned modes need to reach plain's best after 2000 rounds. The share of
+    the network's dense layers in its training time comes from CUDA events
+    around every training launch of one batch."""
     from paper_2311_02101_gb300 import proposal as P
     rng = np.random.default_rng(args.seed + 17)
 
@@ -672,26 +738,58 @@ def proposal_probe(ms, torch, stream, sets, args):
     p = ms.maxsat_default_params(sets=sets)
     t0 = time.perf_counter()
     train = gen(args.proposal_train, 500, 2000)
-    labels = P.label_with_solver(train, p, restarts=256, steps=1000, seed=3, stream=stream)
+    labels = P.label_with_solver(train, p, restarts=256, steps=500, seed=3, batch=512,
+                                 stream=stream)
     t1 = time.perf_counter()
     model = ms.maxsat_mp_create(3, seed=0)
-    epochs = 20
-    losses = P.train(model, train, labels, p, epochs=epochs, batch=32, lr=2e-3, stream=stream)
+    losses = P.train(model, train, labels, p, epochs=args.proposal_epochs, batch=32, lr=2e-3,
+                     stream=stream)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    cps = [0, 50, 100, 200, 400, 600, 800, 1000, 1500, 2000]
-    modes = ("plain", "learned", "learned+flips")
+    # the training launches of one batch of 32 formulas, each timed by CUDA events
+    ctx = ms.maxsat_create_batch(train[:32], p, stream)
+    y = torch.tensor(np.concatenate(labels[:32]).astype(np.uint8), device="cuda")
+    torch.cuda.synchronize()
+    ms.maxsat_set_profiling(ctx, True)
+    for _ in range(10):
+        ms.maxsat_mp_gradient(model, ctx, y)
+        ms.maxsat_mp_adam(model, ctx, 1e-12)
+    kt = ms.maxsat_kernel_times(ctx)
+    ms.maxsat_set_profiling(ctx, False)
+    ms.maxsat_destroy(ctx)
+    tot = sum(v[1] for v in kt.values())
+    dense_share = sum(v[1] for k, v in kt.items() if k.startswith("mp_dense")) / tot
+    # features-only baseline, fitted on (a sample of) the training variables
+    Xtr = np.concatenate([_features(f[0], f[1], f[2]) for f in train[:2000]])
+    ytr = np.concatenate(labels[:2000]).astype(np.float64)
+    wlog = _logistic_fit(Xtr, ytr)
+    held = gen(args.proposal_held_out, 2000, 2000)
+    held_labels = P.label_with_solver(held, p, restarts=256, steps=500, seed=5, batch=32,
+                                      stream=stream)
+    cps = list(range(0, 2001, 50))
+    modes = ("plain", "learned", "learned+flips", "features")
     mean = {k: np.zeros(len(cps)) for k in modes}
-    frac, frac_t, frac_f, frac_ft = [], [], [], []
-    test = gen(8, 2000, 2000)
-    for f in test:
+    fr = {k: [] for k in modes[1:]}
+    ft = {k: [] for k in modes[1:]}
+    net_bce, net_acc, feat_bce, feat_acc = [], [], [], []
+    for f, yl in zip(held, held_labels):
         ctx = ms.maxsat_create(*f, p, stream)
+        prob = P.propose(model, ctx)
+        b, a = _bce_acc(prob, yl)
+        net_bce.append(b)
+        net_acc.append(a)
+        pfeat = (1.0 / (1.0 + np.exp(-_features(f[0], f[1], f[2]) @ wlog))).astype(np.float32)
+        b, a = _bce_acc(pfeat, yl)
+        feat_bce.append(b)
+        feat_acc.append(a)
         curves, times = {}, {}
         for mode in modes:
             torch.cuda.synchronize()
             ts = time.perf_counter()
             if mode == "plain":
                 ms.maxsat_reset(ctx, 256, 11)
+            elif mode == "features":  # starts from the features-only model
+                ms.maxsat_reset_probs(ctx, 256, 11, pfeat)
             else:
                 prob = P.propose(model, ctx)
                 ms.maxsat_reset_probs(ctx, 256, 11, prob)
@@ -708,30 +806,41 @@ def proposal_probe(ms, torch, stream, sets, args):
                 tt.append(time.perf_counter() - ts)
                 cur.append(int(st["best_cost"].min()))
             curves[mode], times[mode] = cur, tt
-            mean[mode] += np.array(cur, float) / len(test)
+            mean[mode] += np.array(cur, float) / len(held)
         target = curves["plain"][-1]
-        k = next((i for i, c in enumerate(curves["learned"]) if c <= target), None)
-        frac.append(cps[k] / cps[-1] if k is not None else None)
-        frac_t.append(times["learned"][k] / times["plain"][-1] if k is not None else None)
-        k = next((i for i, c in enumerate(curves["learned+flips"]) if c <= target), None)
-        frac_f.append(cps[k] / cps[-1] if k is not None else None)
-        frac_ft.append(times["learned+flips"][k] / times["plain"][-1] if k is not None else None)
+        for mode in fr:
+            k = next((i for i, c in enumerate(curves[mode]) if c <= target), None)
+            fr[mode].append(cps[k] / cps[-1] if k is not None else None)
+            ft[mode].append(times[mode][k] / times["plain"][-1] if k is not None else None)
         ms.maxsat_destroy(ctx)
     ms.maxsat_mp_destroy(model)
-    ok = [x for x in frac if x is not None]
-    return dict(train_formulas=len(train), label_s=t1 - t0, train_s=t2 - t1,
-                train_steps=len(losses), loss_first=losses[0],
-                loss_last=float(np.mean(losses[-32:])), held_out=len(test), checkpoints=cps,
-                mean_best_plain=[int(x) for x in mean["plain"]],
-                mean_best_learned=[int(x) for x in mean["learned"]],
-                mean_best_learned_flips=[int(x) for x in mean["learned+flips"]],
-                rounds_fraction_to_plain_final=frac, wall_fraction_to_plain_final=frac_t,
-                median_rounds_fraction=float(np.median(ok)) if ok else None,
-                flips_rounds_fraction_to_plain_final=frac_f,
-                flips_wall_fraction_to_plain_final=frac_ft,
-                flips_median_wall_fraction=(float(np.median([x for x in frac_ft if x is not None]))
-                                            if any(x is not None for x in frac_ft) else None),
-                note="checkpoint scoring (maxsat_score + state copy) is inside both wall times")
+
+    def med(xs):
+        ok = [x for x in xs if x is not None]
+        return float(np.median(ok)) if len(ok) == len(xs) else None
+
+    return dict(formulas=len(train), label_rounds=500, label_s=t1 - t0, train_s=t2 - t1,
+                epochs=args.proposal_epochs, train_steps=len(losses), loss_first=losses[0],
+                loss_last=float(np.mean(losses[-64:])), held_out=len(held),
+                held_out_bce=float(np.mean(net_bce)), held_out_accuracy=float(np.mean(net_acc)),
+                features_only=dict(weights=wlog.tolist(), bce=float(np.mean(feat_bce)),
+                                   accuracy=float(np.mean(feat_acc))),
+                dense_layer_share_of_training=dense_share,
+                training_kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()},
+                checkpoint_every=50,
+                mean_best_plain=[int(x) for x in mean["plain"][::4]],
+                mean_best_learned=[int(x) for x in mean["learned"][::4]],
+                mean_best_learned_flips=[int(x) for x in mean["learned+flips"][::4]],
+                rounds_fraction_learned=fr["learned"], wall_fraction_learned=ft["learned"],
+                rounds_fraction_flips=fr["learned+flips"], wall_fraction_flips=ft["learned+flips"],
+                mean_best_features_start=[int(x) for x in mean["features"][::4]],
+                wall_fraction_features_start=ft["features"],
+                median_wall_fraction=med(ft["learned"]),
+                flips_median_wall_fraction=med(ft["learned+flips"]),
+                features_start_median_wall_fraction=med(ft["features"]),
+                note="mean_best_* every 200 rounds; a fraction is None when the mode does not "
+                     "reach plain's final best by round 2000 (then the median is None); "
+                     "checkpoint scoring (maxsat_score + state copy) is inside every wall time")
 
 
 def pt_probe(ms, torch, n, off, lits, w, B, stream, args, E=8, period=10):
@@ -839,12 +948,42 @@ def ragged_probe(ms, torch, stream, sets, args):
     ms.maxsat_set_profiling(ctx, False)
     best, _ = ms.maxsat_solve(ctx, B, 50, 7)
     ms.maxsat_destroy(ctx)
-    return dict(workload="ragged-512", instances=len(insts), clauses=m_tot, clause_block=cb,
-                variables=int(sum(i[0] for i in insts)), B=B, rounds=K, ms_per_round=ms_round,
-                evals_per_s=m_tot * B / (ms_round / 1e3), unit="evals/s",
-                kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()},
-                launches_per_round=sum(v[0] for k, v in kt.items()) / max(10, K // 4),
-                best_cost_sum_50_rounds=int(np.sum(best)))
+    out = dict(workload="ragged-512", instances=len(insts), clauses=m_tot, clause_block=cb,
+               variables=int(sum(i[0] for i in insts)), B=B, rounds=K, ms_per_round=ms_round,
+               evals_per_s=m_tot * B / (ms_round / 1e3), unit="evals/s",
+               kernels_us={k: 1e3 * v[1] / v[0] for k, v in kt.items()},
+               launches_per_round=sum(v[0] for k, v in kt.items()) / max(10, K // 4),
+               best_cost_sum_50_rounds=int(np.sum(best)))
+    # the comparator: the same formulas, one (sparse) context each, the same
+    # K rounds from one CUDA graph per context; issued on one stream, then
+    # round-robin over 16 streams so that small formulas can run side by side
+    streams = [stream] + [torch.cuda.Stream() for _ in range(15)]
+    for label, nstreams in (("per_instance", 1), ("per_instance_16_streams", 16)):
+        try:
+            ctxs = [ms.maxsat_create(*inst, ms.maxsat_default_params(
+                        sets=sets, path=ms.MAXSAT_PATH_SPARSE, steps_per_graph=K),
+                        streams[k % nstreams])
+                    for k, inst in enumerate(insts)]
+        except ms.MaxsatError as e:
+            out[label] = dict(unavailable=str(e))
+            continue
+        for c in ctxs:
+            ms.maxsat_reset(c, B, 7)
+            ms.maxsat_step(c, K)  # captures each context's graph, warms up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in ctxs:
+            ms.maxsat_step(c, K)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        for c in ctxs:
+            ms.maxsat_destroy(c)
+        out[label] = dict(ms_per_round=1e3 * wall / K, evals_per_s=m_tot * B * K / wall,
+                          graphs=len(ctxs), streams=nstreams,
+                          note="host wall clock around all contexts' graph launches")
+    if "ms_per_round" in out.get("per_instance", {}):
+        out["per_instance_evals_per_s"] = out["per_instance"]["evals_per_s"]
+    return out
 
 
 def dense_eval_probe(ms, torch, n, off, lits, w, B, stream, sets, args):
@@ -1052,8 +1191,13 @@ def summary_of(line):
         out["ragged"] = {k: rg[k] for k in ("evals_per_s", "per_instance_evals_per_s") if k in rg}
     pr = line.get("proposal")
     if pr:
-        out["proposal"] = {k: pr[k] for k in ("median_wall_fraction", "flips_median_wall_fraction",
-                                              "held_out", "formulas") if k in pr}
+        out["proposal"] = {k: (round(pr[k], 4) if isinstance(pr[k], float) else pr[k])
+                           for k in ("median_wall_fraction", "flips_median_wall_fraction",
+                                     "held_out", "formulas", "held_out_bce", "held_out_accuracy",
+                                     "dense_layer_share_of_training",
+                                     "features_start_median_wall_fraction") if k in pr}
+        if "features_only" in pr:
+            out["proposal"]["features_only_bce"] = round(pr["features_only"]["bce"], 4)
     return out
 
 

@@ -350,7 +350,8 @@ int maxsat_reset_probs(maxsat_ctx* ctx, int32_t restarts, uint64_t seed, const f
 
 /* Per-kernel timing. While profiling is on, maxsat_step and maxsat_score use
  * plain launches (no CUDA graph) and bracket every kernel launch with CUDA
- * events on the context's stream; maxsat_kernel_times then synchronises and
+ * events on the context's stream (the learned proposal's launches on that
+ * context too, named mp_*); maxsat_kernel_times then synchronises and
  * reports, per kernel name, the number of launches and their total device
  * time in milliseconds since profiling was switched on. names receives up to
  * max_kernels NUL-terminated names of at most 31 characters (32 bytes each).

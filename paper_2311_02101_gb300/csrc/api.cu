@@ -1972,6 +1972,18 @@ int mp_fail(maxsat_mp* mp, int code, const std::string& msg) {
   else g_create_error = msg;
   return code;
 }
+
+// an MP launch, bracketed by CUDA events under the formula context's
+// profiling (maxsat_set_profiling / maxsat_kernel_times), as the Gibbs kernels
+#define MPT(mp, ctx, name, expr)                                                \
+  do {                                                                          \
+    if ((ctx)->profiling) {                                                     \
+      const int rc_ = timed((ctx), (ctx)->stream, name, [&]() { return (expr); }); \
+      if (rc_ != MAXSAT_OK) return mp_fail(mp, rc_, (ctx)->err);                \
+    } else {                                                                    \
+      MPCK(mp, expr);                                                           \
+    }                                                                           \
+  } while (0)
 #define MPCK(mp, expr)                                                         \
   do {                                                                          \
     cudaError_t e_ = (expr);                                                    \
@@ -2045,18 +2057,18 @@ int mp_forward(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* y, float* prob) {
   int rc = mp_reserve(mp, n, m);
   if (rc != MAXSAT_OK) return rc;
   const MpLayout& Y = mp->lay;
-  MPCK(mp, mp_launch_features(F, mp->f, mp->g, mp->inv_len, mp->inv_deg, st));
-  MPCK(mp, mp_launch_proj(mp->f, n, mp->Pb + Y.Wf, mp->hv[0], st));
-  MPCK(mp, mp_launch_proj(mp->g, m, mp->Pb + Y.Wg, mp->hc[0], st));
+  MPT(mp, ctx, "mp_features", mp_launch_features(F, mp->f, mp->g, mp->inv_len, mp->inv_deg, st));
+  MPT(mp, ctx, "mp_proj", mp_launch_proj(mp->f, n, mp->Pb + Y.Wf, mp->hv[0], st));
+  MPT(mp, ctx, "mp_proj", mp_launch_proj(mp->g, m, mp->Pb + Y.Wg, mp->hc[0], st));
   for (int l = 0; l < L; ++l) {
-    MPCK(mp, mp_launch_clause_agg(F, mp->hv[l], mp->inv_len, nullptr, mp->mc[l], false, st));
-    MPCK(mp, mp_launch_dense_fwd(mp->mc[l], mp->hc[l], m, mp->Pb + Y.Wc[l], mp->P + Y.bc[l],
+    MPT(mp, ctx, "mp_clause_agg", mp_launch_clause_agg(F, mp->hv[l], mp->inv_len, nullptr, mp->mc[l], false, st));
+    MPT(mp, ctx, "mp_dense_fwd", mp_launch_dense_fwd(mp->mc[l], mp->hc[l], m, mp->Pb + Y.Wc[l], mp->P + Y.bc[l],
                                  mp->hc[l + 1], st));
-    MPCK(mp, mp_launch_var_agg(F, mp->hc[l + 1], nullptr, mp->inv_deg, mp->av[l], false, st));
-    MPCK(mp, mp_launch_dense_fwd(mp->av[l], mp->hv[l], n, mp->Pb + Y.Wv[l], mp->P + Y.bv[l],
+    MPT(mp, ctx, "mp_var_agg", mp_launch_var_agg(F, mp->hc[l + 1], nullptr, mp->inv_deg, mp->av[l], false, st));
+    MPT(mp, ctx, "mp_dense_fwd", mp_launch_dense_fwd(mp->av[l], mp->hv[l], n, mp->Pb + Y.Wv[l], mp->P + Y.bv[l],
                                  mp->hv[l + 1], st));
   }
-  MPCK(mp, mp_launch_out(mp->hv[L], n, mp->P + Y.wo, mp->P + Y.bo, y, prob, y ? mp->dz : nullptr,
+  MPT(mp, ctx, "mp_out", mp_launch_out(mp->hv[L], n, mp->P + Y.wo, mp->P + Y.bo, y, prob, y ? mp->dz : nullptr,
                          y ? mp->loss_part : nullptr, st));
   return MAXSAT_OK;
 }
@@ -2141,25 +2153,31 @@ int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev
   const MpLayout& Y = mp->lay;
   cudaStream_t st = ctx->stream;
   float* G = mp->G;
-  MPCK(mp, mp_launch_out_bwd(mp->hv[L], mp->dz, n, mp->P + Y.wo, mp->dhv, mp->part, G + Y.wo, st));
+  MPT(mp, ctx, "mp_out_bwd", mp_launch_out_bwd(mp->hv[L], mp->dz, n, mp->P + Y.wo, mp->dhv, mp->part, G + Y.wo, st));
   bool carry = false;  // dhc holds the gradient of h_c^l from clause layer l + 1
   for (int l = L - 1; l >= 0; --l) {
     // variable layer l: h_v^{l+1} = relu(Wv_l [a_v ; h_v^l] + bv_l)
-    MPCK(mp, mp_launch_dense_bwd(mp->dhv, mp->hv[l + 1], mp->av[l], mp->hv[l], n,
-                                 mp->Pb + Y.Wv[l], mp->dav, mp->dhv2, mp->part, G + Y.Wv[l], st));
+    MPT(mp, ctx, "mp_dense_bwd_x", mp_launch_dense_bwd_x(mp->dhv, mp->hv[l + 1], n,
+                                 mp->Pb + Y.Wv[l], mp->dav, mp->dhv2, st));
+    MPT(mp, ctx, "mp_dense_wgrad", mp_launch_dense_wgrad(mp->dhv, mp->hv[l + 1], mp->av[l],
+                                 mp->hv[l], n, mp->part, G + Y.Wv[l], st));
+    MPT(mp, ctx, "mp_dense_wsum", mp_launch_dense_wsum(mp->part, n, G + Y.Wv[l], st));
     // a_v = (1 / deg_v) sum s h_c^{l+1}: gradient of h_c^{l+1}
-    MPCK(mp, mp_launch_clause_agg(F, mp->dav, nullptr, mp->inv_deg, mp->dhc, carry, st));
+    MPT(mp, ctx, "mp_clause_agg", mp_launch_clause_agg(F, mp->dav, nullptr, mp->inv_deg, mp->dhc, carry, st));
     // clause layer l: h_c^{l+1} = relu(Wc_l [m_c ; h_c^l] + bc_l)
-    MPCK(mp, mp_launch_dense_bwd(mp->dhc, mp->hc[l + 1], mp->mc[l], mp->hc[l], m,
-                                 mp->Pb + Y.Wc[l], mp->dmc, mp->dhc2, mp->part, G + Y.Wc[l], st));
+    MPT(mp, ctx, "mp_dense_bwd_x", mp_launch_dense_bwd_x(mp->dhc, mp->hc[l + 1], m,
+                                 mp->Pb + Y.Wc[l], mp->dmc, mp->dhc2, st));
+    MPT(mp, ctx, "mp_dense_wgrad", mp_launch_dense_wgrad(mp->dhc, mp->hc[l + 1], mp->mc[l],
+                                 mp->hc[l], m, mp->part, G + Y.Wc[l], st));
+    MPT(mp, ctx, "mp_dense_wsum", mp_launch_dense_wsum(mp->part, m, G + Y.Wc[l], st));
     // m_c = (1 / len_c) sum s h_v^l: gradient of h_v^l
-    MPCK(mp, mp_launch_var_agg(F, mp->dmc, mp->inv_len, nullptr, mp->dhv2, true, st));
+    MPT(mp, ctx, "mp_var_agg", mp_launch_var_agg(F, mp->dmc, mp->inv_len, nullptr, mp->dhv2, true, st));
     std::swap(mp->dhv, mp->dhv2);
     std::swap(mp->dhc, mp->dhc2);
     carry = true;
   }
-  MPCK(mp, mp_launch_proj_bwd(mp->dhv, mp->hv[0], mp->f, n, mp->part, G + Y.Wf, st));
-  MPCK(mp, mp_launch_proj_bwd(mp->dhc, mp->hc[0], mp->g, m, mp->part, G + Y.Wg, st));
+  MPT(mp, ctx, "mp_proj_bwd", mp_launch_proj_bwd(mp->dhv, mp->hv[0], mp->f, n, mp->part, G + Y.Wf, st));
+  MPT(mp, ctx, "mp_proj_bwd", mp_launch_proj_bwd(mp->dhc, mp->hc[0], mp->g, m, mp->part, G + Y.Wg, st));
   if (loss) {
     const int nb = (n + 7) / 8;
     std::vector<double> lp((size_t)nb);
@@ -2175,7 +2193,7 @@ int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev
 int maxsat_mp_adam(maxsat_mp* mp, maxsat_ctx* ctx, float lr) {
   if (!mp || !ctx || !(lr > 0.f)) return MAXSAT_EINVAL;
   mp->step += 1;
-  MPCK(mp, mp_launch_adam(mp->P, mp->G, mp->M, mp->V, mp->lay.total, lr, 0.9f, 0.999f, 1e-8f,
+  MPT(mp, ctx, "mp_adam", mp_launch_adam(mp->P, mp->G, mp->M, mp->V, mp->lay.total, lr, 0.9f, 0.999f, 1e-8f,
                           mp->step, mp->Pb, ctx->stream));
   return MAXSAT_OK;
 }

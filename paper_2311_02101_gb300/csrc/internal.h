@@ -211,9 +211,12 @@ cudaError_t mp_launch_var_agg(const DevFormula& F, const float* h, const float* 
 cudaError_t mp_launch_dense_fwd(const float* A, const float* Bm, int rows, const __nv_bfloat16* W,
                                 const float* b, float* out, cudaStream_t st);
 // gW receives 64 x 128 weight gradients followed by the 64 bias gradients
-cudaError_t mp_launch_dense_bwd(const float* dout, const float* out, const float* A,
-                                const float* Bm, int rows, const __nv_bfloat16* W, float* dA,
-                                float* dB, float* part, float* gW, cudaStream_t st);
+cudaError_t mp_launch_dense_bwd_x(const float* dout, const float* out, int rows,
+                                  const __nv_bfloat16* W, float* dA, float* dB, cudaStream_t st);
+cudaError_t mp_launch_dense_wgrad(const float* dout, const float* out, const float* A,
+                                  const float* Bm, int rows, float* part, float* gW,
+                                  cudaStream_t st);
+cudaError_t mp_launch_dense_wsum(const float* part, int rows, float* gW, cudaStream_t st);
 cudaError_t mp_launch_proj_bwd(const float* dout, const float* out, const float* in, int rows,
                                float* part, float* gW, cudaStream_t st);
 cudaError_t mp_launch_out(const float* h, int n, const float* wo, const float* bo,

@@ -15,9 +15,10 @@
 // every Adam step); activations, biases and all sums are FP32. Every kernel is
 // hand-written: the signed-mean aggregations walk the same clause and
 // variable incidence lists as the Gibbs round (one warp per clause or
-// variable, two features per lane), the dense layers stage the weights in
-// shared memory, and weight gradients are reduced in two deterministic
-// stages (per-block partials, then a fixed-order sum). No atomics.
+// variable, two features per lane), the 64 x 128 dense layers run on the
+// tensor cores (mma.sync BF16, activations as three BF16 terms), and weight
+// gradients are reduced in two deterministic stages (per-block partials,
+// then a fixed-order sum). No atomics.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,7 +35,8 @@ namespace rbmsat {
 namespace {
 
 constexpr int kH = 64;
-constexpr int kRowsW = 256;  // rows per block of the weight-gradient partials
+constexpr int kRowsW = 256;    // rows per block of the projections' weight-gradient partials
+constexpr int kRowsTc = 256;   // rows per block of the dense layers' weight-gradient partials
 
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
 
@@ -132,60 +134,247 @@ __global__ void k_mp_var_agg(DevFormula F, const float* h, const float* cscale,
 }
 
 // ------------------------------------------------------------ dense layers
-// out[r] = relu(W [A[r] ; B[r]] + b), W 64 x 128 (BF16), 256 threads, 32 rows
-// per block (4 rows at a time, one output feature per thread).
+// The three 64 x 128 contractions of a dense layer (forward, input gradient,
+// weight gradient) run on the tensor cores: mma.sync m16n8k16 with BF16
+// operands and FP32 accumulation. The weights are BF16 already; an FP32
+// activation or gradient v enters as three BF16 terms hi + mid + lo (hi =
+// bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid)), so that products
+// with BF16 weights sum to FP32 accuracy; the weight gradient, a product of
+// two FP32 operands, keeps the three leading cross terms (hi x hi, hi x mid,
+// mid x hi).
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// the three BF16 terms of a pair of FP32 values, packed as BF16 pairs
+__device__ __forceinline__ void split3(float x0, float x1, uint32_t& t0, uint32_t& t1,
+                                       uint32_t& t2) {
+  const float h0 = __bfloat162float(__float2bfloat16_rn(x0));
+  const float h1 = __bfloat162float(__float2bfloat16_rn(x1));
+  const float r0 = x0 - h0, r1 = x1 - h1;  // exact
+  const float m0 = __bfloat162float(__float2bfloat16_rn(r0));
+  const float m1 = __bfloat162float(__float2bfloat16_rn(r1));
+  t0 = pack_bf16(h0, h1);
+  t1 = pack_bf16(m0, m1);
+  t2 = pack_bf16(r0 - m0, r1 - m1);
+}
+
+__device__ __forceinline__ float2 ld2(const float* base, int rows, int r, int k) {
+  return r < rows ? *reinterpret_cast<const float2*>(base + (size_t)r * kH + k)
+                  : make_float2(0.f, 0.f);
+}
+
+// out[r] = relu(W [A[r] ; B[r]] + b), W 64 x 128 (BF16): one warp = 16 rows
+// x 64 outputs, 8 warps per block.
 __global__ void __launch_bounds__(256) k_mp_dense_fwd(const float* A, const float* Bm, int rows,
                                                       const __nv_bfloat16* W, const float* b,
                                                       float* out) {
-  __shared__ float Wt[2 * kH][kH];  // transposed: Wt[k][j]
-  __shared__ float x[4][2 * kH];
-  for (int e = threadIdx.x; e < kH * 2 * kH; e += 256) {
-    const int j = e / (2 * kH), k = e % (2 * kH);
-    Wt[k][j] = __bfloat162float(W[e]);
-  }
-  const int ri = threadIdx.x >> 6, j = threadIdx.x & 63;
-  const float bj = b[j];
-  for (int g = 0; g < 8; ++g) {
-    const int r0 = blockIdx.x * 32 + g * 4;
-    __syncthreads();
-    for (int e = threadIdx.x; e < 4 * 2 * kH; e += 256) {
-      const int rr = e / (2 * kH), k = e % (2 * kH), r = r0 + rr;
-      x[rr][k] = r < rows ? (k < kH ? A[(size_t)r * kH + k] : Bm[(size_t)r * kH + k - kH]) : 0.f;
+  __shared__ uint32_t Ws[kH][kH + 4];  // W as BF16 pairs along k: Ws[j][k / 2]
+  const uint32_t* W2 = reinterpret_cast<const uint32_t*>(W);
+  for (int e = threadIdx.x; e < kH * kH; e += 256) Ws[e / kH][e % kH] = W2[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = (blockIdx.x * 8 + warp) * 16;
+  if (r0 >= rows) return;
+  const int ra = r0 + g, rb = r0 + g + 8;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < 8; ++s) {  // k-steps of 16: [A ; B]
+    const float* src = s < 4 ? A : Bm;
+    const int kc = (s & 3) * 16 + 2 * t;
+    const float2 x0 = ld2(src, rows, ra, kc), x1 = ld2(src, rows, rb, kc);
+    const float2 x2 = ld2(src, rows, ra, kc + 8), x3 = ld2(src, rows, rb, kc + 8);
+    uint32_t ah[4], am[4], al[4];
+    split3(x0.x, x0.y, ah[0], am[0], al[0]);
+    split3(x1.x, x1.y, ah[1], am[1], al[1]);
+    split3(x2.x, x2.y, ah[2], am[2], al[2]);
+    split3(x3.x, x3.y, ah[3], am[3], al[3]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int j = nt * 8 + g;
+      const uint32_t b0 = Ws[j][8 * s + t], b1 = Ws[j][8 * s + 4 + t];
+      mma_bf16(acc[nt], ah, b0, b1);
+      mma_bf16(acc[nt], am, b0, b1);
+      mma_bf16(acc[nt], al, b0, b1);
     }
-    __syncthreads();
-    const int r = r0 + ri;
-    float acc = bj;
-#pragma unroll 16
-    for (int k = 0; k < 2 * kH; ++k) acc = fmaf(Wt[k][j], x[ri][k], acc);
-    if (r < rows) out[(size_t)r * kH + j] = relu(acc);
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int j = nt * 8 + 2 * t;
+    const float b0 = b[j], b1 = b[j + 1];
+    if (ra < rows)
+      *reinterpret_cast<float2*>(out + (size_t)ra * kH + j) =
+          make_float2(relu(acc[nt][0] + b0), relu(acc[nt][1] + b1));
+    if (rb < rows)
+      *reinterpret_cast<float2*>(out + (size_t)rb * kH + j) =
+          make_float2(relu(acc[nt][2] + b0), relu(acc[nt][3] + b1));
   }
 }
 
-// dX = (dout * [out > 0]) W: dA[r] = first 64 columns, dB[r] = last 64 (written).
+__device__ __forceinline__ float2 ld_delta(const float* dout, const float* out, int rows, int r,
+                                           int j) {
+  if (r >= rows) return make_float2(0.f, 0.f);
+  const float2 d = *reinterpret_cast<const float2*>(dout + (size_t)r * kH + j);
+  const float2 o = *reinterpret_cast<const float2*>(out + (size_t)r * kH + j);
+  return make_float2(o.x > 0.f ? d.x : 0.f, o.y > 0.f ? d.y : 0.f);
+}
+
+// dX = (dout * [out > 0]) W: dA[r] = its first 64 columns, dB[r] the last
+// 64 (written). One warp = 16 rows x 128 columns.
 __global__ void __launch_bounds__(256) k_mp_dense_bwd_x(const float* dout, const float* out,
                                                         int rows, const __nv_bfloat16* W,
                                                         float* dA, float* dB) {
-  __shared__ float Ws[kH][2 * kH];
-  __shared__ float d[2][kH];
-  for (int e = threadIdx.x; e < kH * 2 * kH; e += 256) Ws[e / (2 * kH)][e % (2 * kH)] = __bfloat162float(W[e]);
-  const int ri = threadIdx.x >> 7, k = threadIdx.x & 127;
-  for (int g = 0; g < 16; ++g) {
-    const int r0 = blockIdx.x * 32 + g * 2;
-    __syncthreads();
-    if (threadIdx.x < 2 * kH) {
-      const int rr = threadIdx.x / kH, jj = threadIdx.x % kH, r = r0 + rr;
-      d[rr][jj] = r < rows && out[(size_t)r * kH + jj] > 0.f ? dout[(size_t)r * kH + jj] : 0.f;
-    }
-    __syncthreads();
-    const int r = r0 + ri;
-    float acc = 0.f;
-#pragma unroll 16
-    for (int j = 0; j < kH; ++j) acc = fmaf(d[ri][j], Ws[j][k], acc);
-    if (r < rows) {
-      if (k < kH) dA[(size_t)r * kH + k] = acc;
-      else dB[(size_t)r * kH + k - kH] = acc;
+  __shared__ uint32_t WT[2 * kH][kH / 2 + 4];  // W^T as BF16 pairs along j: WT[k][j / 2]
+  for (int e = threadIdx.x; e < 2 * kH * (kH / 2); e += 256) {
+    const int k = e / (kH / 2), jp = e % (kH / 2);
+    const __nv_bfloat16 lo = W[(2 * jp) * 2 * kH + k], hi = W[(2 * jp + 1) * 2 * kH + k];
+    WT[k][jp] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = (blockIdx.x * 8 + warp) * 16;
+  if (r0 >= rows) return;
+  const int ra = r0 + g, rb = r0 + g + 8;
+  float acc[16][4];
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {  // k-steps of 16 over the 64 outputs j
+    const int jc = s * 16 + 2 * t;
+    const float2 d0 = ld_delta(dout, out, rows, ra, jc), d1 = ld_delta(dout, out, rows, rb, jc);
+    const float2 d2 = ld_delta(dout, out, rows, ra, jc + 8);
+    const float2 d3 = ld_delta(dout, out, rows, rb, jc + 8);
+    uint32_t ah[4], am[4], al[4];
+    split3(d0.x, d0.y, ah[0], am[0], al[0]);
+    split3(d1.x, d1.y, ah[1], am[1], al[1]);
+    split3(d2.x, d2.y, ah[2], am[2], al[2]);
+    split3(d3.x, d3.y, ah[3], am[3], al[3]);
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+      const int k = nt * 8 + g;
+      const uint32_t b0 = WT[k][8 * s + t], b1 = WT[k][8 * s + 4 + t];
+      mma_bf16(acc[nt], ah, b0, b1);
+      mma_bf16(acc[nt], am, b0, b1);
+      mma_bf16(acc[nt], al, b0, b1);
     }
   }
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    float* dst = nt < 8 ? dA : dB;
+    const int k = (nt & 7) * 8 + 2 * t;
+    if (ra < rows)
+      *reinterpret_cast<float2*>(dst + (size_t)ra * kH + k) = make_float2(acc[nt][0], acc[nt][1]);
+    if (rb < rows)
+      *reinterpret_cast<float2*>(dst + (size_t)rb * kH + k) = make_float2(acc[nt][2], acc[nt][3]);
+  }
+}
+
+// Per-block partial weight gradients of a 64 x 128 dense layer over kRowsTc
+// rows: part[blk] = [sum_r delta[r][j] x[r][k] (64 x 128) ; sum_r delta[r][j]
+// (64)], delta = dout * [out > 0], x = [A ; B]. Rows pass through shared
+// memory 32 at a time as BF16 terms, transposed so that a fragment's row pair
+// is one 32-bit word; warp w owns outputs j of tile w % 4 and columns k of
+// half w / 4. Each output's bias sum is split over the four threads that
+// stage it and combined in a fixed order.
+__global__ void __launch_bounds__(256) k_mp_wgrad_tc(const float* dout, const float* out,
+                                                     const float* A, const float* Bm, int rows,
+                                                     float* part) {
+  constexpr int R = 32;              // rows per pass
+  __shared__ uint32_t dT[2][kH][R / 2 + 4];       // hi, mid terms of delta: [j][row pair]
+  __shared__ uint32_t xT[2][2 * kH][R / 2 + 4];   // hi, mid terms of x: [k][row pair]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mi = warp & 3, nh = warp >> 2;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+  float accb = 0.f;
+  const int rbase = blockIdx.x * kRowsTc;
+  for (int c0 = rbase; c0 < rbase + kRowsTc && c0 < rows; c0 += R) {
+    __syncthreads();
+    // thread t always stages output j = t % 64 (row pairs t / 64, + 4, ...)
+    // and keeps its share of the bias sum
+    for (int e = threadIdx.x; e < (R / 2) * kH; e += 256) {
+      const int rp = e / kH, j = e % kH, r = c0 + 2 * rp;
+      float v0 = 0.f, v1 = 0.f;
+      if (r < rows && out[(size_t)r * kH + j] > 0.f) v0 = dout[(size_t)r * kH + j];
+      if (r + 1 < rows && out[(size_t)(r + 1) * kH + j] > 0.f) v1 = dout[(size_t)(r + 1) * kH + j];
+      accb += v0;
+      accb += v1;
+      uint32_t th, tm, tl;
+      split3(v0, v1, th, tm, tl);
+      dT[0][j][rp] = th;
+      dT[1][j][rp] = tm;
+    }
+    for (int e = threadIdx.x; e < (R / 2) * 2 * kH; e += 256) {
+      const int rp = e / (2 * kH), k = e % (2 * kH), r = c0 + 2 * rp;
+      const float* src = k < kH ? A : Bm;
+      const int kk = k < kH ? k : k - kH;
+      const float v0 = r < rows ? src[(size_t)r * kH + kk] : 0.f;
+      const float v1 = r + 1 < rows ? src[(size_t)(r + 1) * kH + kk] : 0.f;
+      uint32_t th, tm, tl;
+      split3(v0, v1, th, tm, tl);
+      xT[0][k][rp] = th;
+      xT[1][k][rp] = tm;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < R / 16; ++ks) {
+      const int j = mi * 16 + g;
+      uint32_t a[2][4];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        a[p][0] = dT[p][j][8 * ks + t];
+        a[p][1] = dT[p][j + 8][8 * ks + t];
+        a[p][2] = dT[p][j][8 * ks + 4 + t];
+        a[p][3] = dT[p][j + 8][8 * ks + 4 + t];
+      }
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const int k = nh * 64 + nt * 8 + g;
+        const uint32_t bh0 = xT[0][k][8 * ks + t], bh1 = xT[0][k][8 * ks + 4 + t];
+        const uint32_t bm0 = xT[1][k][8 * ks + t], bm1 = xT[1][k][8 * ks + 4 + t];
+        mma_bf16(acc[nt], a[0], bh0, bh1);
+        mma_bf16(acc[nt], a[0], bm0, bm1);
+        mma_bf16(acc[nt], a[1], bh0, bh1);
+      }
+    }
+  }
+  float* p = part + (size_t)blockIdx.x * (kH * 2 * kH + kH);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int j = mi * 16 + g, k = nh * 64 + nt * 8 + 2 * t;
+    p[j * 2 * kH + k] = acc[nt][0];
+    p[j * 2 * kH + k + 1] = acc[nt][1];
+    p[(j + 8) * 2 * kH + k] = acc[nt][2];
+    p[(j + 8) * 2 * kH + k + 1] = acc[nt][3];
+  }
+  // the four threads of output j combine their bias shares in a fixed order
+  __syncthreads();
+  float* sb = reinterpret_cast<float*>(&dT[0][0][0]);
+  sb[threadIdx.x] = accb;
+  __syncthreads();
+  if (threadIdx.x < kH)
+    p[kH * 2 * kH + threadIdx.x] = ((sb[threadIdx.x] + sb[threadIdx.x + kH]) +
+                                    sb[threadIdx.x + 2 * kH]) + sb[threadIdx.x + 3 * kH];
 }
 
 // Per-block partial weight gradients of a dense layer over kRowsW rows:
@@ -238,14 +427,23 @@ __global__ void __launch_bounds__(256) k_mp_wgrad_parts(const float* dout, const
   if (threadIdx.x < kH) p[E + threadIdx.x] = accb;
 }
 
-// grad[e] = sum over blocks of part[blk][e] (fixed order), e < count; rows of
-// part are `stride` apart
+// grad[e] = sum over blocks of part[blk][e], e < count; rows of part are
+// `stride` apart. One warp per entry: lane l sums blocks l, l + 32, ... in
+// order, then a fixed shuffle tree (the same order on every run).
 __global__ void k_mp_sum_parts(const float* part, int nblk, int stride, int count, float* grad) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (e >= count) return;
   float s = 0.f;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * stride + e];
-  grad[e] = s;
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * stride + e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) grad[e] = s;
+}
+
+cudaError_t launch_sum_parts(const float* part, int nblk, int stride, int count, float* grad,
+                             cudaStream_t st) {
+  k_mp_sum_parts<<<(count + 7) / 8, 256, 0, st>>>(part, nblk, stride, count, grad);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- read-out
@@ -415,20 +613,29 @@ cudaError_t mp_launch_var_agg(const DevFormula& F, const float* h, const float* 
 
 cudaError_t mp_launch_dense_fwd(const float* A, const float* Bm, int rows, const __nv_bfloat16* W,
                                 const float* b, float* out, cudaStream_t st) {
-  if (rows > 0) k_mp_dense_fwd<<<blocks(rows, 32), 256, 0, st>>>(A, Bm, rows, W, b, out);
+  if (rows > 0) k_mp_dense_fwd<<<blocks(rows, 128), 256, 0, st>>>(A, Bm, rows, W, b, out);
   return cudaGetLastError();
 }
 
-cudaError_t mp_launch_dense_bwd(const float* dout, const float* out, const float* A,
-                                const float* Bm, int rows, const __nv_bfloat16* W, float* dA,
-                                float* dB, float* part, float* gW, cudaStream_t st) {
-  if (rows <= 0) return cudaMemsetAsync(gW, 0, sizeof(float) * (kH * 2 * kH + kH), st);
-  k_mp_dense_bwd_x<<<blocks(rows, 32), 256, 0, st>>>(dout, out, rows, W, dA, dB);
-  const int nb = blocks(rows, kRowsW);
-  k_mp_wgrad_parts<2 * kH><<<nb, 256, 0, st>>>(dout, out, A, Bm, rows, part);
-  const int width = kH * 2 * kH + kH;
-  k_mp_sum_parts<<<blocks(width, 256), 256, 0, st>>>(part, nb, width, width, gW);
+cudaError_t mp_launch_dense_bwd_x(const float* dout, const float* out, int rows,
+                                  const __nv_bfloat16* W, float* dA, float* dB, cudaStream_t st) {
+  if (rows > 0) k_mp_dense_bwd_x<<<blocks(rows, 128), 256, 0, st>>>(dout, out, rows, W, dA, dB);
   return cudaGetLastError();
+}
+
+cudaError_t mp_launch_dense_wgrad(const float* dout, const float* out, const float* A,
+                                  const float* Bm, int rows, float* part, float* gW,
+                                  cudaStream_t st) {
+  if (rows <= 0) return cudaMemsetAsync(gW, 0, sizeof(float) * (kH * 2 * kH + kH), st);
+  k_mp_wgrad_tc<<<blocks(rows, kRowsTc), 256, 0, st>>>(dout, out, A, Bm, rows, part);
+  return cudaGetLastError();
+}
+
+// sums the weight-gradient partials of mp_launch_dense_wgrad over `rows` rows
+cudaError_t mp_launch_dense_wsum(const float* part, int rows, float* gW, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const int width = kH * 2 * kH + kH;
+  return launch_sum_parts(part, blocks(rows, kRowsTc), width, width, gW, st);
 }
 
 cudaError_t mp_launch_proj_bwd(const float* dout, const float* out, const float* in, int rows,
@@ -437,8 +644,7 @@ cudaError_t mp_launch_proj_bwd(const float* dout, const float* out, const float*
   const int nb = blocks(rows, kRowsW);
   k_mp_wgrad_parts<3><<<nb, 256, 0, st>>>(dout, out, in, nullptr, rows, part);
   // the projection has no bias: only the first 64 x 3 entries of each part
-  k_mp_sum_parts<<<1, 256, 0, st>>>(part, nb, kH * 3 + kH, kH * 3, gW);
-  return cudaGetLastError();
+  return launch_sum_parts(part, nb, kH * 3 + kH, kH * 3, gW, st);
 }
 
 cudaError_t mp_launch_out(const float* h, int n, const float* wo, const float* bo,
@@ -452,8 +658,7 @@ cudaError_t mp_launch_out_bwd(const float* h, const float* dz, int n, const floa
                               float* part, float* g_wo, cudaStream_t st) {
   const int nb = blocks(n, kRowsW);
   k_mp_out_bwd<<<nb, kH, 0, st>>>(h, dz, n, wo, dh, part);
-  k_mp_sum_parts<<<1, kH + 1, 0, st>>>(part, nb, kH + 1, kH + 1, g_wo);  // wo then bo
-  return cudaGetLastError();
+  return launch_sum_parts(part, nb, kH + 1, kH + 1, g_wo, st);  // wo then bo
 }
 
 cudaError_t mp_launch_adam(float* P, const float* G, float* M, float* V, int count, float lr,

@@ -152,7 +152,7 @@ def test_eval_mixed_lengths_weighted(ms, stream, golden_table):
     ms.maxsat_destroy(ctx)
 
 
-@pytest.mark.parametrize("which", ["edge", "mixed12", "w3sat", "u3sat"])
+@pytest.mark.parametrize("which", ["edge", "mixed12", "w3sat", "u3sat", "mixed-full"])
 def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which):
     """FP8 tensor-core gather (pattern-encoding matrix, tcgen05) against the
     literal-by-literal oracle: E4M3 operands up to length 9, E5M2 beyond."""
@@ -163,8 +163,10 @@ def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which)
         inst, table, J, B = inst_of(workloads.mixed_length(n=1500, m=7000, seed=4)), golden_table, 4, 300
     elif which == "w3sat":
         inst, table, J, B = inst_of(workloads.weighted_3sat(1000, 6000, 1000, seed=0)), golden_table, 4, 4096
-    else:  # unweighted: every 32-row group shares one weight
+    elif which == "u3sat":  # unweighted: every 32-row group shares one weight
         inst, table, J, B = inst_of(workloads.random_ksat(300, 1290, 3, seed=8)), small_table, 1, 700
+    else:  # mixed lengths 2..12 at full size: a 2 GB clause matrix, E5M2 operands
+        inst, table, J, B = inst_of(workloads.mixed_length(seed=0)), golden_table, 4, 300
     ctx = make_ctx(ms, stream, inst, table, n_buckets=J, path=ms.MAXSAT_PATH_DENSE)
     assert ms.maxsat_get_path(ctx) == ms.MAXSAT_PATH_DENSE
     rng = np.random.default_rng(5)
@@ -314,6 +316,20 @@ def test_full_size_mixed_sampled(ms, stream, golden_table):
     inst = inst_of(workloads.mixed_length(seed=0))
     B, T, seed = 1024, 3, 2
     gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=0)
+    rows = np.array([0, 255, 511, 512, 1023])
+    ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows,
+                     B_total=B)
+    assert_same(gpu, ora, T, 0.01, rows=rows)
+
+
+def test_full_size_mixed_dense_sampled(ms, stream, golden_table):
+    """Mixed lengths at full size on the dense path (a 2 GB FP8 clause matrix,
+    E5M2 above length 9, 16-bit hidden patterns): sampled chains against the
+    oracle, as on the sparse path."""
+    inst = inst_of(workloads.mixed_length(seed=0))
+    B, T, seed = 1024, 3, 2
+    gpu = run_gpu(ms, stream, inst, golden_table, B, T, seed, n_buckets=4, spg=0,
+                  path=ms.MAXSAT_PATH_DENSE)
     rows = np.array([0, 255, 511, 512, 1023])
     ora = run_oracle(inst, golden_table, len(rows), T, seed, n_buckets=4, chain_ids=rows,
                      B_total=B)
