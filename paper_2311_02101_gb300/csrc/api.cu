@@ -299,7 +299,8 @@ int32_t weight_bucket(int64_t w, int64_t wmin, int32_t J) {
 template <class Fn>
 int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
   if (!ctx->profiling) {
-    CK(ctx, body());
+    const cudaError_t e = body();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, name);
     return MAXSAT_OK;
   }
   int k = 0;
@@ -314,7 +315,8 @@ int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
   CK(ctx, cudaEventCreate(&mk.stop));
   ctx->marks.push_back(mk);
   CK(ctx, cudaEventRecord(mk.start, st));
-  CK(ctx, body());
+  const cudaError_t e = body();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, name);
   CK(ctx, cudaEventRecord(mk.stop, st));
   return MAXSAT_OK;
 }

@@ -92,6 +92,18 @@ struct DevTables {
   const uint32_t* pv;
 };
 
+// Lets kernel `kern` launch with `dyn` bytes of dynamic shared memory: when
+// dynamic plus the kernel's static shared memory exceed the default 48 KB per
+// block, the launch needs the opt-in attribute.
+template <typename K>
+cudaError_t allow_dynamic_smem(K kern, int dyn) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if ((size_t)dyn + fa.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+}
+
 // Philox round keys of one seed (computed on the host, read by the kernels
 // from parameter space).
 struct RoundKeys {

@@ -674,6 +674,38 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size
   }
 }
 
+// The end of a visible update for one variable and 8 chains given their
+// integer logits z (units 2^-Q): best-so-far copy of improved chains, the
+// visible draws x ~ Bernoulli(P[z]) (Eq. 3) and nu (Sec. 4.4).
+__device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains& C,
+                                             const uint32_t* pv, float alpha, uint32_t t,
+                                             int2 vi, int g8, size_t o, int b0, uint64_t xold,
+                                             float4 n0, float4 n1, const int (&z)[8]) {
+  keep_improved(C, vi.x, o, b0, xold);
+  const uint4 r =
+      philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), t,
+                               kPhaseVisible | ((uint32_t)vi.x << 8)),
+                    C.keys);
+  float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+  // nu in FP32 with a fixed operation sequence (one rounding per step):
+  // var = fl(P (65536 - P)) 2^-32, nu = fma(1 - alpha, nu, fl(alpha var))
+  const float keep = __fsub_rn(1.0f, alpha);
+  uint64_t xnew = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int qq = max(-T.qmax, min(T.qmax, z[q]));
+    const uint32_t P = pv[qq + T.qmax];
+    // rho (1 - rho) with rho = P / 65536: P (65536 - P) <= 2^30, scaled by 2^-32
+    const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
+    nu[q] = __fmaf_rn(keep, nu[q], __fmul_rn(alpha, var));
+    xnew |= (uint64_t)(lane16(r, q) < P) << (8 * q);
+  }
+  float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
+  nu4[0] = make_float4(nu[0], nu[1], nu[2], nu[3]);
+  nu4[1] = make_float4(nu[4], nu[5], nu[6], nu[7]);
+  *reinterpret_cast<uint64_t*>(C.xt + o) = xnew;
+}
+
 constexpr int kVisBatch = 4;
 static_assert(32 % kVisBatch == 0, "incidence windows hold whole batches");
 
@@ -785,29 +817,7 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
     sums(std::true_type{});
   else
     sums(std::false_type{});
-  keep_improved(C, vi.x, o, b0, xold);
-
-  const uint4 r =
-      philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), t,
-                               kPhaseVisible | ((uint32_t)vi.x << 8)),
-                    C.keys);
-  float nu[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-  // nu in FP32 with a fixed operation sequence (one rounding per step):
-  // var = fl(P (65536 - P)) 2^-32, nu = fma(1 - alpha, nu, fl(alpha var))
-  const float keep = __fsub_rn(1.0f, alpha);
-  uint64_t xnew = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int qq = max(-T.qmax, min(T.qmax, z[q]));
-    const uint32_t P = pv[qq + T.qmax];
-    // rho (1 - rho) with rho = P / 65536: P (65536 - P) <= 2^30, scaled by 2^-32
-    const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
-    nu[q] = __fmaf_rn(keep, nu[q], __fmul_rn(alpha, var));
-    xnew |= (uint64_t)(lane16(r, q) < P) << (8 * q);
-  }
-  nu4[0] = make_float4(nu[0], nu[1], nu[2], nu[3]);
-  nu4[1] = make_float4(nu[4], nu[5], nu[6], nu[7]);
-  *reinterpret_cast<uint64_t*>(C.xt + o) = xnew;
+  visible_tail(T, C, pv, alpha, t, vi, g8, o, b0, xold, n0, n1, z);
 }
 
 __global__ void __launch_bounds__(256) k_keep_copy(DevFormula F, DevChains C, int n, int vg0) {
@@ -890,11 +900,8 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
   if constexpr (MODE == kStep && SM && sizeof(HT) == 1) {
     if (T.one_chunk && T.rec3 && F.cl4 && C.cost32 && octets_single_temperature(T, C)) {
       const int sm3 = gather3_smem_bytes(T);
-      if (sm3 > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_gather3, cudaFuncAttributeMaxDynamicSharedMemorySize, sm3);
-        if (e != cudaSuccess) return e;
-      }
+      const cudaError_t e = allow_dynamic_smem(k_gather3, sm3);
+      if (e != cudaSuccess) return e;
       return launch_pdl(k_gather3, grid, sm3, st, F, T, C, P, tdev, t_rel, cost_part, fe_part,
                         tickets);
     }
@@ -903,8 +910,8 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
   auto kern = k_gather<MODE, SM, HT, false>;
   if constexpr (MODE == kStep && sizeof(HT) == 1)
     if (T.one_chunk) kern = k_gather<MODE, SM, HT, true>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    const cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   if constexpr (MODE == kStep)
@@ -918,9 +925,7 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
 template <bool SM, typename HT, bool ONE>
 int gather_occupancy(int smem) {
   auto kern = k_gather<kStep, SM, HT, ONE>;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return 1;
+  if (allow_dynamic_smem(kern, smem) != cudaSuccess) return 1;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem) != cudaSuccess) return 1;
   return nb > 0 ? nb : 1;
@@ -951,8 +956,8 @@ cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormu
                             const DevTables& T, const DevChains& C, float alpha,
                             const uint32_t* tdev, uint32_t t_rel) {
   auto kern = k_visible<SM, HT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    const cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   const int groups = (F.n + 7) / 8;
@@ -1013,10 +1018,7 @@ int gather_blocks_per_sm(const DevTables& T, bool wide) {
   if (use_sm && one && T.rec3) {
     // k_gather3 runs whenever the chains' octets have single temperatures
     const int sm3 = gather3_smem_bytes(T);
-    if (sm3 > 48 * 1024 &&
-        cudaFuncSetAttribute(k_gather3, cudaFuncAttributeMaxDynamicSharedMemorySize, sm3) !=
-            cudaSuccess)
-      return 1;
+    if (allow_dynamic_smem(k_gather3, sm3) != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather3, 256, sm3) != cudaSuccess)
       return 1;

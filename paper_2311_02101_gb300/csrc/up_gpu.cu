@@ -288,9 +288,8 @@ cudaError_t launch_up_chains(const UpDev& U, const uint8_t* xs, const float* nus
   if (W < 1 || B < 1 || U.n_inst < 1) return cudaErrorInvalidValue;
   const int wbytes = up_warp_bytes(U.n_max);
   const int smem = W * wbytes;
-  if (smem > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_up_chains, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  {
+    const cudaError_t e = allow_dynamic_smem(k_up_chains, smem);
     if (e != cudaSuccess) return e;
   }
   // three quarters of the unified memory as shared memory: as many chains per
