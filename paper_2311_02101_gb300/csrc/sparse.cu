@@ -404,11 +404,12 @@ __global__ void __launch_bounds__(256, ONE ? 4 : 3) k_gather(DevFormula F, DevTa
 //  - The weighted unsatisfied costs stay in registers: each chain adds the
 //    clause weight times its 0/1 "no true literal" byte, without branches.
 //  - Latency: the state bytes and weight of the next clause are loaded while
-//    the current one is sampled (two clauses per loop trip), and each block
-//    first asks the L2 for its slice of the chain tile's state rows and for
-//    its clause records and weights (bulk prefetches), so the loop rarely
-//    waits on DRAM after the previous round's writes. 2 blocks of 256
-//    threads per SM: the registers of two clauses in flight, no spills.
+//    the current one is sampled, and each block first asks the L2 for its
+//    slice of the chain tile's state rows and for its clause records and
+//    weights (bulk prefetches), so the loop rarely waits on DRAM after the
+//    previous round's writes. 2 blocks of 256 threads per SM (no spills;
+//    measured faster than 3 or 4 blocks with spills, and than two clauses per
+//    loop trip).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   uint32_t v;
@@ -556,7 +557,6 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   if (c0 < c_end) wc = (int32_t)__ldg(F.cl_w + c0);
   load_clause_state(xtb, Bp, rec_n, xa, xb, xc);
   if (c0 + 8 < c_end) rec_n = __ldg(F.cl4 + c0 + 8);
-#pragma unroll 2
   for (int c = c0; c < c_end; c += 8) {
     uint2 na = make_uint2(0u, 0u), nb = na, nc = na;
     const uint32_t ninfo = (uint32_t)rec_n.w;
