@@ -393,13 +393,18 @@ int plan_blocks(const maxsat_ctx* ctx, int cb) {
   return (int)std::min<int64_t>(nb, INT32_MAX);
 }
 
-int upload_plan(maxsat_ctx* ctx, DevAllocs& A, int cb, GatherPlan* P, int64_t* wmax) {
+// Clause blocks of about cb clauses per instance. *wmax: the largest weight
+// sum of a block; *wmax8 (optional): the largest weight sum of the clauses
+// one warp of the one-chunk gather takes (every eighth clause of a block).
+int upload_plan(maxsat_ctx* ctx, DevAllocs& A, int cb, GatherPlan* P, int64_t* wmax,
+                int64_t* wmax8 = nullptr) {
   // one grid row per block: at most 65535 blocks
   while (plan_blocks(ctx, cb) > 65535 && cb < (1 << 29)) cb *= 2;
   if (plan_blocks(ctx, cb) > 65535) return fail(ctx, MAXSAT_EINVAL, "too many clause blocks");
   std::vector<int4> blk;
   std::vector<int32_t> ib(1, 0);
   *wmax = 0;
+  if (wmax8) *wmax8 = 0;
   for (int in = 0; in < ctx->n_inst; ++in) {
     const int c0 = ctx->inst_cl_base[in], c1 = ctx->inst_cl_base[in + 1];
     // block sizes in whole groups of 8 clauses (a block's 8 warps then take
@@ -411,9 +416,14 @@ int upload_plan(maxsat_ctx* ctx, DevAllocs& A, int cb, GatherPlan* P, int64_t* w
       const int64_t g = groups / nb + (k < groups % nb ? 1 : 0);
       const int e = (int)std::min<int64_t>(c1, c + 8 * g);
       blk.push_back(make_int4(in, c, e, c0));
-      int64_t sum = 0;
-      for (int q = c; q < e; ++q) sum += ctx->h_w[q];
+      int64_t sum = 0, part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int q = c; q < e; ++q) {
+        sum += ctx->h_w[q];
+        part[(q - c) & 7] += ctx->h_w[q];
+      }
       *wmax = std::max(*wmax, sum);
+      if (wmax8)
+        for (int64_t v : part) *wmax8 = std::max(*wmax8, v);
       c = e;
     }
     ib.push_back((int32_t)blk.size());
@@ -446,8 +456,8 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   ctx->gather_cb = ctx->cb_force > 0 ? ctx->cb_force
                                      : gather_clause_block(ctx->m, Bp / kChainTile, ctx->gather_slots);
   DevAllocs& A = ctx->chain_mem;
-  int64_t wmax_block = 0;
-  int rcp = upload_plan(ctx, A, ctx->gather_cb, &ctx->plan, &wmax_block);
+  int64_t wmax_block = 0, wmax_warp = 0;
+  int rcp = upload_plan(ctx, A, ctx->gather_cb, &ctx->plan, &wmax_block, &wmax_warp);
   if (rcp != MAXSAT_OK) return rcp;
   const int nblk = ctx->plan.n_blk;
   const size_t nI = (size_t)ctx->n_inst * Bp;
@@ -455,6 +465,9 @@ int alloc_chains(maxsat_ctx* ctx, int32_t B) {
   C = DevChains{};
   // 32-bit per-block cost rows when no clause block's weight sum reaches 2^31
   C.cost32 = wmax_block < ((int64_t)1 << 31) ? 1 : 0;
+  // two chains' costs share a 32-bit register in the one-chunk gather when
+  // every warp's weight sum fits 16 bits
+  C.cost16 = wmax_warp < 65536 ? 1 : 0;
   C.n_inst = ctx->n_inst;
   C.B = B;
   C.Bp = Bp;
@@ -1113,6 +1126,14 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
       cl4[c] = make_int4(lv[0], lv[1], lv[2], len > 0 ? (cl_grp[c] << 8) | (neg << 2) | len : 0);
     }
     UP(cl4, F.cl4);
+  }
+  T.plain3 = 0;
+  if (T.one_chunk && m > 0) {
+    bool all3 = true;
+    for (int64_t c = 0; c < m && all3; ++c) all3 = cl_off[c + 1] - cl_off[c] == 3;
+    bool sat = false;
+    for (const GroupMeta& gm : ctx->tabs.meta) sat = sat || gm.sat;
+    T.plain3 = all3 && !sat ? 1 : 0;
   }
   T.rec3 = nullptr;
   T.rec3_words = 0;

@@ -77,6 +77,8 @@ struct DevTables {
   int32_t n_groups;
   int32_t rec_len, gq_len, pv_len;  // element counts
   int32_t one_chunk;   // every group's pattern record is 16 bytes (L <= 3)
+  int32_t plain3;      // every clause has exactly 3 literals and no hidden
+                       // probability is 65536 / 65536
   const int32_t* feq;  // fixed-point clause free energies (parallel tempering)
   int32_t smem_bytes;  // bytes to stage all tables in shared memory, 0 = too big
   const GroupMeta* meta;
@@ -117,6 +119,8 @@ struct DevChains {
   int32_t B_total;  // chains of the whole ensemble (temperature blocks)
   float inv_B_total;  // 1 / B_total (first guess of the temperature index)
   int32_t cost32;     // sparse gather: every clause block's weight sum < 2^31
+  int32_t cost16;     // one-chunk gather: a thread's clauses of one block (its
+                      // eighth of the block) weigh less than 2^16 in total
   int32_t n_inst;     // formulas: best / cost / fe / improved are n_inst x Bp,
                       // tickets n_inst x (Bp / kChainTile)
   uint32_t key0, key1;

@@ -438,10 +438,11 @@ __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
 }
 
 // The 8 state bytes of the thread's chains for each literal of clause record
-// r (zero for absent literals).
+// r (zero for absent literals; ALL3: every clause has 3 literals).
+template <bool ALL3>
 __device__ __forceinline__ void load_clause_state(const uint8_t* xtb, int Bp, const int4& r,
                                                   uint2& xa, uint2& xb, uint2& xc) {
-  const int len = r.w & 3;
+  const int len = ALL3 ? 3 : r.w & 3;
   xa = len > 0 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.x * Bp)) : make_uint2(0u, 0u);
   xb = len > 1 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.y * Bp)) : make_uint2(0u, 0u);
   xc = len > 2 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.z * Bp)) : make_uint2(0u, 0u);
@@ -482,6 +483,11 @@ __device__ __forceinline__ void octet_draws(uint32_t a_lo, uint32_t a_hi, uint32
   chain_draws<SAT, 7>(a_hi, rb, R, fe[7], h_hi);
 }
 
+// PLAIN3: every clause has exactly 3 literals and no group has a saturated
+// hidden unit (T.plain3). COST16: a warp's clauses of its block weigh less
+// than 2^16 in total (C.cost16), so chains 2j and 2j + 1 keep their costs in
+// the low and high half of one register.
+template <bool PLAIN3, bool COST16>
 __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, DevChains C,
                                                     GatherPlan P, const uint32_t* tdev,
                                                     uint32_t t_rel, int64_t* cost_part,
@@ -507,7 +513,7 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   const uint32_t gstride = (uint32_t)E * 256u;       // from one group to the next
   // the weighted unsatisfied cost of the thread's 8 chains in registers:
   // the host runs this kernel only when every clause block's weight sum is
-  // below 2^31 (C.cost32)
+  // below 2^31 (C.cost32); with COST16, cost[j] packs chains 2j and 2j + 1
   int32_t cost[8];
   float fe[8];
 #pragma unroll
@@ -555,14 +561,14 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   uint32_t info = (uint32_t)rec_n.w;
   int32_t wc = 0;
   if (c0 < c_end) wc = (int32_t)__ldg(F.cl_w + c0);
-  load_clause_state(xtb, Bp, rec_n, xa, xb, xc);
+  load_clause_state<PLAIN3>(xtb, Bp, rec_n, xa, xb, xc);
   if (c0 + 8 < c_end) rec_n = __ldg(F.cl4 + c0 + 8);
   for (int c = c0; c < c_end; c += 8) {
     uint2 na = make_uint2(0u, 0u), nb = na, nc = na;
     const uint32_t ninfo = (uint32_t)rec_n.w;
     int32_t nwc = 0;
     if (c + 8 < c_end) {
-      load_clause_state(xtb, Bp, rec_n, na, nb, nc);
+      load_clause_state<PLAIN3>(xtb, Bp, rec_n, na, nb, nc);
       nwc = (int32_t)__ldg(F.cl_w + c + 8);
     }
     if (c + 16 < c_end) rec_n = __ldg(F.cl4 + c + 16);
@@ -583,15 +589,23 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
     // the clause weight times its byte, without branches
     const uint32_t u_lo = (~(lo + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
     const uint32_t u_hi = (~(hi + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+    if (COST16) {
+      // bytes 2j, 2j + 1 -> 16-bit halves of one word
+      cost[0] += (int32_t)(__byte_perm(u_lo, 0u, 0x4140u) * (uint32_t)w_cur);
+      cost[1] += (int32_t)(__byte_perm(u_lo, 0u, 0x4342u) * (uint32_t)w_cur);
+      cost[2] += (int32_t)(__byte_perm(u_hi, 0u, 0x4140u) * (uint32_t)w_cur);
+      cost[3] += (int32_t)(__byte_perm(u_hi, 0u, 0x4342u) * (uint32_t)w_cur);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      cost[q] += (int32_t)__byte_perm(u_lo, 0u, 0x4440u | q) * w_cur;
-      cost[q + 4] += (int32_t)__byte_perm(u_hi, 0u, 0x4440u | q) * w_cur;
+      for (int q = 0; q < 4; ++q) {
+        cost[q] += (int32_t)__byte_perm(u_lo, 0u, 0x4440u | q) * w_cur;
+        cost[q + 4] += (int32_t)__byte_perm(u_hi, 0u, 0x4440u | q) * w_cur;
+      }
     }
-    if (len == 0) continue;  // an empty clause has no clause RBM
+    if (!PLAIN3 && len == 0) continue;  // an empty clause has no clause RBM
 
     const uint32_t rb = tab_e + grp * gstride;
-    const bool sat = (lds32(rb + 128u) & 0x100u) != 0;
+    const bool sat = !PLAIN3 && (lds32(rb + 128u) & 0x100u) != 0;
     // Philox rounds 0..2: the clause's share, then each unit's
     const uint32_t cl = (uint32_t)(c - cl_base);
     const uint64_t p0 = (uint64_t)kPhiloxM0 * cl;
@@ -621,6 +635,13 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   // per-block partial sums; the block that arrives last among its instance's
   // blocks for this tile of 256 chains reduces them in block order and keeps
   // improvements (as k_gather)
+  if (COST16) {
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {
+      cost[2 * j + 1] = (int32_t)((uint32_t)cost[j] >> 16);
+      cost[2 * j] = cost[j] & 0xFFFF;
+    }
+  }
   int32_t* my_cost32 = reinterpret_cast<int32_t*>(&s_cost[0][0]) + warp * 256 + lane * 8;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -881,6 +902,14 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, int smem, cudaStream_
 // moves them to a 256-byte boundary
 int gather3_smem_bytes(const DevTables& T) { return T.rec3_words * 4 + 256; }
 
+using Gather3Fn = void (*)(DevFormula, DevTables, DevChains, GatherPlan, const uint32_t*,
+                           uint32_t, int64_t*, float*, int32_t*);
+
+Gather3Fn gather3_kernel(const DevTables& T, const DevChains& C) {
+  if (T.plain3) return C.cost16 ? k_gather3<true, true> : k_gather3<true, false>;
+  return C.cost16 ? k_gather3<false, true> : k_gather3<false, false>;
+}
+
 // every octet of chains has one temperature: each temperature block starts
 // at a multiple of 8 (block e starts at ceil(e B_total / E); local chain 0 is
 // a multiple of 8 of the ensemble)
@@ -900,9 +929,10 @@ cudaError_t gather_variant(dim3 grid, int smem, cudaStream_t st, const DevFormul
   if constexpr (MODE == kStep && SM && sizeof(HT) == 1) {
     if (T.one_chunk && T.rec3 && F.cl4 && C.cost32 && octets_single_temperature(T, C)) {
       const int sm3 = gather3_smem_bytes(T);
-      const cudaError_t e = allow_dynamic_smem(k_gather3, sm3);
+      auto kern = gather3_kernel(T, C);
+      const cudaError_t e = allow_dynamic_smem(kern, sm3);
       if (e != cudaSuccess) return e;
-      return launch_pdl(k_gather3, grid, sm3, st, F, T, C, P, tdev, t_rel, cost_part, fe_part,
+      return launch_pdl(kern, grid, sm3, st, F, T, C, P, tdev, t_rel, cost_part, fe_part,
                         tickets);
     }
   }
@@ -1017,10 +1047,12 @@ int gather_blocks_per_sm(const DevTables& T, bool wide) {
   const bool one = T.one_chunk && !wide;
   if (use_sm && one && T.rec3) {
     // k_gather3 runs whenever the chains' octets have single temperatures
+    // (the variant with the most registers stands for all four)
     const int sm3 = gather3_smem_bytes(T);
-    if (allow_dynamic_smem(k_gather3, sm3) != cudaSuccess) return 1;
+    if (allow_dynamic_smem(k_gather3<false, false>, sm3) != cudaSuccess) return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather3, 256, sm3) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather3<false, false>, 256, sm3) !=
+        cudaSuccess)
       return 1;
     return nb > 0 ? nb : 1;
   }

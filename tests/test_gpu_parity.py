@@ -102,7 +102,7 @@ def assert_same(gpu, ora, T, alpha, rows=None):
     assert np.array_equal(g["nu"], ora.nu32), "nu (FP32 sequence)"
 
 
-def edge_instance(seed=0, kmax=4):
+def edge_instance(seed=0, kmax=4, wmax=40):
     """Random clauses of lengths 1..kmax plus duplicates, a tautology, an empty
     clause, a variable in no clause, and weights spanning several buckets
     (kmax = 3: every clause has one-chunk tables and a 16-byte clause record)."""
@@ -112,7 +112,7 @@ def edge_instance(seed=0, kmax=4):
     _, off, lits, _ = workloads.from_lengths(n - 1, lengths, rng)
     cl = [list(lits[off[c]:off[c + 1]]) for c in range(len(lengths))]
     cl += [[3, 3, -5], [7, -7], [], [12]] + ([[-2, -2, -2, 9]] if kmax >= 4 else [])
-    w = list(rng.integers(1, 40, size=len(cl)))
+    w = list(rng.integers(1, wmax, size=len(cl)))
     return oracle.Instance.from_clauses(n, cl, w)
 
 
@@ -199,6 +199,39 @@ def test_trajectory_edge_cases(ms, stream, small_table, kmax):
     T, seed, B = 25, 3, 40
     gpu = run_gpu(ms, stream, inst, small_table, B, T, seed, alpha=0.05)
     assert_same(gpu, run_oracle(inst, small_table, B, T, seed, alpha=0.05), T, 0.05)
+
+
+def test_trajectory_edge_cases_heavy_weights(ms, stream, small_table):
+    """Clauses of 1..3 literals and an empty one with weights up to 30000: a
+    warp's clauses weigh more than 2^16, so the one-chunk gather keeps one
+    32-bit cost per chain."""
+    inst = edge_instance(2, 3, wmax=30000)
+    T, seed, B = 25, 4, 64
+    gpu = run_gpu(ms, stream, inst, small_table, B, T, seed)
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
+
+
+@pytest.mark.parametrize("w_hi", [32768, 32769])
+def test_gather_cost_halves_at_the_16_bit_limit(ms, stream, small_table, w_hi):
+    """16 clauses of 3 literals form one clause block whose warp k takes
+    clauses k and k + 8, weighing 32767 and w_hi: warp sums of 65535 let two
+    chains share a 32-bit cost register (a chain leaving both clauses
+    unsatisfied fills its 16-bit half), 65536 does not."""
+    rng = np.random.default_rng(21)
+    n, off, lits, _ = workloads.from_lengths(12, np.full(16, 3), rng)
+    w = np.array([32767] * 8 + [w_hi] * 8, dtype=np.int64)
+    inst = oracle.Instance(n, off, lits, w)
+    T, seed, B = 20, 7, 256
+    gpu = run_gpu(ms, stream, inst, small_table, B, T, seed)
+    ora = run_oracle(inst, small_table, B, T, seed)
+    assert_same(gpu, ora, T, 0.01)
+    # the first round's gather sees chains that leave both clauses of a warp
+    # unsatisfied (initial states)
+    x0 = oracle.init_chains(n, B, seed).x
+    cl = inst.clauses()
+    both = sum(int(np.sum(oracle.evaluate(oracle.Instance.from_clauses(n, [cl[k], cl[k + 8]]),
+                                          x0) == 2)) for k in range(8))
+    assert both > 0
 
 
 def test_trajectory_mixed_weighted_buckets(ms, stream, golden_table):
