@@ -211,8 +211,10 @@ int maxsat_step(maxsat_ctx* ctx, int64_t steps);
 int maxsat_score(maxsat_ctx* ctx);
 
 /* Weighted unsatisfied cost of B arbitrary assignments (the MaxSAT objective,
- * Sec. 1). assign_dev: B x n device bytes; cost_dev: B device int64 (n_inst x
- * B for a batch). Independent of the chains. Asynchronous. */
+ * Sec. 1). assign_dev: B x n device bytes, row-major, 0 = false and 1 =
+ * true, no alignment required; cost_dev: B device int64 (n_inst x B for a
+ * batch). Independent of the chains. Asynchronous; a call with a larger B
+ * than any before grows the evaluation scratch first. */
 int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B,
                 int64_t* cost_dev);
 

@@ -241,12 +241,46 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   }
 }
 
+// 16 bytes of X (chain b, variables i0 .. i0 + 15) from the assignment
+// bytes: +1 / -1 (nonzero / zero) as FP8, 0 past n; 8-byte loads when the
+// row segment allows them, else byte loads.
+__device__ __forceinline__ uint4 convert16(const uint8_t* __restrict__ assign, int n, int b,
+                                           int i0, uint32_t minus_one4) {
+  const uint8_t* p = assign + (size_t)b * n + i0;
+  uint32_t w[4] = {0u, 0u, 0u, 0u}, valid[4] = {0u, 0u, 0u, 0u};
+  if (i0 + 16 <= n && (reinterpret_cast<uintptr_t>(p) & 7u) == 0) {
+    const uint2 lo = __ldg(reinterpret_cast<const uint2*>(p));
+    const uint2 hi = __ldg(reinterpret_cast<const uint2*>(p) + 1);
+    w[0] = lo.x;
+    w[1] = lo.y;
+    w[2] = hi.x;
+    w[3] = hi.y;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) valid[q] = 0xFFFFFFFFu;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (i0 + k < n) {
+        w[k >> 2] |= (uint32_t)__ldg(p + k) << (8 * (k & 3));
+        valid[k >> 2] |= 0xFFu << (8 * (k & 3));
+      }
+  }
+  uint32_t o[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    // bit 7 of each byte: the byte is nonzero; flipping the sign of -1 gives +1
+    const uint32_t nz = (((w[q] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w[q]) & 0x80808080u;
+    o[q] = (minus_one4 ^ nz) & valid[q];
+  }
+  return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
 // assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
 // variables, 0 for padding variables and padding chains; 16 output bytes
 // (one 16-byte store) per thread. Also zeroes the B costs the product then
 // accumulates into.
 __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, int Bp, int n_pad,
-                             uint8_t one, uint8_t minus_one, uint8_t* __restrict__ X,
+                             uint32_t minus_one4, uint8_t* __restrict__ X,
                              int64_t* __restrict__ cost) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,17 +288,8 @@ __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, i
   const int chunks = n_pad / 16;
   if (idx >= (size_t)Bp * chunks) return;
   const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
-  uint32_t wv[4] = {0u, 0u, 0u, 0u};
-  if (b < B) {
-    const uint8_t* row = assign + (size_t)b * n;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int i = i0 + k;
-      const uint32_t v = i < n ? (__ldg(row + i) ? one : minus_one) : 0u;
-      wv[k >> 2] |= v << (8 * (k & 3));
-    }
-  }
-  reinterpret_cast<uint4*>(X)[idx] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  reinterpret_cast<uint4*>(X)[idx] =
+      b < B ? convert16(assign, n, b, i0, minus_one4) : make_uint4(0u, 0u, 0u, 0u);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -400,12 +425,11 @@ cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, in
 
 cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n_pad, bool e5m2,
                               uint8_t* X, int64_t* cost, cudaStream_t st) {
-  uint8_t one, minus_one;
-  fp8_encode_int(1, e5m2, &one);
+  uint8_t minus_one;
   fp8_encode_int(-1, e5m2, &minus_one);
   const size_t total = std::max((size_t)Bp * (n_pad / 16), (size_t)B);
-  k_assign_fp8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(assign, B, n, Bp, n_pad, one,
-                                                                 minus_one, X, cost);
+  k_assign_fp8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      assign, B, n, Bp, n_pad, 0x01010101u * minus_one, X, cost);
   return cudaGetLastError();
 }
 

@@ -181,6 +181,44 @@ def test_dense_eval_matches_oracle(ms, stream, small_table, golden_table, which)
     ms.maxsat_destroy(ctx)
 
 
+@pytest.mark.parametrize("case", ["odd-n", "unaligned", "heavy", "batch-sizes"])
+def test_dense_eval_layouts_and_batch_sizes(ms, stream, small_table, case):
+    """The FP8 evaluation against the oracle: rows of n % 4 != 0 bytes, rows
+    starting off a 4-byte boundary, 64-bit weight sums (total weight >=
+    2^31), and one context evaluating several batch sizes in turn (a partial
+    tile of one chain, growth of the scratch, smaller sizes after larger)."""
+    import torch
+    rng = np.random.default_rng(11)
+    if case == "odd-n":
+        inst, sizes = inst_of(workloads.random_ksat(333, 1500, 3, seed=2, wmax=90)), [257]
+    elif case == "unaligned":
+        inst, sizes = inst_of(workloads.random_ksat(400, 1700, 3, seed=3, wmax=90)), [300]
+    elif case == "heavy":
+        n_, off, lits, _ = workloads.random_ksat(500, 2000, 3, seed=4)
+        w = rng.integers(1 << 38, 1 << 40, size=len(off) - 1).astype(np.int64)
+        inst, sizes = oracle.Instance(n_, off, lits, w), [384]
+    else:
+        inst, sizes = inst_of(workloads.random_ksat(700, 3000, 3, seed=5, wmax=500)), \
+            [1, 128, 129, 4096, 5, 1000]
+    ctx = make_ctx(ms, stream, inst, small_table, path=ms.MAXSAT_PATH_DENSE)
+    assert ms.maxsat_get_path(ctx) == ms.MAXSAT_PATH_DENSE
+    for B in sizes:
+        X = rng.integers(0, 2, size=(B, inst.n)).astype(np.uint8)
+        with torch.cuda.stream(stream):
+            if case == "unaligned":
+                buf = torch.zeros(B * inst.n + 1, dtype=torch.uint8, device="cuda")
+                xd = buf[1:].view(B, inst.n)
+                xd.copy_(torch.from_numpy(X).cuda())
+                assert xd.data_ptr() % 4 == 1
+            else:
+                xd = torch.from_numpy(X).cuda()
+            cd = torch.full((B,), -1, dtype=torch.int64, device="cuda")
+        ms.maxsat_eval(ctx, xd, cd)
+        stream.synchronize()
+        assert np.array_equal(cd.cpu().numpy(), oracle.evaluate(inst, X)), B
+    ms.maxsat_destroy(ctx)
+
+
 # --------------------------------------------------------------------------
 # Gibbs trajectories
 # --------------------------------------------------------------------------
