@@ -102,11 +102,14 @@ typedef struct {
                               graphs run no faster and take longer to build;
                               0 = plain launches */
   int32_t tune_blocks;   /* 1: at the first maxsat_reset for each B, time a few
-                            clause-block sizes of the sparse gather (3 rounds
-                            each, CUDA events) and keep the fastest. Costs,
-                            states and draws do not depend on the blocking;
-                            the free energy's float summation order does.
-                            Default 0 (the wave-fitted size) */
+                            clause-block sizes of the sparse gather, then the
+                            visible update's load batch (2, 4 or 8 incidences
+                            in flight per thread), 6 rounds each in two
+                            passes with CUDA events, and keep the fastest.
+                            Costs, states and draws do not depend on either;
+                            the free energy's float summation order depends
+                            on the blocking. Default 0 (the wave-fitted size,
+                            batch 4) */
   int32_t up_device;     /* 1: maxsat_up_begin / maxsat_up_end run unit
                             propagation and the merge on the GPU when the
                             chains are on the sparse path and one chain's
@@ -116,6 +119,10 @@ typedef struct {
                             shared memory; otherwise, and with 0, on host
                             threads as the paper does (single formulas
                             only). Same results either way. Default 1 */
+  int32_t visible_batch; /* incidences per thread whose hidden-pattern loads
+                            the sparse visible update keeps in flight: 2, 4
+                            or 8, or 0 for 4 unless tune_blocks measures
+                            another. Same results for every value. Default 0 */
 } maxsat_params;
 
 typedef struct maxsat_ctx maxsat_ctx;
@@ -185,6 +192,11 @@ int maxsat_get_n_instances(const maxsat_ctx* ctx);
  * to the SM count, or measured with params.tune_blocks); 0 before the first
  * maxsat_reset; a negative code for a NULL context. */
 int maxsat_get_clause_block(const maxsat_ctx* ctx);
+
+/* Incidences per thread whose hidden-pattern loads the sparse visible update
+ * keeps in flight together (params.visible_batch, else 4 or measured with
+ * params.tune_blocks); a negative code for a NULL context. */
+int maxsat_get_visible_batch(const maxsat_ctx* ctx);
 
 /* Starts B fresh chains (Fig. code initialisation): every variable drawn
  * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */

@@ -190,8 +190,10 @@ struct maxsat_ctx {
   int gather_slots = 0;  // SMs x resident gather blocks per SM
   int gather_cb = 0;     // clauses per gather block for the chains' Bp
   int cb_force = 0;      // clause block used instead of the wave-fitted one (0 = none)
+  int vis_batch = 4;     // visible update: incidences whose loads are in flight together
   int tuned_B = 0;       // B of the last measured clause-block choice
   std::vector<std::pair<int, float>> tune_ms;  // measured (clause block, ms per round)
+  std::vector<std::pair<int, float>> tune_vis_ms;  // measured (visible batch, ms per round)
   bool wide_h = false;  // hidden patterns need 16 bits (some group has L > 8)
 
   cudaGraphExec_t graph = nullptr;
@@ -348,7 +350,8 @@ int launch_round(maxsat_ctx* ctx, cudaStream_t st, const uint32_t* tdev, uint32_
         launch_gather(kStep, ctx->F, ctx->T, C, C.xt, C.B, C.Bp, ctx->plan, tdev, t_rel,
                       C.cost_part, C.fe_part, C.tickets, nullptr, ctx->wide_h, st));
   TIMED(ctx, st, "visible",
-        launch_visible(ctx->F, ctx->T, C, (float)ctx->prm.alpha, tdev, t_rel, ctx->wide_h, st));
+        launch_visible(ctx->F, ctx->T, C, (float)ctx->prm.alpha, tdev, t_rel, ctx->wide_h, st,
+                       ctx->vis_batch));
   return MAXSAT_OK;
 }
 
@@ -636,13 +639,18 @@ int choose_path(maxsat_ctx* ctx, int32_t B) {
   return MAXSAT_OK;
 }
 
-// Measured clause-block size of the sparse gather (params.tune_blocks): times
-// 6 Gibbs rounds for each candidate (the wave-fitted size, half and twice it,
-// and the plain m / 256 rule) with CUDA events, in two passes, and keeps the
-// fastest minimum; it leaves the wave-fitted size only for a gain above 2 %.
+// Measured launch shapes of the sparse round (params.tune_blocks): times 6
+// Gibbs rounds for each candidate with CUDA events, in two passes, and keeps
+// the fastest minimum. First the gather's clause-block size (the
+// wave-fitted size, half and twice it, and the plain m / 256 rule), then,
+// with that size, the visible update's load batch (2, 4 or 8 incidences in
+// flight per thread). A candidate replaces the default (wave-fitted size,
+// batch 4) only for a gain above 2 %.
 int tune_blocks(maxsat_ctx* ctx, int32_t B) {
   const int Bp = (B + kChainTile - 1) / kChainTile * kChainTile;
   ctx->cb_force = 0;
+  const int vis_fixed = ctx->prm.visible_batch;  // 0: measured below
+  ctx->vis_batch = vis_fixed ? vis_fixed : 4;
   if (ctx->gather_slots == 0) {
     int rc0 = alloc_chains(ctx, B);  // sets gather_slots
     if (rc0 != MAXSAT_OK) return rc0;
@@ -657,52 +665,75 @@ int tune_blocks(maxsat_ctx* ctx, int32_t B) {
   const bool prof = ctx->profiling;
   ctx->profiling = false;
   ctx->tune_ms.clear();
+  ctx->tune_vis_ms.clear();
+  // ms per round of the current shape (fresh chains, 2 warm-up rounds)
+  auto time_rounds = [&](float* ms_out) -> int {
+    ctx->have_chains = false;
+    int r0 = alloc_chains(ctx, B);
+    if (r0 != MAXSAT_OK) return r0;
+    ctx->C.keys = philox_keys(0x5EEDu, 0u);
+    ctx->C.g8_off = 0;
+    ctx->C.B_total = B;
+    ctx->C.inv_B_total = 1.0f / (float)B;
+    cudaError_t e = launch_init_sparse(ctx->F, ctx->C, ctx->n, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "init");
+    constexpr int kWarm = 2, kRounds = 6;
+    for (int r = 0; r < kWarm + kRounds; ++r) {
+      if (r == kWarm) cudaEventRecord(e0, ctx->stream);
+      r0 = launch_round(ctx, ctx->stream, nullptr, (uint32_t)r);
+      if (r0 != MAXSAT_OK) return r0;
+    }
+    cudaEventRecord(e1, ctx->stream);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms / kRounds;
+    return MAXSAT_OK;
+  };
   std::map<int, float> best_of;  // clause block actually used -> fastest ms per round
   int rc = MAXSAT_OK;
   for (int pass = 0; pass < 2 && rc == MAXSAT_OK; ++pass)
     for (int cb : cand) {
       ctx->cb_force = cb;
-      ctx->have_chains = false;
-      rc = alloc_chains(ctx, B);
-      if (rc != MAXSAT_OK) break;
-      ctx->C.keys = philox_keys(0x5EEDu, 0u);
-      ctx->C.g8_off = 0;
-      ctx->C.B_total = B;
-      ctx->C.inv_B_total = 1.0f / (float)B;
-      cudaError_t e = launch_init_sparse(ctx->F, ctx->C, ctx->n, ctx->stream);
-      if (e != cudaSuccess) {
-        rc = cuda_fail(ctx, e, "init");
-        break;
-      }
-      constexpr int kWarm = 2, kRounds = 6;
-      for (int r = 0; r < kWarm + kRounds && rc == MAXSAT_OK; ++r) {
-        if (r == kWarm) cudaEventRecord(e0, ctx->stream);
-        rc = launch_round(ctx, ctx->stream, nullptr, (uint32_t)r);
-      }
-      if (rc != MAXSAT_OK) break;
-      cudaEventRecord(e1, ctx->stream);
-      e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        rc = cuda_fail(ctx, e, "cudaEventSynchronize");
-        break;
-      }
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= kRounds;
+      rc = time_rounds(&ms);
+      if (rc != MAXSAT_OK) break;
       ctx->tune_ms.emplace_back(ctx->gather_cb, ms);
       auto it = best_of.find(ctx->gather_cb);
       if (it == best_of.end() || ms < it->second) best_of[ctx->gather_cb] = ms;
     }
+  int best = fit;
+  if (rc == MAXSAT_OK) {
+    float best_ms = best_of.count(fit) ? best_of[fit] : 1e30f;
+    for (const auto& kv : best_of)
+      if (kv.second < 0.98f * best_ms) {
+        best_ms = kv.second;
+        best = kv.first;
+      }
+  }
+  ctx->cb_force = best;
+  std::map<int, float> vis_of;  // visible batch -> fastest ms per round
+  for (int pass = 0; pass < 2 && rc == MAXSAT_OK && !vis_fixed; ++pass)
+    for (int vb : {2, 4, 8}) {
+      ctx->vis_batch = vb;
+      float ms = 0.f;
+      rc = time_rounds(&ms);
+      if (rc != MAXSAT_OK) break;
+      ctx->tune_vis_ms.emplace_back(vb, ms);
+      auto it = vis_of.find(vb);
+      if (it == vis_of.end() || ms < it->second) vis_of[vb] = ms;
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->profiling = prof;
+  ctx->vis_batch = vis_fixed ? vis_fixed : 4;
   if (rc != MAXSAT_OK) return rc;
-  int best = fit;
-  float best_ms = best_of.count(fit) ? best_of[fit] : 1e30f;
-  for (const auto& kv : best_of)
-    if (kv.second < 0.98f * best_ms) {
-      best_ms = kv.second;
-      best = kv.first;
+  float vis_ms = vis_of.count(4) ? vis_of[4] : 1e30f;
+  for (const auto& kv : vis_of)
+    if (kv.second < 0.98f * vis_ms) {
+      vis_ms = kv.second;
+      ctx->vis_batch = kv.first;
     }
   ctx->cb_force = best;
   ctx->tuned_B = B;
@@ -855,6 +886,7 @@ void maxsat_default_params(maxsat_params* p) {
   p->steps_per_graph = 100;
   p->tune_blocks = 0;
   p->up_device = 1;
+  p->visible_batch = 0;
 }
 
 const char* maxsat_last_error(const maxsat_ctx* ctx) {
@@ -915,6 +947,9 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   if (prm.path < 0 || prm.path > 2) return fail(nullptr, MAXSAT_EINVAL, "unknown path");
   if (prm.steps_per_graph < 0 || prm.steps_per_graph > 100000)
     return fail(nullptr, MAXSAT_EINVAL, "steps_per_graph out of range");
+  if (prm.visible_batch != 0 && prm.visible_batch != 2 && prm.visible_batch != 4 &&
+      prm.visible_batch != 8)
+    return fail(nullptr, MAXSAT_EINVAL, "visible_batch must be 0, 2, 4 or 8");
   if (prm.n_sets < 0 || (prm.n_sets > 0 && !prm.sets)) return fail(nullptr, MAXSAT_EINVAL, "sets is NULL");
 
   if (n_inst > 1 && prm.path == MAXSAT_PATH_DENSE)
@@ -932,6 +967,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   ctx->m = (int32_t)m;
   ctx->nnz = (int32_t)nnz;
   ctx->prm = prm;
+  ctx->vis_batch = prm.visible_batch ? prm.visible_batch : 4;
   static const double kDefaultFstar[2] = {0.068, 0.528};
   for (int e = 0; e < prm.n_temps; ++e) {
     double f = prm.fstar ? prm.fstar[e] : (prm.n_temps == 2 ? kDefaultFstar[e] : 0.068 + (0.528 - 0.068) * e / std::max(1, prm.n_temps - 1));
@@ -1281,6 +1317,11 @@ int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
 int maxsat_get_clause_block(const maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   return ctx->gather_cb;
+}
+
+int maxsat_get_visible_batch(const maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  return ctx->vis_batch;
 }
 
 int maxsat_get_n_instances(const maxsat_ctx* ctx) {

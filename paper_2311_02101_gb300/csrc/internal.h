@@ -290,9 +290,11 @@ cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables&
                           const GatherPlan& P, const uint32_t* tdev, uint32_t t_rel,
                           int64_t* cost_part, float* fe_part, int32_t* tickets,
                           int64_t* eval_out, bool wide_h, cudaStream_t st);
+// batch: incidences per thread whose hidden-pattern loads are in flight
+// together (2, 4 or 8)
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
                            float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide_h,
-                           cudaStream_t st);
+                           cudaStream_t st, int batch = 4);
 cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st);
 cudaError_t launch_advance(uint32_t* tdev, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t st);

@@ -727,13 +727,14 @@ __device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains
   *reinterpret_cast<uint64_t*>(C.xt + o) = xnew;
 }
 
-constexpr int kVisBatch = 4;
-static_assert(32 % kVisBatch == 0, "incidence windows hold whole batches");
-
-template <bool SM, typename HT>
-__global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, DevChains C,
+// BATCH: incidences whose pattern loads are in flight together (a divisor
+// of 32; the launch picks it, measured by the block tuner). Batch 8 runs 3
+// blocks per SM (its loads need more than 64 registers), the others 4.
+template <bool SM, typename HT, int BATCH>
+__global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
                                                  uint32_t t_rel, int vg0) {
+  static_assert(32 % BATCH == 0, "incidence windows hold whole batches");
   pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_inc[8][32];  // per warp: a window of its variable's incidences
@@ -782,23 +783,23 @@ __global__ void __launch_bounds__(256, 4) k_visible(DevFormula F, DevTables T, D
       for (int q = 0; q < 8; ++q) e[q] = temp_of(gb0 + q, T.n_temps, C.B_total, C.inv_B_total);
     }
     // the variable's incidences pass through this warp's shared-memory slot
-    // 32 at a time (one coalesced load); kVisBatch (a divisor of 32) per
+    // 32 at a time (one coalesced load); BATCH (a divisor of 32) per
     // pass, their pattern loads in flight together, the last pass predicated
     // (warp-uniform)
-    for (int jj = j_begin; jj < j_end; jj += kVisBatch) {
+    for (int jj = j_begin; jj < j_end; jj += BATCH) {
       const int w = (jj - j_begin) & 31;
       if (w == 0) {
         __syncwarp();
         if (jj + lane < j_end) s_inc[warp][lane] = __ldg(F.var_inc + jj + lane);
         __syncwarp();
       }
-      HV v[kVisBatch];
+      HV v[BATCH];
 #pragma unroll
-      for (int u = 0; u < kVisBatch; ++u)
+      for (int u = 0; u < BATCH; ++u)
         if (jj + u < j_end)
           v[u] = __ldg(reinterpret_cast<const HV*>(H + (size_t)s_inc[warp][w + u].x * C.Bp + b0));
 #pragma unroll
-      for (int u = 0; u < kVisBatch; ++u) {
+      for (int u = 0; u < BATCH; ++u) {
         if (jj + u >= j_end) break;
         const int4 inc = s_inc[warp][w + u];
         const int base = inc.y & 0x7FFFFFFF;
@@ -984,8 +985,9 @@ cudaError_t gather_mode(dim3 grid, cudaStream_t st, bool wide, const DevFormula&
 template <bool SM, typename HT>
 cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormula& F,
                             const DevTables& T, const DevChains& C, float alpha,
-                            const uint32_t* tdev, uint32_t t_rel) {
-  auto kern = k_visible<SM, HT>;
+                            const uint32_t* tdev, uint32_t t_rel, int batch) {
+  auto kern = batch >= 8 ? k_visible<SM, HT, 8> : batch <= 2 ? k_visible<SM, HT, 2>
+                                                             : k_visible<SM, HT, 4>;
   {
     const cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -1095,14 +1097,15 @@ cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables&
 
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
                            float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide,
-                           cudaStream_t st) {
+                           cudaStream_t st, int batch) {
   dim3 grid(C.Bp / kChainTile, (F.n + 7) / 8);
   const int sm = visible_smem_bytes(T);
   const bool use_sm = sm <= kSmemLimit;
-  if (use_sm && !wide) return visible_variant<true, uint8_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel);
-  if (use_sm) return visible_variant<true, uint16_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel);
-  if (!wide) return visible_variant<false, uint8_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel);
-  return visible_variant<false, uint16_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel);
+  if (use_sm && !wide)
+    return visible_variant<true, uint8_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel, batch);
+  if (use_sm) return visible_variant<true, uint16_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel, batch);
+  if (!wide) return visible_variant<false, uint8_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel, batch);
+  return visible_variant<false, uint16_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel, batch);
 }
 
 cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st) {

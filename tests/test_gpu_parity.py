@@ -65,10 +65,10 @@ def inst_of(gen):
 
 
 def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0,
-             tune=0, up_device=1):
+             tune=0, up_device=1, vb=0):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=n_temps, n_buckets=n_buckets,
                                       alpha=alpha, steps_per_graph=spg, path=path,
-                                      tune_blocks=tune, up_device=up_device)
+                                      tune_blocks=tune, up_device=up_device, visible_batch=vb)
     params.fstar = None
     return ms.maxsat_create(inst.n, inst.off, inst.lits, inst.w, params, stream)
 
@@ -602,9 +602,32 @@ def test_batch_full_size_sampled(ms, stream, golden_table):
     ms.maxsat_destroy(ctx)
 
 
+@pytest.mark.parametrize("vb,kmax", [(2, 3), (8, 3), (2, 4), (8, 4)])
+def test_visible_batches_keep_parity(ms, stream, small_table, vb, kmax):
+    """Every load batch of the visible update (2 and 8 beside the default 4
+    of the other tests) gives the oracle's trajectory, on one-chunk (kmax 3)
+    and multi-chunk tables."""
+    inst = edge_instance(5, kmax)
+    T, seed, B = 20, 6, 300
+    ctx = make_ctx(ms, stream, inst, small_table, vb=vb)
+    assert ms.maxsat_get_visible_batch(ctx) == vb
+    ms.maxsat_reset(ctx, B, seed)
+    ms.maxsat_step(ctx, T)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
+
+
+def test_visible_batch_is_checked(ms, stream, small_table):
+    inst = edge_instance(5, 3)
+    with pytest.raises(ms.MaxsatError):
+        make_ctx(ms, stream, inst, small_table, vb=3)
+
+
 def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
-    """With tune_blocks the gather's clause-block size is measured at the first
-    reset; the trajectory is the oracle's whatever size wins."""
+    """With tune_blocks the gather's clause-block size and then the visible
+    update's load batch are measured at the first reset; the trajectory is
+    the oracle's whatever shape wins."""
     inst = inst_of(workloads.mixed_length(n=400, m=2000, seed=9))
     T, seed, B = 10, 5, 512
     ctx = make_ctx(ms, stream, inst, golden_table, n_buckets=4, path=ms.MAXSAT_PATH_SPARSE,
@@ -612,6 +635,7 @@ def test_measured_clause_blocks_keep_parity(ms, stream, golden_table):
     ms.maxsat_reset(ctx, B, seed)
     cb = ms.maxsat_get_clause_block(ctx)
     assert cb >= 16
+    assert ms.maxsat_get_visible_batch(ctx) in (2, 4, 8)
     ms.maxsat_step(ctx, T)
     gpu = ms.maxsat_get_state(ctx)
     ms.maxsat_destroy(ctx)
