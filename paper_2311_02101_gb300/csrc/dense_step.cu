@@ -612,6 +612,10 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
     const uint32_t tround = step_index(a.tdev, a.t_rel);
     // nu update with the sparse path's exact FP32 operation sequence
     const float keep = __fsub_rn(1.0f, a.alpha);
+    uint8_t* __restrict__ Xs = a.X;
+    float* __restrict__ nus = a.nu;
+    uint8_t* __restrict__ bxs = a.best_x;
+    const uint8_t* __restrict__ impv = C.improved;
     int li = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
       const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
@@ -622,30 +626,40 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
       tc::fence_after_sync();
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
                              (uint32_t)(buf * kBN + cgrp * kCols);
-      for (int j = 0; j < kCols / 32; ++j) {
-        uint32_t r[32];
-        tc::tmem_ld32(taddr + (uint32_t)(j * 32), r);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int sub = 0; sub < 4; ++sub) {
-          const int b0 = tn * kBN + cgrp * kCols + j * 32 + sub * 8;
-          const uint4 R = philox4x32_10(
-              make_uint4((uint32_t)i, (uint32_t)(C.g8_off + (b0 >> 3)), tround, kPhaseVisible),
-              C.keys);
-          if (!valid) continue;
+      // 8 chains (TMEM columns) at a time: their accumulators and state
+      // loads first, then the draws and the stores
+#pragma unroll 1
+      for (int c8 = 0; c8 < kCols / 8; ++c8) {
+        const int b0 = tn * kBN + cgrp * kCols + c8 * 8;
+        uint32_t r[8];
+        tc::tmem_ld8(taddr + (uint32_t)(c8 * 8), r);
+        uint32_t xo[8];
+        float nv[8];
+        if (valid) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            const int b = b0 + q;
-            const int z = __float2int_rn(__uint_as_float(r[sub * 8 + q]));
-            const int qq = max(-T.qmax, min(T.qmax, z));
-            const uint32_t P = pv[qq + T.qmax];
-            const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
-            const size_t o = (size_t)b * a.n_pad + i;
-            const uint8_t xold = a.X[o];
-            if (C.improved[b]) a.best_x[o] = xold == a.one ? 1 : 0;
-            a.nu[o] = __fmaf_rn(keep, a.nu[o], __fmul_rn(a.alpha, var));
-            a.X[o] = lane16(R, q) < P ? a.one : a.minus_one;
+            const size_t o = (size_t)(b0 + q) * a.n_pad + i;
+            xo[q] = Xs[o];
+            nv[q] = nus[o];
           }
+        }
+        const uint2 imp = *reinterpret_cast<const uint2*>(impv + b0);  // 8 flag bytes
+        const uint4 R = philox4x32_10(
+            make_uint4((uint32_t)i, (uint32_t)(C.g8_off + (b0 >> 3)), tround, kPhaseVisible),
+            C.keys);
+        tc::tmem_ld_wait();
+        if (!valid) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int z = __float2int_rn(__uint_as_float(r[q]));
+          const int qq = max(-T.qmax, min(T.qmax, z));
+          const uint32_t P = pv[qq + T.qmax];
+          const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
+          const size_t o = (size_t)(b0 + q) * a.n_pad + i;
+          if (((q < 4 ? imp.x : imp.y) >> (8 * (q & 3))) & 0xFFu)
+            bxs[o] = xo[q] == a.one ? 1 : 0;
+          nus[o] = __fmaf_rn(keep, nv[q], __fmul_rn(a.alpha, var));
+          Xs[o] = lane16(R, q) < P ? a.one : a.minus_one;
         }
       }
       tc::fence_before_sync();
