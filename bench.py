@@ -327,9 +327,9 @@ def run_mine(args):
     stream = torch.cuda.Stream()
     path_code = {"auto": ms.MAXSAT_PATH_AUTO, "sparse": ms.MAXSAT_PATH_SPARSE,
                  "dense": ms.MAXSAT_PATH_DENSE}[args.path]
-    # wave-fitted clause blocks (the measured choice, tune_blocks, is used for
-    # the 512-formula batch below, where it pays)
-    params = ms.maxsat_default_params(path=path_code)
+    # launch shapes measured at the first reset (tune_blocks: the gather's
+    # clause block, then the visible update's load batch)
+    params = ms.maxsat_default_params(path=path_code, tune_blocks=1)
     ctx = ms.maxsat_create(n, off, lits, w, params, stream)
     # every rank runs its own shard of one ensemble of ws * B chains (weak
     # scaling): global chains rank * B .. rank * B + B - 1
@@ -531,6 +531,7 @@ def run_mine(args):
                 data="synthetic",
                 config=dict(workload=args.workload, n=n, m=m, B=B, path=path, path_requested=args.path,
                             steps_per_graph=S, clause_block=ms.maxsat_get_clause_block(ctx),
+                            visible_batch=ms.maxsat_get_visible_batch(ctx),
                             parallelism=f"chain-shards{ws}",
                             l2=f"flushed before every timed round ({2 * l2 >> 20} MB buffer written "
                                f"outside the round's event interval; the chains' state, about "
