@@ -219,9 +219,10 @@ struct maxsat_ctx {
   int64_t* d_row_w = nullptr;     // m_pad weights (0 for padding rows)
   uint8_t* d_grp_small = nullptr; // per 32-row group: 1 when its rows share one weight
   CUtensorMap tmA{};
-  uint8_t* dXe = nullptr;         // eval scratch: Bp x n_pad FP8 states
+  uint8_t* dXe[2] = {nullptr, nullptr};  // eval scratch: two Bp x n_pad FP8 state buffers
   int dev_Bp = 0;
-  CUtensorMap tmXe{};
+  CUtensorMap tmXe[2] = {};
+  int ev_buf = 0;                 // state buffer of the next evaluation
   int* d_err = nullptr;           // device wait-timeout code (0 = none)
   // dense scatter-add (GEMM2): block-diagonal variable x incidence matrix
   int tiles_v = 0, kmax = 0;
@@ -1494,17 +1495,24 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
       // grow the eval scratch (releasing the old one waits for the device)
       ctx->dense_eval_mem.release();
       ctx->dev_Bp = 0;
-      CK(ctx, ctx->dense_eval_mem.alloc(&ctx->dXe, (size_t)Bp * ctx->n_pad));
-      std::string e = make_tmap_2d(&ctx->tmXe, ctx->dXe, ctx->n_pad, Bp, ctx->n_pad, 128, 256, false);
-      if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
+      for (int k = 0; k < 2; ++k) {
+        CK(ctx, ctx->dense_eval_mem.alloc(&ctx->dXe[k], (size_t)Bp * ctx->n_pad));
+        std::string e =
+            make_tmap_2d(&ctx->tmXe[k], ctx->dXe[k], ctx->n_pad, Bp, ctx->n_pad, 128, 256, false);
+        if (!e.empty()) return fail(ctx, MAXSAT_ECUDA, e);
+      }
       ctx->dev_Bp = Bp;
     }
     const int Bt = ctx->dev_Bp;
+    // alternate state buffers: this conversion may run beside the previous
+    // evaluation's product, which reads the other one
+    const int xb = ctx->ev_buf;
+    ctx->ev_buf ^= 1;
     TIMED(ctx, ctx->stream, "assign_fp8",
-          launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe, cost_dev,
-                            ctx->stream));
+          launch_assign_fp8(assign_dev, B, ctx->n, Bt, ctx->n_pad, ctx->e5m2, ctx->dXe[xb],
+                            cost_dev, ctx->stream));
     TIMED(ctx, ctx->stream, "gemm1_eval",
-          launch_gemm1_eval(ctx->tmA, ctx->tmXe, ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
+          launch_gemm1_eval(ctx->tmA, ctx->tmXe[xb], ctx->m, ctx->m_pad, ctx->n_pad, B, Bt, ctx->e5m2,
                             ctx->d_row_len, ctx->d_row_w, ctx->d_grp_small, cost_dev, ctx->d_err,
                             ctx->stream));
     return MAXSAT_OK;

@@ -35,6 +35,9 @@
 // the FP8 B operand and zeroes the costs; k_gemm1_eval is its programmatic
 // dependent, so its setup (barriers, TMEM, tensor-map prefetch) overlaps the
 // conversion and it waits (griddepcontrol.wait) only before touching them.
+// Consecutive evaluations alternate between two state buffers, and each
+// product lets the next conversion start at once: that conversion runs beside
+// the product and waits for its end only before it zeroes the costs.
 // Every mbarrier wait is bounded; a timeout records an error code that the
 // host reads after the launch, and the kernel still releases its TMEM.
 #include <cuda.h>
@@ -118,6 +121,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   const uint32_t tmem = S.tmem_slot;
   // the B operand and the zeroed costs come from the preceding conversion
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next evaluation's conversion (into the other state buffer) may start
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (warp == 0) {
     if (lane == 0) {
@@ -277,19 +282,25 @@ __device__ __forceinline__ uint4 convert16(const uint8_t* __restrict__ assign, i
 
 // assign (B x n bytes, nonzero = true) -> X (Bp x n_pad FP8): +1 / -1 for
 // variables, 0 for padding variables and padding chains; 16 output bytes
-// (one 16-byte store) per thread. Also zeroes the B costs the product then
-// accumulates into.
+// (one 16-byte store) per thread. Then zeroes the B costs the product
+// accumulates into. It is the programmatic dependent of the launch before it
+// on the stream: when that is the previous evaluation's product (which lets
+// it start early, and reads the other state buffer), the conversion runs
+// beside it, and only the zeroing of the costs, which that product may
+// still be adding into, waits for its end.
 __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, int Bp, int n_pad,
                              uint32_t minus_one4, uint8_t* __restrict__ X,
                              int64_t* __restrict__ cost) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < (size_t)B) cost[idx] = 0;
   const int chunks = n_pad / 16;
-  if (idx >= (size_t)Bp * chunks) return;
-  const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
-  reinterpret_cast<uint4*>(X)[idx] =
-      b < B ? convert16(assign, n, b, i0, minus_one4) : make_uint4(0u, 0u, 0u, 0u);
+  if (idx < (size_t)Bp * chunks) {
+    const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
+    reinterpret_cast<uint4*>(X)[idx] =
+        b < B ? convert16(assign, n, b, i0, minus_one4) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (idx < (size_t)B) cost[idx] = 0;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -428,9 +439,17 @@ cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n
   uint8_t minus_one;
   fp8_encode_int(-1, e5m2, &minus_one);
   const size_t total = std::max((size_t)Bp * (n_pad / 16), (size_t)B);
-  k_assign_fp8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-      assign, B, n, Bp, n_pad, 0x01010101u * minus_one, X, cost);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((total + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_assign_fp8, assign, B, n, Bp, n_pad, 0x01010101u * minus_one,
+                            X, cost);
 }
 
 }  // namespace rbmsat

@@ -308,7 +308,9 @@ std::string build_gather_matrix(int n, int m, const int64_t* off, const int32_t*
 std::string make_tmap_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t rows,
                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows, bool bf16);
 // adds every chain's weighted unsatisfied cost into out (B, zeroed by
-// launch_assign_fp8, which must be the launch just before it on st)
+// launch_assign_fp8, which must be the launch just before it on st); lets
+// the next launch on st start early (the next evaluation's conversion, into
+// the other state buffer)
 cudaError_t launch_gemm1_eval(const CUtensorMap& tmA, const CUtensorMap& tmB, int m, int m_pad,
                               int n_pad, int B, int Bp, bool e5m2, const int32_t* row_len,
                               const int64_t* row_w, const uint8_t* grp_small, int64_t* out,
