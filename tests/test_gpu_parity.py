@@ -219,6 +219,33 @@ def test_dense_eval_layouts_and_batch_sizes(ms, stream, small_table, case):
     ms.maxsat_destroy(ctx)
 
 
+def test_dense_evals_back_to_back(ms, stream, small_table):
+    """Consecutive dense evaluations overlap (the next conversion runs beside
+    the previous product, into the other state buffer): five evaluations
+    queued without a synchronisation, into separate cost arrays and, last,
+    two into the same one, each against the oracle."""
+    import torch
+    inst = inst_of(workloads.random_ksat(400, 1700, 3, seed=7, wmax=60))
+    ctx = make_ctx(ms, stream, inst, small_table, path=ms.MAXSAT_PATH_DENSE)
+    assert ms.maxsat_get_path(ctx) == ms.MAXSAT_PATH_DENSE
+    rng = np.random.default_rng(17)
+    B = 520
+    Xs = [rng.integers(0, 2, size=(B, inst.n)).astype(np.uint8) for _ in range(5)]
+    with torch.cuda.stream(stream):
+        xd = [torch.from_numpy(X).cuda() for X in Xs]
+        cd = [torch.full((B,), -1, dtype=torch.int64, device="cuda") for _ in range(4)]
+    stream.synchronize()
+    for k in range(3):
+        ms.maxsat_eval(ctx, xd[k], cd[k])
+    ms.maxsat_eval(ctx, xd[3], cd[3])
+    ms.maxsat_eval(ctx, xd[4], cd[3])  # the same cost array: the later evaluation wins
+    stream.synchronize()
+    for k in range(3):
+        assert np.array_equal(cd[k].cpu().numpy(), oracle.evaluate(inst, Xs[k])), k
+    assert np.array_equal(cd[3].cpu().numpy(), oracle.evaluate(inst, Xs[4]))
+    ms.maxsat_destroy(ctx)
+
+
 # --------------------------------------------------------------------------
 # Gibbs trajectories
 # --------------------------------------------------------------------------
