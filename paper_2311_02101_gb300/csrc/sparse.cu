@@ -733,13 +733,20 @@ __device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains
 template <bool SM, typename HT, int BATCH>
 __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula F, DevTables T, DevChains C,
                                                  float alpha, const uint32_t* tdev,
-                                                 uint32_t t_rel, int vg0) {
+                                                 uint32_t t_rel, int v0, int tile_major) {
   static_assert(32 % BATCH == 0, "incidence windows hold whole batches");
   pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_inc[8][32];  // per warp: a window of its variable's incidences
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
+  // tile_major: blocks walk every variable group of one chain tile before the
+  // next tile (x = variable group, y = chain tile from v0), so a tile's hidden
+  // patterns, m x 256 entries, stay in the L2 while its variables pull them
+  // (taken when all of them would not fit). Otherwise x = chain tile, y =
+  // variable group from v0.
+  const int tile = tile_major ? v0 + (int)blockIdx.y : (int)blockIdx.x;
+  const int vgroup = tile_major ? (int)blockIdx.x : v0 + (int)blockIdx.y;
+  const int g8 = tile * 32 + lane, b0 = g8 * 8;
   const int16_t* gq = T.gq;
   const uint32_t* pv = T.pv;
   if (SM) {
@@ -751,7 +758,7 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
     pv = reinterpret_cast<const uint32_t*>(smem + gb);
   }
   // variables in descending degree: a block's 8 warps carry similar work
-  const int slot = (vg0 + blockIdx.y) * 8 + warp;
+  const int slot = vgroup * 8 + warp;
   if (slot >= F.n) return;
   const int i = F.var_order ? __ldg(F.var_order + slot) : slot;
   const int2 vi = var_instance(F, i);
@@ -992,11 +999,31 @@ cudaError_t visible_variant(dim3 grid, int smem, cudaStream_t st, const DevFormu
     const cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
-  const int groups = (F.n + 7) / 8;
-  for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
-    grid.y = std::min(kMaxGridY, groups - vg0);
-    const cudaError_t e = launch_pdl(kern, grid, smem, st, F, T, C, alpha, tdev, t_rel, vg0);
-    if (e != cudaSuccess) return e;
+  const int groups = (F.n + 7) / 8, tiles = (int)grid.x;
+  // tile-major when the hidden patterns exceed half the L2
+  static int l2 = -1;
+  if (l2 < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+      l2 = 0;
+  }
+  const int tm = (double)F.m * C.Bp * sizeof(HT) > 0.5 * (double)l2 ? 1 : 0;
+  if (tm) {
+    // x = variable groups, y = chain tiles (launches of at most kMaxGridY tiles)
+    grid.x = (unsigned)groups;
+    for (int t0 = 0; t0 < tiles; t0 += kMaxGridY) {
+      grid.y = std::min(kMaxGridY, tiles - t0);
+      const cudaError_t e = launch_pdl(kern, grid, smem, st, F, T, C, alpha, tdev, t_rel, t0, tm);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    // x = chain tiles, y = variable groups (launches of at most kMaxGridY groups)
+    for (int vg0 = 0; vg0 < groups; vg0 += kMaxGridY) {
+      grid.y = std::min(kMaxGridY, groups - vg0);
+      const cudaError_t e = launch_pdl(kern, grid, smem, st, F, T, C, alpha, tdev, t_rel, vg0, tm);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaGetLastError();
 }
