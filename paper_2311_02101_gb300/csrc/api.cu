@@ -1141,18 +1141,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
           return var_off[a + 1] - var_off[a] > var_off[b + 1] - var_off[b];
         });
       }
-    // one record per slot: the visible update reads it with one load
-    std::vector<int4> vrec(n);
-    std::vector<int32_t> sinst(n_inst > 1 ? n : 0);
-    for (int k = 0; k < n_inst; ++k)
-      for (int s = var_base[k]; s < var_base[k + 1]; ++s) {
-        const int v = order[s];
-        vrec[s] = make_int4(v, var_off[v], var_off[v + 1], v - var_base[k]);
-        if (n_inst > 1) sinst[s] = k;
-      }
-    UP(vrec, F.var_rec);
-    F.slot_inst = nullptr;
-    if (n_inst > 1) UP(sinst, F.slot_inst);
+    UP(order, F.var_order);
   }
   F.cl4 = nullptr;
   if (T.one_chunk) {

@@ -57,12 +57,9 @@ struct DevFormula {
                            // length}, bit k of `negated` set when literal k is
                            // negated, when every clause has at most 3
                            // literals (one-chunk tables); else NULL
-  const int4* var_rec;       // n: the visible update's slots in order, each
-                             // {variable, first incidence, end incidence,
-                             // index within its formula}: variables by degree,
-                             // highest first (ties to the lower index), within
-                             // windows of 512 variables of one formula
-  const int32_t* slot_inst;  // n: formula of each slot's variable; NULL for one formula
+  const int32_t* var_order;  // n: the visible update's order: variables by
+                             // degree, highest first (ties to the lower index),
+                             // within windows of 512 variables of one formula
 };
 
 // Work list of the clause gather: blocks of consecutive clauses that never

@@ -684,9 +684,10 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   if (tid == 0) *ticket = 0;
 }
 
-// best-so-far copy of the improved chains among 8 (imp: their 8 flag bytes)
-__device__ __forceinline__ void keep_flagged(const DevChains& C, size_t o, uint64_t imp,
-                                             uint64_t xold) {
+__device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size_t o, int b0,
+                                              uint64_t xold) {
+  const uint64_t imp =
+      *reinterpret_cast<const uint64_t*>(C.improved + (size_t)inst * C.Bp + b0);
   if (imp) {
     const uint64_t mask = imp * 0xFFull;  // 0x01 flags -> 0xFF byte masks
     uint64_t* bx = reinterpret_cast<uint64_t*>(C.best_xt + o);
@@ -694,21 +695,14 @@ __device__ __forceinline__ void keep_flagged(const DevChains& C, size_t o, uint6
   }
 }
 
-__device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size_t o, int b0,
-                                              uint64_t xold) {
-  keep_flagged(C, o, *reinterpret_cast<const uint64_t*>(C.improved + (size_t)inst * C.Bp + b0),
-               xold);
-}
-
 // The end of a visible update for one variable and 8 chains given their
 // integer logits z (units 2^-Q): best-so-far copy of improved chains, the
 // visible draws x ~ Bernoulli(P[z]) (Eq. 3) and nu (Sec. 4.4).
 __device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains& C,
                                              const uint32_t* pv, float alpha, uint32_t t,
-                                             int2 vi, int g8, size_t o, uint64_t imp,
-                                             uint64_t xold, float4 n0, float4 n1,
-                                             const int (&z)[8]) {
-  keep_flagged(C, o, imp, xold);
+                                             int2 vi, int g8, size_t o, int b0, uint64_t xold,
+                                             float4 n0, float4 n1, const int (&z)[8]) {
+  keep_improved(C, vi.x, o, b0, xold);
   const uint4 r =
       philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), t,
                                kPhaseVisible | ((uint32_t)vi.x << 8)),
@@ -766,14 +760,8 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
   // variables in descending degree: a block's 8 warps carry similar work
   const int slot = vgroup * 8 + warp;
   if (slot >= F.n) return;
-  // the slot's variable and incidence range, and its first window of
-  // incidences (formula data, not written by the preceding launch) before the
-  // wait
-  const int4 vr = __ldg(F.var_rec + slot);
-  const int i = vr.x, j_begin = vr.y, j_end = vr.z;
-  const int2 vi = make_int2(F.slot_inst ? __ldg(F.slot_inst + slot) : 0, vr.w);
-  if (j_begin + lane < j_end) s_inc[warp][lane] = __ldg(F.var_inc + j_begin + lane);
-  __syncwarp();
+  const int i = F.var_order ? __ldg(F.var_order + slot) : slot;
+  const int2 vi = var_instance(F, i);
   pdl_wait();  // chain state from here on
   const uint32_t t = step_index(tdev, t_rel);
   const int gb0 = C.g8_off * 8 + b0;  // global chain index
@@ -789,7 +777,7 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
   const uint64_t xold = *reinterpret_cast<const uint64_t*>(C.xt + o);
   float4* nu4 = reinterpret_cast<float4*>(C.nu + o);
   const float4 n0 = nu4[0], n1 = nu4[1];
-  const uint64_t imp = *reinterpret_cast<const uint64_t*>(C.improved + (size_t)vi.x * C.Bp + b0);
+  const int j_begin = __ldg(F.var_off + i), j_end = __ldg(F.var_off + i + 1);
   // z += sgn * 2^Q G[e][pattern][slot] over the variable's incidences
   // (clause inc.x, table base | sign inc.y, stride K inc.z, per-temperature
   // stride 2^L K inc.w); a negated literal's base lies in the table's negated
@@ -807,7 +795,7 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
     // (warp-uniform)
     for (int jj = j_begin; jj < j_end; jj += BATCH) {
       const int w = (jj - j_begin) & 31;
-      if (w == 0 && jj != j_begin) {  // (the first window is loaded above)
+      if (w == 0) {
         __syncwarp();
         if (jj + lane < j_end) s_inc[warp][lane] = __ldg(F.var_inc + jj + lane);
         __syncwarp();
@@ -858,7 +846,7 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
     sums(std::true_type{});
   else
     sums(std::false_type{});
-  visible_tail(T, C, pv, alpha, t, vi, g8, o, imp, xold, n0, n1, z);
+  visible_tail(T, C, pv, alpha, t, vi, g8, o, b0, xold, n0, n1, z);
 }
 
 __global__ void __launch_bounds__(256) k_keep_copy(DevFormula F, DevChains C, int n, int vg0) {
