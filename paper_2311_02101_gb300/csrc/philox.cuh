@@ -45,15 +45,23 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
+// acc |= mask when x < w (unsigned): one compare and one predicated OR
+__device__ __forceinline__ void or_below(uint32_t& acc, uint32_t x, uint32_t w, uint32_t mask) {
+  asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+      : "+r"(acc)
+      : "r"(x), "r"(w), "r"(mask));
+}
+
 // Hidden draws of one clause for 8 chains (Eq. 2 / Eq. 6 with the negation
 // transform) from the chains' pattern records. Unit h draws from the Philox
 // block at counter (clause, chain-octet | h << 24, round, hidden phase),
 // chain q taking 16-bit lane q (low half of word q / 2 for even q, high half
 // for odd q), and bit h of hp[q] becomes [u < P]. Record word 1 + h holds
 // (min(P, 65535) << 16) | [P == 65536]: with u moved into the high half of
-// a 32-bit word x, the draw is [x < word] (| bit 0 when the group has a
-// saturated unit). tab points at the group's records as 16-byte chunks and
-// row4[q] is chain q's record in chunks; chunk j holds words 4j .. 4j + 3,
+// a 32-bit word x, the draw is [x < word] (in a group with a saturated unit,
+// x keeps only u, so that 0xFFFF0001 is above every x). tab points at the
+// group's records as 16-byte chunks and row4[q] is chain q's record in
+// chunks; chunk j holds words 4j .. 4j + 3,
 // i.e. units 4j - 1 .. 4j + 2 (word 0 of chunk 0 is the free energy).
 // hidden_words draws words I0 .. I0 + NW - 1 of chunk j (those below hi);
 // its NW Philox blocks run as straight-line code so that their multiply
@@ -76,21 +84,24 @@ __device__ __forceinline__ void hidden_words(const uint4* tab, const int (&row4)
                                          K)
                          : make_uint4(0u, 0u, 0u, 0u);
   }
-  const uint32_t vm = ((hi >= 4 ? 0xFu : (1u << hi) - 1u) >> I0) & ((1u << NW) - 1u);
+  // the hidden-pattern bit of each word's unit 4 j + I0 + i - 1 (0 past hi,
+  // so that OR changes nothing)
+  uint32_t mk[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) mk[i] = I0 + i < hi ? 1u << (4 * j + I0 + i - 1) : 0u;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const uint4 r = tab[row4[q] + j];
     if (FE) fe[q] += __uint_as_float(r.x);
-    uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < NW; ++i) {
-      uint32_t x = word_of(R[i], q >> 1);
-      if (!(q & 1)) x = __byte_perm(x, 0u, 0x1032);  // the low-half draw moves up
-      const uint32_t w = word_of(r, I0 + i);
-      bits |= (uint32_t)(x < w) << i;
-      if (SAT) bits |= (w & 1u) << i;
+      // u in the high half of x: the low-half draw moves up; with a saturated
+      // unit in the group (word 0xFFFF0001) the high-half draw drops the low
+      // half, so x stays below it
+      const uint32_t word = word_of(R[i], q >> 1);
+      const uint32_t x = (q & 1) ? (SAT ? (word & 0xFFFF0000u) : word) : (word << 16);
+      or_below(hp[q], x, word_of(r, I0 + i), mk[i]);
     }
-    hp[q] |= ((bits & vm) << (4 * j + I0)) >> 1;
   }
 }
 
