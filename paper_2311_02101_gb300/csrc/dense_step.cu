@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "dense_common.cuh"
 #include "internal.h"
@@ -45,7 +46,7 @@ constexpr int kBN = 256;   // chains per tile
 constexpr int kBK1 = 128;  // GEMM1 K-block: 128 FP8
 constexpr int kBK2 = 64;   // GEMM2 K-block: 64 16-bit elements
 constexpr int kS1 = 3;     // GEMM1 ring stages (step mode)
-constexpr int kS2 = 3;     // GEMM2 ring stages (at most)
+constexpr int kS2 = 4;     // GEMM2 ring stages (at most)
 constexpr int kStage1A = kBM * kBK1, kStage1B = kBN * kBK1;        // 16 KB, 32 KB
 constexpr int kStage2A = kBM * kBK2 * 2, kStage2B = kBN * kBK2 * 2;  // 16 KB, 32 KB
 constexpr int kEpi1 = 16;  // GEMM1 epilogue warps (4 per TMEM lane quarter)
@@ -346,18 +347,23 @@ struct G2Smem {
   uint32_t tmem_slot;
 };
 
-// GEMM2 ring stage: P^T tile, G tile, the K-block's staged hidden patterns
-// (64 incidences x 256 chains) and its 64 incidence records.
+// GEMM2 ring stage: P^T tile, the K-block's staged hidden patterns (64
+// incidences x 256 chains) and its 64 incidence records. The G tiles the
+// builders write alternate between two buffers after the ring: G of K-block g
+// may be overwritten once the MMA of K-block g - 2 is done, which every
+// builder knows once the records of K-block g + kStages - 2 have landed (the
+// producer refilled that stage after the MMA of g - 2 released it).
 template <typename HT>
 struct G2Stage {
   static constexpr int kA = kStage2A;
-  static constexpr int kB = kStage2B;
   static constexpr int kH = kBK2 * kBN * (int)sizeof(HT);  // staged hidden patterns [u][chain]
   static constexpr int kInc = 1024;
-  static constexpr int kBytes = kA + kB + kH + kInc;  // multiple of 1024
-  static constexpr int kStages = sizeof(HT) == 1 ? 3 : 2;
-  static constexpr int kTabOff =
-      (kStages * kBytes + (int)sizeof(G2Smem) + 127) / 128 * 128;
+  static constexpr int kBytes = kA + kH + kInc;  // multiple of 1024
+  static constexpr int kStages = sizeof(HT) == 1 ? 4 : 3;
+  static constexpr int kAhead = kStages - 2;  // K-blocks between a stage's copies and its build
+  static constexpr int kB = kStage2B;
+  static constexpr int kBOff = kStages * kBytes;
+  static constexpr int kTabOff = (kBOff + 2 * kB + (int)sizeof(G2Smem) + 127) / 128 * 128;
 };
 
 struct G2Args {
@@ -389,15 +395,15 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t base = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t* ring = smem_raw + (base - tc::smem_u32(smem_raw));
-  G2Smem& S = *reinterpret_cast<G2Smem*>(ring + NS * St::kBytes);
+  G2Smem& S = *reinterpret_cast<G2Smem*>(ring + St::kBOff + 2 * St::kB);
   // staged tables start on a 128-byte boundary (16-byte vector stores)
   uint8_t* tabs = ring + St::kTabOff;
   auto stA = [&](int s) { return ring + s * St::kBytes; };
-  auto stB = [&](int s) { return ring + s * St::kBytes + St::kA; };
-  auto stH = [&](int s) { return reinterpret_cast<HT*>(ring + s * St::kBytes + St::kA + St::kB); };
+  auto stH = [&](int s) { return reinterpret_cast<HT*>(ring + s * St::kBytes + St::kA); };
   auto stI = [&](int s) {
-    return reinterpret_cast<int4*>(ring + s * St::kBytes + St::kA + St::kB + St::kH);
+    return reinterpret_cast<int4*>(ring + s * St::kBytes + St::kA + St::kH);
   };
+  auto stB = [&](uint32_t g) { return ring + St::kBOff + (g & 1u) * St::kB; };  // G of K-block g
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_tiles = a.tiles_v * a.tiles_n;
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
           ok = tc::mbar_wait(&S.built[s], ph, a.err, 22, kWait);
           if (!ok) break;
           tc::fence_after_sync();
-          const uint32_t a0 = tc::smem_u32(stA(s)), b0 = tc::smem_u32(stB(s));
+          const uint32_t a0 = tc::smem_u32(stA(s)), b0 = tc::smem_u32(stB(g));
 #pragma unroll
           for (int kk = 0; kk < kBK2 / 16; ++kk)
             tc::mma<false>(d, tc::sw128_desc(a0 + kk * 32), tc::sw128_desc(b0 + kk * 32), a.idesc,
@@ -495,9 +501,10 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
   } else if (warp < 2 + kBld) {
     // builders. Copy phase: thread = 2 items (incidence u, 16 consecutive
     // chains), cp.async of their hidden-pattern bytes into the stage's staging
-    // area one K-block ahead. Build phase: thread = (chain, 8 incidences) x 4,
-    // reads the staged bytes, looks the contributions up and writes 16-byte
-    // chunks of the G tile (row = chain, 128-byte swizzle).
+    // area kAhead K-blocks ahead. Build phase: thread = (4 consecutive chains,
+    // 8 incidences): one record load and one load of the 4 staged patterns
+    // per incidence, 4 table lookups, then one 16-byte chunk of the G tile
+    // (row = chain, 128-byte swizzle) per chain.
     const int bt = threadIdx.x - 64;  // 0 .. 511
     const HT* H = static_cast<const HT*>(a.H);
     auto issue_copies = [&](int s, int jk0, int jk1, int ttn) {
@@ -516,92 +523,133 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
       }
       tc::cp_async_arrive(&S.hready[s]);
     };
-    // flat walk over (tile, K-block) in the producer's order
-    int tile = blockIdx.x, kb = 0;
-    int tn = 0, k0 = 0, k1 = 0, nkb = 0;
-    if (tile < num_tiles) {
-      const int tv = tile / a.tiles_n;
-      tn = tile % a.tiles_n;
-      k0 = __ldg(a.kstart + tv);
-      k1 = __ldg(a.kstart + tv + 1);
-      nkb = __ldg(a.kblocks + tv);
-    }
-    uint32_t g = 0;
-    bool ok = tile < num_tiles;
-    if (ok) {
-      ok = tc::mbar_wait(&S.loaded[0], 0u, a.err, 23, kWait);
-      if (ok) issue_copies(0, k0, k1, tn);
-    }
-    const int chain = bt & (kBN - 1);
-    const int hk = bt / kBN;  // which half of the K-block (32 incidences)
-    while (ok) {
-      const int s = (int)(g % NS);
-      const uint32_t ph = (g / NS) & 1u;
-      // next K-block (possibly of the next tile): records, then its copies
-      int ntile = tile, nkb_i = kb + 1;
-      if (nkb_i >= nkb) {
-        ntile = tile + gridDim.x;
-        nkb_i = 0;
+    // two cursors over (tile, K-block) in the producer's order: copies (cc,
+    // flat index gc) run kAhead K-blocks ahead of the build (cb, flat index g)
+    struct Cursor {
+      int tile, kb, tn, k0, k1, nkb;
+    };
+    auto enter_tile = [&](Cursor& c) {
+      if (c.tile < num_tiles) {
+        const int tv = c.tile / a.tiles_n;
+        c.tn = c.tile % a.tiles_n;
+        c.k0 = __ldg(a.kstart + tv);
+        c.k1 = __ldg(a.kstart + tv + 1);
+        c.nkb = __ldg(a.kblocks + tv);
       }
-      int ntn = tn, nk0 = k0, nk1 = k1, nnkb = nkb;
-      if (ntile < num_tiles) {
-        if (ntile != tile) {
-          const int ntv = ntile / a.tiles_n;
-          ntn = ntile % a.tiles_n;
-          nk0 = __ldg(a.kstart + ntv);
-          nk1 = __ldg(a.kstart + ntv + 1);
-          nnkb = __ldg(a.kblocks + ntv);
-        }
-        const int ns = (int)((g + 1) % NS);
-        const uint32_t nph = ((g + 1) / NS) & 1u;
-        ok = tc::mbar_wait(&S.loaded[ns], nph, a.err, 23, kWait);
+    };
+    auto advance = [&](Cursor& c) {
+      if (++c.kb >= c.nkb) {
+        c.tile += gridDim.x;
+        c.kb = 0;
+        enter_tile(c);
+      }
+    };
+    Cursor cb{(int)blockIdx.x, 0, 0, 0, 0, 0};
+    enter_tile(cb);
+    Cursor cc = cb;
+    uint32_t gc = 0, g = 0;
+    bool ok = true;
+    auto wait_records = [&]() {
+      ok = tc::mbar_wait(&S.loaded[gc % NS], (gc / NS) & 1u, a.err, 23, kWait);
+    };
+    auto copy_next = [&]() {
+      issue_copies((int)(gc % NS), cc.k0 + cc.kb * kBK2, cc.k1, cc.tn);
+      advance(cc);
+      ++gc;
+    };
+    for (int d = 0; d < St::kAhead && ok && cc.tile < num_tiles; ++d) {
+      wait_records();
+      if (ok) copy_next();
+    }
+    const int quad = bt & (kBN / 4 - 1);  // chains 4 quad .. 4 quad + 3
+    const int chunk = bt / (kBN / 4);     // incidences 8 chunk .. 8 chunk + 7
+    // slot r of a thread holds chain 4 quad + off[r]: the rotation by quad / 2
+    // gives the 8 lanes of each store phase 8 different 16-byte bank groups
+    int off[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) off[r] = (r + (quad >> 1)) & 3;
+    while (ok && cb.tile < num_tiles) {
+      // the copies of K-block g + kAhead are issued after this build's proxy
+      // fence, so that the fence does not wait for them to land
+      const bool more = cc.tile < num_tiles;
+      if (more) {
+        wait_records();
         if (!ok) break;
-        issue_copies(ns, nk0 + nkb_i * kBK2, nk1, ntn);
+      } else if (g >= 2) {
+        // no copies left to order it: wait for the MMA that last read this
+        // G buffer (K-block g - 2)
+        ok = tc::mbar_wait(&S.empty[(g - 2) % NS], ((g - 2) / NS) & 1u, a.err, 27, kWait);
+        if (!ok) break;
       }
       // build the current K-block once every builder's copies have landed
-      ok = tc::mbar_wait(&S.hready[s], ph, a.err, 26, kWait);
+      const int s = (int)(g % NS);
+      ok = tc::mbar_wait(&S.hready[s], (g / NS) & 1u, a.err, 26, kWait);
       if (!ok) break;
       {
-        const int jj0 = k0 + kb * kBK2;
+        const int jj0 = cb.k0 + cb.kb * kBK2, k1 = cb.k1;
         const int4* inc = stI(s);
-        const HT* hs = stH(s);
-        uint8_t* rowp = stB(s) + chain * 128;
-        const int e = temp_of(C.g8_off * 8 + tn * kBN + chain, T.n_temps, C.B_total, C.inv_B_total);
+        const HT* hs = stH(s) + 4 * quad;
+        uint8_t* gt = stB(g);
+        int e[4];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-          const int chunk = hk * 4 + ch;
-          uint32_t pk[4];
+        for (int r = 0; r < 4; ++r)
+          e[r] = temp_of(C.g8_off * 8 + cb.tn * kBN + 4 * quad + off[r], T.n_temps, C.B_total,
+                         C.inv_B_total);
+        uint32_t pk[4][4];
+        // FULL: all 64 incidences of the K-block exist (every K-block but a
+        // tile's last), so that the loads of different incidences carry no
+        // branch between them and overlap
+        auto lookups = [&](auto full) {
 #pragma unroll
           for (int u2 = 0; u2 < 4; ++u2) {
-            uint32_t two = 0;
+            uint32_t two[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int hf = 0; hf < 2; ++hf) {
               const int u = chunk * 8 + u2 * 2 + hf;
-              uint32_t v = 0;  // 16-bit pattern of the contribution (0 = +0.0)
-              if (jj0 + u < k1) {
+              if (decltype(full)::value || jj0 + u < k1) {  // else the pattern stays 0 (+0.0)
                 const int4 m = inc[u];
-                const int hp = (int)hs[u * kBN + chain];
-                v = gq[(m.y & 0x7FFFFFFF) + e * m.w + hp * m.z];
+                const int b = m.y & 0x7FFFFFFF;
+                uint32_t hw0, hw1 = 0;  // the 4 chains' hidden patterns
+                if constexpr (sizeof(HT) == 1) {
+                  hw0 = *reinterpret_cast<const uint32_t*>(hs + u * kBN);
+                } else {
+                  const uint2 t2 = *reinterpret_cast<const uint2*>(hs + u * kBN);
+                  hw0 = t2.x;
+                  hw1 = t2.y;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                  uint32_t hp;
+                  if constexpr (sizeof(HT) == 1)
+                    hp = (hw0 >> (8 * off[r])) & 0xFFu;
+                  else
+                    hp = (((off[r] & 2) ? hw1 : hw0) >> (16 * (off[r] & 1))) & 0xFFFFu;
+                  const uint32_t v = gq[b + e[r] * m.w + (int)hp * m.z];
+                  two[r] |= v << (16 * hf);
+                }
               }
-              two |= v << (16 * hf);
             }
-            pk[u2] = two;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) pk[r][u2] = two[r];
           }
-          *reinterpret_cast<uint4*>(rowp + ((chunk ^ (chain & 7)) << 4)) =
-              make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        };
+        if (jj0 + kBK2 <= k1)
+          lookups(std::true_type{});
+        else
+          lookups(std::false_type{});
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int chain = 4 * quad + off[r];
+          *reinterpret_cast<uint4*>(gt + chain * 128 + ((chunk ^ (chain & 7)) << 4)) =
+              make_uint4(pk[r][0], pk[r][1], pk[r][2], pk[r][3]);
         }
         tc::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&S.built[s]);
       }
+      if (more) copy_next();
       ++g;
-      if (ntile >= num_tiles) break;
-      tile = ntile;
-      kb = nkb_i;
-      tn = ntn;
-      k0 = nk0;
-      k1 = nk1;
-      nkb = nnkb;
+      advance(cb);
     }
   } else {
     // epilogue: row = variable; two warps per TMEM lane quarter split the chains
