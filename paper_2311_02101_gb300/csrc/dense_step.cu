@@ -16,12 +16,13 @@
 //                 are sorted by variable, so a tile of 128 variables only
 //                 spans its own incidence range: the product is
 //                 block-diagonal and each tile loops over its own K-blocks.
-//                 TMA loads P^T; 8 builder warps expand the hidden patterns
+//                 TMA loads P^T; 16 builder warps expand the hidden patterns
 //                 into the 128-byte-swizzled G tile in shared memory (table
 //                 lookups, no HBM round trip); one thread issues
-//                 tcgen05.mma kind::f16; 8 epilogue warps draw the new states
-//                 (Eq. 3), update nu (Sec. 4.4) and copy improved states into
-//                 the best-so-far.
+//                 tcgen05.mma kind::f16; 4 epilogue warps (joined by the
+//                 builders on a CTA's last tile) draw the new states (Eq. 3),
+//                 update nu (Sec. 4.4) and copy improved states into the
+//                 best-so-far.
 // State (dense layout): x as FP8 +-1, chains x n_pad (the B operand of the
 // gather); nu float and best x bytes in the same layout.
 #include <cuda.h>
@@ -51,7 +52,7 @@ constexpr int kStage1A = kBM * kBK1, kStage1B = kBN * kBK1;        // 16 KB, 32 
 constexpr int kStage2A = kBM * kBK2 * 2, kStage2B = kBN * kBK2 * 2;  // 16 KB, 32 KB
 constexpr int kEpi1 = 16;  // GEMM1 epilogue warps (4 per TMEM lane quarter)
 constexpr int kBld = 16;   // GEMM2 builder warps (a chain and half a K-block per thread)
-constexpr int kEpi2 = 8;   // GEMM2 epilogue warps (2 per lane quarter)
+constexpr int kEpi2 = 4;   // GEMM2 epilogue warps (1 per lane quarter)
 constexpr long long kWait = 4000000000LL;
 
 __device__ __forceinline__ uint32_t step_index(const uint32_t* tdev, uint32_t t_rel) {
@@ -325,7 +326,23 @@ __global__ void k_keep_dense(const int64_t* __restrict__ cost_part, const float*
   if (b >= C.Bp) return;
   int64_t cs = 0;
   float fs = 0.f;
-  for (int k = 0; k < tiles_m; ++k) {
+  int k = 0;
+  // eight tiles' partials loaded ahead of their sums (the sums stay in tile order)
+  for (; k + 8 <= tiles_m; k += 8) {
+    int64_t cp[8];
+    float fp[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      cp[j] = cost_part[(size_t)(k + j) * C.Bp + b];
+      fp[j] = fe_part[(size_t)(k + j) * C.Bp + b];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      cs += cp[j];
+      fs += fp[j];
+    }
+  }
+  for (; k < tiles_m; ++k) {
     cs += cost_part[(size_t)k * C.Bp + b];
     fs += fe_part[(size_t)k * C.Bp + b];
   }
@@ -439,6 +456,52 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = S.tmem_slot;
+
+  // visible update (Eq. 3, nu of Sec. 4.4, best-keep copy) of 8 chains,
+  // TMEM columns 8 c .. 8 c + 7 of accumulator buf, for the calling warp's
+  // TMEM lane quarter (32 variables) of tile (tv, tn): the accumulators and
+  // state loads first, then the draws and the stores
+  auto visible8 = [&](int tv, int tn, int buf, int c) {
+    const uint32_t tround = step_index(a.tdev, a.t_rel);
+    const float keep = __fsub_rn(1.0f, a.alpha);  // the sparse path's exact FP32 operation sequence
+    uint8_t* __restrict__ Xs = a.X;
+    float* __restrict__ nus = a.nu;
+    uint8_t* __restrict__ bxs = a.best_x;
+    const uint8_t* __restrict__ impv = C.improved;
+    const int quarter = warp & 3;
+    const int i = tv * kBM + quarter * 32 + lane;
+    const bool valid = i < a.n;
+    const int b0 = tn * kBN + c * 8;
+    uint32_t r[8];
+    tc::tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kBN + c * 8), r);
+    uint32_t xo[8];
+    float nv[8];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const size_t o = (size_t)(b0 + q) * a.n_pad + i;
+        xo[q] = Xs[o];
+        nv[q] = nus[o];
+      }
+    }
+    const uint2 imp = *reinterpret_cast<const uint2*>(impv + b0);  // 8 flag bytes
+    const uint4 R = philox4x32_10(
+        make_uint4((uint32_t)i, (uint32_t)(C.g8_off + (b0 >> 3)), tround, kPhaseVisible), C.keys);
+    tc::tmem_ld_wait();
+    if (!valid) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int z = __float2int_rn(__uint_as_float(r[q]));
+      const int qq = max(-T.qmax, min(T.qmax, z));
+      const uint32_t P = pv[qq + T.qmax];
+      const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
+      const size_t o = (size_t)(b0 + q) * a.n_pad + i;
+      if (((q < 4 ? imp.x : imp.y) >> (8 * (q & 3))) & 0xFFu) bxs[o] = xo[q] == a.one ? 1 : 0;
+      nus[o] = __fmaf_rn(keep, nv[q], __fmul_rn(a.alpha, var));
+      Xs[o] = lane16(R, q) < P ? a.one : a.minus_one;
+    }
+  };
+  constexpr int kShare = kEpi2 / 4 + kBld / 4;  // warps per lane quarter on a CTA's last tile
 
   if (warp == 0) {
     // producer warp: P^T tile by TMA and the K-block's incidence records by
@@ -651,64 +714,47 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
       ++g;
       advance(cb);
     }
+    // the visible update of the CTA's last tile, shared with the epilogue
+    // warps (worker kEpi2 / 4 + index among the quarter's builder warps)
+    if (ok && (int)blockIdx.x < num_tiles) {
+      const int nt = (num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x;  // its local index
+      const int lt = (int)blockIdx.x + nt * (int)gridDim.x;
+      tc::mbar_wait(&S.tfull[nt & 1], (uint32_t)(nt >> 1) & 1u, a.err, 28, kWait);
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int c = kEpi2 / 4 + (warp - 2) / 4; c < kBN / 8; c += kShare)
+        visible8(lt / a.tiles_n, lt % a.tiles_n, nt & 1, c);
+    }
   } else {
-    // epilogue: row = variable; two warps per TMEM lane quarter split the chains
-    constexpr int kCols = kBN * 4 / kEpi2;  // 128
-    const int quarter = warp & 3;
+    // epilogue: row = variable. A tile's 32 groups of 8 chains go to the
+    // epilogue warps of each lane quarter; the CTA's last tile is shared with
+    // the builder warps, idle by then (kShare warps per quarter)
     const int ew = warp - 2 - kBld;  // 0 .. kEpi2 - 1
     const int cgrp = ew / 4;
-    const uint32_t tround = step_index(a.tdev, a.t_rel);
-    // nu update with the sparse path's exact FP32 operation sequence
-    const float keep = __fsub_rn(1.0f, a.alpha);
-    uint8_t* __restrict__ Xs = a.X;
-    float* __restrict__ nus = a.nu;
-    uint8_t* __restrict__ bxs = a.best_x;
-    const uint8_t* __restrict__ impv = C.improved;
     int li = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++li) {
       const int tv = tile / a.tiles_n, tn = tile % a.tiles_n;
       const int buf = li & 1;
-      const int i = tv * kBM + quarter * 32 + lane;
-      const bool valid = i < a.n;
+      {
+        // the tile's state rows into L2 while its mainloop runs: thread =
+        // one chain, its 128 variables (one line of x, four of nu; n_pad is
+        // a multiple of 128)
+        for (int ch = ew * 32 + lane; ch < kBN; ch += kEpi2 * 32) {
+          const size_t row = (size_t)(tn * kBN + ch) * a.n_pad + (size_t)tv * kBM;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.X + row));
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.nu + row + 32 * q));
+        }
+      }
       tc::mbar_wait(&S.tfull[buf], (uint32_t)(li >> 1) & 1u, a.err, 25, kWait);
       tc::fence_after_sync();
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) +
-                             (uint32_t)(buf * kBN + cgrp * kCols);
-      // 8 chains (TMEM columns) at a time: their accumulators and state
-      // loads first, then the draws and the stores
+      if (tile + (int)gridDim.x < num_tiles) {
 #pragma unroll 1
-      for (int c8 = 0; c8 < kCols / 8; ++c8) {
-        const int b0 = tn * kBN + cgrp * kCols + c8 * 8;
-        uint32_t r[8];
-        tc::tmem_ld8(taddr + (uint32_t)(c8 * 8), r);
-        uint32_t xo[8];
-        float nv[8];
-        if (valid) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const size_t o = (size_t)(b0 + q) * a.n_pad + i;
-            xo[q] = Xs[o];
-            nv[q] = nus[o];
-          }
-        }
-        const uint2 imp = *reinterpret_cast<const uint2*>(impv + b0);  // 8 flag bytes
-        const uint4 R = philox4x32_10(
-            make_uint4((uint32_t)i, (uint32_t)(C.g8_off + (b0 >> 3)), tround, kPhaseVisible),
-            C.keys);
-        tc::tmem_ld_wait();
-        if (!valid) continue;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int z = __float2int_rn(__uint_as_float(r[q]));
-          const int qq = max(-T.qmax, min(T.qmax, z));
-          const uint32_t P = pv[qq + T.qmax];
-          const float var = __fmul_rn(__uint2float_rn(P * (65536u - P)), 2.3283064365386963e-10f);
-          const size_t o = (size_t)(b0 + q) * a.n_pad + i;
-          if (((q < 4 ? imp.x : imp.y) >> (8 * (q & 3))) & 0xFFu)
-            bxs[o] = xo[q] == a.one ? 1 : 0;
-          nus[o] = __fmaf_rn(keep, nv[q], __fmul_rn(a.alpha, var));
-          Xs[o] = lane16(R, q) < P ? a.one : a.minus_one;
-        }
+        for (int c = cgrp; c < kBN / 8; c += kEpi2 / 4) visible8(tv, tn, buf, c);
+      } else {
+#pragma unroll 1
+        for (int c = cgrp; c < kBN / 8; c += kShare) visible8(tv, tn, buf, c);
       }
       tc::fence_before_sync();
       __syncwarp();
@@ -842,7 +888,7 @@ cudaError_t launch_gemm1_step(bool sample, const CUtensorMap& tmA, const CUtenso
 
 cudaError_t launch_keep_dense(const int64_t* cost_part, const float* fe_part, int tiles_m,
                               const DevChains& C, cudaStream_t st) {
-  k_keep_dense<<<(C.Bp + 255) / 256, 256, 0, st>>>(cost_part, fe_part, tiles_m, C);
+  k_keep_dense<<<(C.Bp + 63) / 64, 64, 0, st>>>(cost_part, fe_part, tiles_m, C);
   return cudaGetLastError();
 }
 
