@@ -629,8 +629,12 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
     // slot r of a thread holds chain 4 quad + off[r]: the rotation by quad / 2
     // gives the 8 lanes of each store phase 8 different 16-byte bank groups
     int off[4];
+    uint32_t sel[4];  // byte permutation that moves slot r's pattern to the low bits
 #pragma unroll
-    for (int r = 0; r < 4; ++r) off[r] = (r + (quad >> 1)) & 3;
+    for (int r = 0; r < 4; ++r) {
+      off[r] = (r + (quad >> 1)) & 3;
+      sel[r] = sizeof(HT) == 1 ? 0x4440u | (uint32_t)off[r] : 0x10u + 0x22u * (uint32_t)off[r];
+    }
     while (ok && cb.tile < num_tiles) {
       // the copies of K-block g + kAhead are issued after this build's proxy
       // fence, so that the fence does not wait for them to land
@@ -658,21 +662,26 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
         for (int r = 0; r < 4; ++r)
           e[r] = temp_of(C.g8_off * 8 + cb.tn * kBN + 4 * quad + off[r], T.n_temps, C.B_total,
                          C.inv_B_total);
+        // the quad's chains of one temperature (all but at most E - 1 quads)
+        const bool same_e = e[1] == e[0] && e[2] == e[0] && e[3] == e[0];
+        const char* gqc = reinterpret_cast<const char*>(gq);
         uint32_t pk[4][4];
         // FULL: all 64 incidences of the K-block exist (every K-block but a
         // tile's last), so that the loads of different incidences carry no
-        // branch between them and overlap
-        auto lookups = [&](auto full) {
+        // branch between them and overlap. UNI: one temperature, so one table
+        // row per incidence serves the four chains.
+        auto lookups = [&](auto full, auto uni) {
 #pragma unroll
           for (int u2 = 0; u2 < 4; ++u2) {
-            uint32_t two[4] = {0u, 0u, 0u, 0u};
+            uint32_t v0[4] = {0u, 0u, 0u, 0u}, v1[4] = {0u, 0u, 0u, 0u};  // 0 = +0.0
 #pragma unroll
             for (int hf = 0; hf < 2; ++hf) {
               const int u = chunk * 8 + u2 * 2 + hf;
-              if (decltype(full)::value || jj0 + u < k1) {  // else the pattern stays 0 (+0.0)
+              if (decltype(full)::value || jj0 + u < k1) {
                 const int4 m = inc[u];
                 const int b = m.y & 0x7FFFFFFF;
-                uint32_t hw0, hw1 = 0;  // the 4 chains' hidden patterns
+                const int z2 = 2 * m.z;  // bytes between hidden patterns
+                uint32_t hw0, hw1 = 0;   // the 4 chains' hidden patterns
                 if constexpr (sizeof(HT) == 1) {
                   hw0 = *reinterpret_cast<const uint32_t*>(hs + u * kBN);
                 } else {
@@ -684,22 +693,34 @@ __global__ void __launch_bounds__(64 + 32 * (kBld + kEpi2), 1)
                 for (int r = 0; r < 4; ++r) {
                   uint32_t hp;
                   if constexpr (sizeof(HT) == 1)
-                    hp = (hw0 >> (8 * off[r])) & 0xFFu;
+                    hp = __byte_perm(hw0, 0u, sel[r]);
                   else
-                    hp = (((off[r] & 2) ? hw1 : hw0) >> (16 * (off[r] & 1))) & 0xFFFFu;
-                  const uint32_t v = gq[b + e[r] * m.w + (int)hp * m.z];
-                  two[r] |= v << (16 * hf);
+                    hp = __byte_perm(hw0, hw1, sel[r]) & 0xFFFFu;
+                  const int row = decltype(uni)::value ? b + e[0] * m.w : b + e[r] * m.w;
+                  const uint32_t v =
+                      *reinterpret_cast<const uint16_t*>(gqc + 2 * row + (int)hp * z2);
+                  if (hf == 0)
+                    v0[r] = v;
+                  else
+                    v1[r] = v;
                 }
               }
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) pk[r][u2] = two[r];
+            for (int r = 0; r < 4; ++r) pk[r][u2] = __byte_perm(v0[r], v1[r], 0x5410u);
           }
         };
-        if (jj0 + kBK2 <= k1)
-          lookups(std::true_type{});
-        else
-          lookups(std::false_type{});
+        if (same_e) {
+          if (jj0 + kBK2 <= k1)
+            lookups(std::true_type{}, std::true_type{});
+          else
+            lookups(std::false_type{}, std::true_type{});
+        } else {
+          if (jj0 + kBK2 <= k1)
+            lookups(std::true_type{}, std::false_type{});
+          else
+            lookups(std::false_type{}, std::false_type{});
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int chain = 4 * quad + off[r];
