@@ -511,6 +511,11 @@ def run_mine(args):
     fp32 = fp32_form_probe(ms, torch, n, off, lits, w, B, stream, sets, seed, args,
                            ms_total / args.steps) if not args.no_fp32 else None
     ragged = ragged_probe(ms, torch, stream, sets, args) if not args.no_ragged else None
+    persistent = persistent_probe(
+        ms, torch, stream,
+        lambda p: ms.maxsat_create(n, off, lits, w, ms.maxsat_default_params(
+            sets=sets, path=ms.MAXSAT_PATH_SPARSE, tune_blocks=1, persistent_round=p), stream),
+        B, m, args)
     up = up_probe(ms, torch, n, off, lits, w, B, stream, sets, args) if not args.no_up else None
     prop = proposal_probe(ms, torch, stream, sets, args) if not args.no_proposal else None
     pt = pt_probe(ms, torch, n, off, lits, w, B, stream, args) if not args.no_pt else None
@@ -542,7 +547,8 @@ def run_mine(args):
                 gpu_launches=launches_timed, dense_eval=dense_eval, paths=paths,
                 best=dict(cost=gbest[0], chain=gbest[1], rounds=args.warmup + 3 + 3 * args.steps,
                           chains=ws * B),
-                fp32_form=fp32, ragged=ragged, unit_prop=up, proposal=prop, tempering=pt,
+                fp32_form=fp32, ragged=ragged, persistent_round=persistent, unit_prop=up,
+                proposal=prop, tempering=pt,
                 configs=configs)
     line["summary"] = summary_of(line)
     ms.maxsat_destroy(ctx)
@@ -984,6 +990,48 @@ def ragged_probe(ms, torch, stream, sets, args):
                           note="host wall clock around all contexts' graph launches")
     if "ms_per_round" in out.get("per_instance", {}):
         out["per_instance_evals_per_s"] = out["per_instance"]["evals_per_s"]
+    # the persistent round on the same batch
+    out["persistent_round"] = persistent_probe(
+        ms, torch, stream,
+        lambda pr: ms.maxsat_create_batch(insts, ms.maxsat_default_params(
+            sets=sets, tune_blocks=1, persistent_round=pr), stream),
+        B, m_tot, args)
+    return out
+
+
+def persistent_probe(ms, torch, stream, make, B, m_tot, args):
+    """The persistent round (one cooperative launch per 100 rounds, grid
+    barriers between the gather and the visible update) against the
+    two-launch round replayed from CUDA graphs of 100 rounds, on contexts of
+    the same formula(s) made by make(persistent_round): K rounds each between
+    one pair of CUDA events after warm-up rounds, state carried in L2 from
+    round to round in both (as the steady-state rate)."""
+    K = 200
+    out = {}
+    for label, p in (("two_launch", 0), ("persistent", 1)):
+        try:
+            ctx = make(p)
+        except ms.MaxsatError as e:
+            return dict(unavailable=str(e))
+        ms.maxsat_reset(ctx, B, 7)
+        active = ms.maxsat_get_persistent_round(ctx)
+        ms.maxsat_step(ctx, 100)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        ms.maxsat_step(ctx, K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_round = a.elapsed_time(b) / K
+        st = ms.maxsat_get_state(ctx)  # reads the device error code of the persistent form
+        out[label] = dict(ms_per_round=ms_round, evals_per_s=m_tot * B / (ms_round / 1e3),
+                          persistent_active=active, clause_block=ms.maxsat_get_clause_block(ctx),
+                          visible_batch=ms.maxsat_get_visible_batch(ctx) if not active else 4,
+                          best_cost_sum=int(np.sum(st["best_cost"])))
+        ms.maxsat_destroy(ctx)
+    out.update(rounds=K, launches_per_100_rounds=dict(two_launch=200, persistent=1),
+               persistent_over_two_launch_time=out["persistent"]["ms_per_round"]
+               / out["two_launch"]["ms_per_round"])
     return out
 
 
@@ -1190,6 +1238,12 @@ def summary_of(line):
     rg = line.get("ragged")
     if rg and "evals_per_s" in rg:
         out["ragged"] = {k: rg[k] for k in ("evals_per_s", "per_instance_evals_per_s") if k in rg}
+    for key, pr in (("persistent", line.get("persistent_round")),
+                    ("ragged_persistent", (rg or {}).get("persistent_round"))):
+        if pr and "persistent" in pr:
+            out[key] = dict(ms=round(pr["persistent"]["ms_per_round"], 4),
+                            two_launch_ms=round(pr["two_launch"]["ms_per_round"], 4),
+                            active=pr["persistent"]["persistent_active"])
     pr = line.get("proposal")
     if pr:
         out["proposal"] = {k: (round(pr[k], 4) if isinstance(pr[k], float) else pr[k])

@@ -123,6 +123,22 @@ typedef struct {
                             the sparse visible update keeps in flight: 2, 4
                             or 8, or 0 for 4 unless tune_blocks measures
                             another. Same results for every value. Default 0 */
+  int32_t persistent_round; /* 1: maxsat_step runs its sparse rounds as one
+                            persistent cooperative launch per
+                            max(1, steps_per_graph) rounds: every block
+                            resident, the gather's and the visible update's
+                            blocks walked by the same CTAs, grid barriers
+                            between the phases (bounded waits: a wait that
+                            gives up after about 2 s makes the next
+                            maxsat_solve / maxsat_get_state fail with
+                            MAXSAT_ECUDA). Only for clauses of at most 3
+                            literals on single-temperature chain octets,
+                            without profiling and while no GPU unit
+                            propagation is pending; otherwise the two-launch
+                            round runs (maxsat_get_persistent_round tells).
+                            Same results bit for bit. Default 0 (two launches
+                            per round with programmatic dependent launch,
+                            replayed from CUDA graphs) */
 } maxsat_params;
 
 typedef struct maxsat_ctx maxsat_ctx;
@@ -197,6 +213,11 @@ int maxsat_get_clause_block(const maxsat_ctx* ctx);
  * keeps in flight together (params.visible_batch, else 4 or measured with
  * params.tune_blocks); a negative code for a NULL context. */
 int maxsat_get_visible_batch(const maxsat_ctx* ctx);
+
+/* 1 when maxsat_step runs the current chains' rounds as persistent launches
+ * (params.persistent_round and the context qualifies), 0 when it runs the
+ * two-launch round; a negative code for a NULL context. */
+int maxsat_get_persistent_round(const maxsat_ctx* ctx);
 
 /* Starts B fresh chains (Fig. code initialisation): every variable drawn
  * uniformly (Bernoulli(0.5)), nu = 0.25, best cost = INT64_MAX, step t = 0. */

@@ -46,7 +46,8 @@ class maxsat_params(ctypes.Structure):
                 ("path", ctypes.c_int32), ("fit_iters", ctypes.c_int32),
                 ("n_sets", ctypes.c_int32), ("sets", ctypes.POINTER(maxsat_rbm_set)),
                 ("steps_per_graph", ctypes.c_int32), ("tune_blocks", ctypes.c_int32),
-                ("up_device", ctypes.c_int32), ("visible_batch", ctypes.c_int32)]
+                ("up_device", ctypes.c_int32), ("visible_batch", ctypes.c_int32),
+                ("persistent_round", ctypes.c_int32)]
 
 
 _lib = None
@@ -71,6 +72,7 @@ def lib():
         L.maxsat_get_n_instances.argtypes = [P]
         L.maxsat_get_clause_block.argtypes = [P]
         L.maxsat_get_visible_batch.argtypes = [P]
+        L.maxsat_get_persistent_round.argtypes = [P]
         L.maxsat_mp_create.argtypes = [ctypes.POINTER(P), i32, u64]
         L.maxsat_mp_n_params.argtypes = [P]
         L.maxsat_mp_set_params.argtypes = [P, P]
@@ -106,7 +108,8 @@ def lib():
         L.maxsat_set_profiling.argtypes = [P, i32]
         L.maxsat_kernel_times.argtypes = [P, i32, P, P, P]
         for name in ["maxsat_create", "maxsat_create_batch", "maxsat_get_n_instances",
-                     "maxsat_get_clause_block", "maxsat_get_visible_batch", "maxsat_up_begin",
+                     "maxsat_get_clause_block", "maxsat_get_visible_batch",
+                     "maxsat_get_persistent_round", "maxsat_up_begin",
                      "maxsat_up_end", "maxsat_up",
                      "maxsat_mp_create", "maxsat_mp_n_params", "maxsat_mp_set_params",
                      "maxsat_mp_get_params", "maxsat_mp_forward", "maxsat_mp_gradient",
@@ -238,6 +241,10 @@ def maxsat_get_clause_block(ctx: Context) -> int:
 
 def maxsat_get_visible_batch(ctx: Context) -> int:
     return int(lib().maxsat_get_visible_batch(ctx.handle))
+
+
+def maxsat_get_persistent_round(ctx: Context) -> int:
+    return int(lib().maxsat_get_persistent_round(ctx.handle))
 
 
 def maxsat_reset(ctx: Context, restarts: int, seed: int):

@@ -224,6 +224,8 @@ struct maxsat_ctx {
   CUtensorMap tmXe[2] = {};
   int ev_buf = 0;                 // state buffer of the next evaluation
   int* d_err = nullptr;           // device wait-timeout code (0 = none)
+  uint32_t* d_bar = nullptr;      // persistent round: grid-barrier arrivals and give-up flag
+  bool persist_ran = false;       // some maxsat_step ran persistent launches (read d_err)
   // dense scatter-add (GEMM2): block-diagonal variable x incidence matrix
   int tiles_v = 0, kmax = 0;
   bool g_bf16 = true;             // G operand BF16 (else FP16)
@@ -518,8 +520,10 @@ int check_device_error(maxsat_ctx* ctx) {
   int code = 0;
   CK(ctx, cudaMemcpy(&code, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (code != 0)
-    return fail(ctx, MAXSAT_ECUDA, "a tensor-core pipeline wait timed out (code " +
-                                       std::to_string(code) + "); results are invalid");
+    return fail(ctx, MAXSAT_ECUDA,
+                std::string(code == 16 ? "a grid barrier of the persistent round"
+                                       : "a tensor-core pipeline wait") +
+                    " timed out (code " + std::to_string(code) + "); results are invalid");
   return MAXSAT_OK;
 }
 
@@ -888,6 +892,7 @@ void maxsat_default_params(maxsat_params* p) {
   p->tune_blocks = 0;
   p->up_device = 1;
   p->visible_batch = 0;
+  p->persistent_round = 0;
 }
 
 const char* maxsat_last_error(const maxsat_ctx* ctx) {
@@ -951,6 +956,8 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   if (prm.visible_batch != 0 && prm.visible_batch != 2 && prm.visible_batch != 4 &&
       prm.visible_batch != 8)
     return fail(nullptr, MAXSAT_EINVAL, "visible_batch must be 0, 2, 4 or 8");
+  if (prm.persistent_round != 0 && prm.persistent_round != 1)
+    return fail(nullptr, MAXSAT_EINVAL, "persistent_round must be 0 or 1");
   if (prm.n_sets < 0 || (prm.n_sets > 0 && !prm.sets)) return fail(nullptr, MAXSAT_EINVAL, "sets is NULL");
 
   if (n_inst > 1 && prm.path == MAXSAT_PATH_DENSE)
@@ -1226,6 +1233,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
   {
     cudaError_t e = A.alloc(&ctx->d_t, 1);
     if (e == cudaSuccess) e = A.alloc(&ctx->d_err, 1);
+    if (e == cudaSuccess) e = A.alloc(&ctx->d_bar, 2);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
       delete ctx;
@@ -1325,6 +1333,20 @@ int maxsat_get_visible_batch(const maxsat_ctx* ctx) {
   return ctx->vis_batch;
 }
 
+// the persistent round runs maxsat_step's rounds: requested, sparse chains
+// that it covers, no per-kernel profiling, no GPU unit propagation pending
+// (its side-stream kernel shares the SMs the cooperative launch must hold)
+static bool persistent_round_active(const maxsat_ctx* ctx) {
+  return ctx->prm.persistent_round && ctx->have_chains && !ctx->dense && !ctx->profiling &&
+         !(ctx->up_pending && ctx->up_on_gpu) &&
+         persistent_round_supported(ctx->T, ctx->C, ctx->F, ctx->wide_h);
+}
+
+int maxsat_get_persistent_round(const maxsat_ctx* ctx) {
+  if (!ctx) return MAXSAT_EINVAL;
+  return persistent_round_active(ctx) ? 1 : 0;
+}
+
 int maxsat_get_n_instances(const maxsat_ctx* ctx) {
   if (!ctx) return MAXSAT_EINVAL;
   return ctx->n_inst;
@@ -1380,6 +1402,20 @@ int maxsat_step(maxsat_ctx* ctx, int64_t steps) {
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_step before maxsat_reset");
   if (steps < 0) return fail(ctx, MAXSAT_EINVAL, "steps must be >= 0");
   if ((uint64_t)ctx->t + (uint64_t)steps > 0xFFFFFFFFull) return fail(ctx, MAXSAT_EINVAL, "round index would exceed 2^32");
+  if (persistent_round_active(ctx)) {
+    const int64_t chunk = std::max(1, ctx->prm.steps_per_graph);
+    while (steps > 0) {
+      const int r = (int)std::min(steps, chunk);
+      CK(ctx, launch_round_persistent(ctx->F, ctx->T, ctx->C, ctx->plan, ctx->t, r,
+                                      (float)ctx->prm.alpha, ctx->d_bar, ctx->d_err,
+                                      ctx->stream));
+      ctx->persist_ran = true;
+      ctx->t += (uint32_t)r;
+      ctx->d_t_synced = false;
+      steps -= r;
+    }
+    return MAXSAT_OK;
+  }
   const int S = ctx->profiling ? 0 : ctx->prm.steps_per_graph;
   while (steps > 0) {
     if (S > 0 && steps >= S) {
@@ -1557,7 +1593,7 @@ int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
     }
   }
   if (best_assign) CK(ctx, cudaStreamSynchronize(ctx->stream));
-  if (ctx->dense) return check_device_error(ctx);
+  if (ctx->dense || ctx->persist_ran) return check_device_error(ctx);
   return MAXSAT_OK;
 }
 
@@ -1622,6 +1658,7 @@ int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
                               K, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   if (t) *t = ctx->t;
+  if (ctx->persist_ran) return check_device_error(ctx);
   return MAXSAT_OK;
 }
 

@@ -295,6 +295,18 @@ cudaError_t launch_gather(GatherMode mode, const DevFormula& F, const DevTables&
 cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevChains& C,
                            float alpha, const uint32_t* tdev, uint32_t t_rel, bool wide_h,
                            cudaStream_t st, int batch = 4);
+// the persistent round (one cooperative launch of `rounds` Gibbs rounds,
+// grid barriers between the phases) covers this context's sparse round:
+// clauses of at most 3 literals, single-temperature octets, byte patterns
+bool persistent_round_supported(const DevTables& T, const DevChains& C, const DevFormula& F,
+                                bool wide_h);
+constexpr int kMaxPersistentRounds = 1 << 16;
+// rounds t0 .. t0 + rounds - 1 (absolute indices); bar: 2 device words,
+// zeroed on st before the launch; err: device error code (16 = a grid
+// barrier wait gave up after about 2 s)
+cudaError_t launch_round_persistent(const DevFormula& F, const DevTables& T, const DevChains& C,
+                                    const GatherPlan& P, uint32_t t0, int rounds, float alpha,
+                                    uint32_t* bar, int* err, cudaStream_t st);
 cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st);
 cudaError_t launch_advance(uint32_t* tdev, uint32_t by, cudaStream_t st);
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t st);

@@ -437,15 +437,26 @@ __device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// A load of chain state: through the read-only path when the state cannot
+// change during the launch, else from the L2 (CG: a persistent launch whose
+// other phase writes it; read-only cache lines could be stale there).
+template <bool CG, typename V>
+__device__ __forceinline__ V ld_state(const V* p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
 // The 8 state bytes of the thread's chains for each literal of clause record
 // r (zero for absent literals; ALL3: every clause has 3 literals).
-template <bool ALL3>
+template <bool ALL3, bool CG>
 __device__ __forceinline__ void load_clause_state(const uint8_t* xtb, int Bp, const int4& r,
                                                   uint2& xa, uint2& xb, uint2& xc) {
   const int len = ALL3 ? 3 : r.w & 3;
-  xa = len > 0 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.x * Bp)) : make_uint2(0u, 0u);
-  xb = len > 1 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.y * Bp)) : make_uint2(0u, 0u);
-  xc = len > 2 ? __ldg(reinterpret_cast<const uint2*>(xtb + (size_t)r.z * Bp)) : make_uint2(0u, 0u);
+  xa = len > 0 ? ld_state<CG>(reinterpret_cast<const uint2*>(xtb + (size_t)r.x * Bp)) : make_uint2(0u, 0u);
+  xb = len > 1 ? ld_state<CG>(reinterpret_cast<const uint2*>(xtb + (size_t)r.y * Bp)) : make_uint2(0u, 0u);
+  xc = len > 2 ? ld_state<CG>(reinterpret_cast<const uint2*>(xtb + (size_t)r.z * Bp)) : make_uint2(0u, 0u);
 }
 
 // Unit H's draw for chain Q of the octet against threshold word w: bit
@@ -487,26 +498,40 @@ __device__ __forceinline__ void octet_draws(uint32_t a_lo, uint32_t a_hi, uint32
 // hidden unit (T.plain3). COST16: a warp's clauses of its block weigh less
 // than 2^16 in total (C.cost16), so chains 2j and 2j + 1 keep their costs in
 // the low and high half of one register.
-template <bool PLAIN3, bool COST16>
-__global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, DevChains C,
-                                                    GatherPlan P, const uint32_t* tdev,
-                                                    uint32_t t_rel, int64_t* cost_part,
-                                                    float* fe_part, int32_t* tickets) {
-  pdl_release();
+// One block of the gather: chain tile bx of gx, clause block by of gy.
+// PERSIST: a block of the persistent round (k_round_persistent), which has
+// staged the record blocks already, orders its phases by grid barriers
+// instead of programmatic dependent launch, and reads the chain state from
+// the L2.
+template <bool PLAIN3, bool COST16, bool PERSIST>
+__device__ __forceinline__ void gather3_block(const DevFormula& F, const DevTables& T,
+                                              const DevChains& C, const GatherPlan& P,
+                                              const uint32_t* tdev, uint32_t t_rel,
+                                              int64_t* cost_part, float* fe_part,
+                                              int32_t* tickets, uint32_t vbx, uint32_t vby,
+                                              uint32_t vgx, uint32_t vgy) {
+  // the launch's own block and grid indices unless the block is virtual
+#define G3_BX (PERSIST ? vbx : blockIdx.x)
+#define G3_BY (PERSIST ? vby : blockIdx.y)
+#define G3_GX (PERSIST ? vgx : gridDim.x)
+#define G3_GY (PERSIST ? vgy : gridDim.y)
+  if constexpr (!PERSIST) pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_cost[8][256];
   __shared__ float s_fe[8][256];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g8 = blockIdx.x * 32 + lane, b0 = g8 * 8;
+  const int g8 = G3_BX * 32 + lane, b0 = g8 * 8;
   const int Bp = C.Bp;
-  const int4 bd = __ldg(P.blk + blockIdx.y);
+  const int4 bd = __ldg(P.blk + G3_BY);
   const int inst = bd.x, c_begin = bd.y, c_end = bd.z, cl_base = bd.w;
   // the record blocks, staged at a 256-byte boundary of the dynamic shared memory
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t tab = (s0 + 255u) & ~255u;
-  stage(smem + (tab - s0), T.rec3, T.rec3_words * 4);
-  __syncthreads();
+  if constexpr (!PERSIST) {
+    stage(smem + (tab - s0), T.rec3, T.rec3_words * 4);
+    __syncthreads();
+  }
   const int E = T.n_temps;
   const int e0 = temp_of(C.g8_off * 8 + b0, E, C.B_total, C.inv_B_total);
   const uint32_t tab_e = tab + (uint32_t)e0 * 256u;  // group 0 at the thread's temperature
@@ -521,12 +546,12 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
     cost[q] = 0;
     fe[q] = 0.f;
   }
-  pdl_wait();  // chain state from here on
+  if constexpr (!PERSIST) pdl_wait();  // chain state from here on
   // bulk L2 prefetches: the blocks of a chain tile split its n state rows
   // (256 bytes each) among themselves; each block fetches its own clause
   // records and weights
-  for (int r = blockIdx.y + (int)gridDim.y * threadIdx.x; r < F.n; r += (int)gridDim.y * 256)
-    l2_prefetch(C.xt + (size_t)r * Bp + blockIdx.x * 256, 256);
+  for (int r = G3_BY + (int)G3_GY * threadIdx.x; r < F.n; r += (int)G3_GY * 256)
+    l2_prefetch(C.xt + (size_t)r * Bp + G3_BX * 256, 256);
   if (threadIdx.x == 0 && c_end > c_begin) {
     l2_prefetch(F.cl4 + c_begin, (uint32_t)(c_end - c_begin) * 16u);
     const uintptr_t w0 = reinterpret_cast<uintptr_t>(F.cl_w + c_begin) & ~(uintptr_t)15;
@@ -561,14 +586,14 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   uint32_t info = (uint32_t)rec_n.w;
   int32_t wc = 0;
   if (c0 < c_end) wc = (int32_t)__ldg(F.cl_w + c0);
-  load_clause_state<PLAIN3>(xtb, Bp, rec_n, xa, xb, xc);
+  load_clause_state<PLAIN3, PERSIST>(xtb, Bp, rec_n, xa, xb, xc);
   if (c0 + 8 < c_end) rec_n = __ldg(F.cl4 + c0 + 8);
   for (int c = c0; c < c_end; c += 8) {
     uint2 na = make_uint2(0u, 0u), nb = na, nc = na;
     const uint32_t ninfo = (uint32_t)rec_n.w;
     int32_t nwc = 0;
     if (c + 8 < c_end) {
-      load_clause_state<PLAIN3>(xtb, Bp, rec_n, na, nb, nc);
+      load_clause_state<PLAIN3, PERSIST>(xtb, Bp, rec_n, na, nb, nc);
       nwc = (int32_t)__ldg(F.cl_w + c + 8);
     }
     if (c + 16 < c_end) rec_n = __ldg(F.cl4 + c + 16);
@@ -657,18 +682,18 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
     tc += reinterpret_cast<const int32_t*>(&s_cost[0][0])[w * 256 + tid];
     tf += s_fe[w][tid];
   }
-  const size_t out = (size_t)blockIdx.y * Bp + (size_t)blockIdx.x * 256 + tid;
+  const size_t out = (size_t)G3_BY * Bp + (size_t)G3_BX * 256 + tid;
   cost_part[out] = tc;
   fe_part[out] = tf;
   __threadfence();
   __syncthreads();
   const int k0 = __ldg(P.inst_blk + inst), k1 = __ldg(P.inst_blk + inst + 1);
-  int32_t* ticket = tickets + inst * gridDim.x + blockIdx.x;
+  int32_t* ticket = tickets + inst * G3_GX + G3_BX;
   if (tid == 0) s_last = atomicAdd(ticket, 1) == k1 - k0 - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const int b = blockIdx.x * 256 + tid;
+  const int b = G3_BX * 256 + tid;
   int64_t csum = 0;
   float fsum = 0.f;
   for (int k = k0; k < k1; ++k) {
@@ -678,16 +703,33 @@ __global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, D
   const size_t ib = (size_t)inst * Bp + b;
   C.cost[ib] = csum;
   C.fe[ib] = fsum;
-  const bool imp = csum < C.best[ib];
+  const bool imp = csum < (PERSIST ? __ldcg(C.best + ib) : C.best[ib]);
   if (imp) C.best[ib] = csum;
   C.improved[ib] = imp ? 1 : 0;
   if (tid == 0) *ticket = 0;
+#undef G3_BX
+#undef G3_BY
+#undef G3_GX
+#undef G3_GY
 }
 
+template <bool PLAIN3, bool COST16>
+__global__ void __launch_bounds__(256, 2) k_gather3(DevFormula F, DevTables T, DevChains C,
+                                                    GatherPlan P, const uint32_t* tdev,
+                                                    uint32_t t_rel, int64_t* cost_part,
+                                                    float* fe_part, int32_t* tickets) {
+  gather3_block<PLAIN3, COST16, false>(F, T, C, P, tdev, t_rel, cost_part, fe_part, tickets,
+                                       blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+// CG: the improved flags come from the L2 (a persistent launch: another
+// block wrote them in this launch)
+template <bool CG = false>
 __device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size_t o, int b0,
                                               uint64_t xold) {
-  const uint64_t imp =
-      *reinterpret_cast<const uint64_t*>(C.improved + (size_t)inst * C.Bp + b0);
+  const unsigned long long* fl =
+      reinterpret_cast<const unsigned long long*>(C.improved + (size_t)inst * C.Bp + b0);
+  const uint64_t imp = CG ? __ldcg(fl) : *fl;
   if (imp) {
     const uint64_t mask = imp * 0xFFull;  // 0x01 flags -> 0xFF byte masks
     uint64_t* bx = reinterpret_cast<uint64_t*>(C.best_xt + o);
@@ -698,11 +740,12 @@ __device__ __forceinline__ void keep_improved(const DevChains& C, int inst, size
 // The end of a visible update for one variable and 8 chains given their
 // integer logits z (units 2^-Q): best-so-far copy of improved chains, the
 // visible draws x ~ Bernoulli(P[z]) (Eq. 3) and nu (Sec. 4.4).
+template <bool CG = false>
 __device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains& C,
                                              const uint32_t* pv, float alpha, uint32_t t,
                                              int2 vi, int g8, size_t o, int b0, uint64_t xold,
                                              float4 n0, float4 n1, const int (&z)[8]) {
-  keep_improved(C, vi.x, o, b0, xold);
+  keep_improved<CG>(C, vi.x, o, b0, xold);
   const uint4 r =
       philox4x32_10(make_uint4((uint32_t)vi.y, (uint32_t)(g8 + C.g8_off), t,
                                kPhaseVisible | ((uint32_t)vi.x << 8)),
@@ -730,39 +773,41 @@ __device__ __forceinline__ void visible_tail(const DevTables& T, const DevChains
 // BATCH: incidences whose pattern loads are in flight together (a divisor
 // of 32; the launch picks it, measured by the block tuner). Batch 8 runs 3
 // blocks per SM (its loads need more than 64 registers), the others 4.
-template <bool SM, typename HT, int BATCH>
-__global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula F, DevTables T, DevChains C,
-                                                 float alpha, const uint32_t* tdev,
-                                                 uint32_t t_rel, int v0, int tile_major) {
+// One block of the visible update: chain tile `tile`, variable group
+// `vgroup` (8 variables, one per warp). With SM the tables are staged at
+// byte vis_off of the dynamic shared memory. PERSIST: a block of the
+// persistent round (k_round_persistent), which has staged the tables already,
+// orders its phases by grid barriers and reads the hidden patterns from the
+// L2.
+template <bool SM, typename HT, int BATCH, bool PERSIST>
+__device__ __forceinline__ void visible_block(const DevFormula& F, const DevTables& T,
+                                              const DevChains& C, float alpha,
+                                              const uint32_t* tdev, uint32_t t_rel, int tile,
+                                              int vgroup, int vis_off) {
   static_assert(32 % BATCH == 0, "incidence windows hold whole batches");
-  pdl_release();
+  if constexpr (!PERSIST) pdl_release();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_inc[8][32];  // per warp: a window of its variable's incidences
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // tile_major: blocks walk every variable group of one chain tile before the
-  // next tile (x = variable group, y = chain tile from v0), so a tile's hidden
-  // patterns, m x 256 entries, stay in the L2 while its variables pull them
-  // (taken when all of them would not fit). Otherwise x = chain tile, y =
-  // variable group from v0.
-  const int tile = tile_major ? v0 + (int)blockIdx.y : (int)blockIdx.x;
-  const int vgroup = tile_major ? (int)blockIdx.x : v0 + (int)blockIdx.y;
   const int g8 = tile * 32 + lane, b0 = g8 * 8;
   const int16_t* gq = T.gq;
   const uint32_t* pv = T.pv;
   if (SM) {
     const int gb = align16(T.gq_len * 4);  // both halves
-    stage(smem, T.gq, gb);
-    stage(smem + gb, T.pv, align16(T.pv_len * 4));
-    __syncthreads();
-    gq = reinterpret_cast<const int16_t*>(smem);
-    pv = reinterpret_cast<const uint32_t*>(smem + gb);
+    if constexpr (!PERSIST) {
+      stage(smem + vis_off, T.gq, gb);
+      stage(smem + vis_off + gb, T.pv, align16(T.pv_len * 4));
+      __syncthreads();
+    }
+    gq = reinterpret_cast<const int16_t*>(smem + vis_off);
+    pv = reinterpret_cast<const uint32_t*>(smem + vis_off + gb);
   }
   // variables in descending degree: a block's 8 warps carry similar work
   const int slot = vgroup * 8 + warp;
   if (slot >= F.n) return;
   const int i = F.var_order ? __ldg(F.var_order + slot) : slot;
   const int2 vi = var_instance(F, i);
-  pdl_wait();  // chain state from here on
+  if constexpr (!PERSIST) pdl_wait();  // chain state from here on
   const uint32_t t = step_index(tdev, t_rel);
   const int gb0 = C.g8_off * 8 + b0;  // global chain index
   const int e0 = temp_of(gb0, T.n_temps, C.B_total, C.inv_B_total);
@@ -804,7 +849,7 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
 #pragma unroll
       for (int u = 0; u < BATCH; ++u)
         if (jj + u < j_end)
-          v[u] = __ldg(reinterpret_cast<const HV*>(H + (size_t)s_inc[warp][w + u].x * C.Bp + b0));
+          v[u] = ld_state<PERSIST>(reinterpret_cast<const HV*>(H + (size_t)s_inc[warp][w + u].x * C.Bp + b0));
 #pragma unroll
       for (int u = 0; u < BATCH; ++u) {
         if (jj + u >= j_end) break;
@@ -846,7 +891,111 @@ __global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula 
     sums(std::true_type{});
   else
     sums(std::false_type{});
-  visible_tail(T, C, pv, alpha, t, vi, g8, o, b0, xold, n0, n1, z);
+  visible_tail<PERSIST>(T, C, pv, alpha, t, vi, g8, o, b0, xold, n0, n1, z);
+}
+
+template <bool SM, typename HT, int BATCH>
+__global__ void __launch_bounds__(256, BATCH >= 8 ? 3 : 4) k_visible(DevFormula F, DevTables T, DevChains C,
+                                                 float alpha, const uint32_t* tdev,
+                                                 uint32_t t_rel, int v0, int tile_major) {
+  // tile_major: blocks walk every variable group of one chain tile before the
+  // next tile (x = variable group, y = chain tile from v0), so a tile's hidden
+  // patterns, m x 256 entries, stay in the L2 while its variables pull them
+  // (taken when all of them would not fit). Otherwise x = chain tile, y =
+  // variable group from v0.
+  const int tile = tile_major ? v0 + (int)blockIdx.y : (int)blockIdx.x;
+  const int vgroup = tile_major ? (int)blockIdx.x : v0 + (int)blockIdx.y;
+  visible_block<SM, HT, BATCH, false>(F, T, C, alpha, tdev, t_rel, tile, vgroup, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent round: `rounds` Gibbs rounds in one cooperative launch. Every
+// block walks the virtual blocks of the gather (chain tile fastest, as the
+// gather's grid), meets the other blocks at a grid barrier, walks the
+// virtual blocks of the visible update (the visible launch's order), and
+// meets them again before the next round. The blocks are the same as the
+// two-launch round's, so states, costs, draws and free energies are the
+// same bit for bit. Clauses of at most 3 literals on single-temperature
+// octets, byte hidden patterns, tables in shared memory (the k_gather3 and
+// k_visible<true, uint8_t, 4> case); the host checks this.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kErrGridBarrier = 16;                    // device error code of a barrier timeout
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier of a cooperative launch (every block resident): bar[0] counts
+// arrivals over the launch (zeroed before it), bar[1] is set when some block
+// gave up waiting. A wait gives up after about 2 s, records kErrGridBarrier
+// in *err and sets bar[1]; every block then leaves at its next barrier, so
+// the launch ends and the host reads the code. Returns false when the block
+// must leave.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, uint32_t& target, int* err) {
+  __shared__ int s_go;
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int go = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(bar) < target) {
+      if (ld_acquire_gpu(bar + 1) != 0u) {
+        go = 0;
+        break;
+      }
+      if (clock64() - t0 > kBarrierWaitCycles) {
+        atomicCAS(err, 0, kErrGridBarrier);
+        atomicExch(bar + 1, 1u);
+        go = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_go = go;
+  }
+  __syncthreads();
+  return s_go != 0;
+}
+
+template <bool PLAIN3, bool COST16>
+__global__ void __launch_bounds__(256, 2)
+    k_round_persistent(DevFormula F, DevTables T, DevChains C, GatherPlan P, uint32_t t0,
+                       int rounds, float alpha, int tile_major, int vis_off, uint32_t* bar,
+                       int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // both kernels' tables, once: the gather's record blocks at the first
+  // 256-byte boundary, the visible update's tables at vis_off
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t tab = (s0 + 255u) & ~255u;
+  stage(smem + (tab - s0), T.rec3, T.rec3_words * 4);
+  const int gb = align16(T.gq_len * 4);
+  stage(smem + vis_off, T.gq, gb);
+  stage(smem + vis_off + gb, T.pv, align16(T.pv_len * 4));
+  __syncthreads();
+  const uint32_t tiles = (uint32_t)(C.Bp / kChainTile);
+  const uint32_t n_blk = (uint32_t)P.n_blk;
+  const uint32_t groups = (uint32_t)((F.n + 7) / 8);
+  const uint32_t n_gather = tiles * n_blk, n_visible = tiles * groups;
+  uint32_t target = 0;
+  for (int r = 0; r < rounds; ++r) {
+    const uint32_t t = t0 + (uint32_t)r;
+    for (uint32_t vb = blockIdx.x; vb < n_gather; vb += gridDim.x)
+      gather3_block<PLAIN3, COST16, true>(F, T, C, P, nullptr, t, C.cost_part, C.fe_part,
+                                          C.tickets, vb % tiles, vb / tiles, tiles, n_blk);
+    if (!grid_barrier(bar, target, err)) return;
+    for (uint32_t vb = blockIdx.x; vb < n_visible; vb += gridDim.x) {
+      const int tile = (int)(tile_major ? vb / groups : vb % tiles);
+      const int vgroup = (int)(tile_major ? vb % groups : vb / tiles);
+      visible_block<true, uint8_t, 4, true>(F, T, C, alpha, nullptr, t, tile, vgroup, vis_off);
+    }
+    if (!grid_barrier(bar, target, err)) return;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_keep_copy(DevFormula F, DevChains C, int n, int vg0) {
@@ -1133,6 +1282,51 @@ cudaError_t launch_visible(const DevFormula& F, const DevTables& T, const DevCha
   if (use_sm) return visible_variant<true, uint16_t>(grid, sm, st, F, T, C, alpha, tdev, t_rel, batch);
   if (!wide) return visible_variant<false, uint8_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel, batch);
   return visible_variant<false, uint16_t>(grid, 0, st, F, T, C, alpha, tdev, t_rel, batch);
+}
+
+bool persistent_round_supported(const DevTables& T, const DevChains& C, const DevFormula& F,
+                                bool wide) {
+  return !wide && T.one_chunk && T.rec3 && F.cl4 && C.cost32 && octets_single_temperature(T, C) &&
+         gather_smem_bytes(T) <= kSmemLimit && visible_smem_bytes(T) <= kSmemLimit;
+}
+
+cudaError_t launch_round_persistent(const DevFormula& F, const DevTables& T, const DevChains& C,
+                                    const GatherPlan& P, uint32_t t0, int rounds, float alpha,
+                                    uint32_t* bar, int* err, cudaStream_t st) {
+  if (rounds < 1 || rounds > kMaxPersistentRounds) return cudaErrorInvalidValue;
+  auto kern = T.plain3 ? (C.cost16 ? k_round_persistent<true, true> : k_round_persistent<true, false>)
+                       : (C.cost16 ? k_round_persistent<false, true> : k_round_persistent<false, false>);
+  const int vis_off = align16(gather3_smem_bytes(T));
+  const int smem = vis_off + visible_smem_bytes(T);
+  cudaError_t e = allow_dynamic_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0, l2 = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // every block resident (cooperative launch); never more blocks than either
+  // phase has virtual blocks
+  const long long tiles = C.Bp / kChainTile;
+  const long long work = std::max(tiles * P.n_blk, tiles * ((F.n + 7) / 8));
+  const int grid = (int)std::min<long long>((long long)per_sm * sms, std::max(work, 1LL));
+  // tile-major visible order when the hidden patterns exceed half the L2 (as
+  // the two-launch round)
+  const int tm = (double)F.m * C.Bp > 0.5 * (double)l2 ? 1 : 0;
+  if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, F, T, C, P, t0, rounds, alpha, tm, vis_off, bar, err);
 }
 
 cudaError_t launch_keep_copy(const DevFormula& F, const DevChains& C, int n, cudaStream_t st) {

@@ -65,10 +65,11 @@ def inst_of(gen):
 
 
 def make_ctx(ms, stream, inst, table, n_temps=2, n_buckets=1, alpha=0.01, spg=0, path=0,
-             tune=0, up_device=1, vb=0):
+             tune=0, up_device=1, vb=0, persist=0):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=n_temps, n_buckets=n_buckets,
                                       alpha=alpha, steps_per_graph=spg, path=path,
-                                      tune_blocks=tune, up_device=up_device, visible_batch=vb)
+                                      tune_blocks=tune, up_device=up_device, visible_batch=vb,
+                                      persistent_round=persist)
     params.fstar = None
     return ms.maxsat_create(inst.n, inst.off, inst.lits, inst.w, params, stream)
 
@@ -545,9 +546,11 @@ def small_batch(seed=3):
     return insts
 
 
-def batch_ctx(ms, stream, insts, table, n_buckets=4, alpha=0.01, up_device=1):
+def batch_ctx(ms, stream, insts, table, n_buckets=4, alpha=0.01, up_device=1, persist=0,
+              spg=100):
     params = ms.maxsat_default_params(sets=table.sets, n_temps=2, n_buckets=n_buckets,
-                                      alpha=alpha, up_device=up_device)
+                                      alpha=alpha, up_device=up_device,
+                                      persistent_round=persist, steps_per_graph=spg)
     params.fstar = None
     return ms.maxsat_create_batch(insts, params, stream)
 
@@ -859,3 +862,107 @@ def test_parallel_tempering_rejects_bad_ensembles(ms, stream, table4):
         ms.maxsat_pt_swap(ctx, 0)
     assert e.value.code == ms.MAXSAT_EINVAL
     ms.maxsat_destroy(ctx)
+
+
+# --------------------------------------------------------------------------
+# Persistent round (params.persistent_round): one cooperative launch of
+# several rounds, grid barriers between the gather and the visible update
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["3sat", "edge", "heavy"])
+def test_persistent_round_matches_oracle(ms, stream, small_table, case):
+    """3-literal formulas, clauses of 0..3 literals with duplicates and a
+    tautology, and heavy weights (one 32-bit cost per chain) each take the
+    persistent round; 30 rounds in launches of 7 (a ragged last launch)
+    follow the oracle's trajectory."""
+    inst = {"3sat": lambda: inst_of(workloads.random_ksat(50, 215, 3, seed=0)),
+            "edge": lambda: edge_instance(1, 3),
+            "heavy": lambda: edge_instance(2, 3, wmax=30000)}[case]()
+    T, seed, B = 30, 11, 256
+    ctx = make_ctx(ms, stream, inst, small_table, alpha=0.05, spg=7, persist=1)
+    ms.maxsat_reset(ctx, B, seed)
+    assert ms.maxsat_get_persistent_round(ctx) == 1
+    ms.maxsat_step(ctx, 12)
+    ms.maxsat_step(ctx, T - 12)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    assert gpu["t"] == T
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed, alpha=0.05), T, 0.05)
+
+
+def test_persistent_round_falls_back_where_it_does_not_apply(ms, stream, small_table):
+    """4-literal clauses (multi-chunk tables) and octets that straddle a
+    temperature block (B = 300) keep the two-launch round, with the same
+    results."""
+    inst = edge_instance(1, 4)
+    ctx = make_ctx(ms, stream, inst, small_table, persist=1)
+    ms.maxsat_reset(ctx, 256, 3)
+    assert ms.maxsat_get_persistent_round(ctx) == 0
+    ms.maxsat_destroy(ctx)
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    T, seed, B = 10, 4, 300
+    ctx = make_ctx(ms, stream, inst, small_table, spg=4, persist=1)
+    ms.maxsat_reset(ctx, B, seed)
+    assert ms.maxsat_get_persistent_round(ctx) == 0
+    ms.maxsat_step(ctx, T)
+    gpu = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    assert_same(gpu, run_oracle(inst, small_table, B, T, seed), T, 0.01)
+
+
+def test_persistent_batch_matches_oracle(ms, stream, golden_table):
+    """The 11-formula batch (one formula without clauses, one with an empty
+    clause and a tautology) at B = 256: every formula follows the oracle
+    run alone with its batch index."""
+    insts = small_batch()
+    T, seed, B = 9, 17, 256
+    ctx = batch_ctx(ms, stream, insts, golden_table, persist=1, spg=4)
+    ms.maxsat_reset(ctx, B, seed)
+    assert ms.maxsat_get_persistent_round(ctx) == 1
+    ms.maxsat_step(ctx, T)
+    g = ms.maxsat_get_state(ctx)
+    vb = ctx.var_base
+    for k, (n, off, lits, w) in enumerate(insts):
+        inst = oracle.Instance(n, off, lits, w)
+        st = oracle.init_chains(n, B, seed, instance=k)
+        oracle.gibbs(inst, golden_table, st, T, seed, n_temps=2, n_buckets=4,
+                     threads=os.cpu_count() or 4)
+        sl = slice(int(vb[k]), int(vb[k + 1]))
+        assert np.array_equal(g["x"][:, sl], st.x), k
+        assert np.array_equal(g["best_x"][:, sl], st.best_x), k
+        assert np.array_equal(g["best_cost"][k], st.best_cost), k
+        assert np.array_equal(g["cost"][k], st.cost), k
+        np.testing.assert_allclose(g["free_energy"][k], st.free_energy, rtol=1e-3, atol=1e-6)
+        assert np.array_equal(g["nu"][:, sl], st.nu32), k
+    ms.maxsat_destroy(ctx)
+
+
+def _state_of_rounds(ms, stream, make, B, T, seed, chunks):
+    ctx = make()
+    ms.maxsat_reset(ctx, B, seed)
+    persistent = ms.maxsat_get_persistent_round(ctx)
+    for c in chunks:
+        ms.maxsat_step(ctx, c)
+    g = ms.maxsat_get_state(ctx)
+    ms.maxsat_destroy(ctx)
+    return persistent, g
+
+
+@pytest.mark.parametrize("workload", ["w3sat-n1000-m6000", "ragged-512"])
+def test_persistent_equals_two_launch_full_size(ms, stream, golden_table, workload):
+    """At full size, in the launch configurations the bench times (weighted
+    3-SAT n = 1000, m = 6000, 4096 chains; 512 formulas of 256 chains each),
+    the persistent round and the graph-replayed two-launch round give the
+    same states, costs, best-so-far, nu and free energies, bit for bit."""
+    spec = workloads.WORKLOADS[workload]
+    B, T, seed = spec["B"], 7, 5
+    if spec.get("batch"):
+        insts = spec["gen"](0)
+        make = lambda p: batch_ctx(ms, stream, insts, golden_table, persist=p, spg=3)
+    else:
+        inst = inst_of(spec["gen"](0))
+        make = lambda p: make_ctx(ms, stream, inst, golden_table, n_buckets=4, spg=3, persist=p)
+    p0, two = _state_of_rounds(ms, stream, lambda: make(0), B, T, seed, (T,))
+    p1, per = _state_of_rounds(ms, stream, lambda: make(1), B, T, seed, (2, T - 2))
+    assert (p0, p1) == (0, 1)
+    for k in ["x", "best_cost", "best_x", "cost", "free_energy", "nu"]:
+        assert np.array_equal(two[k], per[k]), k
