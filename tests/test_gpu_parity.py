@@ -611,7 +611,9 @@ def test_batch_eval_and_solve_match_oracle(ms, stream, golden_table):
 
 def test_batch_full_size_sampled(ms, stream, golden_table):
     """512 formulas, n log-uniform in [100, 5000], m / n in [4, 8], B = 256:
-    three formulas (first, middle, last) recomputed by the oracle."""
+    the first, middle and last formulas, the smallest and the largest, and
+    the ones with the lowest and highest clause ratio recomputed by the
+    oracle."""
     insts = workloads.ragged_batch(seed=0)
     B, T, seed = 256, 4, 23
     ctx = batch_ctx(ms, stream, insts, golden_table)
@@ -619,7 +621,11 @@ def test_batch_full_size_sampled(ms, stream, golden_table):
     ms.maxsat_step(ctx, T)
     g = ms.maxsat_get_state(ctx)
     vb = ctx.var_base
-    for k in (0, 255, 511):
+    ns = np.array([i[0] for i in insts])
+    ratio = np.array([(len(i[1]) - 1) / i[0] for i in insts])
+    picks = sorted({0, 255, 511, int(np.argmin(ns)), int(np.argmax(ns)), int(np.argmin(ratio)),
+                    int(np.argmax(ratio))})
+    for k in picks:
         n, off, lits, w = insts[k]
         inst = oracle.Instance(n, off, lits, w)
         st = oracle.init_chains(n, B, seed, instance=k)
