@@ -9,6 +9,7 @@
 // `steps_per_graph` rounds (the paper dispatches 500 rounds at a time,
 // appendix "Batching operations").
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -30,6 +31,16 @@ using namespace rbmsat;
 namespace {
 
 thread_local std::string g_create_error;
+
+// An NVTX range over a scope (entry points and kernel launches), so that a
+// profiler's timeline (ncu --nvtx, Nsight Systems) groups the work by call;
+// without an attached tool each push and pop is a no-op call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device blocks freed by contexts, kept per device for later contexts:
 // cudaMalloc and cudaFree take tens of microseconds each (and cudaFree waits
@@ -303,6 +314,7 @@ int32_t weight_bucket(int64_t w, int64_t wmin, int32_t J) {
 // Launches `body` on `st`, bracketed by CUDA events when profiling.
 template <class Fn>
 int timed(maxsat_ctx* ctx, cudaStream_t st, const char* name, Fn body) {
+  NvtxRange range(name);
   if (!ctx->profiling) {
     const cudaError_t e = body();
     if (e != cudaSuccess) return cuda_fail(ctx, e, name);
@@ -1273,6 +1285,7 @@ static int create_impl(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* of
 int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
                   const int32_t* lits, const int64_t* weights, const maxsat_params* params,
                   void* cuda_stream) {
+  NvtxRange range("maxsat_create");
   g_create_error.clear();
   if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
   *out = nullptr;
@@ -1284,6 +1297,7 @@ int maxsat_create(maxsat_ctx** out, int32_t n, int64_t m, const int64_t* off,
 int maxsat_create_batch(maxsat_ctx** out, int32_t n_inst, const int32_t* n_vars,
                         const int64_t* n_clauses, const int64_t* clause_off, const int32_t* lits,
                         const int64_t* weights, const maxsat_params* params, void* cuda_stream) {
+  NvtxRange range("maxsat_create_batch");
   g_create_error.clear();
   if (!out) return fail(nullptr, MAXSAT_EINVAL, "out is NULL");
   *out = nullptr;
@@ -1358,6 +1372,7 @@ int maxsat_reset(maxsat_ctx* ctx, int32_t B, uint64_t seed) {
 
 int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_offset,
                        int32_t total_chains) {
+  NvtxRange range("maxsat_reset_shard");
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 1 || B > (1 << 26)) return fail(ctx, MAXSAT_EINVAL, "restarts must be in 1..2^26");
   if (chain_offset < 0 || chain_offset % 8 != 0 || total_chains < chain_offset + B ||
@@ -1398,6 +1413,7 @@ int maxsat_reset_shard(maxsat_ctx* ctx, int32_t B, uint64_t seed, int32_t chain_
 }
 
 int maxsat_step(maxsat_ctx* ctx, int64_t steps) {
+  NvtxRange range("maxsat_step");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_step before maxsat_reset");
   if (steps < 0) return fail(ctx, MAXSAT_EINVAL, "steps must be >= 0");
@@ -1442,6 +1458,7 @@ int maxsat_step(maxsat_ctx* ctx, int64_t steps) {
 }
 
 int maxsat_score(maxsat_ctx* ctx) {
+  NvtxRange range("maxsat_score");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_score before maxsat_reset");
   const DevChains& C = ctx->C;
@@ -1522,6 +1539,7 @@ static int ensure_eval_scratch(maxsat_ctx* ctx, int Bp) {
 }
 
 int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* cost_dev) {
+  NvtxRange range("maxsat_eval");
   if (!ctx) return MAXSAT_EINVAL;
   if (B < 0 || (B > 0 && (!assign_dev || !cost_dev))) return fail(ctx, MAXSAT_EINVAL, "bad eval arguments");
   if (B == 0) return MAXSAT_OK;
@@ -1565,6 +1583,7 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
 
 int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
                  uint8_t* best_assign, int64_t* best_cost) {
+  NvtxRange range("maxsat_solve");
   if (!ctx) return MAXSAT_EINVAL;
   int rc = maxsat_reset(ctx, B, seed);
   if (rc == MAXSAT_OK) rc = maxsat_step(ctx, steps);
@@ -1599,6 +1618,7 @@ int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
 
 int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
                      uint8_t* best_x, int64_t* cost, float* free_energy, uint32_t* t) {
+  NvtxRange range("maxsat_get_state");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "no chains (call maxsat_reset)");
   const int B = ctx->C.B, Bp = ctx->C.Bp, n = ctx->n;
@@ -1665,6 +1685,7 @@ int maxsat_get_state(maxsat_ctx* ctx, uint8_t* x, float* nu, int64_t* best_cost,
 int maxsat_set_state(maxsat_ctx* ctx, int32_t B, uint64_t seed, const uint8_t* x,
                      const float* nu, const int64_t* best_cost, const uint8_t* best_x,
                      uint32_t t) {
+  NvtxRange range("maxsat_set_state");
   if (!ctx) return MAXSAT_EINVAL;
   if (!x || !nu || !best_cost || !best_x) return fail(ctx, MAXSAT_EINVAL, "set_state needs x, nu, best_cost, best_x");
   int rc = maxsat_reset(ctx, B, seed);  // allocates and fills the padding chains
@@ -1808,6 +1829,7 @@ static int merge_candidates(maxsat_ctx* ctx, std::vector<uint8_t>& cand) {
 }
 
 int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau) {
+  NvtxRange range("maxsat_propose_flips");
   if (!ctx || !prob) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_propose_flips before maxsat_reset");
   if (ctx->n_inst != 1 && ctx->dense)
@@ -1846,6 +1868,7 @@ int maxsat_propose_flips(maxsat_ctx* ctx, const float* prob, float tau) {
 }
 
 int maxsat_pt_swap(maxsat_ctx* ctx, int32_t parity, int32_t* accepted) {
+  NvtxRange range("maxsat_pt_swap");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_pt_swap before maxsat_reset");
   if (parity != 0 && parity != 1) return fail(ctx, MAXSAT_EINVAL, "parity must be 0 or 1");
@@ -2008,6 +2031,7 @@ static int up_end_gpu(maxsat_ctx* ctx) {
 }
 
 int maxsat_up_begin(maxsat_ctx* ctx) {
+  NvtxRange range("maxsat_up_begin");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->have_chains) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_begin before maxsat_reset");
   const bool gpu = ctx->prm.up_device && gpu_merge_form(ctx);
@@ -2035,6 +2059,7 @@ int maxsat_up_begin(maxsat_ctx* ctx) {
 }
 
 int maxsat_up_end(maxsat_ctx* ctx) {
+  NvtxRange range("maxsat_up_end");
   if (!ctx) return MAXSAT_EINVAL;
   if (!ctx->up_pending) return fail(ctx, MAXSAT_ESTATE, "maxsat_up_end without maxsat_up_begin");
   if (ctx->up_on_gpu) return up_end_gpu(ctx);
@@ -2249,11 +2274,13 @@ int maxsat_mp_get_params(maxsat_mp* mp, float* theta, float* grad) {
 }
 
 int maxsat_mp_forward(maxsat_mp* mp, maxsat_ctx* ctx, float* prob_dev) {
+  NvtxRange range("maxsat_mp_forward");
   if (!mp || !ctx || !prob_dev) return MAXSAT_EINVAL;
   return mp_forward(mp, ctx, nullptr, prob_dev);
 }
 
 int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev, double* loss) {
+  NvtxRange range("maxsat_mp_gradient");
   if (!mp || !ctx || !labels_dev) return MAXSAT_EINVAL;
   int rc = mp_forward(mp, ctx, labels_dev, nullptr);
   if (rc != MAXSAT_OK) return rc;
@@ -2300,6 +2327,7 @@ int maxsat_mp_gradient(maxsat_mp* mp, maxsat_ctx* ctx, const uint8_t* labels_dev
 }
 
 int maxsat_mp_adam(maxsat_mp* mp, maxsat_ctx* ctx, float lr) {
+  NvtxRange range("maxsat_mp_adam");
   if (!mp || !ctx || !(lr > 0.f)) return MAXSAT_EINVAL;
   mp->step += 1;
   MPT(mp, ctx, "mp_adam", mp_launch_adam(mp->P, mp->G, mp->M, mp->V, mp->lay.total, lr, 0.9f, 0.999f, 1e-8f,
@@ -2318,6 +2346,7 @@ void maxsat_mp_destroy(maxsat_mp* mp) {
 }
 
 int maxsat_reset_probs(maxsat_ctx* ctx, int32_t B, uint64_t seed, const float* prob) {
+  NvtxRange range("maxsat_reset_probs");
   if (!ctx || !prob) return MAXSAT_EINVAL;
   const int n = ctx->n;
   std::vector<uint32_t> P((size_t)n);
