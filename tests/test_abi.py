@@ -45,6 +45,7 @@ def test_default_params():
     assert (p.n_temps, p.n_buckets, p.quant_bits, p.path, p.fit_iters, p.steps_per_graph) == \
         (2, 4, 4, ms.MAXSAT_PATH_AUTO, 50000, 100)
     assert p.alpha == 0.01 and p.bucket_gamma == 0.5 and not p.fstar and p.n_sets == 0
+    assert (p.tune_blocks, p.up_device, p.visible_batch, p.persistent_round) == (0, 1, 0, 0)
 
 
 @pytest.mark.parametrize("K,fs", [(2, 0.528), (3, 0.068), (3, 0.528), (5, 0.528)])
@@ -97,6 +98,18 @@ def test_create_batch_validates_before_device(insts, msg):
         ms.maxsat_create_batch(insts)
     assert e.value.code == ms.MAXSAT_EINVAL
     assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("persistent_round", 2, "persistent_round must be 0 or 1"),
+    ("visible_batch", 3, "visible_batch must be 0, 2, 4 or 8"),
+    ("steps_per_graph", -1, "steps_per_graph out of range"),
+])
+def test_params_are_validated_before_device(field, value, msg):
+    p = ms.maxsat_default_params(**{field: value})
+    with pytest.raises(ms.MaxsatError) as e:
+        ms.maxsat_create(3, [0, 2], [1, -2], None, p)
+    assert e.value.code == ms.MAXSAT_EINVAL and msg in str(e.value)
 
 
 def test_create_batch_dense_path_is_rejected():
