@@ -292,15 +292,16 @@ __global__ void k_assign_fp8(const uint8_t* __restrict__ assign, int B, int n, i
                              uint32_t minus_one4, uint8_t* __restrict__ X,
                              int64_t* __restrict__ cost) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int chunks = n_pad / 16;
-  if (idx < (size_t)Bp * chunks) {
+  for (size_t idx = first; idx < (size_t)Bp * chunks; idx += stride) {
     const int b = (int)(idx / chunks), i0 = (int)(idx % chunks) * 16;
     reinterpret_cast<uint4*>(X)[idx] =
         b < B ? convert16(assign, n, b, i0, minus_one4) : make_uint4(0u, 0u, 0u, 0u);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (idx < (size_t)B) cost[idx] = 0;
+  for (size_t idx = first; idx < (size_t)B; idx += stride) cost[idx] = 0;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -439,8 +440,20 @@ cudaError_t launch_assign_fp8(const uint8_t* assign, int B, int n, int Bp, int n
   uint8_t minus_one;
   fp8_encode_int(-1, e5m2, &minus_one);
   const size_t total = std::max((size_t)Bp * (n_pad / 16), (size_t)B);
+  // at most 3 blocks per SM (30 registers a thread): all of them stay
+  // resident beside the previous evaluation's product (one CTA of 576
+  // threads at 61 registers per SM), so the conversion is done before that
+  // product ends and only the zeroing waits for it
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  const size_t blocks = std::min((total + 255) / 256, (size_t)3 * (size_t)sms);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((total + 255) / 256));
+  cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(256);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
