@@ -53,3 +53,40 @@ def test_reduce_best_two_ranks(case, expect):
         assert p.exitcode == 0
     for rank, c, ch, a in res:
         assert (c, ch, a) == expect, rank
+
+
+def _rank_dies(rank, world, port, out):
+    """Rank 1 leaves between rounds, before the final exchange (as a rank
+    whose host fails); rank 0's exchange must then fail with an error within
+    the process group's timeout instead of waiting forever."""
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)
+    try:
+        dd.reduce_best(5, 0, np.zeros(4, np.uint8))
+        out.put((rank, "returned"))
+    except Exception as e:  # the collective reports the lost peer
+        out.put((rank, "error: " + type(e).__name__))
+
+
+def test_reduce_best_reports_a_lost_rank():
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_dies, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.monotonic()
+    for p in procs:
+        p.start()
+    rank, status = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and status.startswith("error"), status
+    assert procs[1].exitcode == 3
+    assert time.monotonic() - t0 < 100
