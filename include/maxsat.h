@@ -258,6 +258,21 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B,
 int maxsat_solve(maxsat_ctx* ctx, int32_t restarts, int64_t steps, uint64_t seed,
                  uint8_t* best_assign, int64_t* best_cost);
 
+/* maxsat_solve under a wall-clock budget: the search samples until the time
+ * limit and outputs the best assignment seen (Sec. 4.2; 300 s per instance in
+ * the experiments, Sec. 5 "Incomplete score metric"; the appendix code
+ * returns when its time budget is exhausted). reset, then chunks of
+ * `chunk` rounds (<= 0: max(1, steps_per_graph)), each synchronised, while
+ * less than `seconds` of host wall time have passed since the call and
+ * fewer than max_steps rounds have run (the last chunk is cut to max_steps);
+ * then the final score and the best as maxsat_solve. *steps_done (may be
+ * NULL) receives the rounds run; with the same seed the result equals
+ * maxsat_solve with that many steps. MAXSAT_EINVAL for a negative or NaN
+ * budget. Synchronises. */
+int maxsat_solve_timed(maxsat_ctx* ctx, int32_t restarts, double seconds, int64_t max_steps,
+                       int64_t chunk, uint64_t seed, uint8_t* best_assign,
+                       int64_t* best_cost, int64_t* steps_done);
+
 /* Copies chain state to host buffers (each may be NULL): x and best_x are
  * B x n bytes, nu is B x n float, best_cost / cost are B int64 (cost = last
  * scored state), free_energy B float (last scored state, Eq. 1 summed over

@@ -96,6 +96,7 @@ def lib():
         L.maxsat_score.argtypes = [P]
         L.maxsat_eval.argtypes = [P, P, i32, P]
         L.maxsat_solve.argtypes = [P, i32, i64, u64, P, P]
+        L.maxsat_solve_timed.argtypes = [P, i32, f64, i64, i64, u64, P, P, P]
         L.maxsat_get_state.argtypes = [P, P, P, P, P, P, P, P]
         L.maxsat_set_state.argtypes = [P, i32, u64, P, P, P, P, u32]
         L.maxsat_get_path.argtypes = [P]
@@ -117,7 +118,8 @@ def lib():
                      "maxsat_propose_flips",
                      "maxsat_reset", "maxsat_reset_shard", "maxsat_step",
                      "maxsat_score",
-                     "maxsat_eval", "maxsat_solve", "maxsat_get_state", "maxsat_set_state",
+                     "maxsat_eval", "maxsat_solve", "maxsat_solve_timed", "maxsat_get_state",
+                     "maxsat_set_state",
                      "maxsat_get_path", "maxsat_fit_or_rbm", "maxsat_set_profiling",
                      "maxsat_kernel_times", "maxsat_eval_noalloc"]:
             getattr(L, name).restype = i32
@@ -327,6 +329,22 @@ def maxsat_solve(ctx: Context, restarts: int, steps: int, seed: int):
     if ctx.n_inst == 1:
         return int(cost[0]), best
     return cost, best
+
+
+def maxsat_solve_timed(ctx: Context, restarts: int, seconds: float, seed: int,
+                       max_steps: int = 2 ** 62, chunk: int = 0):
+    """maxsat_solve under a wall-clock budget; returns (best cost(s), best
+    assignment, rounds run)."""
+    best = np.zeros(ctx.n, np.uint8)
+    cost = np.zeros(ctx.n_inst, np.int64)
+    done = ctypes.c_int64(0)
+    _check(lib().maxsat_solve_timed(ctx.handle, int(restarts), float(seconds), int(max_steps),
+                                    int(chunk), int(seed) & (2 ** 64 - 1), _np_ptr(best),
+                                    _np_ptr(cost), ctypes.byref(done)), ctx)
+    ctx.B = int(restarts)
+    if ctx.n_inst == 1:
+        return int(cost[0]), best, int(done.value)
+    return cost, best, int(done.value)
 
 
 def maxsat_get_state(ctx: Context):

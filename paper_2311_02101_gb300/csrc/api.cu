@@ -12,6 +12,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -1581,6 +1582,9 @@ int maxsat_eval(maxsat_ctx* ctx, const uint8_t* assign_dev, int32_t B, int64_t* 
   return MAXSAT_OK;
 }
 
+// The best over the chains after the final score (maxsat_solve, maxsat_solve_timed).
+static int copy_best(maxsat_ctx* ctx, int32_t B, uint8_t* best_assign, int64_t* best_cost);
+
 int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
                  uint8_t* best_assign, int64_t* best_cost) {
   NvtxRange range("maxsat_solve");
@@ -1589,6 +1593,35 @@ int maxsat_solve(maxsat_ctx* ctx, int32_t B, int64_t steps, uint64_t seed,
   if (rc == MAXSAT_OK) rc = maxsat_step(ctx, steps);
   if (rc == MAXSAT_OK) rc = maxsat_score(ctx);
   if (rc != MAXSAT_OK) return rc;
+  return copy_best(ctx, B, best_assign, best_cost);
+}
+
+int maxsat_solve_timed(maxsat_ctx* ctx, int32_t B, double seconds, int64_t max_steps,
+                       int64_t chunk, uint64_t seed, uint8_t* best_assign, int64_t* best_cost,
+                       int64_t* steps_done) {
+  NvtxRange range("maxsat_solve_timed");
+  if (!ctx) return MAXSAT_EINVAL;
+  if (!(seconds >= 0.0) || max_steps < 0)
+    return fail(ctx, MAXSAT_EINVAL, "seconds and max_steps must be >= 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (chunk <= 0) chunk = std::max(1, ctx->prm.steps_per_graph);
+  int rc = maxsat_reset(ctx, B, seed);
+  if (rc != MAXSAT_OK) return rc;
+  int64_t done = 0;
+  // the time left is checked on the host between chunks, each synchronised
+  while (done < max_steps &&
+         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() < seconds) {
+    const int64_t k = std::min(chunk, max_steps - done);
+    if ((rc = maxsat_step(ctx, k)) != MAXSAT_OK) return rc;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    done += k;
+  }
+  if (steps_done) *steps_done = done;
+  if ((rc = maxsat_score(ctx)) != MAXSAT_OK) return rc;
+  return copy_best(ctx, B, best_assign, best_cost);
+}
+
+static int copy_best(maxsat_ctx* ctx, int32_t B, uint8_t* best_assign, int64_t* best_cost) {
   // per formula: its lowest best cost, ties to the lowest chain
   const int K = ctx->n_inst, Bp = ctx->C.Bp;
   std::vector<int64_t> best((size_t)K * B);

@@ -379,6 +379,29 @@ def test_solve_matches_oracle(ms, stream, small_table):
     assert oracle.evaluate(inst, assign[None])[0] == cost
 
 
+def test_solve_timed_is_solve_of_the_rounds_it_ran(ms, stream, small_table):
+    """The wall-clock budget only decides how many rounds run: with max_steps
+    reached first the result is maxsat_solve's (and the oracle's) of those
+    rounds; with a short budget it stops after whole chunks and equals
+    maxsat_solve of the rounds it reports."""
+    inst = inst_of(workloads.random_ksat(50, 215, 3, seed=0))
+    ctx = make_ctx(ms, stream, inst, small_table, spg=16)
+    cost, assign, done = ms.maxsat_solve_timed(ctx, 256, 60.0, 21, max_steps=40, chunk=16)
+    assert done == 40
+    ob, ox, _ = oracle.solve(inst, small_table, 256, 40, 21, n_temps=2,
+                             threads=os.cpu_count() or 4)
+    assert cost == ob and np.array_equal(assign, ox)
+    cost2, assign2, done2 = ms.maxsat_solve_timed(ctx, 256, 0.02, 5, chunk=8)
+    assert done2 >= 8 and done2 % 8 == 0
+    ref, ref_assign = ms.maxsat_solve(ctx, 256, done2, 5)
+    assert cost2 == ref and np.array_equal(assign2, ref_assign)
+    c0, _, d0 = ms.maxsat_solve_timed(ctx, 256, 0.0, 5)
+    assert d0 == 0 and c0 == ms.maxsat_solve(ctx, 256, 0, 5)[0]
+    with pytest.raises(ms.MaxsatError):
+        ms.maxsat_solve_timed(ctx, 256, -1.0, 5)
+    ms.maxsat_destroy(ctx)
+
+
 def test_brute_force_twin(ms, stream, table3):
     inst = inst_of(workloads.random_ksat(18, 77, 3, seed=0))
     ctx = make_ctx(ms, stream, inst, table3, spg=50)
