@@ -102,6 +102,24 @@ def test_eval_matches_matrix_form():
     assert np.array_equal(oracle.evaluate(inst, X), cost)
 
 
+def test_padding_by_repetition_keeps_the_satisfying_set():
+    """Sec. 4.3: a clause padded to length K by repeating one of its
+    variables with the same polarity has the same satisfying assignments, so
+    every assignment keeps its cost (the build groups clauses by length
+    instead of padding them, R14; the cost must not depend on it)."""
+    rng = np.random.default_rng(11)
+    n = 12
+    lengths = rng.integers(1, 5, size=60)
+    _, off, lits, w = workloads.from_lengths(n, lengths, rng)
+    plain = oracle.Instance(n, off, lits, w)
+    K = 4
+    padded = [c + [c[int(rng.integers(0, len(c)))]] * (K - len(c)) for c in plain.clauses()]
+    inst = oracle.Instance.from_clauses(n, padded, list(w))
+    assert set(np.diff(inst.off)) == {K}
+    X = np.array(list(itertools.product([0, 1], repeat=n)), np.uint8)
+    assert np.array_equal(oracle.evaluate(inst, X), oracle.evaluate(plain, X))
+
+
 def test_printed_count_form_misses_negated_literals():
     """The count printed in the appendix listing tests only positive
     polarities, so a clause made only of negated literals is never counted as
