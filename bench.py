@@ -1013,17 +1013,21 @@ def persistent_probe(ms, torch, stream, make, B, m_tot, args):
             ctx = make(p)
         except ms.MaxsatError as e:
             return dict(unavailable=str(e))
-        ms.maxsat_reset(ctx, B, 7)
-        active = ms.maxsat_get_persistent_round(ctx)
-        ms.maxsat_step(ctx, 100)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        ms.maxsat_step(ctx, K)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms_round = a.elapsed_time(b) / K
-        st = ms.maxsat_get_state(ctx)  # reads the device error code of the persistent form
+        try:
+            ms.maxsat_reset(ctx, B, 7)
+            active = ms.maxsat_get_persistent_round(ctx)
+            ms.maxsat_step(ctx, 100)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            ms.maxsat_step(ctx, K)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_round = a.elapsed_time(b) / K
+            st = ms.maxsat_get_state(ctx)  # reads the device error code of the persistent form
+        except ms.MaxsatError as e:
+            ms.maxsat_destroy(ctx)
+            return dict(unavailable=f"{label}: {e}")
         out[label] = dict(ms_per_round=ms_round, evals_per_s=m_tot * B / (ms_round / 1e3),
                           persistent_active=active, clause_block=ms.maxsat_get_clause_block(ctx),
                           visible_batch=ms.maxsat_get_visible_batch(ctx) if not active else 4,
