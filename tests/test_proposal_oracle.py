@@ -1,6 +1,7 @@
 """Pins of the learned-proposal oracle (numpy, FP64): its analytic gradient
 against central finite differences, its aggregation against a per-clause loop,
-and the BF16 rounding against exact cases."""
+the BF16 rounding against exact cases, and the flip-proposal rule against a
+hand-written case."""
 import numpy as np
 
 import workloads
@@ -50,3 +51,19 @@ def test_bf16_rounding():
     # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties to the even mantissa (1.0)
     want = [1.0, 1.0, 1.0 + 2 ** -7, 1.0 + 2 ** -6, -2.5, 0.0]
     assert np.array_equal(mp.bf16_round(vals), np.array(want))
+
+
+def test_flip_proposals_hand_written():
+    """Flip proposals (the network's confident values written into every
+    chain): with tau = 1/4, p >= 3/4 sets the variable to 1, p <= 1/4 to 0,
+    anything between keeps the chain's value; both bounds are inclusive."""
+    import oracle
+    x = np.array([[0, 1, 0, 1, 0, 1],
+                  [1, 0, 1, 0, 1, 0]], np.uint8)
+    p = np.array([0.75, 0.25, 0.7499999, 0.2500001, 0.99, 0.0], np.float32)
+    want = np.array([[1, 0, 0, 1, 1, 0],
+                     [1, 0, 1, 0, 1, 0]], np.uint8)
+    assert np.array_equal(oracle.flip_proposals(x, p, 0.25), want)
+    # tau = 0 sets only certain variables
+    assert np.array_equal(oracle.flip_proposals(x, np.array([1, 0, .5, .5, .5, .5], np.float32), 0.0),
+                          np.array([[1, 0, 0, 1, 0, 1], [1, 0, 1, 0, 1, 0]], np.uint8))
