@@ -165,6 +165,17 @@ def test_fit_reaches_or_targets():
         assert oracle.fit_loss(K, fs, Wq, bq) < 4 * oracle.fit_loss(K, fs, W, b) + 1e-3
 
 
+def test_hidden_unit_counts_follow_the_printed_rule():
+    """Appendix "Pretraining": 3 hidden units for clause size 3 and K + 1
+    for K in 4..7 (written out here from that sentence); the fitted W has
+    that many columns."""
+    printed = {3: 3, 4: 5, 5: 6, 6: 7, 7: 8}
+    for K, L in printed.items():
+        assert oracle.hidden_units_for(K) == L
+    W, b = oracle.fit_or_rbm(4, 0.528, iters=10)
+    assert W.shape == (4, 5) and b.shape == (5,)
+
+
 def test_tied_weights_cannot_fit_or():
     """Reading check: with one weight shared by all inputs of a hidden unit,
     -F(s) = sum_h softplus(b_h + w_h s) is convex in the count s, while the OR
